@@ -1,0 +1,202 @@
+/*
+ * ftcj.h -- C ABI of the GB300 (sm_103a) long-range Fourier-transformed
+ * Coulomb build: the integral-direct planewave density fitting of the
+ * G != 0 Ewald term of the periodic Coulomb matrix of arXiv 2509.16460.
+ *
+ * Problem statement followed (paper Sec. 2.2-2.4):
+ *   D^{0n}  = (1/Nk) sum_k exp(-i k.R_n) D^k                 (Eq. "FT for D")
+ *   rho(G)  = sum_{mu nu L} D^{0[L]}_{mu nu} (mu0 nuL|G)      (LR step 1)
+ *   V(-G)   = rho(-G) v(G),  v(G) = 4 pi exp(-G^2/4w^2)/(Omega G^2)
+ *                                                             (LR step 2)
+ *   J^{0L}_{mu nu} = sum_{G != 0} (mu0 nuL|G) V(-G)           (LR step 3,
+ *                                                  Eq. "Ewald J", 2nd term)
+ *   J^k     = sum_L exp(+i k.R_L) J^{0L}                      (Eq. "FT of J")
+ *   E_J     = 1/2 sum_{G != 0} v(G) |rho(G)|^2
+ * with (mu0 nuL|G) = int phi_mu(r) phi_nu(r - R_L) exp(-i G.r) dr
+ * (Eq. "AFT for pair density"), G over the reciprocal lattice inside
+ * |G| < Gcut, pairs of primitive shells screened by their overlap.
+ *
+ * Units: bohr, hartree.  Lattice rows are the lattice vectors a_i.  The
+ * k-mesh is Gamma-centred, k_m = sum_i (m_i/N_i) b_i, flattened as
+ * m = (m1*N2 + m2)*N3 + m3; BvK cells n use the same flattening.
+ *
+ * AO order: shell order; inside a Cartesian shell lx = l..0, ly = l-lx..0
+ * (xx, xy, xz, yy, yz, zz); inside a spherical shell m = -l..l except p,
+ * which is (x, y, z).  Every primitive is unit-normalised; the shell's
+ * coefficients multiply normalised primitives.  Shells up to l = 2.
+ *
+ * Complex arrays are interleaved (re, im) doubles.
+ *
+ * Preconditions of the build: D^k Hermitian for every k and time-reversal
+ * symmetric, D^{-k} = conj(D^k), so that D^{0n} and J^{0n} are real.  The
+ * fold step keeps Re D^{0n}; ftcj_plan_info reports nothing about the
+ * input, use ftcj_check_density to measure a violation.
+ *
+ * Errors: every call returns FTCJ_OK (0) or a negative FTCJ_E* code; no
+ * exception or abort crosses this boundary.  ftcj_last_error() gives a
+ * thread-local message for the last failing call on the calling thread.
+ *
+ * Ownership: the caller owns every input and output buffer.  The plan owns
+ * all device scratch, allocated in ftcj_plan_create and freed in
+ * ftcj_plan_destroy; the build calls allocate nothing.
+ *
+ * Threading: a plan is used by one host thread and one stream at a time.
+ */
+#ifndef FTCJ_H
+#define FTCJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FTCJ_OK 0
+#define FTCJ_EINVAL (-1)       /* bad argument or input */
+#define FTCJ_ENOMEM (-2)       /* device or host allocation failed */
+#define FTCJ_ECUDA (-3)        /* a CUDA runtime call failed */
+#define FTCJ_ETIMEOUT (-4)     /* a bounded device wait gave up */
+#define FTCJ_EUNSUPPORTED (-5) /* valid input outside what this build handles */
+
+#define FTCJ_PREC_FP64 0       /* every step in FP64 */
+
+#define FTCJ_LMAX 2            /* highest shell angular momentum */
+
+typedef struct {
+    double A[9]; /* row i = lattice vector a_i (bohr), row-major */
+} ftcj_cell;
+
+typedef struct {
+    int centre;          /* index into ftcj_basis.xyz */
+    int l;               /* 0..FTCJ_LMAX */
+    int spherical;       /* 1: real solid harmonics, 0: Cartesian */
+    int nprim;           /* >= 1 */
+    const double* exps;  /* [nprim] > 0 */
+    const double* coefs; /* [nprim], multiply unit-normalised primitives */
+} ftcj_shell;
+
+typedef struct {
+    int ncentre;
+    const double* xyz; /* [ncentre][3] Cartesian bohr */
+    int nshell;
+    const ftcj_shell* shells;
+} ftcj_basis;
+
+typedef struct {
+    double omega;       /* Ewald range-separation parameter w > 0 (1/bohr) */
+    double gcut;        /* sphere radius; <= 0: 2 w sqrt(ln(1/eps_g)) */
+    double eps_g;       /* kernel floor exp(-Gcut^2/4w^2) when gcut <= 0 */
+    double pair_thresh; /* keep primitive pairs with overlap bound > this */
+    int precision;      /* FTCJ_PREC_FP64 */
+    int max_dens;       /* densities per device batch (scratch is sized for it); <= 0: 1 */
+} ftcj_params;
+
+typedef struct {
+    int nao;                  /* AOs per cell */
+    int nk;                   /* k-points = BvK cells */
+    int nshell;
+    int ngroup;               /* distinct (centre, exponent) primitive groups */
+    int64_t npairs;           /* pair records after the (a0,bL)<->(b0,a-L) reduction */
+    int64_t npairs_ordered;   /* ordered screened primitive-shell pairs */
+    int64_t ng_half;          /* G vectors in the half sphere (rho is stored there) */
+    int64_t ng_full;          /* G != 0 in the full sphere = 2 ng_half */
+    int64_t pair_g_units;     /* npairs_ordered * ng_full: the work unit count */
+    int64_t pairs_by_class[5];/* pair records per L = l_a + l_b class */
+    int nlines;               /* G lines along b_1 walked per pair */
+    int nchunks;              /* G chunks (grid dimension of the walks) */
+    double gcut;
+    double volume;
+    size_t device_bytes;      /* device memory held by the plan */
+} ftcj_info;
+
+typedef struct ftcj_plan ftcj_plan;
+
+/* Plan for one cell, basis, k-mesh and parameter set.  Runs the pair
+ * screening and sorting on the device (default stream, synchronised) and
+ * allocates all scratch.  cell/basis/params are copied; the caller may free
+ * them afterwards.  Errors: EINVAL (bad lattice, centres, exponents, omega,
+ * k-mesh), EUNSUPPORTED (l > FTCJ_LMAX, precision not FP64, a G line
+ * longer than the walk chunk), ENOMEM, ECUDA. */
+int ftcj_plan_create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3],
+                     const ftcj_params* params, ftcj_plan** out);
+
+/* Sizes and counts of a plan (host struct, filled by the call). */
+int ftcj_plan_info(const ftcj_plan* plan, ftcj_info* out);
+
+/* Frees the plan and its device memory.  NULL is ignored. */
+void ftcj_plan_destroy(ftcj_plan* plan);
+
+/* Whole long-range build, steps a2..a8, on `stream` (a cudaStream_t; NULL =
+ * legacy default stream).  All pointers are DEVICE memory owned by the
+ * caller:
+ *   Dk  complex [ndens][Nk][nao][nao]  (read)
+ *   Jk  complex [ndens][Nk][nao][nao]  (written)
+ *   EJ  double  [ndens]                (written, hartree per cell)
+ * ndens >= 1; densities are processed in batches of params.max_dens.
+ * Asynchronous: returns after enqueueing.  Errors: EINVAL, ECUDA. */
+int ftcj_jbuild(ftcj_plan* plan, int ndens, const double* Dk, double* Jk, double* EJ, void* stream);
+
+/* The same build on HOST buffers (same layouts): copies D^k in, runs the
+ * build, copies J^k and E_J out, and synchronises `stream`.  Staging uses
+ * plan-owned device buffers sized at plan creation for max_dens densities;
+ * ndens may exceed it (batched). */
+int ftcj_jbuild_host(ftcj_plan* plan, int ndens, const double* Dk_host, double* Jk_host, double* EJ_host,
+                     void* stream);
+
+/* ---- the individual steps (device pointers, asynchronous on stream) ---- */
+
+/* a2: D^{0n} = Re (1/Nk) sum_k exp(-i k.R_n) D^k (Eq. "FT for D").
+ * Dk complex [ndens][Nk][nao][nao] -> D0n double [ndens][Ncell][nao][nao],
+ * ndens <= max_dens. */
+int ftcj_fold_density(ftcj_plan* plan, int ndens, const double* Dk, double* D0n, void* stream);
+
+/* a3 + a4: Hermite densities of every pair record (Alg. 2) and the
+ * structure-factor pass over the half sphere (Alg. 1):
+ * D0n double [ndens][Ncell][nao][nao] -> rho complex [ndens][ng_half] in
+ * the order of ftcj_get_gvectors.  ndens <= max_dens. */
+int ftcj_rho(ftcj_plan* plan, int ndens, const double* D0n, double* rho, void* stream);
+
+/* a5: V and E_J from rho on the half sphere:
+ * W(G) = 2 v(G) conj(rho(G)) complex [ndens][ng_half];
+ * EJ[d] = sum_half v |rho|^2 (= 1/2 sum over the full sphere). */
+int ftcj_potential(ftcj_plan* plan, int ndens, const double* rho, double* W, double* EJ, void* stream);
+
+/* a6 + a7: back-contraction (Alg. S1) and transform to AOs (Alg. S2):
+ * W complex [ndens][ng_half] -> J0n double [ndens][Ncell][nao][nao]
+ * (J^{0L} folded into the BvK cells; overwritten).  ndens <= max_dens. */
+int ftcj_jback(ftcj_plan* plan, int ndens, const double* W, double* J0n, void* stream);
+
+/* a8: J^k = sum_n exp(+i k.R_n) J^{0n} (Eq. "FT of J"):
+ * J0n double [ndens][Ncell][nao][nao] -> Jk complex [ndens][Nk][nao][nao].
+ * ndens <= max_dens. */
+int ftcj_unfold_j(ftcj_plan* plan, int ndens, const double* J0n, double* Jk, void* stream);
+
+/* Largest |Im D^{0n}| and largest |D^{0n}_{mu nu} - D^{0,-n}_{nu mu}| of
+ * the input (host doubles out), i.e. how far D^k is from the precondition.
+ * Synchronises `stream`.  ndens <= max_dens. */
+int ftcj_check_density(ftcj_plan* plan, int ndens, const double* Dk, double* max_imag, double* max_asym,
+                       void* stream);
+
+/* ---- plan exports (host buffers, filled by the call) ---- */
+
+/* n triples [ng_half][3] of the half sphere, in rho's storage order. */
+int ftcj_get_gvectors(const ftcj_plan* plan, int* n_out);
+
+/* Pair records [npairs][6]: group a, group b, L1, L2, L3, weight (1 for a
+ * self pair, 2 when the record also stands for its mirror (b0, a-L)). */
+int ftcj_get_pairs(const ftcj_plan* plan, int* out);
+
+/* Primitive groups: centre[ngroup], exponent[ngroup], and the member list
+ * [nmember][3] = (group, shell, primitive index); returns nmember through
+ * *nmember (pass members = NULL to query). */
+int ftcj_get_groups(const ftcj_plan* plan, int* centre, double* exponent, int* members, int* nmember);
+
+const char* ftcj_strerror(int code);
+const char* ftcj_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FTCJ_H */

@@ -1,0 +1,131 @@
+// Public build entry points: argument checks and the order of the steps.
+#include <algorithm>
+
+#include "ftcj_internal.h"
+
+using namespace ftcj;
+
+namespace {
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int check(const ftcj_plan* P, int ndens, bool batch_limit) {
+    if (!P) return fail(FTCJ_EINVAL, "null plan");
+    if (ndens < 1) return fail(FTCJ_EINVAL, "ndens must be >= 1");
+    if (batch_limit && ndens > P->max_dens) return fail(FTCJ_EINVAL, "ndens above the plan's max_dens");
+    return FTCJ_OK;
+}
+
+// one batch of <= max_dens densities; every pointer is device memory
+int build_batch(ftcj_plan* P, int nd, const double* Dk, double* Jk, double* EJ, cudaStream_t s) {
+    int rc;
+    if ((rc = launch_fold(P, nd, Dk, P->d_D0n, s))) return rc;
+    if ((rc = launch_hermite(P, nd, P->d_D0n, s))) return rc;
+    if ((rc = launch_rho_walk(P, nd, s))) return rc;
+    if ((rc = launch_rho_reduce(P, nd, P->d_rho, P->d_W, EJ, nullptr, s))) return rc;
+    if ((rc = launch_j_walk(P, nd, P->d_W, s))) return rc;
+    if ((rc = launch_jtransform(P, nd, P->d_J0n, s))) return rc;
+    if ((rc = launch_unfold(P, nd, P->d_J0n, Jk, s))) return rc;
+    return FTCJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ftcj_fold_density(ftcj_plan* P, int ndens, const double* Dk, double* D0n, void* stream) {
+    int rc = check(P, ndens, true);
+    if (rc) return rc;
+    if (!Dk || !D0n) return fail(FTCJ_EINVAL, "null buffer");
+    return launch_fold(P, ndens, Dk, D0n, as_stream(stream));
+}
+
+int ftcj_rho(ftcj_plan* P, int ndens, const double* D0n, double* rho, void* stream) {
+    int rc = check(P, ndens, true);
+    if (rc) return rc;
+    if (!D0n || !rho) return fail(FTCJ_EINVAL, "null buffer");
+    cudaStream_t s = as_stream(stream);
+    if ((rc = launch_hermite(P, ndens, D0n, s))) return rc;
+    if ((rc = launch_rho_walk(P, ndens, s))) return rc;
+    return launch_rho_reduce(P, ndens, rho, nullptr, nullptr, nullptr, s);
+}
+
+int ftcj_potential(ftcj_plan* P, int ndens, const double* rho, double* W, double* EJ, void* stream) {
+    int rc = check(P, ndens, false);
+    if (rc) return rc;
+    if (!rho || !W || !EJ) return fail(FTCJ_EINVAL, "null buffer");
+    cudaStream_t s = as_stream(stream);
+    // batches keep the energy partials inside the plan's scratch
+    for (int b0 = 0; b0 < ndens; b0 += P->max_dens) {
+        int nd = std::min(P->max_dens, ndens - b0);
+        size_t off = (size_t)b0 * P->ng_half * 2;
+        if ((rc = launch_rho_reduce(P, nd, nullptr, W + off, EJ + b0, rho + off, s))) return rc;
+    }
+    return FTCJ_OK;
+}
+
+int ftcj_jback(ftcj_plan* P, int ndens, const double* W, double* J0n, void* stream) {
+    int rc = check(P, ndens, true);
+    if (rc) return rc;
+    if (!W || !J0n) return fail(FTCJ_EINVAL, "null buffer");
+    cudaStream_t s = as_stream(stream);
+    if ((rc = launch_j_walk(P, ndens, W, s))) return rc;
+    return launch_jtransform(P, ndens, J0n, s);
+}
+
+int ftcj_unfold_j(ftcj_plan* P, int ndens, const double* J0n, double* Jk, void* stream) {
+    int rc = check(P, ndens, true);
+    if (rc) return rc;
+    if (!J0n || !Jk) return fail(FTCJ_EINVAL, "null buffer");
+    return launch_unfold(P, ndens, J0n, Jk, as_stream(stream));
+}
+
+int ftcj_jbuild(ftcj_plan* P, int ndens, const double* Dk, double* Jk, double* EJ, void* stream) {
+    int rc = check(P, ndens, false);
+    if (rc) return rc;
+    if (!Dk || !Jk || !EJ) return fail(FTCJ_EINVAL, "null buffer");
+    cudaStream_t s = as_stream(stream);
+    size_t per = (size_t)P->nk * P->nao * P->nao * 2;  // doubles per complex density
+    for (int b0 = 0; b0 < ndens; b0 += P->max_dens) {
+        int nd = std::min(P->max_dens, ndens - b0);
+        if ((rc = build_batch(P, nd, Dk + b0 * per, Jk + b0 * per, EJ + b0, s))) return rc;
+    }
+    return FTCJ_OK;
+}
+
+int ftcj_jbuild_host(ftcj_plan* P, int ndens, const double* Dk_host, double* Jk_host, double* EJ_host,
+                     void* stream) {
+    int rc = check(P, ndens, false);
+    if (rc) return rc;
+    if (!Dk_host || !Jk_host || !EJ_host) return fail(FTCJ_EINVAL, "null buffer");
+    cudaStream_t s = as_stream(stream);
+    size_t per = (size_t)P->nk * P->nao * P->nao * 2;
+    for (int b0 = 0; b0 < ndens; b0 += P->max_dens) {
+        int nd = std::min(P->max_dens, ndens - b0);
+        FTCJ_CUDA(cudaMemcpyAsync(P->d_Dk_stage, Dk_host + b0 * per, sizeof(double) * nd * per,
+                                  cudaMemcpyHostToDevice, s));
+        if ((rc = build_batch(P, nd, P->d_Dk_stage, P->d_Jk_stage, P->d_EJ_stage, s))) return rc;
+        FTCJ_CUDA(cudaMemcpyAsync(Jk_host + b0 * per, P->d_Jk_stage, sizeof(double) * nd * per,
+                                  cudaMemcpyDeviceToHost, s));
+        FTCJ_CUDA(cudaMemcpyAsync(EJ_host + b0, P->d_EJ_stage, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
+    }
+    FTCJ_CUDA(cudaStreamSynchronize(s));
+    return FTCJ_OK;
+}
+
+int ftcj_check_density(ftcj_plan* P, int ndens, const double* Dk, double* max_imag, double* max_asym,
+                       void* stream) {
+    int rc = check(P, ndens, true);
+    if (rc) return rc;
+    if (!Dk || !max_imag || !max_asym) return fail(FTCJ_EINVAL, "null buffer");
+    cudaStream_t s = as_stream(stream);
+    if ((rc = launch_check_density(P, ndens, Dk, P->d_check, s))) return rc;
+    double h[2];
+    FTCJ_CUDA(cudaMemcpyAsync(h, P->d_check, sizeof(h), cudaMemcpyDeviceToHost, s));
+    FTCJ_CUDA(cudaStreamSynchronize(s));
+    *max_imag = h[0];
+    *max_asym = h[1];
+    return FTCJ_OK;
+}
+
+}  // extern "C"

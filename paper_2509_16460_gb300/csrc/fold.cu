@@ -1,0 +1,205 @@
+// Steps a2 and a8: the k <-> BvK transforms (Eqs. "FT for D" and "FT of J")
+//   D^{0n} = Re (1/Nk) sum_k exp(-i k.R_n) D^k,
+//   J^k    = sum_n exp(+i k.R_n) J^{0n},
+// done as one small DFT per mesh axis (separable over the Gamma-centred
+// mesh), each stage a coalesced pass over the [dens][cell][nao*nao] array
+// with the AO-pair index fastest.
+#include <algorithm>
+#include <vector>
+
+#include "ftcj_internal.h"
+
+namespace ftcj {
+namespace {
+
+constexpr int kTw = 16;  // twiddle table edge (k-mesh dimensions <= 16)
+
+__global__ void k_twiddles(double2* __restrict__ tw, int n0, int n1, int n2) {
+    int a = blockIdx.x;
+    int N = a == 0 ? n0 : (a == 1 ? n1 : n2);
+    int m = threadIdx.y, n = threadIdx.x;
+    double2 v = make_double2(0.0, 0.0);
+    if (m < N && n < N) {
+        int r = (m * n) % N;
+        double s, c;
+        sincospi(2.0 * (double)r / (double)N, &s, &c);
+        v = make_double2(c, -s);  // exp(-2 pi i m n / N)
+    }
+    tw[(a * kTw + m) * kTw + n] = v;
+}
+
+// One axis of the separable transform.  Element idx = ((d*nk + cell)*E + e);
+// out(.., n_axis, ..) = scale * sum_m w(m, n_axis) in(.., m, ..), with
+// w = tw or conj(tw).  IN_REAL / OUT_REAL select double or interleaved complex.
+template <bool IN_REAL, bool OUT_REAL>
+__global__ void k_dft_axis(const double* __restrict__ in, double* __restrict__ out, long long total, long long E,
+                           int N1, int N2, int N3, int axis, const double2* __restrict__ tw, int conj_tw,
+                           double scale) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    int nk = N1 * N2 * N3;
+    long long e = idx % E;
+    long long t = idx / E;
+    int cell = (int)(t % nk);
+    long long d = t / nk;
+    int i3 = cell % N3, i2 = (cell / N3) % N2, i1 = cell / (N2 * N3);
+    int na, Na;
+    long long stride;
+    if (axis == 0) {
+        na = i1;
+        Na = N1;
+        stride = (long long)N2 * N3 * E;
+    } else if (axis == 1) {
+        na = i2;
+        Na = N2;
+        stride = (long long)N3 * E;
+    } else {
+        na = i3;
+        Na = N3;
+        stride = E;
+    }
+    long long base = (d * nk + cell) * E + e - (long long)na * stride;
+    const double2* w = tw + axis * kTw * kTw;
+    double sr = 0.0, si = 0.0;
+    for (int m = 0; m < Na; ++m) {
+        double2 c = w[m * kTw + na];
+        double wr = c.x, wi = conj_tw ? -c.y : c.y;
+        long long q = base + (long long)m * stride;
+        if (IN_REAL) {
+            double x = in[q];
+            sr = fma(wr, x, sr);
+            si = fma(wi, x, si);
+        } else {
+            double2 x = reinterpret_cast<const double2*>(in)[q];
+            sr = fma(wr, x.x, fma(-wi, x.y, sr));
+            si = fma(wr, x.y, fma(wi, x.x, si));
+        }
+    }
+    if (OUT_REAL) {
+        out[idx] = scale * sr;
+    } else {
+        reinterpret_cast<double2*>(out)[idx] = make_double2(scale * sr, scale * si);
+    }
+}
+
+__global__ void k_complex_to_real(const double2* __restrict__ in, double* __restrict__ out, long long n, double s) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = s * in[i].x;
+}
+
+__global__ void k_real_to_complex(const double* __restrict__ in, double2* __restrict__ out, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_double2(in[i], 0.0);
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double* a, double v) {
+    // non-negative doubles order like their bit patterns
+    atomicMax(reinterpret_cast<unsigned long long*>(a), (unsigned long long)__double_as_longlong(v));
+}
+
+// max |Im D^{0n}| and max |Re D^{0n}_{mu nu} - Re D^{0,-n}_{nu mu}| over a complex fold
+__global__ void k_check(const double2* __restrict__ D, long long ndens, int N1, int N2, int N3, int nao,
+                        double* __restrict__ out) {
+    long long nn = (long long)nao * nao;
+    int nk = N1 * N2 * N3;
+    long long total = ndens * nk * nn;
+    double mi = 0.0, ma = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        long long e = i % nn;
+        long long t = i / nn;
+        int cell = (int)(t % nk);
+        long long d = t / nk;
+        int mu = (int)(e / nao), nu = (int)(e % nao);
+        int i3 = cell % N3, i2 = (cell / N3) % N2, i1 = cell / (N2 * N3);
+        int mcell = (((N1 - i1) % N1) * N2 + ((N2 - i2) % N2)) * N3 + ((N3 - i3) % N3);
+        double2 a = D[i];
+        double2 b = D[(d * nk + mcell) * nn + (long long)nu * nao + mu];
+        mi = fmax(mi, fabs(a.y));
+        ma = fmax(ma, fabs(a.x - b.x));
+    }
+    atomic_max_nonneg(out, mi);
+    atomic_max_nonneg(out + 1, ma);
+}
+
+inline unsigned nblocks(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+int launch_twiddles(ftcj_plan* P) {
+    k_twiddles<<<3, dim3(kTw, kTw)>>>(reinterpret_cast<double2*>(P->d_tw), P->km[0], P->km[1], P->km[2]);
+    FTCJ_CUDA(cudaGetLastError());
+    return FTCJ_OK;
+}
+
+// Runs the stages over the axes with N > 1.  mode 0: fold (complex in, real
+// out, scale 1/nk, exp(-i..)); mode 1: unfold (real in, complex out,
+// exp(+i..)); mode 2: fold keeping the complex result (for the input check).
+static int run_stages(ftcj_plan* P, int ndens, const double* in, double* out, int mode, cudaStream_t s) {
+    long long E = (long long)P->nao * P->nao;
+    long long total = (long long)ndens * P->nk * E;
+    const double2* tw = reinterpret_cast<const double2*>(P->d_tw);
+    std::vector<int> axes;
+    if (mode == 1) {
+        for (int a = 0; a < 3; ++a)
+            if (P->km[a] > 1) axes.push_back(a);
+    } else {
+        for (int a = 2; a >= 0; --a)
+            if (P->km[a] > 1) axes.push_back(a);
+    }
+    const int B = 256;
+    if (total == 0) return FTCJ_OK;
+    if (axes.empty()) {
+        if (mode == 0) k_complex_to_real<<<nblocks(total, B), B, 0, s>>>(reinterpret_cast<const double2*>(in), out,
+                                                                         total, 1.0);
+        else if (mode == 1) k_real_to_complex<<<nblocks(total, B), B, 0, s>>>(in, reinterpret_cast<double2*>(out),
+                                                                              total);
+        else FTCJ_CUDA(cudaMemcpyAsync(out, in, sizeof(double) * 2 * total, cudaMemcpyDeviceToDevice, s));
+        FTCJ_CUDA(cudaGetLastError());
+        return FTCJ_OK;
+    }
+    double* bufs[2] = {P->d_cbuf0, P->d_cbuf1};
+    int conj = mode == 1 ? 1 : 0;
+    for (size_t st = 0; st < axes.size(); ++st) {
+        bool first = st == 0, last = st + 1 == axes.size();
+        const double* src = first ? in : bufs[(st - 1) & 1];
+        double* dst = last ? out : bufs[st & 1];
+        double scale = (last && mode != 1) ? 1.0 / P->nk : 1.0;
+        int ax = axes[st];
+        unsigned g = nblocks(total, B);
+        if (mode == 1 && first) {
+            k_dft_axis<true, false><<<g, B, 0, s>>>(src, dst, total, E, P->km[0], P->km[1], P->km[2], ax, tw, conj,
+                                                    scale);
+        } else if (mode == 0 && last) {
+            k_dft_axis<false, true><<<g, B, 0, s>>>(src, dst, total, E, P->km[0], P->km[1], P->km[2], ax, tw, conj,
+                                                    scale);
+        } else {
+            k_dft_axis<false, false><<<g, B, 0, s>>>(src, dst, total, E, P->km[0], P->km[1], P->km[2], ax, tw, conj,
+                                                     scale);
+        }
+        FTCJ_CUDA(cudaGetLastError());
+    }
+    return FTCJ_OK;
+}
+
+int launch_fold(ftcj_plan* P, int ndens, const double* Dk, double* D0n, cudaStream_t s) {
+    return run_stages(P, ndens, Dk, D0n, 0, s);
+}
+
+int launch_unfold(ftcj_plan* P, int ndens, const double* J0n, double* Jk, cudaStream_t s) {
+    return run_stages(P, ndens, J0n, Jk, 1, s);
+}
+
+int launch_check_density(ftcj_plan* P, int ndens, const double* Dk, double* out2, cudaStream_t s) {
+    // the complex fold goes to the host-variant staging buffer, which is free here
+    double* full = P->d_Jk_stage;
+    int rc = run_stages(P, ndens, Dk, full, 2, s);
+    if (rc) return rc;
+    FTCJ_CUDA(cudaMemsetAsync(out2, 0, 2 * sizeof(double), s));
+    k_check<<<256, 256, 0, s>>>(reinterpret_cast<const double2*>(full), ndens, P->km[0], P->km[1], P->km[2], P->nao,
+                                out2);
+    FTCJ_CUDA(cudaGetLastError());
+    return FTCJ_OK;
+}
+
+}  // namespace ftcj

@@ -1,0 +1,177 @@
+// Internal declarations of the GB300 long-range Coulomb library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ftcj.h"
+
+namespace ftcj {
+
+constexpr int kLmax = FTCJ_LMAX;           // highest shell l
+constexpr int kLpair = 2 * kLmax;          // highest pair class L = l_a + l_b
+constexpr int kNclass = kLpair + 1;        // classes 0..4
+constexpr int kNcartMax = (kLmax + 1) * (kLmax + 2) / 2;
+constexpr int kMaxTerms = (kLpair + 1) * (kLpair + 2) * (kLpair + 3) / 6;  // 35
+constexpr int kTile = 128;                 // pair records per walker block
+constexpr int kBatch = 32;                 // points per rho reduction batch
+constexpr int kChunkMax = 4096;            // G points per walk chunk
+constexpr int kSortTile = 1024;            // candidates per sort tile
+
+__host__ __device__ constexpr int nterms(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
+__host__ __device__ constexpr int nmono(int lam) { return (lam + 1) * (lam + 2) / 2; }
+__host__ __device__ constexpr int lam_offset(int lam) { return lam * (lam + 1) * (lam + 2) / 6; }
+// position of the monomial (a, b, lam-a-b) of total degree lam, order a = lam..0, b = lam-a..0
+__host__ __device__ inline int mono_index(int lam, int a, int b) {
+    int idx = 0;
+    for (int x = lam; x > a; --x) idx += lam - x + 1;
+    return idx + (lam - a - b);
+}
+
+// A primitive group: one (centre, exponent) shared by one or more shells.
+struct GroupDev {
+    double x, y, z, alpha;
+    int lmax, mem0, mem1, centre;
+};
+
+// One shell that uses a group's primitive.  coef already holds the contraction
+// coefficient times the radial normalisation (2a/pi)^{3/4} (4a)^{l/2}.
+struct MemberDev {
+    int l, sph, ao, pad;
+    double coef;
+};
+
+// A screened pair record (a in the home cell, b in cell L).
+struct PairDev {
+    int ga, gb;
+    int L[3];
+    int cell, mcell;  // BvK index of [L] and [-L]
+    int weight;       // 1 self pair, 2 stands for its mirror too
+    int cls;          // la_max + lb_max
+    int pad;
+    double P[3];
+    double p;
+    double K;         // exp(-mu |A-B-R_L|^2) (pi/p)^{3/2}
+};
+
+// Per-pair constants of the G walk (recurrence multipliers).
+struct PairWalk {
+    double c;             // 1/(4p)
+    double f1, f2, f3;    // fractional coordinates of P, reduced to [-1/2, 1/2)
+    double q1, q2, q3;    // exp(-2c M_ii)
+    double x12, y12, x13, y13, x23, y23;  // exp(-/+ 2c M_ij)
+    double e1r, e1i, e2r, e2i, e3r, e3i;  // exp(-2 pi i f_j)
+    double pad;
+};
+
+// One G line along b_1 at fixed (n2, n3) in the walk, with the transition
+// from the previous line of the same chunk.
+enum : int { OP_FIRST = 0, OP_N2F = 1, OP_NEGSTART = 2, OP_N2B = 3, OP_N3 = 4 };
+struct WLine {
+    int n2, n3, lo, hi, op, pt;  // pt: index of the line's first stored point
+};
+struct WChunk {
+    int l0, l1, p0, p1;  // lines [l0,l1), points [p0,p1)
+};
+
+struct Tile {
+    int cls, first, count, pad;  // pairs [first, first+count) of one class
+};
+
+}  // namespace ftcj
+
+struct ftcj_plan {
+    // geometry and parameters
+    double A[9], B[9], M[9];
+    double vol, omega, gcut;
+    int km[3], nk;
+    ftcj_params params;
+    int max_dens;
+    // basis
+    int nao, nshell, ngroup, nmember;
+    std::vector<ftcj::GroupDev> groups;
+    std::vector<ftcj::MemberDev> members;
+    std::vector<int> member_shell, member_prim, member_group;
+    // walk
+    std::vector<ftcj::WLine> lines;
+    std::vector<ftcj::WChunk> chunks;
+    std::vector<int> gvec;  // [ng_half][3]
+    int64_t ng_half;
+    int max_chunk_pts;
+    int n1_min, n1_max;
+    // pairs
+    int64_t npairs, npairs_ordered;
+    int64_t class_start[ftcj::kNclass + 1];
+    int64_t term_base[ftcj::kNclass];  // SoA offset of each class in a per-density term array
+    int64_t total_terms;
+    std::vector<ftcj::Tile> tiles;  // ordered by decreasing class
+    int npb;                         // rho pass: blocks per (chunk, density)
+    int num_sms;
+    // device buffers
+    ftcj::GroupDev* d_groups = nullptr;
+    ftcj::MemberDev* d_members = nullptr;
+    ftcj::PairDev* d_pairs = nullptr;
+    ftcj::PairWalk* d_walk = nullptr;
+    ftcj::WLine* d_lines = nullptr;
+    ftcj::WChunk* d_chunks = nullptr;
+    ftcj::Tile* d_tiles = nullptr;
+    int* d_gvec = nullptr;
+    double* d_vg = nullptr;          // v(G) on the half sphere
+    double* d_tw = nullptr;          // twiddles, [3][16][16] complex
+    double* d_Tmat = nullptr;        // relative-coordinate transforms, per lambda
+    double* d_D0n = nullptr;         // [max_dens][nk][nao][nao]
+    double* d_J0n = nullptr;
+    double* d_cbuf0 = nullptr;       // complex [max_dens][nk][nao][nao]
+    double* d_cbuf1 = nullptr;
+    double* d_Dp = nullptr;          // [max_dens][total_terms]
+    double* d_Jp = nullptr;          // [max_dens][nchunks][total_terms]
+    double* d_rho_part = nullptr;    // complex [max_dens][npb][ng_half]
+    double* d_rho = nullptr;         // complex [max_dens][ng_half]
+    double* d_W = nullptr;           // complex [max_dens][ng_half]
+    double* d_Epart = nullptr;       // [max_dens][nEblocks]
+    double* d_Dk_stage = nullptr;    // host-variant staging, complex [max_dens][nk][nao][nao]
+    double* d_Jk_stage = nullptr;
+    double* d_EJ_stage = nullptr;
+    double* d_check = nullptr;       // [2]
+    int nEblocks = 0;
+    size_t device_bytes = 0;
+};
+
+namespace ftcj {
+
+// error reporting (thread-local message)
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+#define FTCJ_CUDA(call)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return ::ftcj::cuda_fail(e_, #call); \
+    } while (0)
+
+// --- setup (screen.cu) ---
+int screen_and_sort(ftcj_plan* P);  // fills pairs, walk constants, tiles
+
+// --- fold / unfold (fold.cu) ---
+int launch_fold(ftcj_plan* P, int ndens, const double* Dk, double* D0n, cudaStream_t s);
+int launch_unfold(ftcj_plan* P, int ndens, const double* J0n, double* Jk, cudaStream_t s);
+int launch_check_density(ftcj_plan* P, int ndens, const double* Dk, double* out2, cudaStream_t s);
+int launch_twiddles(ftcj_plan* P);
+
+// --- Hermite densities and J back-transform (hermite.cu) ---
+int upload_hermite_tables(ftcj_plan* P);
+int launch_hermite(ftcj_plan* P, int ndens, const double* D0n, cudaStream_t s);
+int launch_jtransform(ftcj_plan* P, int ndens, double* J0n, cudaStream_t s);
+
+// --- G walks (walk.cu) ---
+int upload_walk_tables(ftcj_plan* P);
+int launch_vg(ftcj_plan* P);
+int launch_rho_walk(ftcj_plan* P, int ndens, cudaStream_t s);
+int launch_rho_reduce(ftcj_plan* P, int ndens, double* rho_out, double* W_out, double* EJ_out,
+                      const double* rho_in, cudaStream_t s);
+int launch_j_walk(ftcj_plan* P, int ndens, const double* W, cudaStream_t s);
+int rho_walk_blocks_per_sm(ftcj_plan* P, int* out);
+
+}  // namespace ftcj

@@ -1,0 +1,484 @@
+// Plan construction for the long-range Coulomb build: input validation,
+// reciprocal lattice and metric, primitive groups (several shells sharing one
+// primitive are processed together, Sec. 2.4 "multishell"), the walk over the
+// half G sphere as lines along b_1 (Sec. 2.5, Eq. "G-space root finding"),
+// device allocation, and the device-side pair screening.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+
+#include "ftcj_internal.h"
+
+namespace ftcj {
+
+static thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return FTCJ_ECUDA;
+}
+
+namespace {
+
+bool finite(double x) { return std::isfinite(x); }
+
+double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// |G|^2 = n^T M n for the metric M_ij = b_i . b_j
+double qform(const double* M, long n1, long n2, long n3) {
+    double n[3] = {(double)n1, (double)n2, (double)n3};
+    double s = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) s += n[i] * M[3 * i + j] * n[j];
+    return s;
+}
+
+// n1 range of the line (n2, n3) inside |G|^2 < gc2: the roots of
+// M11 n^2 + 2 (M12 n2 + M13 n3) n + Q(0,n2,n3) - gc2 = 0, refined by exact tests.
+bool line_range(const double* M, double gc2, int n2, int n3, int* lo, int* hi) {
+    double M11 = M[0];
+    double beta = M[1] * n2 + M[2] * n3;
+    double c0 = qform(M, 0, n2, n3) - gc2;
+    double disc = beta * beta - M11 * c0;
+    double x0 = -beta / M11;
+    double h = disc > 0 ? std::sqrt(disc) / M11 : 0.0;
+    long a = (long)std::ceil(x0 - h) - 1;
+    long b = (long)std::floor(x0 + h) + 1;
+    while (a <= b && !(qform(M, a, n2, n3) < gc2)) ++a;
+    while (b >= a && !(qform(M, b, n2, n3) < gc2)) --b;
+    if (a > b) return false;
+    while (qform(M, a - 1, n2, n3) < gc2) --a;
+    while (qform(M, b + 1, n2, n3) < gc2) ++b;
+    *lo = (int)a;
+    *hi = (int)b;
+    return true;
+}
+
+int build_walk(ftcj_plan* P) {
+    const double* M = P->M;
+    double gc2 = P->gcut * P->gcut;
+    int lim[3];
+    for (int i = 0; i < 3; ++i) {
+        double an = std::sqrt(dot3(P->A + 3 * i, P->A + 3 * i));
+        lim[i] = (int)std::floor(P->gcut * an / (2.0 * M_PI)) + 1;
+    }
+    P->lines.clear();
+    P->gvec.clear();
+    struct Raw {
+        int n2, n3, lo, hi;
+    };
+    std::vector<Raw> raw;
+    std::vector<int> op;
+    // planes n3 = 0..last non-empty
+    int n3_last = -1;
+    for (int n3 = 0; n3 <= lim[2]; ++n3) {
+        bool any = false;
+        for (int n2 = -lim[1]; n2 <= lim[1] && !any; ++n2) {
+            if (n3 == 0 && n2 < 0) continue;
+            int lo, hi;
+            if (line_range(M, gc2, n2, n3, &lo, &hi)) {
+                if (n3 == 0 && n2 == 0) lo = std::max(lo, 1);
+                if (lo <= hi) any = true;
+            }
+        }
+        if (any) n3_last = n3;
+    }
+    for (int n3 = 0; n3 <= n3_last; ++n3) {
+        int pos_last = 0, neg_last = 0;
+        std::map<int, std::pair<int, int>> rng;
+        for (int n2 = -lim[1]; n2 <= lim[1]; ++n2) {
+            if (n3 == 0 && n2 < 0) continue;
+            int lo, hi;
+            if (!line_range(M, gc2, n2, n3, &lo, &hi)) continue;
+            if (n3 == 0 && n2 == 0) lo = std::max(lo, 1);
+            if (lo > hi) continue;
+            rng[n2] = {lo, hi};
+            if (n2 >= 0) pos_last = std::max(pos_last, n2);
+            else neg_last = std::min(neg_last, n2);
+        }
+        for (int n2 = 0; n2 <= pos_last; ++n2) {
+            auto it = rng.find(n2);
+            int lo = 1, hi = 0;
+            if (it != rng.end()) {
+                lo = it->second.first;
+                hi = it->second.second;
+            }
+            raw.push_back({n2, n3, lo, hi});
+            op.push_back(n2 == 0 ? (n3 == 0 ? OP_FIRST : OP_N3) : OP_N2F);
+        }
+        for (int n2 = -1; n2 >= neg_last && n3 > 0; --n2) {
+            auto it = rng.find(n2);
+            int lo = 1, hi = 0;
+            if (it != rng.end()) {
+                lo = it->second.first;
+                hi = it->second.second;
+            }
+            raw.push_back({n2, n3, lo, hi});
+            op.push_back(n2 == -1 ? OP_NEGSTART : OP_N2B);
+        }
+    }
+    // chunks and point order
+    P->chunks.clear();
+    int pt = 0, cur = 0, l0 = 0, p0 = 0;
+    int n1min = 0, n1max = 0;
+    for (size_t i = 0; i < raw.size(); ++i) {
+        int npts = raw[i].hi >= raw[i].lo ? raw[i].hi - raw[i].lo + 1 : 0;
+        if (npts > kChunkMax) return fail(FTCJ_EUNSUPPORTED, "a G line is longer than the walk chunk");
+        if (cur > 0 && cur + npts > kChunkMax) {
+            P->chunks.push_back({l0, (int)i, p0, pt});
+            l0 = (int)i;
+            p0 = pt;
+            cur = 0;
+        }
+        int o = (i == (size_t)l0) ? OP_FIRST : op[i];
+        P->lines.push_back({raw[i].n2, raw[i].n3, raw[i].lo, raw[i].hi, o, pt});
+        if (npts > 0) {
+            for (int n1 = std::max(raw[i].lo, 0); n1 <= raw[i].hi; ++n1) {
+                P->gvec.push_back(n1);
+                P->gvec.push_back(raw[i].n2);
+                P->gvec.push_back(raw[i].n3);
+            }
+            for (int n1 = std::min(raw[i].hi, -1); n1 >= raw[i].lo; --n1) {
+                P->gvec.push_back(n1);
+                P->gvec.push_back(raw[i].n2);
+                P->gvec.push_back(raw[i].n3);
+            }
+            n1min = std::min(n1min, raw[i].lo);
+            n1max = std::max(n1max, raw[i].hi);
+        }
+        pt += npts;
+        cur += npts;
+    }
+    if (!raw.empty()) P->chunks.push_back({l0, (int)raw.size(), p0, pt});
+    P->ng_half = pt;
+    P->max_chunk_pts = 0;
+    for (auto& c : P->chunks) P->max_chunk_pts = std::max(P->max_chunk_pts, c.p1 - c.p0);
+    P->n1_min = n1min;
+    P->n1_max = n1max;
+    return FTCJ_OK;
+}
+
+template <class T>
+int dalloc(ftcj_plan* P, T** ptr, size_t count) {
+    if (count == 0) count = 1;
+    size_t bytes = sizeof(T) * count;
+    cudaError_t e = cudaMalloc((void**)ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        return fail(FTCJ_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed: " +
+                                     cudaGetErrorString(e));
+    }
+    P->device_bytes += bytes;
+    return FTCJ_OK;
+}
+
+template <class T>
+int upload(ftcj_plan* P, T** ptr, const std::vector<T>& v) {
+    int rc = dalloc(P, ptr, v.size());
+    if (rc) return rc;
+    if (!v.empty()) FTCJ_CUDA(cudaMemcpy(*ptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    return FTCJ_OK;
+}
+
+void free_device(ftcj_plan* P) {
+    void* ptrs[] = {P->d_groups, P->d_members, P->d_pairs, P->d_walk, P->d_lines, P->d_chunks, P->d_tiles,
+                    P->d_gvec, P->d_vg, P->d_tw, P->d_Tmat, P->d_D0n, P->d_J0n, P->d_cbuf0, P->d_cbuf1,
+                    P->d_Dp, P->d_Jp, P->d_rho_part, P->d_rho, P->d_W, P->d_Epart, P->d_Dk_stage,
+                    P->d_Jk_stage, P->d_EJ_stage, P->d_check};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], const ftcj_params* prm,
+           ftcj_plan* P) {
+    if (!cell || !basis || !kmesh || !prm) return fail(FTCJ_EINVAL, "null argument");
+    P->params = *prm;
+    // lattice
+    for (int i = 0; i < 9; ++i) {
+        if (!finite(cell->A[i])) return fail(FTCJ_EINVAL, "non-finite lattice");
+        P->A[i] = cell->A[i];
+    }
+    const double* a = P->A;
+    double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+                 a[2] * (a[3] * a[7] - a[4] * a[6]);
+    if (!(std::fabs(det) > 1e-8)) return fail(FTCJ_EINVAL, "singular lattice");
+    P->vol = std::fabs(det);
+    for (int i = 0; i < 3; ++i) {
+        const double* u = a + 3 * ((i + 1) % 3);
+        const double* v = a + 3 * ((i + 2) % 3);
+        P->B[3 * i + 0] = 2.0 * M_PI * (u[1] * v[2] - u[2] * v[1]) / det;
+        P->B[3 * i + 1] = 2.0 * M_PI * (u[2] * v[0] - u[0] * v[2]) / det;
+        P->B[3 * i + 2] = 2.0 * M_PI * (u[0] * v[1] - u[1] * v[0]) / det;
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) P->M[3 * i + j] = dot3(P->B + 3 * i, P->B + 3 * j);
+    // k mesh
+    P->nk = 1;
+    for (int i = 0; i < 3; ++i) {
+        if (kmesh[i] < 1) return fail(FTCJ_EINVAL, "k-mesh dimensions must be >= 1");
+        if (kmesh[i] > 16) return fail(FTCJ_EUNSUPPORTED, "k-mesh dimension above 16");
+        P->km[i] = kmesh[i];
+        P->nk *= kmesh[i];
+    }
+    // parameters
+    if (!(prm->omega > 0.0) || !finite(prm->omega)) return fail(FTCJ_EINVAL, "omega must be > 0");
+    if (prm->precision != FTCJ_PREC_FP64) return fail(FTCJ_EUNSUPPORTED, "only FTCJ_PREC_FP64 is built");
+    if (!(prm->pair_thresh > 0.0 && prm->pair_thresh < 1.0)) return fail(FTCJ_EINVAL, "pair_thresh in (0,1)");
+    P->omega = prm->omega;
+    if (prm->gcut > 0.0) {
+        P->gcut = prm->gcut;
+    } else {
+        if (!(prm->eps_g > 0.0 && prm->eps_g < 1.0)) return fail(FTCJ_EINVAL, "eps_g in (0,1) when gcut <= 0");
+        P->gcut = 2.0 * prm->omega * std::sqrt(std::log(1.0 / prm->eps_g));
+    }
+    P->max_dens = prm->max_dens > 0 ? prm->max_dens : 1;
+    // basis
+    if (basis->ncentre < 1 || !basis->xyz) return fail(FTCJ_EINVAL, "no centres");
+    if (basis->nshell < 1 || !basis->shells) return fail(FTCJ_EINVAL, "no shells");
+    for (int i = 0; i < 3 * basis->ncentre; ++i)
+        if (!finite(basis->xyz[i])) return fail(FTCJ_EINVAL, "non-finite centre");
+    P->nshell = basis->nshell;
+    int ao = 0;
+    double amin = 1e300;
+    struct Mem {
+        int shell, prim;
+        ftcj::MemberDev m;
+    };
+    std::vector<std::vector<Mem>> gmem;
+    std::vector<std::pair<int, double>> gkey;
+    for (int s = 0; s < basis->nshell; ++s) {
+        const ftcj_shell& sh = basis->shells[s];
+        if (sh.l < 0) return fail(FTCJ_EINVAL, "negative l");
+        if (sh.l > kLmax) return fail(FTCJ_EUNSUPPORTED, "shell l above FTCJ_LMAX");
+        if (sh.centre < 0 || sh.centre >= basis->ncentre) return fail(FTCJ_EINVAL, "shell centre out of range");
+        if (sh.nprim < 1 || !sh.exps || !sh.coefs) return fail(FTCJ_EINVAL, "shell without primitives");
+        int nf = sh.spherical ? 2 * sh.l + 1 : (sh.l + 1) * (sh.l + 2) / 2;
+        for (int k = 0; k < sh.nprim; ++k) {
+            double al = sh.exps[k];
+            if (!(al > 0.0) || !finite(al)) return fail(FTCJ_EINVAL, "exponents must be > 0");
+            if (!finite(sh.coefs[k])) return fail(FTCJ_EINVAL, "non-finite coefficient");
+            amin = std::min(amin, al);
+            int g = -1;
+            for (size_t q = 0; q < gkey.size(); ++q)
+                if (gkey[q].first == sh.centre && gkey[q].second == al) {
+                    g = (int)q;
+                    break;
+                }
+            if (g < 0) {
+                g = (int)gkey.size();
+                gkey.push_back({sh.centre, al});
+                gmem.emplace_back();
+            }
+            double radial = std::pow(2.0 * al / M_PI, 0.75) * std::pow(4.0 * al, 0.5 * sh.l);
+            ftcj::MemberDev m{sh.l, sh.spherical ? 1 : 0, ao, 0, sh.coefs[k] * radial};
+            gmem[g].push_back({s, k, m});
+        }
+        ao += nf;
+    }
+    P->nao = ao;
+    P->ngroup = (int)gkey.size();
+    P->groups.clear();
+    P->members.clear();
+    for (int g = 0; g < P->ngroup; ++g) {
+        ftcj::GroupDev gd;
+        const double* x = basis->xyz + 3 * gkey[g].first;
+        gd.x = x[0];
+        gd.y = x[1];
+        gd.z = x[2];
+        gd.alpha = gkey[g].second;
+        gd.centre = gkey[g].first;
+        gd.mem0 = (int)P->members.size();
+        gd.lmax = 0;
+        for (auto& m : gmem[g]) {
+            P->members.push_back(m.m);
+            P->member_shell.push_back(m.shell);
+            P->member_prim.push_back(m.prim);
+            P->member_group.push_back(g);
+            gd.lmax = std::max(gd.lmax, m.m.l);
+        }
+        gd.mem1 = (int)P->members.size();
+        P->groups.push_back(gd);
+    }
+    P->nmember = (int)P->members.size();
+    // exp(-G^2/4p) must stay representable along the walk
+    if (P->gcut * P->gcut / (8.0 * amin) > 600.0)
+        return fail(FTCJ_EUNSUPPORTED, "Gcut^2/(4 p_min) above 600: exponents too diffuse for this Gcut");
+    int rc = build_walk(P);
+    if (rc) return rc;
+
+    FTCJ_CUDA(cudaFree(0));
+    int dev = 0;
+    FTCJ_CUDA(cudaGetDevice(&dev));
+    FTCJ_CUDA(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev));
+
+    if ((rc = upload(P, &P->d_groups, P->groups))) return rc;
+    if ((rc = upload(P, &P->d_members, P->members))) return rc;
+    if ((rc = upload(P, &P->d_lines, P->lines))) return rc;
+    if ((rc = upload(P, &P->d_chunks, P->chunks))) return rc;
+    if ((rc = upload(P, &P->d_gvec, P->gvec))) return rc;
+    if ((rc = dalloc(P, &P->d_vg, (size_t)P->ng_half))) return rc;
+    if ((rc = dalloc(P, &P->d_tw, (size_t)3 * 16 * 16 * 2))) return rc;
+
+    if ((rc = screen_and_sort(P))) return rc;
+
+    // per-class SoA layout of the Hermite terms
+    P->total_terms = 0;
+    for (int c = 0; c < kNclass; ++c) {
+        P->term_base[c] = P->total_terms;
+        P->total_terms += (P->class_start[c + 1] - P->class_start[c]) * nterms(c);
+    }
+    P->tiles.clear();
+    for (int c = kNclass - 1; c >= 0; --c)
+        for (int64_t f = P->class_start[c]; f < P->class_start[c + 1]; f += kTile) {
+            int cnt = (int)std::min<int64_t>(kTile, P->class_start[c + 1] - f);
+            P->tiles.push_back({c, (int)f, cnt, 0});
+        }
+    if ((rc = upload(P, &P->d_tiles, P->tiles))) return rc;
+    if ((rc = upload_walk_tables(P))) return rc;
+    if ((rc = upload_hermite_tables(P))) return rc;
+    int bps = 1;
+    if ((rc = rho_walk_blocks_per_sm(P, &bps))) return rc;
+    int nch = std::max<int>(1, (int)P->chunks.size());
+    P->npb = std::max(1, std::min<int>((int)std::max<size_t>(1, P->tiles.size()), P->num_sms * bps / nch));
+
+    size_t nn = (size_t)P->nao * P->nao;
+    size_t md = (size_t)P->max_dens;
+    if ((rc = dalloc(P, &P->d_D0n, md * P->nk * nn))) return rc;
+    if ((rc = dalloc(P, &P->d_J0n, md * P->nk * nn))) return rc;
+    if ((rc = dalloc(P, &P->d_cbuf0, 2 * md * P->nk * nn))) return rc;
+    if ((rc = dalloc(P, &P->d_cbuf1, 2 * md * P->nk * nn))) return rc;
+    if ((rc = dalloc(P, &P->d_Dp, md * (size_t)P->total_terms))) return rc;
+    if ((rc = dalloc(P, &P->d_Jp, md * (size_t)nch * (size_t)P->total_terms))) return rc;
+    if ((rc = dalloc(P, &P->d_rho_part, 2 * md * (size_t)P->npb * (size_t)P->ng_half))) return rc;
+    if ((rc = dalloc(P, &P->d_rho, 2 * md * (size_t)P->ng_half))) return rc;
+    if ((rc = dalloc(P, &P->d_W, 2 * md * (size_t)P->ng_half))) return rc;
+    P->nEblocks = (int)std::max<int64_t>(1, (P->ng_half + 255) / 256);
+    if ((rc = dalloc(P, &P->d_Epart, md * (size_t)P->nEblocks))) return rc;
+    if ((rc = dalloc(P, &P->d_Dk_stage, 2 * md * P->nk * nn))) return rc;
+    if ((rc = dalloc(P, &P->d_Jk_stage, 2 * md * P->nk * nn))) return rc;
+    if ((rc = dalloc(P, &P->d_EJ_stage, md))) return rc;
+    if ((rc = dalloc(P, &P->d_check, 2))) return rc;
+    if ((rc = launch_vg(P))) return rc;
+    if ((rc = launch_twiddles(P))) return rc;
+    FTCJ_CUDA(cudaDeviceSynchronize());
+    return FTCJ_OK;
+}
+
+}  // namespace
+}  // namespace ftcj
+
+using namespace ftcj;
+
+extern "C" {
+
+const char* ftcj_strerror(int code) {
+    switch (code) {
+        case FTCJ_OK: return "ok";
+        case FTCJ_EINVAL: return "invalid argument";
+        case FTCJ_ENOMEM: return "out of memory";
+        case FTCJ_ECUDA: return "CUDA error";
+        case FTCJ_ETIMEOUT: return "device wait timed out";
+        case FTCJ_EUNSUPPORTED: return "unsupported input";
+        default: return "unknown error";
+    }
+}
+
+const char* ftcj_last_error(void) { return g_last_error.c_str(); }
+
+int ftcj_plan_create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], const ftcj_params* params,
+                     ftcj_plan** out) {
+    if (!out) return fail(FTCJ_EINVAL, "null output pointer");
+    *out = nullptr;
+    ftcj_plan* P = new (std::nothrow) ftcj_plan();
+    if (!P) return fail(FTCJ_ENOMEM, "host allocation failed");
+    int rc;
+    try {
+        rc = create(cell, basis, kmesh, params, P);
+    } catch (const std::bad_alloc&) {
+        rc = fail(FTCJ_ENOMEM, "host allocation failed");
+    } catch (...) {
+        rc = fail(FTCJ_EINVAL, "unexpected host exception");
+    }
+    if (rc != FTCJ_OK) {
+        free_device(P);
+        delete P;
+        return rc;
+    }
+    *out = P;
+    return FTCJ_OK;
+}
+
+int ftcj_plan_info(const ftcj_plan* P, ftcj_info* o) {
+    if (!P || !o) return fail(FTCJ_EINVAL, "null argument");
+    std::memset(o, 0, sizeof(*o));
+    o->nao = P->nao;
+    o->nk = P->nk;
+    o->nshell = P->nshell;
+    o->ngroup = P->ngroup;
+    o->npairs = P->npairs;
+    o->npairs_ordered = P->npairs_ordered;
+    o->ng_half = P->ng_half;
+    o->ng_full = 2 * P->ng_half;
+    o->pair_g_units = P->npairs_ordered * o->ng_full;
+    for (int c = 0; c < kNclass && c < 5; ++c) o->pairs_by_class[c] = P->class_start[c + 1] - P->class_start[c];
+    o->nlines = (int)P->lines.size();
+    o->nchunks = (int)P->chunks.size();
+    o->gcut = P->gcut;
+    o->volume = P->vol;
+    o->device_bytes = P->device_bytes;
+    return FTCJ_OK;
+}
+
+void ftcj_plan_destroy(ftcj_plan* P) {
+    if (!P) return;
+    free_device(P);
+    delete P;
+}
+
+int ftcj_get_gvectors(const ftcj_plan* P, int* n_out) {
+    if (!P || !n_out) return fail(FTCJ_EINVAL, "null argument");
+    if (!P->gvec.empty()) std::memcpy(n_out, P->gvec.data(), sizeof(int) * P->gvec.size());
+    return FTCJ_OK;
+}
+
+int ftcj_get_pairs(const ftcj_plan* P, int* out) {
+    if (!P || !out) return fail(FTCJ_EINVAL, "null argument");
+    if (P->npairs == 0) return FTCJ_OK;
+    std::vector<PairDev> h((size_t)P->npairs);
+    FTCJ_CUDA(cudaMemcpy(h.data(), P->d_pairs, sizeof(PairDev) * h.size(), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < h.size(); ++i) {
+        out[6 * i + 0] = h[i].ga;
+        out[6 * i + 1] = h[i].gb;
+        out[6 * i + 2] = h[i].L[0];
+        out[6 * i + 3] = h[i].L[1];
+        out[6 * i + 4] = h[i].L[2];
+        out[6 * i + 5] = h[i].weight;
+    }
+    return FTCJ_OK;
+}
+
+int ftcj_get_groups(const ftcj_plan* P, int* centre, double* exponent, int* members, int* nmember) {
+    if (!P) return fail(FTCJ_EINVAL, "null argument");
+    if (nmember) *nmember = P->nmember;
+    for (int g = 0; g < P->ngroup; ++g) {
+        if (centre) centre[g] = P->groups[g].centre;
+        if (exponent) exponent[g] = P->groups[g].alpha;
+    }
+    if (members)
+        for (int m = 0; m < P->nmember; ++m) {
+            members[3 * m + 0] = P->member_group[m];
+            members[3 * m + 1] = P->member_shell[m];
+            members[3 * m + 2] = P->member_prim[m];
+        }
+    return FTCJ_OK;
+}
+
+}  // extern "C"

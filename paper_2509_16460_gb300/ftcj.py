@@ -1,0 +1,307 @@
+"""Thin Python binding of libftcj.so (the C-ABI declared in include/ftcj.h).
+
+Argument marshalling only: torch supplies device memory and streams, every
+step of the build runs in the library's CUDA kernels.  There is no CPU
+fallback: if the library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libftcj.so")
+
+FTCJ_PREC_FP64 = 0
+FTCJ_LMAX = 2
+
+_c_int, _c_double, _c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+class Cell(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_double * 9)]
+
+
+class ShellDesc(ctypes.Structure):
+    _fields_ = [("centre", _c_int), ("l", _c_int), ("spherical", _c_int), ("nprim", _c_int),
+                ("exps", _dp), ("coefs", _dp)]
+
+
+class BasisDesc(ctypes.Structure):
+    _fields_ = [("ncentre", _c_int), ("xyz", _dp), ("nshell", _c_int), ("shells", ctypes.POINTER(ShellDesc))]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("omega", _c_double), ("gcut", _c_double), ("eps_g", _c_double), ("pair_thresh", _c_double),
+                ("precision", _c_int), ("max_dens", _c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("nao", _c_int), ("nk", _c_int), ("nshell", _c_int), ("ngroup", _c_int),
+                ("npairs", ctypes.c_int64), ("npairs_ordered", ctypes.c_int64), ("ng_half", ctypes.c_int64),
+                ("ng_full", ctypes.c_int64), ("pair_g_units", ctypes.c_int64),
+                ("pairs_by_class", ctypes.c_int64 * 5), ("nlines", _c_int), ("nchunks", _c_int),
+                ("gcut", _c_double), ("volume", _c_double), ("device_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["pairs_by_class"] = list(self.pairs_by_class)
+        return d
+
+
+EXPORTED = [
+    "ftcj_plan_create", "ftcj_plan_info", "ftcj_plan_destroy", "ftcj_jbuild", "ftcj_jbuild_host",
+    "ftcj_fold_density", "ftcj_rho", "ftcj_potential", "ftcj_jback", "ftcj_unfold_j", "ftcj_check_density",
+    "ftcj_get_gvectors", "ftcj_get_pairs", "ftcj_get_groups", "ftcj_strerror", "ftcj_last_error",
+]
+
+_lock = threading.Lock()
+_lib: Optional[ctypes.CDLL] = None
+
+
+class FtcjError(RuntimeError):
+    pass
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library; raises if it was not built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise FtcjError(f"CUDA library {LIB_PATH} is missing: run __graft_entry__.build() "
+                                "or python -m paper_2509_16460_gb300.build")
+            L = ctypes.CDLL(LIB_PATH)
+            _declare(L)
+            _lib = L
+    return _lib
+
+
+def _declare(L):
+    P = _c_void_p
+    L.ftcj_plan_create.argtypes = [ctypes.POINTER(Cell), ctypes.POINTER(BasisDesc), _ip, ctypes.POINTER(Params),
+                                   ctypes.POINTER(_c_void_p)]
+    L.ftcj_plan_info.argtypes = [P, ctypes.POINTER(Info)]
+    L.ftcj_plan_destroy.argtypes = [P]
+    L.ftcj_plan_destroy.restype = None
+    for name in ("ftcj_jbuild", "ftcj_jbuild_host"):
+        getattr(L, name).argtypes = [P, _c_int, P, P, P, P]
+    for name in ("ftcj_fold_density", "ftcj_rho", "ftcj_jback", "ftcj_unfold_j"):
+        getattr(L, name).argtypes = [P, _c_int, P, P, P]
+    L.ftcj_potential.argtypes = [P, _c_int, P, P, P, P]
+    L.ftcj_check_density.argtypes = [P, _c_int, P, _dp, _dp, P]
+    L.ftcj_get_gvectors.argtypes = [P, _ip]
+    L.ftcj_get_pairs.argtypes = [P, _ip]
+    L.ftcj_get_groups.argtypes = [P, _ip, _dp, _ip, _ip]
+    L.ftcj_strerror.argtypes = [_c_int]
+    L.ftcj_strerror.restype = ctypes.c_char_p
+    L.ftcj_last_error.argtypes = []
+    L.ftcj_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        f = getattr(L, name)
+        if name not in ("ftcj_plan_destroy", "ftcj_strerror", "ftcj_last_error"):
+            f.restype = _c_int
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        L = lib()
+        raise FtcjError(f"{what}: {L.ftcj_strerror(rc).decode()} ({rc}): {L.ftcj_last_error().decode()}")
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return _c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise FtcjError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise FtcjError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise FtcjError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise FtcjError(f"{name} must be contiguous")
+    return _c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A plan for one cell, basis and k-mesh (ftcj_plan_create)."""
+
+    def __init__(self, A, xyz, shells, kmesh, omega, eps_g=1e-14, gcut=0.0, pair_thresh=1e-12,
+                 precision=FTCJ_PREC_FP64, max_dens=1):
+        L = lib()
+        self._keep = []
+        A = np.ascontiguousarray(A, dtype=np.float64).reshape(3, 3)
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+        self._keep += [A, xyz]
+        cell = Cell()
+        for i, v in enumerate(A.ravel()):
+            cell.A[i] = float(v)
+        sh = (ShellDesc * len(shells))()
+        for i, s in enumerate(shells):
+            e = np.ascontiguousarray(s.exps, dtype=np.float64)
+            c = np.ascontiguousarray(s.coefs, dtype=np.float64)
+            self._keep += [e, c]
+            sh[i] = ShellDesc(int(s.centre), int(s.l), 1 if s.spherical else 0, int(len(e)),
+                              e.ctypes.data_as(_dp), c.ctypes.data_as(_dp))
+        basis = BasisDesc(int(xyz.shape[0]), xyz.ctypes.data_as(_dp), len(shells), sh)
+        km = (ctypes.c_int * 3)(*[int(k) for k in kmesh])
+        prm = Params(float(omega), float(gcut), float(eps_g), float(pair_thresh), int(precision), int(max_dens))
+        h = _c_void_p()
+        _check(L.ftcj_plan_create(ctypes.byref(cell), ctypes.byref(basis), km, ctypes.byref(prm), ctypes.byref(h)),
+               "ftcj_plan_create")
+        self._h = h
+        self.max_dens = int(max_dens)
+        inf = Info()
+        _check(L.ftcj_plan_info(self._h, ctypes.byref(inf)), "ftcj_plan_info")
+        self.info = inf.as_dict()
+        self.nao = inf.nao
+        self.nk = inf.nk
+        self.ng_half = int(inf.ng_half)
+
+    @classmethod
+    def from_workload(cls, w, max_dens=None, precision=FTCJ_PREC_FP64):
+        return cls(w.A, w.xyz, w.shells, w.kmesh, w.omega, eps_g=w.eps_g, gcut=w.gcut, pair_thresh=w.pair_thresh,
+                   precision=precision, max_dens=max_dens or w.ndens)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ftcj_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- whole build ----
+    def jbuild(self, Dk, Jk=None, EJ=None, stream=None):
+        import torch
+        nd = Dk.shape[0]
+        shp = (nd, self.nk, self.nao, self.nao)
+        if Jk is None:
+            Jk = torch.empty(shp, dtype=torch.complex128, device=Dk.device)
+        if EJ is None:
+            EJ = torch.empty(nd, dtype=torch.float64, device=Dk.device)
+        _check(lib().ftcj_jbuild(self._h, nd, _dev_ptr(Dk, torch.complex128, shp, "Dk"),
+                                 _dev_ptr(Jk, torch.complex128, shp, "Jk"), _dev_ptr(EJ, torch.float64, (nd,), "EJ"),
+                                 _stream_ptr(stream)), "ftcj_jbuild")
+        return Jk, EJ
+
+    def jbuild_host(self, Dk, Jk=None, EJ=None, stream=None):
+        """Host buffers in and out (numpy or pinned CPU torch tensors)."""
+        import torch
+        nd = Dk.shape[0]
+        shp = (nd, self.nk, self.nao, self.nao)
+        if isinstance(Dk, np.ndarray):
+            Dk = torch.from_numpy(np.ascontiguousarray(Dk, dtype=np.complex128))
+        if Jk is None:
+            Jk = torch.empty(shp, dtype=torch.complex128)
+        if EJ is None:
+            EJ = torch.empty(nd, dtype=torch.float64)
+        for t, name, dt, s in ((Dk, "Dk", torch.complex128, shp), (Jk, "Jk", torch.complex128, shp),
+                               (EJ, "EJ", torch.float64, (nd,))):
+            if t.is_cuda or t.dtype != dt or tuple(t.shape) != tuple(s) or not t.is_contiguous():
+                raise FtcjError(f"{name}: contiguous host tensor {dt} {s} required")
+        _check(lib().ftcj_jbuild_host(self._h, nd, _c_void_p(Dk.data_ptr()), _c_void_p(Jk.data_ptr()),
+                                      _c_void_p(EJ.data_ptr()), _stream_ptr(stream)), "ftcj_jbuild_host")
+        return Jk, EJ
+
+    # ---- individual steps ----
+    def fold_density(self, Dk, D0n=None, stream=None):
+        import torch
+        nd = Dk.shape[0]
+        shp = (nd, self.nk, self.nao, self.nao)
+        if D0n is None:
+            D0n = torch.empty(shp, dtype=torch.float64, device=Dk.device)
+        _check(lib().ftcj_fold_density(self._h, nd, _dev_ptr(Dk, torch.complex128, shp, "Dk"),
+                                       _dev_ptr(D0n, torch.float64, shp, "D0n"), _stream_ptr(stream)),
+               "ftcj_fold_density")
+        return D0n
+
+    def rho(self, D0n, rho=None, stream=None):
+        import torch
+        nd = D0n.shape[0]
+        if rho is None:
+            rho = torch.empty((nd, self.ng_half), dtype=torch.complex128, device=D0n.device)
+        _check(lib().ftcj_rho(self._h, nd, _dev_ptr(D0n, torch.float64, (nd, self.nk, self.nao, self.nao), "D0n"),
+                              _dev_ptr(rho, torch.complex128, (nd, self.ng_half), "rho"), _stream_ptr(stream)),
+               "ftcj_rho")
+        return rho
+
+    def potential(self, rho, W=None, EJ=None, stream=None):
+        import torch
+        nd = rho.shape[0]
+        if W is None:
+            W = torch.empty((nd, self.ng_half), dtype=torch.complex128, device=rho.device)
+        if EJ is None:
+            EJ = torch.empty(nd, dtype=torch.float64, device=rho.device)
+        _check(lib().ftcj_potential(self._h, nd, _dev_ptr(rho, torch.complex128, (nd, self.ng_half), "rho"),
+                                    _dev_ptr(W, torch.complex128, (nd, self.ng_half), "W"),
+                                    _dev_ptr(EJ, torch.float64, (nd,), "EJ"), _stream_ptr(stream)), "ftcj_potential")
+        return W, EJ
+
+    def jback(self, W, J0n=None, stream=None):
+        import torch
+        nd = W.shape[0]
+        shp = (nd, self.nk, self.nao, self.nao)
+        if J0n is None:
+            J0n = torch.empty(shp, dtype=torch.float64, device=W.device)
+        _check(lib().ftcj_jback(self._h, nd, _dev_ptr(W, torch.complex128, (nd, self.ng_half), "W"),
+                                _dev_ptr(J0n, torch.float64, shp, "J0n"), _stream_ptr(stream)), "ftcj_jback")
+        return J0n
+
+    def unfold_j(self, J0n, Jk=None, stream=None):
+        import torch
+        nd = J0n.shape[0]
+        shp = (nd, self.nk, self.nao, self.nao)
+        if Jk is None:
+            Jk = torch.empty(shp, dtype=torch.complex128, device=J0n.device)
+        _check(lib().ftcj_unfold_j(self._h, nd, _dev_ptr(J0n, torch.float64, shp, "J0n"),
+                                   _dev_ptr(Jk, torch.complex128, shp, "Jk"), _stream_ptr(stream)), "ftcj_unfold_j")
+        return Jk
+
+    def check_density(self, Dk, stream=None):
+        import torch
+        nd = Dk.shape[0]
+        mi, ma = ctypes.c_double(), ctypes.c_double()
+        _check(lib().ftcj_check_density(self._h, nd,
+                                        _dev_ptr(Dk, torch.complex128, (nd, self.nk, self.nao, self.nao), "Dk"),
+                                        ctypes.byref(mi), ctypes.byref(ma), _stream_ptr(stream)),
+               "ftcj_check_density")
+        return mi.value, ma.value
+
+    # ---- exports ----
+    def gvectors(self):
+        out = np.zeros((max(self.ng_half, 1), 3), dtype=np.int32)
+        _check(lib().ftcj_get_gvectors(self._h, out.ctypes.data_as(_ip)), "ftcj_get_gvectors")
+        return out[:self.ng_half]
+
+    def pairs(self):
+        n = int(self.info["npairs"])
+        out = np.zeros((max(n, 1), 6), dtype=np.int32)
+        _check(lib().ftcj_get_pairs(self._h, out.ctypes.data_as(_ip)), "ftcj_get_pairs")
+        return out[:n]
+
+    def groups(self):
+        ng = int(self.info["ngroup"])
+        nm = ctypes.c_int()
+        _check(lib().ftcj_get_groups(self._h, None, None, None, ctypes.byref(nm)), "ftcj_get_groups")
+        cen = np.zeros(max(ng, 1), dtype=np.int32)
+        ex = np.zeros(max(ng, 1))
+        mem = np.zeros((max(nm.value, 1), 3), dtype=np.int32)
+        _check(lib().ftcj_get_groups(self._h, cen.ctypes.data_as(_ip), ex.ctypes.data_as(_dp),
+                                     mem.ctypes.data_as(_ip), ctypes.byref(nm)), "ftcj_get_groups")
+        return cen[:ng], ex[:ng], mem[:nm.value]
