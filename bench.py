@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Benchmark of the long-range planewave-DF Coulomb build (steps a2..a8).
+
+Workload: diamond-like cubic cell a = 6.74 bohr, 8 carbon-like centres,
+spherical s8 p4 d2 per centre (240 AOs), k-mesh 4x4x4 (64 Hermitian,
+time-reversal-symmetric D^k from 16 random occupied orbitals), omega = 0.4,
+exp(-G^2/4w^2) > 1e-14, primitive pairs kept above overlap 1e-12.
+
+One step = one whole build from D^k (resident in HBM) to J^k and E_J.
+Metric value = pair*G evaluations per second, the unit being one ordered
+screened primitive-shell pair times one G != 0 of the full sphere.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own replica of the workload (the bench
+workload is one cell); value is the whole-job rate, timed as the max over
+ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LR J-build ms & pair·G evals/s, split-prec vs FP64 form at max|ΔJ|≤1e-8 Eh"
+UNIT = "pair*G/s"
+WORKLOAD = ("diamond-like cubic a=6.74 bohr, 8 C-like centres, spherical s8p4d2 (240 AOs), "
+            "k 4x4x4 (64 D^k, 16 occupied), omega 0.4, exp(-G^2/4w^2)>1e-14, pair overlap>1e-12")
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                rows.append(parts)
+            except ValueError:
+                pass
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def rho_walk_flops(info, ndens):
+    """Algorithmic FP64 flops of one structure-factor walk launch: (4L + 14) per
+    (pair record, half-sphere G) for a pair record of class L."""
+    return ndens * sum(n * info["ng_half"] * (4 * L + 14) for L, n in enumerate(info["pairs_by_class"]))
+
+
+def j_walk_flops(info, ndens):
+    return rho_walk_flops(info, ndens)
+
+
+def traffic_from_profile(kernel: str):
+    """dram bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (its recorded source hash must match)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_diamond240_k444.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"source_sha256:\s*([0-9a-f]{16,64})", txt)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m or not t:
+        return None
+    src = open(os.path.join(ROOT, "paper_2509_16460_gb300", "csrc", "walk.cu"), "rb").read()
+    if hashlib.sha256(src).hexdigest()[:len(m.group(1))] != m.group(1):
+        return None
+    return float(t.group(1))
+
+
+def cpu_oracle_run(w, pair_stride):
+    import oracle
+    r = oracle.lrj(w, pair_stride=pair_stride, want_j0n=False, want_rho=False)
+    threads = os.cpu_count() or 1
+    try:
+        import ctypes
+        gomp = ctypes.CDLL("libgomp.so.1")
+        threads = int(gomp.omp_get_max_threads())
+    except OSError:
+        pass
+    units = r["units"] * w.ndens
+    return r, units, threads
+
+
+def run_reference(args, world, rank):
+    """The reference arm is the CPU oracle, timed as it stands on the host cores."""
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2509_16460_gb300 import workloads as W
+    oracle.build()
+    w = W.cfg2()
+    stride = 8
+    for _ in range(args.warmup):
+        cpu_oracle_run(w, stride)
+    times, units = [], 0.0
+    threads = 1
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r, units, threads = cpu_oracle_run(w, stride)
+        times.append(time.perf_counter() - t0)
+    mean = statistics.mean(times)
+    value = units / mean
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": "fp64 CPU oracle",
+                   "sample": f"every {stride}th ordered primitive pair, all G (stride {stride})"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"every {stride}th ordered screened primitive pair of the workload, full G sphere"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2509_16460_gb300 import ftcj
+    from paper_2509_16460_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = W.cfg2()
+    plan = ftcj.Plan.from_workload(w)
+    info = plan.info
+    units = float(info["pair_g_units"]) * w.ndens
+    stream = torch.cuda.current_stream()
+    Dk = torch.from_numpy(np.ascontiguousarray(w.Dk)).cuda()
+    Jk = torch.empty_like(Dk)
+    EJ = torch.empty(w.ndens, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        plan.jbuild(Dk, Jk, EJ)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device time per step, L2 flushed between steps ----
+    plan.profile_enable(args.steps)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        plan.jbuild(Dk, Jk, EJ)
+        ev[k][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    phase_ms, batches, launches = plan.profile_read()
+    plan.profile_enable(0)
+    ms = statistics.mean(step_ms)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * units / (ms * 1e-3)
+
+    # ---- end to end through the host-buffer entry point ----
+    Dk_h = torch.from_numpy(np.ascontiguousarray(w.Dk)).pin_memory()
+    Jk_h = torch.empty(Dk_h.shape, dtype=torch.complex128).pin_memory()
+    EJ_h = torch.empty(w.ndens, dtype=torch.float64).pin_memory()
+    plan.jbuild_host(Dk_h, Jk_h, EJ_h)
+    e2e_steps = max(3, min(args.steps, 10))
+    e2e_t = []
+    barrier()
+    for _ in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.jbuild_host(Dk_h, Jk_h, EJ_h)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = statistics.mean(e2e_t)
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = Dk_h.numel() * 16
+    d2h = Jk_h.numel() * 16 + EJ_h.numel() * 8
+
+    # ---- roofline of the dominant kernel (FP64 ALU bound) ----
+    fp64_peak = ftcj.probe_fma_peak(0)
+    walks = {"k_rho_walk": phase_ms["rho_walk"], "k_j_walk": phase_ms["j_walk"]}
+    kname = max(walks, key=walks.get)
+    per_launch_ms = walks[kname] / max(batches, 1)
+    flops = rho_walk_flops(info, w.ndens) if kname == "k_rho_walk" else j_walk_flops(info, w.ndens)
+    achieved = flops / (per_launch_ms * 1e-3)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": traffic_from_profile(kname), "kernel": kname,
+                "peak_source": "measured FP64 FMA throughput (ftcj_probe_fma_peak) on this GPU",
+                "nominal_peak": 152 * 2 * 2 * 2.07e9 / 1e12,
+                "phase_ms_per_step": {k: v / max(batches, 1) for k, v in phase_ms.items()}}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": "fp64", "pair_g_units_per_step": units,
+                   "npairs_ordered": info["npairs_ordered"], "pair_records": info["npairs"],
+                   "ng_full": info["ng_full"], "nao": info["nao"], "nk": info["nk"],
+                   "l2": f"{L2_FLUSH_BYTES >> 20} MB buffer written between timed steps",
+                   "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+        "e2e": {"value": world * units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "clocks": clocks,
+        "wall_s_timed_region": t_wall,
+    }
+
+    if rank == 0 and not args.no_cpu_baseline:
+        # the whole oracle on the host cores: the CPU baseline and the accuracy of this run
+        r, cu, threads = cpu_oracle_run(w, 1)
+        Jg = Jk.cpu().numpy()
+        line["cpu_baseline"] = {"value": cu / r["seconds"], "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": "the whole workload (every pair, full sphere), one build",
+                                "seconds": r["seconds"]}
+        line["max_abs_dJ_vs_oracle"] = float(np.abs(Jg - r["Jk"]).max())
+        line["abs_dEJ_vs_oracle"] = float(np.abs(EJ.cpu().numpy() - r["EJ"]).max())
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -178,6 +178,36 @@ int ftcj_unfold_j(ftcj_plan* plan, int ndens, const double* J0n, double* Jk, voi
 int ftcj_check_density(ftcj_plan* plan, int ndens, const double* Dk, double* max_imag, double* max_asym,
                        void* stream);
 
+/* ---- measurement ---- */
+
+/* Phases of one build batch, in launch order. */
+#define FTCJ_PHASE_FOLD 0      /* a2: k -> BvK transform stages */
+#define FTCJ_PHASE_HERMITE 1   /* a3: Hermite densities */
+#define FTCJ_PHASE_RHO 2       /* a4: structure-factor walk */
+#define FTCJ_PHASE_POTENTIAL 3 /* a5: row reduction, W and E_J */
+#define FTCJ_PHASE_JWALK 4     /* a6: back-contraction walk */
+#define FTCJ_PHASE_JAO 5       /* a7: transform to AOs (and the J^{0n} clear) */
+#define FTCJ_PHASE_UNFOLD 6    /* a8: BvK -> k transform stages */
+#define FTCJ_NPHASE 7
+
+/* Turn per-phase CUDA-event timing of ftcj_jbuild / ftcj_jbuild_host on
+ * (max_batches > 0: events for that many batches are created now) or off
+ * (0: events released).  Events are recorded on the build's stream. */
+int ftcj_profile_enable(ftcj_plan* plan, int max_batches);
+
+/* Sums of the per-phase device times (ms) over the batches recorded since
+ * the last read, the number of batches, and the number of kernels the
+ * library launched in them; waits for the recorded events and resets. */
+int ftcj_profile_read(ftcj_plan* plan, double ms[FTCJ_NPHASE], int* batches, int64_t* launches);
+
+/* Kernel launches of one build batch of nd densities (no launch happens). */
+int ftcj_launches_per_batch(const ftcj_plan* plan, int nd, int64_t* launches);
+
+/* Measured fused multiply-add throughput of this GPU in flop/s (2 per FMA):
+ * precision 0 = FP64, 1 = FP32.  Runs a short register-resident FMA loop on
+ * every SM and synchronises `stream`. */
+int ftcj_probe_fma_peak(int precision, double* flops_per_s, void* stream);
+
 /* ---- plan exports (host buffers, filled by the call) ---- */
 
 /* n triples [ng_half][3] of the half sphere, in rho's storage order. */

@@ -19,13 +19,31 @@ int check(const ftcj_plan* P, int ndens, bool batch_limit) {
 // one batch of <= max_dens densities; every pointer is device memory
 int build_batch(ftcj_plan* P, int nd, const double* Dk, double* Jk, double* EJ, cudaStream_t s) {
     int rc;
+    cudaEvent_t* ev = nullptr;
+    if (P->prof_used < P->prof_max) {
+        ev = P->prof_events.data() + (size_t)P->prof_used * (FTCJ_NPHASE + 1);
+        ++P->prof_used;
+        P->prof_launches += launches_per_batch(P);
+    }
+    auto mark = [&](int i) -> int {
+        if (ev) FTCJ_CUDA(cudaEventRecord(ev[i], s));
+        return FTCJ_OK;
+    };
+    if ((rc = mark(0))) return rc;
     if ((rc = launch_fold(P, nd, Dk, P->d_D0n, s))) return rc;
+    if ((rc = mark(1))) return rc;
     if ((rc = launch_hermite(P, nd, P->d_D0n, s))) return rc;
+    if ((rc = mark(2))) return rc;
     if ((rc = launch_rho_walk(P, nd, s))) return rc;
+    if ((rc = mark(3))) return rc;
     if ((rc = launch_rho_reduce(P, nd, P->d_rho, P->d_W, EJ, nullptr, s))) return rc;
+    if ((rc = mark(4))) return rc;
     if ((rc = launch_j_walk(P, nd, P->d_W, s))) return rc;
+    if ((rc = mark(5))) return rc;
     if ((rc = launch_jtransform(P, nd, P->d_J0n, s))) return rc;
+    if ((rc = mark(6))) return rc;
     if ((rc = launch_unfold(P, nd, P->d_J0n, Jk, s))) return rc;
+    if ((rc = mark(7))) return rc;
     return FTCJ_OK;
 }
 

@@ -138,6 +138,10 @@ struct ftcj_plan {
     double* d_check = nullptr;       // [2]
     int nEblocks = 0;
     size_t device_bytes = 0;
+    // per-phase event timing (ftcj_profile_enable)
+    std::vector<cudaEvent_t> prof_events;  // [max_batches][FTCJ_NPHASE + 1]
+    int prof_max = 0, prof_used = 0;
+    int64_t prof_launches = 0;
 };
 
 namespace ftcj {
@@ -173,5 +177,9 @@ int launch_rho_reduce(ftcj_plan* P, int ndens, double* rho_out, double* W_out, d
                       const double* rho_in, cudaStream_t s);
 int launch_j_walk(ftcj_plan* P, int ndens, const double* W, cudaStream_t s);
 int rho_walk_blocks_per_sm(ftcj_plan* P, int* out);
+
+// --- measurement (profile.cu) ---
+void release_profiling(ftcj_plan* P);
+int64_t launches_per_batch(const ftcj_plan* P);
 
 }  // namespace ftcj

@@ -439,6 +439,7 @@ int ftcj_plan_info(const ftcj_plan* P, ftcj_info* o) {
 
 void ftcj_plan_destroy(ftcj_plan* P) {
     if (!P) return;
+    release_profiling(P);
     free_device(P);
     delete P;
 }

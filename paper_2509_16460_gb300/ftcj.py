@@ -59,7 +59,10 @@ EXPORTED = [
     "ftcj_plan_create", "ftcj_plan_info", "ftcj_plan_destroy", "ftcj_jbuild", "ftcj_jbuild_host",
     "ftcj_fold_density", "ftcj_rho", "ftcj_potential", "ftcj_jback", "ftcj_unfold_j", "ftcj_check_density",
     "ftcj_get_gvectors", "ftcj_get_pairs", "ftcj_get_groups", "ftcj_strerror", "ftcj_last_error",
+    "ftcj_profile_enable", "ftcj_profile_read", "ftcj_launches_per_batch", "ftcj_probe_fma_peak",
 ]
+
+PHASES = ["fold", "hermite", "rho_walk", "potential", "j_walk", "j_to_ao", "unfold"]
 
 _lock = threading.Lock()
 _lib: Optional[ctypes.CDLL] = None
@@ -99,6 +102,10 @@ def _declare(L):
     L.ftcj_get_gvectors.argtypes = [P, _ip]
     L.ftcj_get_pairs.argtypes = [P, _ip]
     L.ftcj_get_groups.argtypes = [P, _ip, _dp, _ip, _ip]
+    L.ftcj_profile_enable.argtypes = [P, _c_int]
+    L.ftcj_profile_read.argtypes = [P, _dp, _ip, ctypes.POINTER(ctypes.c_int64)]
+    L.ftcj_launches_per_batch.argtypes = [P, _c_int, ctypes.POINTER(ctypes.c_int64)]
+    L.ftcj_probe_fma_peak.argtypes = [_c_int, _dp, P]
     L.ftcj_strerror.argtypes = [_c_int]
     L.ftcj_strerror.restype = ctypes.c_char_p
     L.ftcj_last_error.argtypes = []
@@ -283,6 +290,23 @@ class Plan:
                "ftcj_check_density")
         return mi.value, ma.value
 
+    # ---- measurement ----
+    def profile_enable(self, max_batches: int):
+        _check(lib().ftcj_profile_enable(self._h, int(max_batches)), "ftcj_profile_enable")
+
+    def profile_read(self):
+        """(ms per phase dict, batches, kernel launches) since the last read."""
+        ms = (ctypes.c_double * len(PHASES))()
+        nb = ctypes.c_int()
+        nl = ctypes.c_int64()
+        _check(lib().ftcj_profile_read(self._h, ms, ctypes.byref(nb), ctypes.byref(nl)), "ftcj_profile_read")
+        return dict(zip(PHASES, list(ms))), nb.value, nl.value
+
+    def launches_per_batch(self, nd: int = 1) -> int:
+        n = ctypes.c_int64()
+        _check(lib().ftcj_launches_per_batch(self._h, int(nd), ctypes.byref(n)), "ftcj_launches_per_batch")
+        return n.value
+
     # ---- exports ----
     def gvectors(self):
         out = np.zeros((max(self.ng_half, 1), 3), dtype=np.int32)
@@ -305,3 +329,10 @@ class Plan:
         _check(lib().ftcj_get_groups(self._h, cen.ctypes.data_as(_ip), ex.ctypes.data_as(_dp),
                                      mem.ctypes.data_as(_ip), ctypes.byref(nm)), "ftcj_get_groups")
         return cen[:ng], ex[:ng], mem[:nm.value]
+
+
+def probe_fma_peak(precision: int = 0, stream=None) -> float:
+    """Measured FMA throughput (flop/s) of the current GPU: 0 = FP64, 1 = FP32."""
+    out = ctypes.c_double()
+    _check(lib().ftcj_probe_fma_peak(int(precision), ctypes.byref(out), _stream_ptr(stream)), "ftcj_probe_fma_peak")
+    return out.value
