@@ -330,3 +330,12 @@ def test_cfg1_counts(orc):
     w = W.cfg1()
     assert len(orc.gsphere(w.A, orc.gcut_of(w))) == 340
     assert len(orc.pairs(w)) == 1118
+
+
+def test_rho_at_matches_full_build(orc):
+    """The sampled-rho entry used for large cells reproduces the pinned full build."""
+    w = W.tiny(seed=15, kmesh=(2, 1, 1), ndens=2)
+    r = orc.lrj(w)
+    sel = [0, 5, 17, len(r["G"]) - 1]
+    got = orc.rho_at(w, r["G"][sel])
+    np.testing.assert_allclose(got, r["rho"][:, sel], atol=1e-13, rtol=0)
