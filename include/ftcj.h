@@ -162,6 +162,33 @@ int ftcj_rho(ftcj_plan* plan, int ndens, const double* D0n, double* rho, void* s
  * EJ[d] = sum_half v |rho|^2 (= 1/2 sum over the full sphere). */
 int ftcj_potential(ftcj_plan* plan, int ndens, const double* rho, double* W, double* EJ, void* stream);
 
+/* Allocation-free variant of the potential and energy step; needs no plan.
+ * For callers that cannot call cudaMalloc: code running where another
+ * allocator already owns the device memory (a framework's caching allocator
+ * or a pre-reserved pool), and which therefore cannot create a plan, or code
+ * that must not allocate inside its iteration loop.  For the same G list it
+ * gives what ftcj_potential gives:
+ *   W(G) = 2 v(G) conj(rho(G)),  EJ[d] = sum_G v(G) |rho_d(G)|^2,
+ *   v(G) = 4 pi exp(-|G|^2/4w^2) / (Omega |G|^2),  G = n1 b_1 + n2 b_2 + n3 b_3.
+ *   A     host double[9], lattice rows (bohr); omega > 0
+ *   gvec  device int [ng][3] without (0,0,0) (v is not finite there)
+ *   rho   device complex [ndens][ng];  W device complex [ndens][ng] (written)
+ *   EJ    device double [ndens] (written)
+ * Its only scratch, the per-block energy partial sums, is a fixed file-scope
+ * device array of FTCJ_NOALLOC_MAX_PARTIALS doubles (128 KiB) that every GPU
+ * loading the library keeps until the process exits.  No element of it has to
+ * start at zero (a call reads only slots it wrote earlier in the same call);
+ * it keeps the last call's contents; calls that overlap on the GPU share it
+ * and race, so serialise them.  The first call on a device looks up the
+ * array's device address with that device current; make that first call
+ * before any stream capture.  Errors: EINVAL when ndens * ceil(ng/256) >
+ * FTCJ_NOALLOC_MAX_PARTIALS (split the densities over several calls), for a
+ * singular lattice, or omega <= 0.  The paper has no counterpart to this
+ * entry point. */
+#define FTCJ_NOALLOC_MAX_PARTIALS 16384
+int ftcj_potential_noalloc(const double A[9], double omega, int ndens, int64_t ng, const int* gvec,
+                           const double* rho, double* W, double* EJ, void* stream);
+
 /* a6 + a7: back-contraction (Alg. S1) and transform to AOs (Alg. S2):
  * W complex [ndens][ng_half] -> J0n double [ndens][Ncell][nao][nao]
  * (J^{0L} folded into the BvK cells; overwritten).  ndens <= max_dens. */

@@ -60,7 +60,10 @@ EXPORTED = [
     "ftcj_fold_density", "ftcj_rho", "ftcj_potential", "ftcj_jback", "ftcj_unfold_j", "ftcj_check_density",
     "ftcj_get_gvectors", "ftcj_get_pairs", "ftcj_get_groups", "ftcj_strerror", "ftcj_last_error",
     "ftcj_profile_enable", "ftcj_profile_read", "ftcj_launches_per_batch", "ftcj_probe_fma_peak",
+    "ftcj_potential_noalloc",
 ]
+
+FTCJ_NOALLOC_MAX_PARTIALS = 16384
 
 PHASES = ["fold", "hermite", "rho_walk", "potential", "j_walk", "j_to_ao", "unfold"]
 
@@ -106,6 +109,7 @@ def _declare(L):
     L.ftcj_profile_read.argtypes = [P, _dp, _ip, ctypes.POINTER(ctypes.c_int64)]
     L.ftcj_launches_per_batch.argtypes = [P, _c_int, ctypes.POINTER(ctypes.c_int64)]
     L.ftcj_probe_fma_peak.argtypes = [_c_int, _dp, P]
+    L.ftcj_potential_noalloc.argtypes = [_dp, _c_double, _c_int, ctypes.c_int64, P, P, P, P, P]
     L.ftcj_strerror.argtypes = [_c_int]
     L.ftcj_strerror.restype = ctypes.c_char_p
     L.ftcj_last_error.argtypes = []
@@ -336,3 +340,23 @@ def probe_fma_peak(precision: int = 0, stream=None) -> float:
     out = ctypes.c_double()
     _check(lib().ftcj_probe_fma_peak(int(precision), ctypes.byref(out), _stream_ptr(stream)), "ftcj_probe_fma_peak")
     return out.value
+
+
+def potential_noalloc(A, omega, gvec, rho, W=None, EJ=None, stream=None):
+    """ftcj_potential_noalloc: W = 2 v conj(rho) and E_J without a plan and
+    without any device allocation inside the library (see include/ftcj.h).
+    gvec is a CUDA int32 tensor [ng, 3]; rho a CUDA complex128 tensor
+    [ndens, ng]; W and E_J are allocated here by torch when not given."""
+    import torch
+    nd, ng = int(rho.shape[0]), int(rho.shape[1])
+    if W is None:
+        W = torch.empty((nd, ng), dtype=torch.complex128, device=rho.device)
+    if EJ is None:
+        EJ = torch.empty(nd, dtype=torch.float64, device=rho.device)
+    Ah = (ctypes.c_double * 9)(*[float(x) for x in np.asarray(A, dtype=np.float64).ravel()])
+    _check(lib().ftcj_potential_noalloc(Ah, float(omega), nd, ng, _dev_ptr(gvec, torch.int32, (ng, 3), "gvec"),
+                                        _dev_ptr(rho, torch.complex128, (nd, ng), "rho"),
+                                        _dev_ptr(W, torch.complex128, (nd, ng), "W"),
+                                        _dev_ptr(EJ, torch.float64, (nd,), "EJ"), _stream_ptr(stream)),
+           "ftcj_potential_noalloc")
+    return W, EJ
