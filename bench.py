@@ -104,20 +104,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def rho_walk_flops(info, ndens):
-    """Algorithmic FP64 flops of one structure-factor walk launch: (4L + 14) per
-    (pair record, half-sphere G) for a pair record of class L."""
-    return ndens * sum(n * info["ng_half"] * (4 * L + 14) for L, n in enumerate(info["pairs_by_class"]))
-
-
-def j_walk_flops(info, ndens):
-    return rho_walk_flops(info, ndens)
+def walk_flops(info, ndens, form):
+    """Algorithmic flops of one walk launch (structure-factor or back-contraction
+    pass; both have the same count).  Per (pair record of class L, half-sphere G):
+    FP64 form: 4L + 14 flops (an (L+1)-term complex Horner, prefactor x phase
+    and the accumulation); split form: the same arithmetic evaluated in
+    double-float on the FP32 pipe, 38L + 142 FP32 flops (two complex
+    double-float products of 50, one complex-by-real product of 20, L Horner
+    or accumulation steps of 38, and one complex double-float sum of 22)."""
+    per = (lambda L: 4 * L + 14) if form == "fp64" else (lambda L: 38 * L + 142)
+    return ndens * sum(n * info["ng_half"] * per(L) for L, n in enumerate(info["pairs_by_class"]))
 
 
 def traffic_from_profile(kernel: str):
     """dram bytes per launch from the committed ncu summary, if it was taken on
     the current kernel source (its recorded source hash must match)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_diamond240_k444.md")
+    src_name = "walk_split.cu" if kernel.endswith("_split") else "walk.cu"
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -125,7 +128,7 @@ def traffic_from_profile(kernel: str):
     t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     if not m or not t:
         return None
-    src = open(os.path.join(ROOT, "paper_2509_16460_gb300", "csrc", "walk.cu"), "rb").read()
+    src = open(os.path.join(ROOT, "paper_2509_16460_gb300", "csrc", src_name), "rb").read()
     if hashlib.sha256(src).hexdigest()[:len(m.group(1))] != m.group(1):
         return None
     return float(t.group(1))
@@ -206,108 +209,118 @@ def main():
         torch.cuda.synchronize()
 
     w = W.cfg2()
-    plan = ftcj.Plan.from_workload(w)
-    info = plan.info
-    units = float(info["pair_g_units"]) * w.ndens
     stream = torch.cuda.current_stream()
     Dk = torch.from_numpy(np.ascontiguousarray(w.Dk)).cuda()
-    Jk = torch.empty_like(Dk)
-    EJ = torch.empty(w.ndens, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-
-    for _ in range(args.warmup):
-        plan.jbuild(Dk, Jk, EJ)
-    torch.cuda.synchronize()
-
-    # ---- timed region: device time per step, L2 flushed between steps ----
-    plan.profile_enable(args.steps)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    sampler = ClockSampler(local)
-    barrier()
-    sampler.start()
-    t_wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        plan.jbuild(Dk, Jk, EJ)
-        ev[k][1].record(stream)
-    barrier()
-    t_wall = time.perf_counter() - t_wall0
-    clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    phase_ms, batches, launches = plan.profile_read()
-    plan.profile_enable(0)
-    ms = statistics.mean(step_ms)
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * units / (ms * 1e-3)
-
-    # ---- end to end through the host-buffer entry point ----
-    Dk_h = torch.from_numpy(np.ascontiguousarray(w.Dk)).pin_memory()
-    Jk_h = torch.empty(Dk_h.shape, dtype=torch.complex128).pin_memory()
-    EJ_h = torch.empty(w.ndens, dtype=torch.float64).pin_memory()
-    plan.jbuild_host(Dk_h, Jk_h, EJ_h)
-    e2e_steps = max(3, min(args.steps, 10))
-    e2e_t = []
-    barrier()
-    for _ in range(e2e_steps):
-        flush.zero_()
+    peaks = {"fp64": ftcj.probe_fma_peak(0), "split": ftcj.probe_fma_peak(1)}
+    forms = {}
+    results = {}
+    for form, prec in (("split", ftcj.FTCJ_PREC_SPLIT), ("fp64", ftcj.FTCJ_PREC_FP64)):
+        plan = ftcj.Plan.from_workload(w, precision=prec)
+        info = plan.info
+        units = float(info["pair_g_units"]) * w.ndens
+        Jk = torch.empty_like(Dk)
+        EJ = torch.empty(w.ndens, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            plan.jbuild(Dk, Jk, EJ)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        # timed region: device time per step, L2 flushed between steps
+        plan.profile_enable(args.steps)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        sampler = ClockSampler(local)
+        barrier()
+        sampler.start()
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            plan.jbuild(Dk, Jk, EJ)
+            ev[k][1].record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+        clocks = sampler.stop()
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        phase_ms, batches, launches = plan.profile_read()
+        plan.profile_enable(0)
+        ms = statistics.mean(step_ms)
+        if dist is not None:
+            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        value = world * units / (ms * 1e-3)
+        # end to end through the host-buffer entry point
+        Dk_h = torch.from_numpy(np.ascontiguousarray(w.Dk)).pin_memory()
+        Jk_h = torch.empty(Dk_h.shape, dtype=torch.complex128).pin_memory()
+        EJ_h = torch.empty(w.ndens, dtype=torch.float64).pin_memory()
         plan.jbuild_host(Dk_h, Jk_h, EJ_h)
-        e2e_t.append(time.perf_counter() - t0)
-    e2e_s = statistics.mean(e2e_t)
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    h2d = Dk_h.numel() * 16
-    d2h = Jk_h.numel() * 16 + EJ_h.numel() * 8
+        e2e_t = []
+        barrier()
+        for _ in range(max(3, min(args.steps, 10))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            plan.jbuild_host(Dk_h, Jk_h, EJ_h)
+            e2e_t.append(time.perf_counter() - t0)
+        e2e_s = statistics.mean(e2e_t)
+        if dist is not None:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        # roofline of the dominant kernel: FP64 pipe (fp64) or FP32 pipe (split)
+        suffix = "_split" if form == "split" else ""
+        walks = {"k_rho_walk" + suffix: phase_ms["rho_walk"], "k_j_walk" + suffix: phase_ms["j_walk"]}
+        kname = max(walks, key=walks.get)
+        per_launch_ms = walks[kname] / max(batches, 1)
+        achieved = walk_flops(info, w.ndens, form) / (per_launch_ms * 1e-3)
+        peak = peaks[form]
+        roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": traffic_from_profile(kname), "kernel": kname,
+                    "pipe": "FP64" if form == "fp64" else "FP32",
+                    "peak_source": f"measured {'FP64' if form == 'fp64' else 'FP32'} FMA throughput "
+                                   "(ftcj_probe_fma_peak) on this GPU",
+                    "nominal_peak": 152 * 2 * 2.07e9 * (2 if form == "fp64" else 128) / 1e12,
+                    "phase_ms_per_step": {k: v / max(batches, 1) for k, v in phase_ms.items()}}
+        forms[form] = {"value": value, "unit": UNIT, "ms_per_step": ms, "step_ms_min": min(step_ms),
+                       "e2e": {"value": world * units / e2e_s, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
+                               "h2d_bytes_per_step": Dk_h.numel() * 16,
+                               "d2h_bytes_per_step": Jk_h.numel() * 16 + EJ_h.numel() * 8},
+                       "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks,
+                       "wall_s_timed_region": t_wall}
+        results[form] = (Jk.cpu().numpy(), EJ.cpu().numpy())
+        plan.close()
 
-    # ---- roofline of the dominant kernel (FP64 ALU bound) ----
-    fp64_peak = ftcj.probe_fma_peak(0)
-    walks = {"k_rho_walk": phase_ms["rho_walk"], "k_j_walk": phase_ms["j_walk"]}
-    kname = max(walks, key=walks.get)
-    per_launch_ms = walks[kname] / max(batches, 1)
-    flops = rho_walk_flops(info, w.ndens) if kname == "k_rho_walk" else j_walk_flops(info, w.ndens)
-    achieved = flops / (per_launch_ms * 1e-3)
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": traffic_from_profile(kname), "kernel": kname,
-                "peak_source": "measured FP64 FMA throughput (ftcj_probe_fma_peak) on this GPU",
-                "nominal_peak": 152 * 2 * 2 * 2.07e9 / 1e12,
-                "phase_ms_per_step": {k: v / max(batches, 1) for k, v in phase_ms.items()}}
-
+    head = forms["split"]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": "fp64", "pair_g_units_per_step": units,
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32x2 walks (double-float), f64 setup/sums/E_J", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": "split", "pair_g_units_per_step": units,
                    "npairs_ordered": info["npairs_ordered"], "pair_records": info["npairs"],
                    "ng_full": info["ng_full"], "nao": info["nao"], "nk": info["nk"],
                    "l2": f"{L2_FLUSH_BYTES >> 20} MB buffer written between timed steps",
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
-        "e2e": {"value": world * units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
-        "gpu_launches": int(launches),
-        "roofline": roofline,
-        "clocks": clocks,
-        "wall_s_timed_region": t_wall,
+        "e2e": {k: head["e2e"][k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")},
+        "gpu_launches": head["gpu_launches"],
+        "roofline": head["roofline"],
+        "clocks": head["clocks"],
+        "forms": forms,
+        "split_speedup_vs_fp64": forms["fp64"]["ms_per_step"] / head["ms_per_step"],
     }
 
     if rank == 0 and not args.no_cpu_baseline:
         # the whole oracle on the host cores: the CPU baseline and the accuracy of this run
         r, cu, threads = cpu_oracle_run(w, 1)
-        Jg = Jk.cpu().numpy()
         line["cpu_baseline"] = {"value": cu / r["seconds"], "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": "the whole workload (every pair, full sphere), one build",
                                 "seconds": r["seconds"]}
-        line["max_abs_dJ_vs_oracle"] = float(np.abs(Jg - r["Jk"]).max())
-        line["abs_dEJ_vs_oracle"] = float(np.abs(EJ.cpu().numpy() - r["EJ"]).max())
+        for form, (Jg, Eg) in results.items():
+            forms[form]["max_abs_dJ_vs_oracle"] = float(np.abs(Jg - r["Jk"]).max())
+            forms[form]["abs_dEJ_vs_oracle"] = float(np.abs(Eg - r["EJ"]).max())
+        line["max_abs_dJ_vs_oracle"] = forms["split"]["max_abs_dJ_vs_oracle"]
+        line["abs_dEJ_vs_oracle"] = forms["split"]["abs_dEJ_vs_oracle"]
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0

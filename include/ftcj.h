@@ -60,6 +60,7 @@ extern "C" {
 #define FTCJ_EUNSUPPORTED (-5) /* valid input outside what this build handles */
 
 #define FTCJ_PREC_FP64 0       /* every step in FP64 */
+#define FTCJ_PREC_SPLIT 1      /* walks (a4, a6) in double-float FP32 pairs; FP64 setup, sums and E_J */
 
 #define FTCJ_LMAX 2            /* highest shell angular momentum */
 
@@ -88,7 +89,7 @@ typedef struct {
     double gcut;        /* sphere radius; <= 0: 2 w sqrt(ln(1/eps_g)) */
     double eps_g;       /* kernel floor exp(-Gcut^2/4w^2) when gcut <= 0 */
     double pair_thresh; /* keep primitive pairs with overlap bound > this */
-    int precision;      /* FTCJ_PREC_FP64 */
+    int precision;      /* FTCJ_PREC_FP64 or FTCJ_PREC_SPLIT */
     int max_dens;       /* densities per device batch (scratch is sized for it); <= 0: 1 */
 } ftcj_params;
 
@@ -116,7 +117,7 @@ typedef struct ftcj_plan ftcj_plan;
  * screening and sorting on the device (default stream, synchronised) and
  * allocates all scratch.  cell/basis/params are copied; the caller may free
  * them afterwards.  Errors: EINVAL (bad lattice, centres, exponents, omega,
- * k-mesh), EUNSUPPORTED (l > FTCJ_LMAX, precision not FP64, a G line
+ * k-mesh), EUNSUPPORTED (l > FTCJ_LMAX, unknown precision, a G line
  * longer than the walk chunk), ENOMEM, ECUDA. */
 int ftcj_plan_create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3],
                      const ftcj_params* params, ftcj_plan** out);

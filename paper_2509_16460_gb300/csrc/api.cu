@@ -9,6 +9,14 @@ namespace {
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+int rho_walk(ftcj_plan* P, int nd, cudaStream_t s) {
+    return P->precision == FTCJ_PREC_SPLIT ? launch_rho_walk_split(P, nd, s) : launch_rho_walk(P, nd, s);
+}
+
+int j_walk(ftcj_plan* P, int nd, const double* W, cudaStream_t s) {
+    return P->precision == FTCJ_PREC_SPLIT ? launch_j_walk_split(P, nd, W, s) : launch_j_walk(P, nd, W, s);
+}
+
 int check(const ftcj_plan* P, int ndens, bool batch_limit) {
     if (!P) return fail(FTCJ_EINVAL, "null plan");
     if (ndens < 1) return fail(FTCJ_EINVAL, "ndens must be >= 1");
@@ -34,11 +42,11 @@ int build_batch(ftcj_plan* P, int nd, const double* Dk, double* Jk, double* EJ, 
     if ((rc = mark(1))) return rc;
     if ((rc = launch_hermite(P, nd, P->d_D0n, s))) return rc;
     if ((rc = mark(2))) return rc;
-    if ((rc = launch_rho_walk(P, nd, s))) return rc;
+    if ((rc = rho_walk(P, nd, s))) return rc;
     if ((rc = mark(3))) return rc;
     if ((rc = launch_rho_reduce(P, nd, P->d_rho, P->d_W, EJ, nullptr, s))) return rc;
     if ((rc = mark(4))) return rc;
-    if ((rc = launch_j_walk(P, nd, P->d_W, s))) return rc;
+    if ((rc = j_walk(P, nd, P->d_W, s))) return rc;
     if ((rc = mark(5))) return rc;
     if ((rc = launch_jtransform(P, nd, P->d_J0n, s))) return rc;
     if ((rc = mark(6))) return rc;
@@ -64,7 +72,7 @@ int ftcj_rho(ftcj_plan* P, int ndens, const double* D0n, double* rho, void* stre
     if (!D0n || !rho) return fail(FTCJ_EINVAL, "null buffer");
     cudaStream_t s = as_stream(stream);
     if ((rc = launch_hermite(P, ndens, D0n, s))) return rc;
-    if ((rc = launch_rho_walk(P, ndens, s))) return rc;
+    if ((rc = rho_walk(P, ndens, s))) return rc;
     return launch_rho_reduce(P, ndens, rho, nullptr, nullptr, nullptr, s);
 }
 
@@ -87,7 +95,7 @@ int ftcj_jback(ftcj_plan* P, int ndens, const double* W, double* J0n, void* stre
     if (rc) return rc;
     if (!W || !J0n) return fail(FTCJ_EINVAL, "null buffer");
     cudaStream_t s = as_stream(stream);
-    if ((rc = launch_j_walk(P, ndens, W, s))) return rc;
+    if ((rc = j_walk(P, ndens, W, s))) return rc;
     return launch_jtransform(P, ndens, J0n, s);
 }
 

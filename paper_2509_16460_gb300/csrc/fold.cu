@@ -124,6 +124,100 @@ __global__ void k_check(const double2* __restrict__ D, long long ndens, int N1, 
 
 inline unsigned nblocks(long long n, int b) { return (unsigned)((n + b - 1) / b); }
 
+// ---- fused transform: every axis in one pass over HBM -------------------
+// Each thread owns one AO-pair element of one density and keeps its whole
+// column over the mesh (nk complex values) in a thread-private slice of
+// shared memory (stride kFusedT, so a warp's accesses hit distinct banks).
+// The mesh axes are transformed in place: length 2 and 4 by butterflies
+// (only additions; the twiddles are +-1, +-i), other lengths by a direct sum
+// with the twiddle table.
+constexpr int kFusedT = 32;
+constexpr int kFusedMaxNk = 256;
+
+__device__ __forceinline__ void dft_line(double2* col, int base, int stride, int Na, const double2* __restrict__ w,
+                                         bool inverse) {
+    if (Na == 2) {
+        double2 x0 = col[base * kFusedT], x1 = col[(base + stride) * kFusedT];
+        col[base * kFusedT] = make_double2(x0.x + x1.x, x0.y + x1.y);
+        col[(base + stride) * kFusedT] = make_double2(x0.x - x1.x, x0.y - x1.y);
+        return;
+    }
+    if (Na == 4) {
+        double2 x0 = col[base * kFusedT], x1 = col[(base + stride) * kFusedT];
+        double2 x2 = col[(base + 2 * stride) * kFusedT], x3 = col[(base + 3 * stride) * kFusedT];
+        double2 a = make_double2(x0.x + x2.x, x0.y + x2.y), b = make_double2(x0.x - x2.x, x0.y - x2.y);
+        double2 c = make_double2(x1.x + x3.x, x1.y + x3.y), d = make_double2(x1.x - x3.x, x1.y - x3.y);
+        // forward (exp(-2 pi i mn/4)): y1 = b - i d, y3 = b + i d; inverse swaps them
+        double2 bmid = make_double2(b.x + d.y, b.y - d.x);  // b - i d
+        double2 bpid = make_double2(b.x - d.y, b.y + d.x);  // b + i d
+        col[base * kFusedT] = make_double2(a.x + c.x, a.y + c.y);
+        col[(base + 2 * stride) * kFusedT] = make_double2(a.x - c.x, a.y - c.y);
+        col[(base + stride) * kFusedT] = inverse ? bpid : bmid;
+        col[(base + 3 * stride) * kFusedT] = inverse ? bmid : bpid;
+        return;
+    }
+    double2 x[kTw];
+    for (int m = 0; m < Na; ++m) x[m] = col[(base + m * stride) * kFusedT];
+    for (int n = 0; n < Na; ++n) {
+        double sr = 0.0, si = 0.0;
+        for (int m = 0; m < Na; ++m) {
+            double2 c = w[m * kTw + n];
+            double wi = inverse ? -c.y : c.y;
+            sr = fma(c.x, x[m].x, fma(-wi, x[m].y, sr));
+            si = fma(c.x, x[m].y, fma(wi, x[m].x, si));
+        }
+        col[(base + n * stride) * kFusedT] = make_double2(sr, si);
+    }
+}
+
+__device__ void dft_mesh(double2* col, int N1, int N2, int N3, const double2* __restrict__ tw, bool inverse) {
+    // axis 2 (stride 1), axis 1 (stride N3), axis 0 (stride N2*N3)
+    if (N3 > 1)
+        for (int o = 0; o < N1 * N2; ++o) dft_line(col, o * N3, 1, N3, tw + 2 * kTw * kTw, inverse);
+    if (N2 > 1)
+        for (int i1 = 0; i1 < N1; ++i1)
+            for (int i3 = 0; i3 < N3; ++i3) dft_line(col, i1 * N2 * N3 + i3, N3, N2, tw + kTw * kTw, inverse);
+    if (N1 > 1)
+        for (int o = 0; o < N2 * N3; ++o) dft_line(col, o, N2 * N3, N1, tw, inverse);
+}
+
+// D^{0n} = Re (1/nk) sum_k exp(-i k.R_n) D^k for one (density, element) per thread
+__global__ void __launch_bounds__(kFusedT) k_fold_fused(const double2* __restrict__ Dk, double* __restrict__ D0n,
+                                                        long long E, int N1, int N2, int N3,
+                                                        const double2* __restrict__ tw) {
+    extern __shared__ double2 fsm[];
+    const int nk = N1 * N2 * N3;
+    const long long e = (long long)blockIdx.x * kFusedT + threadIdx.x;
+    const long long d = blockIdx.y;
+    double2* col = fsm + threadIdx.x;
+    if (e < E) {
+        const double2* src = Dk + d * nk * E + e;
+        for (int k = 0; k < nk; ++k) col[k * kFusedT] = src[(long long)k * E];
+        dft_mesh(col, N1, N2, N3, tw, false);
+        const double s = 1.0 / nk;
+        double* dst = D0n + d * nk * E + e;
+        for (int n = 0; n < nk; ++n) dst[(long long)n * E] = s * col[n * kFusedT].x;
+    }
+}
+
+// J^k = sum_n exp(+i k.R_n) J^{0n} for one (density, element) per thread
+__global__ void __launch_bounds__(kFusedT) k_unfold_fused(const double* __restrict__ J0n, double2* __restrict__ Jk,
+                                                          long long E, int N1, int N2, int N3,
+                                                          const double2* __restrict__ tw) {
+    extern __shared__ double2 fsm[];
+    const int nk = N1 * N2 * N3;
+    const long long e = (long long)blockIdx.x * kFusedT + threadIdx.x;
+    const long long d = blockIdx.y;
+    double2* col = fsm + threadIdx.x;
+    if (e < E) {
+        const double* src = J0n + d * nk * E + e;
+        for (int n = 0; n < nk; ++n) col[n * kFusedT] = make_double2(src[(long long)n * E], 0.0);
+        dft_mesh(col, N1, N2, N3, tw, true);
+        double2* dst = Jk + d * nk * E + e;
+        for (int k = 0; k < nk; ++k) dst[(long long)k * E] = col[k * kFusedT];
+    }
+}
+
 }  // namespace
 
 int launch_twiddles(ftcj_plan* P) {
@@ -182,12 +276,35 @@ static int run_stages(ftcj_plan* P, int ndens, const double* in, double* out, in
     return FTCJ_OK;
 }
 
+static size_t fused_smem(const ftcj_plan* P) { return sizeof(double2) * (size_t)kFusedT * P->nk; }
+
+int fused_fold_supported(const ftcj_plan* P) { return P->nk > 1 && P->nk <= kFusedMaxNk; }
+
+int setup_fold(ftcj_plan* P) {
+    if (!fused_fold_supported(P)) return FTCJ_OK;
+    FTCJ_CUDA(cudaFuncSetAttribute(k_fold_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem(P)));
+    FTCJ_CUDA(cudaFuncSetAttribute(k_unfold_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem(P)));
+    return FTCJ_OK;
+}
+
 int launch_fold(ftcj_plan* P, int ndens, const double* Dk, double* D0n, cudaStream_t s) {
-    return run_stages(P, ndens, Dk, D0n, 0, s);
+    if (!fused_fold_supported(P)) return run_stages(P, ndens, Dk, D0n, 0, s);
+    long long E = (long long)P->nao * P->nao;
+    dim3 g(nblocks(E, kFusedT), ndens);
+    k_fold_fused<<<g, kFusedT, fused_smem(P), s>>>(reinterpret_cast<const double2*>(Dk), D0n, E, P->km[0], P->km[1],
+                                                   P->km[2], reinterpret_cast<const double2*>(P->d_tw));
+    FTCJ_CUDA(cudaGetLastError());
+    return FTCJ_OK;
 }
 
 int launch_unfold(ftcj_plan* P, int ndens, const double* J0n, double* Jk, cudaStream_t s) {
-    return run_stages(P, ndens, J0n, Jk, 1, s);
+    if (!fused_fold_supported(P)) return run_stages(P, ndens, J0n, Jk, 1, s);
+    long long E = (long long)P->nao * P->nao;
+    dim3 g(nblocks(E, kFusedT), ndens);
+    k_unfold_fused<<<g, kFusedT, fused_smem(P), s>>>(J0n, reinterpret_cast<double2*>(Jk), E, P->km[0], P->km[1],
+                                                     P->km[2], reinterpret_cast<const double2*>(P->d_tw));
+    FTCJ_CUDA(cudaGetLastError());
+    return FTCJ_OK;
 }
 
 int launch_check_density(ftcj_plan* P, int ndens, const double* Dk, double* out2, cudaStream_t s) {

@@ -136,6 +136,9 @@ struct ftcj_plan {
     double* d_Jk_stage = nullptr;
     double* d_EJ_stage = nullptr;
     double* d_check = nullptr;       // [2]
+    void* d_split_init = nullptr;    // split form: walk state at each chunk start, [nchunks][npairs]
+    void* d_split_const = nullptr;   // split form: recurrence multipliers, [npairs]
+    int precision = FTCJ_PREC_FP64;
     int nEblocks = 0;
     size_t device_bytes = 0;
     // per-phase event timing (ftcj_profile_enable)
@@ -163,6 +166,8 @@ int launch_fold(ftcj_plan* P, int ndens, const double* Dk, double* D0n, cudaStre
 int launch_unfold(ftcj_plan* P, int ndens, const double* J0n, double* Jk, cudaStream_t s);
 int launch_check_density(ftcj_plan* P, int ndens, const double* Dk, double* out2, cudaStream_t s);
 int launch_twiddles(ftcj_plan* P);
+int setup_fold(ftcj_plan* P);
+int fused_fold_supported(const ftcj_plan* P);
 
 // --- Hermite densities and J back-transform (hermite.cu) ---
 int upload_hermite_tables(ftcj_plan* P);
@@ -177,6 +182,12 @@ int launch_rho_reduce(ftcj_plan* P, int ndens, double* rho_out, double* W_out, d
                       const double* rho_in, cudaStream_t s);
 int launch_j_walk(ftcj_plan* P, int ndens, const double* W, cudaStream_t s);
 int rho_walk_blocks_per_sm(ftcj_plan* P, int* out);
+
+// --- split-precision walks (walk_split.cu) ---
+int setup_split(ftcj_plan* P);
+int rho_walk_split_blocks_per_sm(ftcj_plan* P, int* out);
+int launch_rho_walk_split(ftcj_plan* P, int ndens, cudaStream_t s);
+int launch_j_walk_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s);
 
 // --- measurement (profile.cu) ---
 void release_profiling(ftcj_plan* P);

@@ -72,6 +72,8 @@ __device__ void pair_geom(const PairDev& pr, const GroupDev& A, const GroupDev& 
     }
 }
 
+// OUT_DF: store D'_ijk as double-float pairs (split form) instead of FP64
+template <bool OUT_DF>
 __global__ void __launch_bounds__(128) k_hermite(const PairDev* __restrict__ pairs, const GroupDev* __restrict__ G,
                                                  const MemberDev* __restrict__ mem, const double* __restrict__ D0n,
                                                  int nao, int nk, Layout lay, double* __restrict__ Dp) {
@@ -136,14 +138,20 @@ __global__ void __launch_bounds__(128) k_hermite(const PairDev* __restrict__ pai
     int L = pr.cls;
     long long cnt = lay.start[L + 1] - lay.start[L];
     long long loc = i - lay.start[L];
-    double* out = Dp + (long long)d * lay.total + lay.base[L] + loc;
+    const long long off = (long long)d * lay.total + lay.base[L] + loc;
     for (int lam = 0; lam <= L; ++lam) {
         int nm = nmono(lam), o = lam_offset(lam);
         const double* T = c_T + c_Toff[lam];
         for (int b = 0; b < nm; ++b) {
             double s = 0.0;
             for (int a = 0; a < nm; ++a) s += T[a * nm + b] * h[o + a];
-            out[(long long)(o + b) * cnt] = pr.K * s;
+            const double v = pr.K * s;
+            if (OUT_DF) {
+                const float hi = (float)v;
+                reinterpret_cast<float2*>(Dp)[off + (long long)(o + b) * cnt] = make_float2(hi, (float)(v - (double)hi));
+            } else {
+                Dp[off + (long long)(o + b) * cnt] = v;
+            }
         }
     }
 }
@@ -335,7 +343,12 @@ int upload_hermite_tables(ftcj_plan* P) {
 int launch_hermite(ftcj_plan* P, int ndens, const double* D0n, cudaStream_t s) {
     if (P->npairs == 0) return FTCJ_OK;
     dim3 g((unsigned)((P->npairs + 127) / 128), ndens);
-    k_hermite<<<g, 128, 0, s>>>(P->d_pairs, P->d_groups, P->d_members, D0n, P->nao, P->nk, make_layout(P), P->d_Dp);
+    if (P->precision == FTCJ_PREC_SPLIT)
+        k_hermite<true><<<g, 128, 0, s>>>(P->d_pairs, P->d_groups, P->d_members, D0n, P->nao, P->nk, make_layout(P),
+                                          P->d_Dp);
+    else
+        k_hermite<false><<<g, 128, 0, s>>>(P->d_pairs, P->d_groups, P->d_members, D0n, P->nao, P->nk,
+                                           make_layout(P), P->d_Dp);
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }

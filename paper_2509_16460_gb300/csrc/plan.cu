@@ -192,7 +192,7 @@ void free_device(ftcj_plan* P) {
     void* ptrs[] = {P->d_groups, P->d_members, P->d_pairs, P->d_walk, P->d_lines, P->d_chunks, P->d_tiles,
                     P->d_gvec, P->d_vg, P->d_tw, P->d_Tmat, P->d_D0n, P->d_J0n, P->d_cbuf0, P->d_cbuf1,
                     P->d_Dp, P->d_Jp, P->d_rho_part, P->d_rho, P->d_W, P->d_Epart, P->d_Dk_stage,
-                    P->d_Jk_stage, P->d_EJ_stage, P->d_check};
+                    P->d_Jk_stage, P->d_EJ_stage, P->d_check, P->d_split_init, P->d_split_const};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -230,7 +230,9 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     }
     // parameters
     if (!(prm->omega > 0.0) || !finite(prm->omega)) return fail(FTCJ_EINVAL, "omega must be > 0");
-    if (prm->precision != FTCJ_PREC_FP64) return fail(FTCJ_EUNSUPPORTED, "only FTCJ_PREC_FP64 is built");
+    if (prm->precision != FTCJ_PREC_FP64 && prm->precision != FTCJ_PREC_SPLIT)
+        return fail(FTCJ_EUNSUPPORTED, "precision must be FTCJ_PREC_FP64 or FTCJ_PREC_SPLIT");
+    P->precision = prm->precision;
     if (!(prm->pair_thresh > 0.0 && prm->pair_thresh < 1.0)) return fail(FTCJ_EINVAL, "pair_thresh in (0,1)");
     P->omega = prm->omega;
     if (prm->gcut > 0.0) {
@@ -344,8 +346,13 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     if ((rc = upload(P, &P->d_tiles, P->tiles))) return rc;
     if ((rc = upload_walk_tables(P))) return rc;
     if ((rc = upload_hermite_tables(P))) return rc;
+    if (P->precision == FTCJ_PREC_SPLIT && (rc = setup_split(P))) return rc;
     int bps = 1;
-    if ((rc = rho_walk_blocks_per_sm(P, &bps))) return rc;
+    if (P->precision == FTCJ_PREC_SPLIT) {
+        if ((rc = rho_walk_split_blocks_per_sm(P, &bps))) return rc;
+    } else {
+        if ((rc = rho_walk_blocks_per_sm(P, &bps))) return rc;
+    }
     int nch = std::max<int>(1, (int)P->chunks.size());
     P->npb = std::max(1, std::min<int>((int)std::max<size_t>(1, P->tiles.size()), P->num_sms * bps / nch));
 
@@ -368,6 +375,7 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     if ((rc = dalloc(P, &P->d_check, 2))) return rc;
     if ((rc = launch_vg(P))) return rc;
     if ((rc = launch_twiddles(P))) return rc;
+    if ((rc = setup_fold(P))) return rc;
     FTCJ_CUDA(cudaDeviceSynchronize());
     return FTCJ_OK;
 }

@@ -18,7 +18,7 @@ void release_profiling(ftcj_plan* P) {
 int64_t launches_per_batch(const ftcj_plan* P) {
     int axes = 0;
     for (int a = 0; a < 3; ++a) axes += P->km[a] > 1;
-    int64_t fold = axes > 0 ? axes : 1;  // stages, or one copy kernel
+    int64_t fold = fused_fold_supported(P) ? 1 : (axes > 0 ? axes : 1);  // fused, stages, or a copy
     int64_t n = 0;
     n += fold;                                         // a2
     n += P->npairs > 0 ? 1 : 0;                        // a3

@@ -1,0 +1,545 @@
+// Split-precision form of the structure-factor pass (Alg. 1) and of the
+// back-contraction (Alg. S1).
+//
+// GB300 issues FP64 at 1/64 of its FP32 rate, so here every per-point and
+// per-line operation runs on the FP32 pipe in double-float arithmetic (a value
+// is hi + lo, two FP32 numbers, ~48 significant bits; df.cuh).  FP64 is kept for
+// what needs it once per pair and chunk: the range reduction of the phase
+// argument n.f, exp(-|G|^2/4p) and the phase at the first line of each walk
+// chunk (k_split_setup, once per plan), the per-G sums of the block rows, and
+// E_J (k_rho_reduce, shared with the FP64 form).
+//
+// The walk is the FP64 form's (walk.cu) with the Gaussian and the phase
+// advanced together: along a line gp(n1) = exp(-|G|^2/4p) exp(-2 pi i n.f) is
+// multiplied by the complex ratio R(n1) = r(n1) exp(-2 pi i f1), and R by the
+// real q1 = exp(-2c M11); lines and planes likewise carry complex ratios.
+#include <algorithm>
+#include <cmath>
+
+#include "df.cuh"
+#include "ftcj_internal.h"
+
+namespace ftcj {
+namespace {
+
+__constant__ double c_Ms[6];  // M11, M22, M33, M12, M13, M23
+
+struct Layout {
+    long long start[kNclass + 1];
+    long long base[kNclass];
+    long long total;
+};
+
+// walk state at a line, all complex: plane centre (0,0,n3) and line centre (0,n2,n3)
+struct SState {
+    cdf gpC, Tc, RF0c, RB0c, rF0c, rB0c;  // plane: value, n3-step ratio, n2-step ratios at n2=0, n1-ratios at n2=0
+    cdf gpL, Sd, RfL, RbL;                // line: value, n2-step ratio (current direction), n1-ratios
+};
+
+__device__ __forceinline__ cdf to_cdf(double re, double im) { return cdf{df_from_double(re), df_from_double(im)}; }
+
+__device__ __forceinline__ void cexp_phase(double th, double& re, double& im) {
+    th -= rint(th);
+    double s, c;
+    sincospi(2.0 * th, &s, &c);
+    re = c;
+    im = -s;
+}
+
+// closed-form state at line (n2, n3) in FP64, stored as double-float
+__device__ void split_state(const PairWalk& w, int n2, int n3, SState& s) {
+    const double c = w.c;
+    const double M11 = c_Ms[0], M22 = c_Ms[1], M33 = c_Ms[2], M12 = c_Ms[3], M13 = c_Ms[4], M23 = c_Ms[5];
+    const double a2 = (double)n2, a3 = (double)n3;
+    double p3r, p3i, p23r, p23i;
+    cexp_phase(a3 * w.f3, p3r, p3i);
+    cexp_phase(a2 * w.f2 + a3 * w.f3, p23r, p23i);
+    double g;
+    g = exp(-c * M33 * a3 * a3);
+    s.gpC = to_cdf(g * p3r, g * p3i);
+    g = exp(-c * M33 * (2.0 * a3 + 1.0));
+    s.Tc = to_cdf(g * w.e3r, g * w.e3i);
+    g = exp(-c * (M22 + 2.0 * M23 * a3));
+    s.RF0c = to_cdf(g * w.e2r, g * w.e2i);
+    g = exp(-c * (M22 - 2.0 * M23 * a3));
+    s.RB0c = to_cdf(g * w.e2r, -g * w.e2i);
+    g = exp(-c * (M11 + 2.0 * M13 * a3));
+    s.rF0c = to_cdf(g * w.e1r, g * w.e1i);
+    g = exp(-c * (M11 - 2.0 * M13 * a3));
+    s.rB0c = to_cdf(g * w.e1r, -g * w.e1i);
+    g = exp(-c * (M22 * a2 * a2 + 2.0 * M23 * a2 * a3 + M33 * a3 * a3));
+    s.gpL = to_cdf(g * p23r, g * p23i);
+    if (n2 >= 0) {
+        g = exp(-c * (M22 * (2.0 * a2 + 1.0) + 2.0 * M23 * a3));
+        s.Sd = to_cdf(g * w.e2r, g * w.e2i);
+    } else {
+        g = exp(-c * (M22 * (1.0 - 2.0 * a2) - 2.0 * M23 * a3));
+        s.Sd = to_cdf(g * w.e2r, -g * w.e2i);
+    }
+    const double beta = M12 * a2 + M13 * a3;
+    g = exp(-c * (M11 + 2.0 * beta));
+    s.RfL = to_cdf(g * w.e1r, g * w.e1i);
+    g = exp(-c * (M11 - 2.0 * beta));
+    s.RbL = to_cdf(g * w.e1r, -g * w.e1i);
+}
+
+// per-pair real multipliers of the recurrences, double-float
+struct SConst {
+    df q1, q2, q3, x12, y12, x13, y13, x23, y23;
+};
+
+// Once per plan: chunk-start states and the multipliers of every pair record.
+__global__ void k_split_setup(const PairWalk* __restrict__ walk, long long npairs, const WLine* __restrict__ lines,
+                              const WChunk* __restrict__ chunks, int nchunks, SState* __restrict__ init,
+                              SConst* __restrict__ cst) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ch = blockIdx.y;
+    if (i >= npairs) return;
+    const PairWalk w = walk[i];
+    const WLine ln = lines[chunks[ch].l0];
+    SState s;
+    split_state(w, ln.n2, ln.n3, s);
+    init[(long long)ch * npairs + i] = s;
+    if (ch == 0) {
+        SConst k;
+        k.q1 = df_from_double(w.q1);
+        k.q2 = df_from_double(w.q2);
+        k.q3 = df_from_double(w.q3);
+        k.x12 = df_from_double(w.x12);
+        k.y12 = df_from_double(w.y12);
+        k.x13 = df_from_double(w.x13);
+        k.y13 = df_from_double(w.y13);
+        k.x23 = df_from_double(w.x23);
+        k.y23 = df_from_double(w.y23);
+        cst[i] = k;
+    }
+}
+
+__device__ __forceinline__ SConst idle_const() {
+    SConst k;
+    const df one{1.f, 0.f};
+    k.q1 = k.q2 = k.q3 = k.x12 = k.y12 = k.x13 = k.y13 = k.x23 = k.y23 = one;
+    return k;
+}
+
+__device__ __forceinline__ SState idle_state() {
+    SState s;
+    const cdf z{{0.f, 0.f}, {0.f, 0.f}};
+    s.gpC = s.Tc = s.RF0c = s.RB0c = s.rF0c = s.rB0c = z;
+    s.gpL = s.Sd = s.RfL = s.RbL = z;
+    return s;
+}
+
+__device__ __forceinline__ void split_step(const SConst& k, int op, SState& s, const SState* init_p, bool valid) {
+    switch (op) {
+        case OP_FIRST:
+            s = valid ? *init_p : idle_state();
+            break;
+        case OP_N2F:
+            s.gpL = cdf_mul(s.gpL, s.Sd);
+            s.Sd = cdf_scale(s.Sd, k.q2);
+            s.RfL = cdf_scale(s.RfL, k.x12);
+            s.RbL = cdf_scale(s.RbL, k.y12);
+            break;
+        case OP_NEGSTART:
+            s.gpL = cdf_mul(s.gpC, s.RB0c);
+            s.Sd = cdf_scale(s.RB0c, k.q2);
+            s.RfL = cdf_scale(s.rF0c, k.y12);
+            s.RbL = cdf_scale(s.rB0c, k.x12);
+            break;
+        case OP_N2B:
+            s.gpL = cdf_mul(s.gpL, s.Sd);
+            s.Sd = cdf_scale(s.Sd, k.q2);
+            s.RfL = cdf_scale(s.RfL, k.y12);
+            s.RbL = cdf_scale(s.RbL, k.x12);
+            break;
+        default:  // OP_N3
+            s.gpC = cdf_mul(s.gpC, s.Tc);
+            s.Tc = cdf_scale(s.Tc, k.q3);
+            s.RF0c = cdf_scale(s.RF0c, k.x23);
+            s.RB0c = cdf_scale(s.RB0c, k.y23);
+            s.rF0c = cdf_scale(s.rF0c, k.x13);
+            s.rB0c = cdf_scale(s.rB0c, k.y13);
+            s.gpL = s.gpC;
+            s.Sd = s.RF0c;
+            s.RfL = s.rF0c;
+            s.RbL = s.rB0c;
+            break;
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void powers23f(int n2, int n3, float pq[L + 1][L + 1]) {
+    float p2[L + 1], p3[L + 1];
+    p2[0] = 1.f;
+    p3[0] = 1.f;
+#pragma unroll
+    for (int j = 1; j <= L; ++j) {
+        p2[j] = p2[j - 1] * (float)n2;  // exact: |n|^4 < 2^24
+        p3[j] = p3[j - 1] * (float)n3;
+    }
+#pragma unroll
+    for (int j = 0; j <= L; ++j)
+#pragma unroll
+        for (int k = 0; k + j <= L; ++k) pq[j][k] = p2[j] * p3[k];
+}
+
+// ---- rho -----------------------------------------------------------------
+
+__device__ __forceinline__ cdf unpack(float4 v) { return cdf{{v.x, v.y}, {v.z, v.w}}; }
+
+__device__ __forceinline__ void split_flush(float4* buf, float4* red, float4* row, int rbase, int nvalid) {
+    __syncthreads();
+    const int tid = threadIdx.x, j = tid & 31, wv = tid >> 5;
+    if (j < nvalid) {
+        cdf s{{0.f, 0.f}, {0.f, 0.f}};
+        const float4* b = buf + j * (kTile + 1) + wv * 32;
+#pragma unroll 4
+        for (int k = 0; k < 32; ++k) s = cdf_add(s, unpack(b[k]));
+        red[wv * 32 + j] = make_float4(s.re.hi, s.re.lo, s.im.hi, s.im.lo);
+    }
+    __syncthreads();
+    if (tid < nvalid) {
+        cdf s = unpack(row[rbase + tid]);
+#pragma unroll
+        for (int q = 0; q < kTile / 32; ++q) s = cdf_add(s, unpack(red[q * 32 + tid]));
+        row[rbase + tid] = make_float4(s.re.hi, s.re.lo, s.im.hi, s.im.lo);
+    }
+}
+
+template <int L>
+__device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* __restrict__ Dp_d,
+                               const SConst* __restrict__ cst, const SState* __restrict__ init_c,
+                               const WLine* __restrict__ lines, const WChunk ch, float4* buf, float4* red,
+                               float4* row) {
+    constexpr int NT = nterms(L);
+    const int tid = threadIdx.x;
+    const bool valid = tid < tl.count;
+    const long long pi = (long long)tl.first + tid;
+    const long long cnt = lay.start[L + 1] - lay.start[L];
+    const long long loc = pi - lay.start[L];
+    df D[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        float2 v = valid ? Dp_d[lay.base[L] + (long long)t * cnt + loc] : make_float2(0.f, 0.f);
+        D[t] = df{v.x, v.y};
+    }
+    const SConst k = valid ? cst[pi] : idle_const();
+    const SState* init_p = init_c + (valid ? pi : 0);
+    SState s;
+    int slot = 0, rbase = 0;
+    for (int li = ch.l0; li < ch.l1; ++li) {
+        const WLine ln = lines[li];
+        split_step(k, ln.op, s, init_p, valid);
+        if (ln.lo > ln.hi) continue;
+        cdf c[L + 1];
+        {
+            float pq[L + 1][L + 1];
+            powers23f<L>(ln.n2, ln.n3, pq);
+#pragma unroll
+            for (int i = 0; i <= L; ++i) c[i] = cdf{{0.f, 0.f}, {0.f, 0.f}};
+            int t = 0;
+#pragma unroll
+            for (int lam = 0; lam <= L; ++lam)
+#pragma unroll
+                for (int i = lam; i >= 0; --i)
+#pragma unroll
+                    for (int j = lam - i; j >= 0; --j) {
+                        const int kk = lam - i - j;
+                        const df v = df_mulf(D[t], pq[j][kk]);
+                        switch (lam & 3) {
+                            case 0: c[i].re = df_add(c[i].re, v); break;
+                            case 1: c[i].im = df_sub(c[i].im, v); break;
+                            case 2: c[i].re = df_sub(c[i].re, v); break;
+                            default: c[i].im = df_add(c[i].im, v); break;
+                        }
+                        ++t;
+                    }
+        }
+#pragma unroll
+        for (int dir = 0; dir < 2; ++dir) {
+            int m0, m1, step;
+            cdf gp, R;
+            if (dir == 0) {
+                if (ln.hi < 0) continue;
+                m0 = 0;
+                m1 = ln.hi;
+                step = 1;
+                gp = s.gpL;
+                R = s.RfL;
+            } else {
+                if (ln.lo > -1) continue;
+                m0 = -1;
+                m1 = ln.lo;
+                step = -1;
+                gp = cdf_mul(s.gpL, s.RbL);
+                R = cdf_scale(s.RbL, k.q1);
+            }
+            for (int m = m0;; m += step) {
+                if (m >= ln.lo && m <= ln.hi) {
+                    const float x = (float)m;
+                    cdf a = c[L];
+#pragma unroll
+                    for (int i = L - 1; i >= 0; --i)
+                        a = cdf{df_add(df_mulf(a.re, x), c[i].re), df_add(df_mulf(a.im, x), c[i].im)};
+                    const cdf z = cdf_mul(gp, a);
+                    buf[slot * (kTile + 1) + tid] = make_float4(z.re.hi, z.re.lo, z.im.hi, z.im.lo);
+                    if (++slot == kBatch) {
+                        split_flush(buf, red, row, rbase, kBatch);
+                        rbase += kBatch;
+                        slot = 0;
+                    }
+                }
+                if (m == m1) break;
+                gp = cdf_mul(gp, R);
+                R = cdf_scale(R, k.q1);
+            }
+        }
+    }
+    if (slot > 0) split_flush(buf, red, row, rbase, slot);
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kTile) k_rho_walk_split(const Tile* __restrict__ tiles, int ntiles, Layout lay,
+                                                          const float2* __restrict__ Dp,
+                                                          const SConst* __restrict__ cst,
+                                                          const SState* __restrict__ init, long long npairs,
+                                                          const WLine* __restrict__ lines,
+                                                          const WChunk* __restrict__ chunks, int npb,
+                                                          double2* __restrict__ rho_part, long long ng_half) {
+    extern __shared__ float4 ssm[];
+    const int b = blockIdx.x, cidx = blockIdx.y, d = blockIdx.z;
+    const WChunk ch = chunks[cidx];
+    const int npts = ch.p1 - ch.p0;
+    float4* buf = ssm;
+    float4* red = buf + kBatch * (kTile + 1);
+    float4* row = red + kTile;
+    for (int i = threadIdx.x; i < npts; i += blockDim.x) row[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    const float2* Dp_d = Dp + (long long)d * lay.total;
+    const SState* init_c = init + (long long)cidx * npairs;
+    for (int t = b; t < ntiles; t += npb) {
+        const Tile tl = tiles[t];
+        switch (tl.cls) {
+            case 0: rho_tile_split<0>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row); break;
+            case 1: rho_tile_split<1>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row); break;
+            case 2: rho_tile_split<2>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row); break;
+            case 3: rho_tile_split<3>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row); break;
+            default: rho_tile_split<4>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row); break;
+        }
+    }
+    __syncthreads();
+    double2* out = rho_part + ((long long)d * npb + b) * ng_half + ch.p0;
+    for (int i = threadIdx.x; i < npts; i += blockDim.x) {
+        const float4 v = row[i];
+        out[i] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    }
+}
+
+// ---- J -------------------------------------------------------------------
+
+template <int L>
+__device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __restrict__ cst,
+                             const SState* __restrict__ init_c, const WLine* __restrict__ lines, const WChunk ch,
+                             const float4* __restrict__ wsm, const float* __restrict__ pw, int n1min,
+                             double* __restrict__ Jp_dc) {
+    constexpr int NT = nterms(L);
+    const int tid = threadIdx.x;
+    const bool valid = tid < tl.count;
+    const long long pi = (long long)tl.first + tid;
+    const long long cnt = lay.start[L + 1] - lay.start[L];
+    const long long loc = pi - lay.start[L];
+    const SConst k = valid ? cst[pi] : idle_const();
+    const SState* init_p = init_c + (valid ? pi : 0);
+    df J[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) J[t] = df{0.f, 0.f};
+    SState s;
+    for (int li = ch.l0; li < ch.l1; ++li) {
+        const WLine ln = lines[li];
+        split_step(k, ln.op, s, init_p, valid);
+        if (ln.lo > ln.hi) continue;
+        cdf A[L + 1];
+#pragma unroll
+        for (int i = 0; i <= L; ++i) A[i] = cdf{{0.f, 0.f}, {0.f, 0.f}};
+        int q = ln.pt - ch.p0;
+#pragma unroll
+        for (int dir = 0; dir < 2; ++dir) {
+            int m0, m1, step;
+            cdf gp, R;
+            if (dir == 0) {
+                if (ln.hi < 0) continue;
+                m0 = 0;
+                m1 = ln.hi;
+                step = 1;
+                gp = s.gpL;
+                R = s.RfL;
+            } else {
+                if (ln.lo > -1) continue;
+                m0 = -1;
+                m1 = ln.lo;
+                step = -1;
+                gp = cdf_mul(s.gpL, s.RbL);
+                R = cdf_scale(s.RbL, k.q1);
+            }
+            for (int m = m0;; m += step) {
+                if (m >= ln.lo && m <= ln.hi) {
+                    const cdf t = cdf_mul(gp, unpack(wsm[q++]));
+                    A[0] = cdf_add(A[0], t);
+                    const float* pwm = pw + (m - n1min) * 5;
+#pragma unroll
+                    for (int i = 1; i <= L; ++i) {
+                        const float p = pwm[i];
+                        A[i] = cdf{df_add(A[i].re, df_mulf(t.re, p)), df_add(A[i].im, df_mulf(t.im, p))};
+                    }
+                }
+                if (m == m1) break;
+                gp = cdf_mul(gp, R);
+                R = cdf_scale(R, k.q1);
+            }
+        }
+        float pq[L + 1][L + 1];
+        powers23f<L>(ln.n2, ln.n3, pq);
+        int t = 0;
+#pragma unroll
+        for (int lam = 0; lam <= L; ++lam)
+#pragma unroll
+            for (int i = lam; i >= 0; --i)
+#pragma unroll
+                for (int j = lam - i; j >= 0; --j) {
+                    const int kk = lam - i - j;
+                    df a;
+                    switch (lam & 3) {
+                        case 0: a = A[i].re; break;
+                        case 1: a = A[i].im; break;
+                        case 2: a = df_neg(A[i].re); break;
+                        default: a = df_neg(A[i].im); break;
+                    }
+                    J[t] = df_add(J[t], df_mulf(a, pq[j][kk]));
+                    ++t;
+                }
+    }
+    if (valid) {
+#pragma unroll
+        for (int t = 0; t < NT; ++t) Jp_dc[lay.base[L] + (long long)t * cnt + loc] = (double)J[t].hi + (double)J[t].lo;
+    }
+}
+
+__global__ void __launch_bounds__(kTile) k_j_walk_split(const Tile* __restrict__ tiles, Layout lay,
+                                                        const SConst* __restrict__ cst,
+                                                        const SState* __restrict__ init, long long npairs,
+                                                        const WLine* __restrict__ lines,
+                                                        const WChunk* __restrict__ chunks, int nchunks,
+                                                        const double2* __restrict__ W, long long ng_half, int n1min,
+                                                        int n1cnt, int max_chunk_pts, double* __restrict__ Jp) {
+    extern __shared__ float4 ssm[];
+    const int tix = blockIdx.x, cidx = blockIdx.y, d = blockIdx.z;
+    const WChunk ch = chunks[cidx];
+    const int npts = ch.p1 - ch.p0;
+    float4* wsm = ssm;
+    float* pw = reinterpret_cast<float*>(ssm + max_chunk_pts);
+    const double2* Wd = W + (long long)d * ng_half + ch.p0;
+    for (int i = threadIdx.x; i < npts; i += blockDim.x) {
+        const double2 v = Wd[i];
+        const df re = df_from_double(v.x), im = df_from_double(v.y);
+        wsm[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+    for (int i = threadIdx.x; i < n1cnt * 5; i += blockDim.x) {
+        const float x = (float)(n1min + i / 5);
+        float v = 1.f;
+        for (int e = 0; e < i % 5; ++e) v *= x;
+        pw[i] = v;
+    }
+    __syncthreads();
+    const Tile tl = tiles[tix];
+    double* Jp_dc = Jp + ((long long)d * nchunks + cidx) * lay.total;
+    const SState* init_c = init + (long long)cidx * npairs;
+    switch (tl.cls) {
+        case 0: j_tile_split<0>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc); break;
+        case 1: j_tile_split<1>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc); break;
+        case 2: j_tile_split<2>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc); break;
+        case 3: j_tile_split<3>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc); break;
+        default: j_tile_split<4>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc); break;
+    }
+}
+
+Layout make_layout(const ftcj_plan* P) {
+    Layout l;
+    for (int c = 0; c <= kNclass; ++c) l.start[c] = P->class_start[c];
+    for (int c = 0; c < kNclass; ++c) l.base[c] = P->term_base[c];
+    l.total = P->total_terms;
+    return l;
+}
+
+size_t rho_smem(const ftcj_plan* P) {
+    return sizeof(float4) * ((size_t)kBatch * (kTile + 1) + kTile + (size_t)std::max(P->max_chunk_pts, 1));
+}
+
+size_t j_smem(const ftcj_plan* P) {
+    const int n1cnt = P->n1_max - P->n1_min + 1;
+    return sizeof(float4) * (size_t)std::max(P->max_chunk_pts, 1) + sizeof(float) * 5 * (size_t)n1cnt;
+}
+
+}  // namespace
+
+int setup_split(ftcj_plan* P) {
+    double M6[6] = {P->M[0], P->M[4], P->M[8], P->M[1], P->M[2], P->M[5]};
+    FTCJ_CUDA(cudaMemcpyToSymbol(c_Ms, M6, sizeof(M6)));
+    const size_t nch = P->chunks.size();
+    const size_t np = (size_t)std::max<int64_t>(P->npairs, 1);
+    FTCJ_CUDA(cudaMalloc(&P->d_split_init, sizeof(SState) * np * std::max<size_t>(nch, 1)));
+    P->device_bytes += sizeof(SState) * np * std::max<size_t>(nch, 1);
+    FTCJ_CUDA(cudaMalloc(&P->d_split_const, sizeof(SConst) * np));
+    P->device_bytes += sizeof(SConst) * np;
+    if (P->npairs > 0 && nch > 0) {
+        dim3 g((unsigned)((P->npairs + 127) / 128), (unsigned)nch);
+        k_split_setup<<<g, 128>>>(P->d_walk, P->npairs, P->d_lines, P->d_chunks, (int)nch,
+                                  reinterpret_cast<SState*>(P->d_split_init),
+                                  reinterpret_cast<SConst*>(P->d_split_const));
+        FTCJ_CUDA(cudaGetLastError());
+    }
+    FTCJ_CUDA(cudaFuncSetAttribute(k_rho_walk_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rho_smem(P)));
+    FTCJ_CUDA(cudaFuncSetAttribute(k_j_walk_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)j_smem(P)));
+    return FTCJ_OK;
+}
+
+int rho_walk_split_blocks_per_sm(ftcj_plan* P, int* out) {
+    int n = 0;
+    FTCJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rho_walk_split, kTile, rho_smem(P)));
+    *out = n > 0 ? n : 1;
+    return FTCJ_OK;
+}
+
+int launch_rho_walk_split(ftcj_plan* P, int ndens, cudaStream_t s) {
+    if (P->ng_half == 0 || P->tiles.empty()) {
+        FTCJ_CUDA(cudaMemsetAsync(P->d_rho_part, 0, sizeof(double2) * (size_t)ndens * P->npb * P->ng_half, s));
+        return FTCJ_OK;
+    }
+    dim3 g(P->npb, (unsigned)P->chunks.size(), ndens);
+    k_rho_walk_split<<<g, kTile, rho_smem(P), s>>>(
+        P->d_tiles, (int)P->tiles.size(), make_layout(P), reinterpret_cast<const float2*>(P->d_Dp),
+        reinterpret_cast<const SConst*>(P->d_split_const), reinterpret_cast<const SState*>(P->d_split_init),
+        P->npairs, P->d_lines, P->d_chunks, P->npb, reinterpret_cast<double2*>(P->d_rho_part), P->ng_half);
+    FTCJ_CUDA(cudaGetLastError());
+    return FTCJ_OK;
+}
+
+int launch_j_walk_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s) {
+    const int nch = (int)P->chunks.size();
+    if (P->tiles.empty()) return FTCJ_OK;
+    if (P->ng_half == 0) {
+        FTCJ_CUDA(cudaMemsetAsync(P->d_Jp, 0, sizeof(double) * (size_t)ndens * std::max(nch, 1) * P->total_terms, s));
+        return FTCJ_OK;
+    }
+    dim3 g((unsigned)P->tiles.size(), nch, ndens);
+    const int n1cnt = P->n1_max - P->n1_min + 1;
+    k_j_walk_split<<<g, kTile, j_smem(P), s>>>(P->d_tiles, make_layout(P),
+                                               reinterpret_cast<const SConst*>(P->d_split_const),
+                                               reinterpret_cast<const SState*>(P->d_split_init), P->npairs,
+                                               P->d_lines, P->d_chunks, nch, reinterpret_cast<const double2*>(W),
+                                               P->ng_half, P->n1_min, n1cnt, P->max_chunk_pts, P->d_Jp);
+    FTCJ_CUDA(cudaGetLastError());
+    return FTCJ_OK;
+}
+
+}  // namespace ftcj

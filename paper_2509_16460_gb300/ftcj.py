@@ -17,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libftcj.so")
 
 FTCJ_PREC_FP64 = 0
+FTCJ_PREC_SPLIT = 1
 FTCJ_LMAX = 2
 
 _c_int, _c_double, _c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
