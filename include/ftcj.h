@@ -91,6 +91,8 @@ typedef struct {
     double pair_thresh; /* keep primitive pairs with overlap bound > this */
     int precision;      /* FTCJ_PREC_FP64 or FTCJ_PREC_SPLIT */
     int max_dens;       /* densities per device batch (scratch is sized for it); <= 0: 1 */
+    int chunk_points;   /* G points per walk chunk, 64..4096; <= 0: 4096 */
+    int rho_blocks;     /* persistent blocks of the structure-factor walk; <= 0: fill the GPU */
 } ftcj_params;
 
 typedef struct {
@@ -205,6 +207,53 @@ int ftcj_unfold_j(ftcj_plan* plan, int ndens, const double* J0n, double* Jk, voi
  * Synchronises `stream`.  ndens <= max_dens. */
 int ftcj_check_density(ftcj_plan* plan, int ndens, const double* Dk, double* max_imag, double* max_asym,
                        void* stream);
+
+/* ---- batches of independent cells ---- */
+
+/* Several independent problems (each its own cell, basis, k-mesh and
+ * parameters, e.g. an uneven set of cells or geometries) built together.
+ * The cells' builds are spread over internal streams (largest estimated
+ * work first, each stream taking the next cell when it is least loaded) and
+ * joined back to the caller's stream, so small cells overlap on the GPU.
+ * With FTCJ_BATCH_AUTOTUNE each cell's walk shape (chunk size, rho-walk
+ * blocks) is chosen by ftcj_autotune before its plan is made. */
+#define FTCJ_BATCH_AUTOTUNE 1
+typedef struct ftcj_batch ftcj_batch;
+
+/* cells/bases/params are arrays of ncell; kmeshes is [ncell][3]. */
+int ftcj_batch_create(int ncell, const ftcj_cell* cells, const ftcj_basis* bases, const int* kmeshes,
+                      const ftcj_params* params, int flags, ftcj_batch** out);
+
+/* Per-cell sizes (as ftcj_plan_info). */
+int ftcj_batch_info(const ftcj_batch* batch, int cell, ftcj_info* out);
+
+/* Builds every cell: ndens[c] densities, device buffers Dk[c], Jk[c] (complex
+ * [ndens][Nk][nao][nao]) and EJ[c] ([ndens]); pointer arrays on the host.
+ * Asynchronous on `stream`. */
+int ftcj_batch_jbuild(ftcj_batch* batch, const int* ndens, const double* const* Dk, double* const* Jk,
+                      double* const* EJ, void* stream);
+
+/* Captures one ftcj_batch_jbuild with these buffers into a CUDA graph held by
+ * the batch (replacing any earlier one); nothing runs during the capture.
+ * `stream` must not be capturing already and must not be the legacy default
+ * stream. */
+int ftcj_batch_capture(ftcj_batch* batch, const int* ndens, const double* const* Dk, double* const* Jk,
+                       double* const* EJ, void* stream);
+
+/* Launches the captured graph on `stream` (the buffers of the capture are
+ * read and written again).  Errors: EINVAL if nothing was captured. */
+int ftcj_batch_replay(ftcj_batch* batch, void* stream);
+
+void ftcj_batch_destroy(ftcj_batch* batch);
+
+/* Autotuner of the walk shape: builds the plan for every candidate
+ * (chunk_points in {512, 1024, 2048, 4096} that hold the longest G line,
+ * rho_blocks in {fill, 2 x fill}), times ftcj_jbuild on a zero density
+ * (the walks' cost does not depend on the values) with CUDA events, and
+ * writes the fastest parameters to *out (and its time to *best_ms, may be
+ * NULL).  Allocates and frees its own buffers; synchronises the device. */
+int ftcj_autotune(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], const ftcj_params* in,
+                  ftcj_params* out, double* best_ms);
 
 /* ---- measurement ---- */
 

@@ -282,9 +282,9 @@ int fused_fold_supported(const ftcj_plan* P) { return P->nk > 1 && P->nk <= kFus
 
 int setup_fold(ftcj_plan* P) {
     if (!fused_fold_supported(P)) return FTCJ_OK;
-    FTCJ_CUDA(cudaFuncSetAttribute(k_fold_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem(P)));
-    FTCJ_CUDA(cudaFuncSetAttribute(k_unfold_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem(P)));
-    return FTCJ_OK;
+    int rc = allow_dynamic_smem((const void*)k_fold_fused, fused_smem(P));
+    if (rc) return rc;
+    return allow_dynamic_smem((const void*)k_unfold_fused, fused_smem(P));
 }
 
 int launch_fold(ftcj_plan* P, int ndens, const double* Dk, double* D0n, cudaStream_t s) {

@@ -81,6 +81,18 @@ struct Tile {
     int cls, first, count, pad;  // pairs [first, first+count) of one class
 };
 
+// Per-cell constants, passed to kernels by value (so plans of different cells
+// can be alive and used together).
+struct CellConst {
+    double A[9];     // rows a_i
+    double Bt[9];    // rows b_i / (2 pi)
+    double M6[6];    // metric b_i.b_j: M11, M22, M33, M12, M13, M23
+    double bn[3];    // |b_i|
+    double vpar[2];  // 4 pi / Omega, 1 / (4 w^2)
+    int km[3];
+    int pad;
+};
+
 }  // namespace ftcj
 
 struct ftcj_plan {
@@ -100,6 +112,7 @@ struct ftcj_plan {
     std::vector<ftcj::WChunk> chunks;
     std::vector<int> gvec;  // [ng_half][3]
     int64_t ng_half;
+    int chunk_max;        // G points per walk chunk (a plan parameter)
     int max_chunk_pts;
     int n1_min, n1_max;
     // pairs
@@ -139,6 +152,7 @@ struct ftcj_plan {
     void* d_split_init = nullptr;    // split form: walk state at each chunk start, [nchunks][npairs]
     void* d_split_const = nullptr;   // split form: recurrence multipliers, [npairs]
     int precision = FTCJ_PREC_FP64;
+    ftcj::CellConst cc;
     int nEblocks = 0;
     size_t device_bytes = 0;
     // per-phase event timing (ftcj_profile_enable)
@@ -157,6 +171,11 @@ int cuda_fail(cudaError_t e, const char* what);
         cudaError_t e_ = (call);                          \
         if (e_ != cudaSuccess) return ::ftcj::cuda_fail(e_, #call); \
     } while (0)
+
+// Lets `func` use up to the device's opt-in shared memory per block (the
+// attribute is per kernel, shared by every plan, so it is never lowered) and
+// fails with EUNSUPPORTED if `need` bytes exceed that maximum.
+int allow_dynamic_smem(const void* func, size_t need);
 
 // --- setup (screen.cu) ---
 int screen_and_sort(ftcj_plan* P);  // fills pairs, walk constants, tiles

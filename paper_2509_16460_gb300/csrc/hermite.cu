@@ -14,6 +14,7 @@
 // a7 applies the transpose of every step to J'_ijk and scatters the AO block
 // into J^{0[L]} (and its mirror into J^{0[-L]}).
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "ftcj_internal.h"
@@ -23,10 +24,8 @@ namespace {
 
 constexpr int kTmatSize = 1 + 9 + 36 + 100 + 225;  // sum over lambda <= 4 of nmono^2
 
-__constant__ double c_A9[9];
 __constant__ double c_U[kLmax + 1][2][kNcartMax][kNcartMax];  // [l][sph][function][cart]
 __constant__ int c_cart[kLmax + 1][kNcartMax][3];
-__constant__ double c_T[kTmatSize];                          // per lambda: [tuv][ijk]
 __constant__ int c_Toff[kLpair + 1];
 
 struct Layout {
@@ -61,13 +60,13 @@ struct PairGeom {
     double E[3][3][3][5];  // [axis][i][j][t]
 };
 
-__device__ void pair_geom(const PairDev& pr, const GroupDev& A, const GroupDev& B, PairGeom& g) {
+__device__ void pair_geom(const PairDev& pr, const GroupDev& A, const GroupDev& B, const double* Acell, PairGeom& g) {
     double Av[3] = {A.x, A.y, A.z};
     double Bv[3] = {B.x, B.y, B.z};
     double a2p = 0.5 / pr.p;
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
-        double Bs = Bv[x] + pr.L[0] * c_A9[x] + pr.L[1] * c_A9[3 + x] + pr.L[2] * c_A9[6 + x];
+        double Bs = Bv[x] + pr.L[0] * Acell[x] + pr.L[1] * Acell[3 + x] + pr.L[2] * Acell[6 + x];
         ecoef(pr.P[x] - Av[x], pr.P[x] - Bs, a2p, A.lmax, B.lmax, g.E[x]);
     }
 }
@@ -76,7 +75,8 @@ __device__ void pair_geom(const PairDev& pr, const GroupDev& A, const GroupDev& 
 template <bool OUT_DF>
 __global__ void __launch_bounds__(128) k_hermite(const PairDev* __restrict__ pairs, const GroupDev* __restrict__ G,
                                                  const MemberDev* __restrict__ mem, const double* __restrict__ D0n,
-                                                 int nao, int nk, Layout lay, double* __restrict__ Dp) {
+                                                 int nao, int nk, Layout lay, double* __restrict__ Dp,
+                                                 const double* __restrict__ Tm, CellConst cc) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int d = blockIdx.y;
     if (i >= lay.start[kNclass]) return;
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(128) k_hermite(const PairDev* __restrict__ pai
     GroupDev A = G[pr.ga];
     GroupDev B = G[pr.gb];
     PairGeom g;
-    pair_geom(pr, A, B, g);
+    pair_geom(pr, A, B, cc.A, g);
     double h[kMaxTerms];
 #pragma unroll
     for (int t = 0; t < kMaxTerms; ++t) h[t] = 0.0;
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(128) k_hermite(const PairDev* __restrict__ pai
     const long long off = (long long)d * lay.total + lay.base[L] + loc;
     for (int lam = 0; lam <= L; ++lam) {
         int nm = nmono(lam), o = lam_offset(lam);
-        const double* T = c_T + c_Toff[lam];
+        const double* T = Tm + c_Toff[lam];
         for (int b = 0; b < nm; ++b) {
             double s = 0.0;
             for (int a = 0; a < nm; ++a) s += T[a * nm + b] * h[o + a];
@@ -161,7 +161,8 @@ __global__ void __launch_bounds__(128) k_jtransform(const PairDev* __restrict__ 
                                                     const GroupDev* __restrict__ G,
                                                     const MemberDev* __restrict__ mem,
                                                     const double* __restrict__ Jp, int nchunks, int nao, int nk,
-                                                    Layout lay, double* __restrict__ J0n) {
+                                                    Layout lay, double* __restrict__ J0n,
+                                                    const double* __restrict__ Tm, CellConst cc) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int d = blockIdx.y;
     if (i >= lay.start[kNclass]) return;
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(128) k_jtransform(const PairDev* __restrict__ 
     double jt[kMaxTerms];
     for (int lam = 0; lam <= L; ++lam) {
         int nm = nmono(lam), o = lam_offset(lam);
-        const double* T = c_T + c_Toff[lam];
+        const double* T = Tm + c_Toff[lam];
         for (int a = 0; a < nm; ++a) {
             double s = 0.0;
             for (int b = 0; b < nm; ++b) s += T[a * nm + b] * jp[o + b];
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(128) k_jtransform(const PairDev* __restrict__ 
     GroupDev A = G[pr.ga];
     GroupDev B = G[pr.gb];
     PairGeom g;
-    pair_geom(pr, A, B, g);
+    pair_geom(pr, A, B, cc.A, g);
     long long nn = (long long)nao * nao;
     double* Jc = J0n + ((long long)d * nk + pr.cell) * nn;
     double* Jm = J0n + ((long long)d * nk + pr.mcell) * nn;
@@ -254,8 +255,14 @@ Layout make_layout(const ftcj_plan* P) {
 // unit-normalised functions (radial part (2a/pi)^{3/4} (4a)^{l/2} is in the
 // member coefficient), and the per-lambda expansion of G_x^t G_y^u G_z^v in
 // n1^i n2^j n3^k for G = sum_i n_i b_i.
+static std::mutex g_table_mutex;
+static bool g_tables_on_device[64] = {};
+
 int upload_hermite_tables(ftcj_plan* P) {
-    FTCJ_CUDA(cudaMemcpyToSymbol(c_A9, P->A, sizeof(double) * 9));
+    int dev = 0;
+    FTCJ_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_table_mutex);
+    const bool need_const = dev < 0 || dev >= 64 || !g_tables_on_device[dev];
     int cart[kLmax + 1][kNcartMax][3] = {};
     for (int l = 0; l <= kLmax; ++l) {
         int n = 0;
@@ -267,7 +274,7 @@ int upload_hermite_tables(ftcj_plan* P) {
                 ++n;
             }
     }
-    FTCJ_CUDA(cudaMemcpyToSymbol(c_cart, cart, sizeof(cart)));
+    if (need_const) FTCJ_CUDA(cudaMemcpyToSymbol(c_cart, cart, sizeof(cart)));
     double U[kLmax + 1][2][kNcartMax][kNcartMax] = {};
     // Cartesian: component c scaled by 1/sqrt((2lx-1)!!(2ly-1)!!(2lz-1)!!)
     auto dfact = [](int n) {
@@ -298,7 +305,7 @@ int upload_hermite_tables(ftcj_plan* P) {
         U[2][1][4][0] = 0.5;   // (xx - yy) sqrt(3)/2, over sqrt(3)
         U[2][1][4][3] = -0.5;
     }
-    FTCJ_CUDA(cudaMemcpyToSymbol(c_U, U, sizeof(U)));
+    if (need_const) FTCJ_CUDA(cudaMemcpyToSymbol(c_U, U, sizeof(U)));
     // G_x^t G_y^u G_z^v with G_x = sum_i n_i B[i][x]: expand as polynomials in (n1, n2, n3)
     std::vector<double> T(kTmatSize, 0.0);
     int Toff[kLpair + 1];
@@ -335,8 +342,13 @@ int upload_hermite_tables(ftcj_plan* P) {
             }
         off += nm * nm;
     }
-    FTCJ_CUDA(cudaMemcpyToSymbol(c_T, T.data(), sizeof(double) * kTmatSize));
-    FTCJ_CUDA(cudaMemcpyToSymbol(c_Toff, Toff, sizeof(Toff)));
+    FTCJ_CUDA(cudaMalloc(&P->d_Tmat, sizeof(double) * kTmatSize));
+    P->device_bytes += sizeof(double) * kTmatSize;
+    FTCJ_CUDA(cudaMemcpy(P->d_Tmat, T.data(), sizeof(double) * kTmatSize, cudaMemcpyHostToDevice));
+    if (need_const) {
+        FTCJ_CUDA(cudaMemcpyToSymbol(c_Toff, Toff, sizeof(Toff)));
+        if (dev >= 0 && dev < 64) g_tables_on_device[dev] = true;
+    }
     return FTCJ_OK;
 }
 
@@ -345,10 +357,10 @@ int launch_hermite(ftcj_plan* P, int ndens, const double* D0n, cudaStream_t s) {
     dim3 g((unsigned)((P->npairs + 127) / 128), ndens);
     if (P->precision == FTCJ_PREC_SPLIT)
         k_hermite<true><<<g, 128, 0, s>>>(P->d_pairs, P->d_groups, P->d_members, D0n, P->nao, P->nk, make_layout(P),
-                                          P->d_Dp);
+                                          P->d_Dp, P->d_Tmat, P->cc);
     else
         k_hermite<false><<<g, 128, 0, s>>>(P->d_pairs, P->d_groups, P->d_members, D0n, P->nao, P->nk,
-                                           make_layout(P), P->d_Dp);
+                                           make_layout(P), P->d_Dp, P->d_Tmat, P->cc);
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }
@@ -359,7 +371,7 @@ int launch_jtransform(ftcj_plan* P, int ndens, double* J0n, cudaStream_t s) {
     if (P->npairs == 0) return FTCJ_OK;
     dim3 g((unsigned)((P->npairs + 127) / 128), ndens);
     k_jtransform<<<g, 128, 0, s>>>(P->d_pairs, P->d_groups, P->d_members, P->d_Jp, (int)P->chunks.size(), P->nao,
-                                   P->nk, make_layout(P), J0n);
+                                   P->nk, make_layout(P), J0n, P->d_Tmat, P->cc);
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }

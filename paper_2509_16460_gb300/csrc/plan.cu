@@ -26,6 +26,15 @@ int cuda_fail(cudaError_t e, const char* what) {
     return FTCJ_ECUDA;
 }
 
+int allow_dynamic_smem(const void* func, size_t need) {
+    int dev = 0, optin = 0;
+    FTCJ_CUDA(cudaGetDevice(&dev));
+    FTCJ_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (need > (size_t)optin) return fail(FTCJ_EUNSUPPORTED, "shared memory of a walk chunk above the device limit");
+    FTCJ_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    return FTCJ_OK;
+}
+
 namespace {
 
 bool finite(double x) { return std::isfinite(x); }
@@ -131,8 +140,8 @@ int build_walk(ftcj_plan* P) {
     int n1min = 0, n1max = 0;
     for (size_t i = 0; i < raw.size(); ++i) {
         int npts = raw[i].hi >= raw[i].lo ? raw[i].hi - raw[i].lo + 1 : 0;
-        if (npts > kChunkMax) return fail(FTCJ_EUNSUPPORTED, "a G line is longer than the walk chunk");
-        if (cur > 0 && cur + npts > kChunkMax) {
+        if (npts > P->chunk_max) return fail(FTCJ_EUNSUPPORTED, "a G line is longer than the walk chunk");
+        if (cur > 0 && cur + npts > P->chunk_max) {
             P->chunks.push_back({l0, (int)i, p0, pt});
             l0 = (int)i;
             p0 = pt;
@@ -220,12 +229,23 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     }
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) P->M[3 * i + j] = dot3(P->B + 3 * i, P->B + 3 * j);
+    std::memset(&P->cc, 0, sizeof(P->cc));
+    for (int i = 0; i < 9; ++i) {
+        P->cc.A[i] = P->A[i];
+        P->cc.Bt[i] = P->B[i] / (2.0 * M_PI);
+    }
+    {
+        const double m6[6] = {P->M[0], P->M[4], P->M[8], P->M[1], P->M[2], P->M[5]};
+        for (int i = 0; i < 6; ++i) P->cc.M6[i] = m6[i];
+        for (int i = 0; i < 3; ++i) P->cc.bn[i] = std::sqrt(P->M[4 * i]);
+    }
     // k mesh
     P->nk = 1;
     for (int i = 0; i < 3; ++i) {
         if (kmesh[i] < 1) return fail(FTCJ_EINVAL, "k-mesh dimensions must be >= 1");
         if (kmesh[i] > 16) return fail(FTCJ_EUNSUPPORTED, "k-mesh dimension above 16");
         P->km[i] = kmesh[i];
+        P->cc.km[i] = kmesh[i];
         P->nk *= kmesh[i];
     }
     // parameters
@@ -235,6 +255,8 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     P->precision = prm->precision;
     if (!(prm->pair_thresh > 0.0 && prm->pair_thresh < 1.0)) return fail(FTCJ_EINVAL, "pair_thresh in (0,1)");
     P->omega = prm->omega;
+    P->cc.vpar[0] = 4.0 * M_PI / P->vol;
+    P->cc.vpar[1] = 1.0 / (4.0 * prm->omega * prm->omega);
     if (prm->gcut > 0.0) {
         P->gcut = prm->gcut;
     } else {
@@ -242,6 +264,9 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
         P->gcut = 2.0 * prm->omega * std::sqrt(std::log(1.0 / prm->eps_g));
     }
     P->max_dens = prm->max_dens > 0 ? prm->max_dens : 1;
+    P->chunk_max = prm->chunk_points > 0 ? prm->chunk_points : kChunkMax;
+    if (P->chunk_max < 64 || P->chunk_max > kChunkMax)
+        return fail(FTCJ_EINVAL, "chunk_points must be in [64, 4096] (or <= 0 for the default)");
     // basis
     if (basis->ncentre < 1 || !basis->xyz) return fail(FTCJ_EINVAL, "no centres");
     if (basis->nshell < 1 || !basis->shells) return fail(FTCJ_EINVAL, "no shells");
@@ -355,6 +380,7 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     }
     int nch = std::max<int>(1, (int)P->chunks.size());
     P->npb = std::max(1, std::min<int>((int)std::max<size_t>(1, P->tiles.size()), P->num_sms * bps / nch));
+    if (prm->rho_blocks > 0) P->npb = std::min<int>(prm->rho_blocks, (int)std::max<size_t>(1, P->tiles.size()));
 
     size_t nn = (size_t)P->nao * P->nao;
     size_t md = (size_t)P->max_dens;

@@ -12,11 +12,6 @@
 namespace ftcj {
 namespace {
 
-__constant__ double c_A[9];     // lattice rows a_i
-__constant__ double c_Bt[9];    // rows b_i / (2 pi): P = sum_j f_j a_j with f_j = c_Bt[j] . P
-__constant__ double c_M[9];     // metric b_i . b_j
-__constant__ double c_bn[3];    // |b_i|
-__constant__ int c_km[3];
 
 // ---- block-wide exclusive scan ------------------------------------------
 __device__ long long block_scan_excl(long long v, long long* s_tot, long long* s_warp) {
@@ -77,7 +72,7 @@ __global__ void k_scan_add(long long* out, const long long* __restrict__ bsum, l
 
 // ---- candidate boxes ----------------------------------------------------
 __global__ void k_screen_count(const GroupDev* __restrict__ G, int ng, double thr, long long* __restrict__ cnt,
-                               int* __restrict__ lim) {
+                               int* __restrict__ lim, CellConst cc) {
     int ga = blockIdx.y;
     int gb = blockIdx.x * blockDim.x + threadIdx.x;
     if (gb >= ng) return;
@@ -92,9 +87,9 @@ __global__ void k_screen_count(const GroupDev* __restrict__ G, int ng, double th
             double dx = G[ga].x - G[gb].x, dy = G[ga].y - G[gb].y, dz = G[ga].z - G[gb].z;
             double dab = sqrt(dx * dx + dy * dy + dz * dz);
             double rmax = sqrt(log(s0 / thr) / mu);
-            l0 = (int)ceil((dab + rmax) * c_bn[0] / (2.0 * M_PI)) + 1;
-            l1 = (int)ceil((dab + rmax) * c_bn[1] / (2.0 * M_PI)) + 1;
-            l2 = (int)ceil((dab + rmax) * c_bn[2] / (2.0 * M_PI)) + 1;
+            l0 = (int)ceil((dab + rmax) * cc.bn[0] / (2.0 * M_PI)) + 1;
+            l1 = (int)ceil((dab + rmax) * cc.bn[1] / (2.0 * M_PI)) + 1;
+            l2 = (int)ceil((dab + rmax) * cc.bn[2] / (2.0 * M_PI)) + 1;
             n = (long long)(2 * l0 + 1) * (2 * l1 + 1) * (2 * l2 + 1);
         }
     }
@@ -132,7 +127,7 @@ __device__ __forceinline__ Cand decode(const long long* __restrict__ off, const 
 
 __global__ void k_screen_eval(const GroupDev* __restrict__ G, int ng, double thr, const long long* __restrict__ off,
                               const int* __restrict__ lim, long long C, unsigned char* __restrict__ flag,
-                              unsigned char* __restrict__ key) {
+                              unsigned char* __restrict__ key, CellConst cc) {
     long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
     Cand q = decode(off, lim, ng, c);
@@ -143,7 +138,7 @@ __global__ void k_screen_eval(const GroupDev* __restrict__ G, int ng, double thr
     double r2 = 0.0;
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
-        double R = AB[x] - (q.L0 * c_A[x] + q.L1 * c_A[3 + x] + q.L2 * c_A[6 + x]);
+        double R = AB[x] - (q.L0 * cc.A[x] + q.L1 * cc.A[3 + x] + q.L2 * cc.A[6 + x]);
         r2 += R * R;
     }
     double s = pow(2.0 * sqrt(a * b) / p, 1.5) * exp(-a * b / p * r2);
@@ -191,7 +186,7 @@ __device__ __forceinline__ int wrapi(int v, int n) {
 __global__ void k_pair_setup(const GroupDev* __restrict__ G, const int* __restrict__ nmem, int ng,
                              const long long* __restrict__ off, const int* __restrict__ lim,
                              const long long* __restrict__ order, long long npairs, PairDev* __restrict__ pairs,
-                             PairWalk* __restrict__ walk, unsigned long long* __restrict__ units) {
+                             PairWalk* __restrict__ walk, unsigned long long* __restrict__ units, CellConst cc) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npairs) return;
     Cand q = decode(off, lim, ng, order[i]);
@@ -206,8 +201,8 @@ __global__ void k_pair_setup(const GroupDev* __restrict__ G, const int* __restri
     r.L[0] = q.L0;
     r.L[1] = q.L1;
     r.L[2] = q.L2;
-    r.cell = (wrapi(q.L0, c_km[0]) * c_km[1] + wrapi(q.L1, c_km[1])) * c_km[2] + wrapi(q.L2, c_km[2]);
-    r.mcell = (wrapi(-q.L0, c_km[0]) * c_km[1] + wrapi(-q.L1, c_km[1])) * c_km[2] + wrapi(-q.L2, c_km[2]);
+    r.cell = (wrapi(q.L0, cc.km[0]) * cc.km[1] + wrapi(q.L1, cc.km[1])) * cc.km[2] + wrapi(q.L2, cc.km[2]);
+    r.mcell = (wrapi(-q.L0, cc.km[0]) * cc.km[1] + wrapi(-q.L1, cc.km[1])) * cc.km[2] + wrapi(-q.L2, cc.km[2]);
     bool self = (q.ga == q.gb) && q.L0 == 0 && q.L1 == 0 && q.L2 == 0;
     r.weight = self ? 1 : 2;
     r.cls = A.lmax + B.lmax;
@@ -215,7 +210,7 @@ __global__ void k_pair_setup(const GroupDev* __restrict__ G, const int* __restri
     double r2 = 0.0;
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
-        double Bs = Bv[x] + q.L0 * c_A[x] + q.L1 * c_A[3 + x] + q.L2 * c_A[6 + x];
+        double Bs = Bv[x] + q.L0 * cc.A[x] + q.L1 * cc.A[3 + x] + q.L2 * cc.A[6 + x];
         r.P[x] = (a * Av[x] + b * Bs) / p;
         double d = Av[x] - Bs;
         r2 += d * d;
@@ -230,21 +225,21 @@ __global__ void k_pair_setup(const GroupDev* __restrict__ G, const int* __restri
     double f[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        double fj = c_Bt[3 * j] * r.P[0] + c_Bt[3 * j + 1] * r.P[1] + c_Bt[3 * j + 2] * r.P[2];
+        double fj = cc.Bt[3 * j] * r.P[0] + cc.Bt[3 * j + 1] * r.P[1] + cc.Bt[3 * j + 2] * r.P[2];
         f[j] = fj - rint(fj);
     }
     w.f1 = f[0];
     w.f2 = f[1];
     w.f3 = f[2];
-    w.q1 = exp(-2.0 * c * c_M[0]);
-    w.q2 = exp(-2.0 * c * c_M[4]);
-    w.q3 = exp(-2.0 * c * c_M[8]);
-    w.x12 = exp(-2.0 * c * c_M[1]);
-    w.y12 = exp(2.0 * c * c_M[1]);
-    w.x13 = exp(-2.0 * c * c_M[2]);
-    w.y13 = exp(2.0 * c * c_M[2]);
-    w.x23 = exp(-2.0 * c * c_M[5]);
-    w.y23 = exp(2.0 * c * c_M[5]);
+    w.q1 = exp(-2.0 * c * cc.M6[0]);
+    w.q2 = exp(-2.0 * c * cc.M6[1]);
+    w.q3 = exp(-2.0 * c * cc.M6[2]);
+    w.x12 = exp(-2.0 * c * cc.M6[3]);
+    w.y12 = exp(2.0 * c * cc.M6[3]);
+    w.x13 = exp(-2.0 * c * cc.M6[4]);
+    w.y13 = exp(2.0 * c * cc.M6[4]);
+    w.x23 = exp(-2.0 * c * cc.M6[5]);
+    w.y23 = exp(2.0 * c * cc.M6[5]);
     double s, co;
     sincospi(2.0 * f[0], &s, &co);
     w.e1r = co;
@@ -316,14 +311,7 @@ static int exclusive_scan(const long long* in, long long* out, long long n, long
 }
 
 int screen_and_sort(ftcj_plan* P) {
-    double Bt[9], bn[3];
-    for (int i = 0; i < 9; ++i) Bt[i] = P->B[i] / (2.0 * M_PI);
-    for (int i = 0; i < 3; ++i) bn[i] = std::sqrt(P->M[4 * i]);
-    FTCJ_CUDA(cudaMemcpyToSymbol(c_A, P->A, sizeof(double) * 9));
-    FTCJ_CUDA(cudaMemcpyToSymbol(c_Bt, Bt, sizeof(double) * 9));
-    FTCJ_CUDA(cudaMemcpyToSymbol(c_M, P->M, sizeof(double) * 9));
-    FTCJ_CUDA(cudaMemcpyToSymbol(c_bn, bn, sizeof(double) * 3));
-    FTCJ_CUDA(cudaMemcpyToSymbol(c_km, P->km, sizeof(int) * 3));
+    const CellConst cc = P->cc;
 
     int ng = P->ngroup;
     long long ngp = (long long)ng * ng;
@@ -342,7 +330,7 @@ int screen_and_sort(ftcj_plan* P) {
 
     if (ng > 65535) return fail(FTCJ_EUNSUPPORTED, "more than 65535 primitive groups");
     dim3 gc((ng + 127) / 128, ng);
-    k_screen_count<<<gc, 128>>>(P->d_groups, ng, thr, cnt, lim);
+    k_screen_count<<<gc, 128>>>(P->d_groups, ng, thr, cnt, lim, cc);
     FTCJ_CUDA(cudaGetLastError());
     long long C = 0;
     int rc = exclusive_scan(cnt, off, ngp, &C);
@@ -356,7 +344,7 @@ int screen_and_sort(ftcj_plan* P) {
     FTCJ_CUDA(s.get(&tc, (size_t)(ntiles * kNclass)));
     FTCJ_CUDA(s.get(&toff, (size_t)(ntiles * kNclass)));
     if (C > 0) {
-        k_screen_eval<<<(unsigned)((C + 255) / 256), 256>>>(P->d_groups, ng, thr, off, lim, C, flag, key);
+        k_screen_eval<<<(unsigned)((C + 255) / 256), 256>>>(P->d_groups, ng, thr, off, lim, C, flag, key, cc);
         FTCJ_CUDA(cudaGetLastError());
     }
     k_tile_count<<<(unsigned)ntiles, kSortTile>>>(flag, key, C, ntiles, tc);
@@ -387,7 +375,7 @@ int screen_and_sort(ftcj_plan* P) {
     FTCJ_CUDA(cudaMemset(utot, 0, sizeof(unsigned long long)));
     if (npairs > 0) {
         k_pair_setup<<<(unsigned)((npairs + 255) / 256), 256>>>(P->d_groups, nmem, ng, off, lim, order, npairs,
-                                                                 P->d_pairs, P->d_walk, units);
+                                                                 P->d_pairs, P->d_walk, units, cc);
         FTCJ_CUDA(cudaGetLastError());
         k_sum_u64<<<256, 256>>>(units, npairs, utot);
         FTCJ_CUDA(cudaGetLastError());

@@ -28,8 +28,6 @@
 namespace ftcj {
 namespace {
 
-__constant__ double c_M6[6];     // M11, M22, M33, M12, M13, M23
-__constant__ double c_vpar[2];   // 4 pi / Omega, 1/(4 w^2)
 
 struct Layout {
     long long start[kNclass + 1];
@@ -58,9 +56,9 @@ __device__ __forceinline__ void phase(double th, double& re, double& im) {
 }
 
 // state at line (n2, n3) and its plane centre, from closed forms
-__device__ __noinline__ void state_first(const PairWalk& w, int n2, int n3, WalkState& s) {
+__device__ __noinline__ void state_first(const PairWalk& w, const double* M6, int n2, int n3, WalkState& s) {
     const double c = w.c;
-    const double M11 = c_M6[0], M22 = c_M6[1], M33 = c_M6[2], M12 = c_M6[3], M13 = c_M6[4], M23 = c_M6[5];
+    const double M11 = M6[0], M22 = M6[1], M33 = M6[2], M12 = M6[3], M13 = M6[4], M23 = M6[5];
     const double a2 = (double)n2, a3 = (double)n3;
     s.gC = exp(-c * M33 * a3 * a3);
     s.TF = exp(-c * M33 * (2.0 * a3 + 1.0));
@@ -79,10 +77,11 @@ __device__ __noinline__ void state_first(const PairWalk& w, int n2, int n3, Walk
     phase(a2 * w.f2 + a3 * w.f3, s.phLr, s.phLi);
 }
 
-__device__ __forceinline__ void state_step(const PairWalk& w, int op, int n2, int n3, WalkState& s) {
+__device__ __forceinline__ void state_step(const PairWalk& w, const double* M6, int op, int n2, int n3,
+                                           WalkState& s) {
     switch (op) {
         case OP_FIRST:
-            state_first(w, n2, n3, s);
+            state_first(w, M6, n2, n3, s);
             break;
         case OP_N2F:
             s.gL *= s.Rd;
@@ -183,7 +182,7 @@ __device__ __forceinline__ void rho_flush(double2* buf, double2* red, double2* r
 }
 
 template <int L>
-__device__ void rho_tile(const Tile& tl, const Layout& lay, const double* __restrict__ Dp_d,
+__device__ void rho_tile(const double* M6, const Tile& tl, const Layout& lay, const double* __restrict__ Dp_d,
                          const PairWalk* __restrict__ walk, const WLine* __restrict__ lines, const WChunk ch,
                          double2* buf, double2* red, double2* row) {
     constexpr int NT = nterms(L);
@@ -201,7 +200,7 @@ __device__ void rho_tile(const Tile& tl, const Layout& lay, const double* __rest
     int rbase = 0;
     for (int li = ch.l0; li < ch.l1; ++li) {
         const WLine ln = lines[li];
-        state_step(w, ln.op, ln.n2, ln.n3, s);
+        state_step(w, M6, ln.op, ln.n2, ln.n3, s);
         if (ln.lo > ln.hi) continue;
         // c_i = sum_{j,k} (-i)^{i+j+k} D'_ijk n2^j n3^k
         double cr[L + 1], ci[L + 1];
@@ -291,7 +290,7 @@ __global__ void __launch_bounds__(kTile) k_rho_walk(const Tile* __restrict__ til
                                                     const double* __restrict__ Dp, const PairWalk* __restrict__ walk,
                                                     const WLine* __restrict__ lines,
                                                     const WChunk* __restrict__ chunks, int npb,
-                                                    double2* __restrict__ rho_part, long long ng_half) {
+                                                    double2* __restrict__ rho_part, long long ng_half, CellConst cc) {
     extern __shared__ double2 smem[];
     const int b = blockIdx.x, cidx = blockIdx.y, d = blockIdx.z;
     const WChunk ch = chunks[cidx];
@@ -305,11 +304,11 @@ __global__ void __launch_bounds__(kTile) k_rho_walk(const Tile* __restrict__ til
     for (int t = b; t < ntiles; t += npb) {
         const Tile tl = tiles[t];
         switch (tl.cls) {
-            case 0: rho_tile<0>(tl, lay, Dp_d, walk, lines, ch, buf, red, row); break;
-            case 1: rho_tile<1>(tl, lay, Dp_d, walk, lines, ch, buf, red, row); break;
-            case 2: rho_tile<2>(tl, lay, Dp_d, walk, lines, ch, buf, red, row); break;
-            case 3: rho_tile<3>(tl, lay, Dp_d, walk, lines, ch, buf, red, row); break;
-            default: rho_tile<4>(tl, lay, Dp_d, walk, lines, ch, buf, red, row); break;
+            case 0: rho_tile<0>(cc.M6, tl, lay, Dp_d, walk, lines, ch, buf, red, row); break;
+            case 1: rho_tile<1>(cc.M6, tl, lay, Dp_d, walk, lines, ch, buf, red, row); break;
+            case 2: rho_tile<2>(cc.M6, tl, lay, Dp_d, walk, lines, ch, buf, red, row); break;
+            case 3: rho_tile<3>(cc.M6, tl, lay, Dp_d, walk, lines, ch, buf, red, row); break;
+            default: rho_tile<4>(cc.M6, tl, lay, Dp_d, walk, lines, ch, buf, red, row); break;
         }
     }
     __syncthreads();
@@ -370,7 +369,7 @@ __global__ void __launch_bounds__(256) k_energy_final(const double* __restrict__
 // ---- J -------------------------------------------------------------------
 
 template <int L>
-__device__ void j_tile(const Tile& tl, const Layout& lay, const PairWalk* __restrict__ walk,
+__device__ void j_tile(const double* M6, const Tile& tl, const Layout& lay, const PairWalk* __restrict__ walk,
                        const WLine* __restrict__ lines, const WChunk ch, const double2* __restrict__ wsm,
                        const double* __restrict__ pw, int n1min, double* __restrict__ Jp_dc) {
     constexpr int NT = nterms(L);
@@ -386,7 +385,7 @@ __device__ void j_tile(const Tile& tl, const Layout& lay, const PairWalk* __rest
     WalkState s;
     for (int li = ch.l0; li < ch.l1; ++li) {
         const WLine ln = lines[li];
-        state_step(w, ln.op, ln.n2, ln.n3, s);
+        state_step(w, M6, ln.op, ln.n2, ln.n3, s);
         if (ln.lo > ln.hi) continue;
         double Ar[L + 1], Ai[L + 1];
 #pragma unroll
@@ -470,7 +469,7 @@ __global__ void __launch_bounds__(kTile) k_j_walk(const Tile* __restrict__ tiles
                                                   const PairWalk* __restrict__ walk, const WLine* __restrict__ lines,
                                                   const WChunk* __restrict__ chunks, int nchunks,
                                                   const double2* __restrict__ W, long long ng_half, int n1min,
-                                                  int n1cnt, int max_chunk_pts, double* __restrict__ Jp) {
+                                                  int n1cnt, int max_chunk_pts, double* __restrict__ Jp, CellConst cc) {
     extern __shared__ double2 smem[];
     const int tix = blockIdx.x, cidx = blockIdx.y, d = blockIdx.z;
     const WChunk ch = chunks[cidx];
@@ -489,21 +488,21 @@ __global__ void __launch_bounds__(kTile) k_j_walk(const Tile* __restrict__ tiles
     const Tile tl = tiles[tix];
     double* Jp_dc = Jp + ((long long)d * nchunks + cidx) * lay.total;
     switch (tl.cls) {
-        case 0: j_tile<0>(tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
-        case 1: j_tile<1>(tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
-        case 2: j_tile<2>(tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
-        case 3: j_tile<3>(tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
-        default: j_tile<4>(tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
+        case 0: j_tile<0>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
+        case 1: j_tile<1>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
+        case 2: j_tile<2>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
+        case 3: j_tile<3>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
+        default: j_tile<4>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
     }
 }
 
-__global__ void k_vg(const int* __restrict__ gvec, long long n, double* __restrict__ vg) {
+__global__ void k_vg(const int* __restrict__ gvec, long long n, double* __restrict__ vg, CellConst cc) {
     long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const double n1 = gvec[3 * p], n2 = gvec[3 * p + 1], n3 = gvec[3 * p + 2];
-    const double g2 = c_M6[0] * n1 * n1 + c_M6[1] * n2 * n2 + c_M6[2] * n3 * n3 +
-                      2.0 * (c_M6[3] * n1 * n2 + c_M6[4] * n1 * n3 + c_M6[5] * n2 * n3);
-    vg[p] = c_vpar[0] * exp(-g2 * c_vpar[1]) / g2;
+    const double g2 = cc.M6[0] * n1 * n1 + cc.M6[1] * n2 * n2 + cc.M6[2] * n3 * n3 +
+                      2.0 * (cc.M6[3] * n1 * n2 + cc.M6[4] * n1 * n3 + cc.M6[5] * n2 * n3);
+    vg[p] = cc.vpar[0] * exp(-g2 * cc.vpar[1]) / g2;
 }
 
 Layout make_layout(const ftcj_plan* P) {
@@ -526,13 +525,9 @@ size_t j_smem_bytes(const ftcj_plan* P) {
 }  // namespace
 
 int upload_walk_tables(ftcj_plan* P) {
-    double M6[6] = {P->M[0], P->M[4], P->M[8], P->M[1], P->M[2], P->M[5]};
-    double vp[2] = {4.0 * M_PI / P->vol, 1.0 / (4.0 * P->omega * P->omega)};
-    FTCJ_CUDA(cudaMemcpyToSymbol(c_M6, M6, sizeof(M6)));
-    FTCJ_CUDA(cudaMemcpyToSymbol(c_vpar, vp, sizeof(vp)));
-    FTCJ_CUDA(cudaFuncSetAttribute(k_rho_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rho_smem_bytes(P)));
-    FTCJ_CUDA(cudaFuncSetAttribute(k_j_walk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)j_smem_bytes(P)));
-    return FTCJ_OK;
+    int rc = allow_dynamic_smem((const void*)k_rho_walk, rho_smem_bytes(P));
+    if (rc) return rc;
+    return allow_dynamic_smem((const void*)k_j_walk, j_smem_bytes(P));
 }
 
 int rho_walk_blocks_per_sm(ftcj_plan* P, int* out) {
@@ -544,7 +539,7 @@ int rho_walk_blocks_per_sm(ftcj_plan* P, int* out) {
 
 int launch_vg(ftcj_plan* P) {
     if (P->ng_half == 0) return FTCJ_OK;
-    k_vg<<<(unsigned)((P->ng_half + 255) / 256), 256>>>(P->d_gvec, P->ng_half, P->d_vg);
+    k_vg<<<(unsigned)((P->ng_half + 255) / 256), 256>>>(P->d_gvec, P->ng_half, P->d_vg, P->cc);
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }
@@ -557,7 +552,7 @@ int launch_rho_walk(ftcj_plan* P, int ndens, cudaStream_t s) {
     dim3 g(P->npb, (unsigned)P->chunks.size(), ndens);
     k_rho_walk<<<g, kTile, rho_smem_bytes(P), s>>>(P->d_tiles, (int)P->tiles.size(), make_layout(P), P->d_Dp,
                                                    P->d_walk, P->d_lines, P->d_chunks, P->npb,
-                                                   reinterpret_cast<double2*>(P->d_rho_part), P->ng_half);
+                                                   reinterpret_cast<double2*>(P->d_rho_part), P->ng_half, P->cc);
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }
@@ -596,7 +591,7 @@ int launch_j_walk(ftcj_plan* P, int ndens, const double* W, cudaStream_t s) {
     int n1cnt = P->n1_max - P->n1_min + 1;
     k_j_walk<<<g, kTile, j_smem_bytes(P), s>>>(P->d_tiles, make_layout(P), P->d_walk, P->d_lines, P->d_chunks, nch,
                                                reinterpret_cast<const double2*>(W), P->ng_half, P->n1_min, n1cnt,
-                                               P->max_chunk_pts, P->d_Jp);
+                                               P->max_chunk_pts, P->d_Jp, P->cc);
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }

@@ -22,7 +22,6 @@
 namespace ftcj {
 namespace {
 
-__constant__ double c_Ms[6];  // M11, M22, M33, M12, M13, M23
 
 struct Layout {
     long long start[kNclass + 1];
@@ -47,9 +46,9 @@ __device__ __forceinline__ void cexp_phase(double th, double& re, double& im) {
 }
 
 // closed-form state at line (n2, n3) in FP64, stored as double-float
-__device__ void split_state(const PairWalk& w, int n2, int n3, SState& s) {
+__device__ void split_state(const PairWalk& w, const double* M6, int n2, int n3, SState& s) {
     const double c = w.c;
-    const double M11 = c_Ms[0], M22 = c_Ms[1], M33 = c_Ms[2], M12 = c_Ms[3], M13 = c_Ms[4], M23 = c_Ms[5];
+    const double M11 = M6[0], M22 = M6[1], M33 = M6[2], M12 = M6[3], M13 = M6[4], M23 = M6[5];
     const double a2 = (double)n2, a3 = (double)n3;
     double p3r, p3i, p23r, p23i;
     cexp_phase(a3 * w.f3, p3r, p3i);
@@ -91,14 +90,14 @@ struct SConst {
 // Once per plan: chunk-start states and the multipliers of every pair record.
 __global__ void k_split_setup(const PairWalk* __restrict__ walk, long long npairs, const WLine* __restrict__ lines,
                               const WChunk* __restrict__ chunks, int nchunks, SState* __restrict__ init,
-                              SConst* __restrict__ cst) {
+                              SConst* __restrict__ cst, CellConst cc) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int ch = blockIdx.y;
     if (i >= npairs) return;
     const PairWalk w = walk[i];
     const WLine ln = lines[chunks[ch].l0];
     SState s;
-    split_state(w, ln.n2, ln.n3, s);
+    split_state(w, cc.M6, ln.n2, ln.n3, s);
     init[(long long)ch * npairs + i] = s;
     if (ch == 0) {
         SConst k;
@@ -483,8 +482,6 @@ size_t j_smem(const ftcj_plan* P) {
 }  // namespace
 
 int setup_split(ftcj_plan* P) {
-    double M6[6] = {P->M[0], P->M[4], P->M[8], P->M[1], P->M[2], P->M[5]};
-    FTCJ_CUDA(cudaMemcpyToSymbol(c_Ms, M6, sizeof(M6)));
     const size_t nch = P->chunks.size();
     const size_t np = (size_t)std::max<int64_t>(P->npairs, 1);
     FTCJ_CUDA(cudaMalloc(&P->d_split_init, sizeof(SState) * np * std::max<size_t>(nch, 1)));
@@ -495,12 +492,12 @@ int setup_split(ftcj_plan* P) {
         dim3 g((unsigned)((P->npairs + 127) / 128), (unsigned)nch);
         k_split_setup<<<g, 128>>>(P->d_walk, P->npairs, P->d_lines, P->d_chunks, (int)nch,
                                   reinterpret_cast<SState*>(P->d_split_init),
-                                  reinterpret_cast<SConst*>(P->d_split_const));
+                                  reinterpret_cast<SConst*>(P->d_split_const), P->cc);
         FTCJ_CUDA(cudaGetLastError());
     }
-    FTCJ_CUDA(cudaFuncSetAttribute(k_rho_walk_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rho_smem(P)));
-    FTCJ_CUDA(cudaFuncSetAttribute(k_j_walk_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)j_smem(P)));
-    return FTCJ_OK;
+    int rc = allow_dynamic_smem((const void*)k_rho_walk_split, rho_smem(P));
+    if (rc) return rc;
+    return allow_dynamic_smem((const void*)k_j_walk_split, j_smem(P));
 }
 
 int rho_walk_split_blocks_per_sm(ftcj_plan* P, int* out) {

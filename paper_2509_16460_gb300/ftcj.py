@@ -40,7 +40,7 @@ class BasisDesc(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("omega", _c_double), ("gcut", _c_double), ("eps_g", _c_double), ("pair_thresh", _c_double),
-                ("precision", _c_int), ("max_dens", _c_int)]
+                ("precision", _c_int), ("max_dens", _c_int), ("chunk_points", _c_int), ("rho_blocks", _c_int)]
 
 
 class Info(ctypes.Structure):
@@ -61,8 +61,11 @@ EXPORTED = [
     "ftcj_fold_density", "ftcj_rho", "ftcj_potential", "ftcj_jback", "ftcj_unfold_j", "ftcj_check_density",
     "ftcj_get_gvectors", "ftcj_get_pairs", "ftcj_get_groups", "ftcj_strerror", "ftcj_last_error",
     "ftcj_profile_enable", "ftcj_profile_read", "ftcj_launches_per_batch", "ftcj_probe_fma_peak",
-    "ftcj_potential_noalloc",
+    "ftcj_potential_noalloc", "ftcj_batch_create", "ftcj_batch_info", "ftcj_batch_jbuild", "ftcj_batch_capture",
+    "ftcj_batch_replay", "ftcj_batch_destroy", "ftcj_autotune",
 ]
+
+FTCJ_BATCH_AUTOTUNE = 1
 
 FTCJ_NOALLOC_MAX_PARTIALS = 16384
 
@@ -111,13 +114,24 @@ def _declare(L):
     L.ftcj_launches_per_batch.argtypes = [P, _c_int, ctypes.POINTER(ctypes.c_int64)]
     L.ftcj_probe_fma_peak.argtypes = [_c_int, _dp, P]
     L.ftcj_potential_noalloc.argtypes = [_dp, _c_double, _c_int, ctypes.c_int64, P, P, P, P, P]
+    VPP = ctypes.POINTER(_c_void_p)
+    L.ftcj_batch_create.argtypes = [_c_int, ctypes.POINTER(Cell), ctypes.POINTER(BasisDesc), _ip,
+                                    ctypes.POINTER(Params), _c_int, ctypes.POINTER(_c_void_p)]
+    L.ftcj_batch_info.argtypes = [P, _c_int, ctypes.POINTER(Info)]
+    L.ftcj_batch_jbuild.argtypes = [P, _ip, VPP, VPP, VPP, P]
+    L.ftcj_batch_capture.argtypes = [P, _ip, VPP, VPP, VPP, P]
+    L.ftcj_batch_replay.argtypes = [P, P]
+    L.ftcj_batch_destroy.argtypes = [P]
+    L.ftcj_batch_destroy.restype = None
+    L.ftcj_autotune.argtypes = [ctypes.POINTER(Cell), ctypes.POINTER(BasisDesc), _ip, ctypes.POINTER(Params),
+                                ctypes.POINTER(Params), _dp]
     L.ftcj_strerror.argtypes = [_c_int]
     L.ftcj_strerror.restype = ctypes.c_char_p
     L.ftcj_last_error.argtypes = []
     L.ftcj_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
         f = getattr(L, name)
-        if name not in ("ftcj_plan_destroy", "ftcj_strerror", "ftcj_last_error"):
+        if name not in ("ftcj_plan_destroy", "ftcj_strerror", "ftcj_last_error", "ftcj_batch_destroy"):
             f.restype = _c_int
 
 
@@ -147,29 +161,136 @@ def _dev_ptr(t, dtype, shape, name):
     return _c_void_p(t.data_ptr())
 
 
+def _describe(A, xyz, shells, keep):
+    """ctypes descriptors of a cell and a basis; arrays are appended to keep."""
+    A = np.ascontiguousarray(A, dtype=np.float64).reshape(3, 3)
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    keep += [A, xyz]
+    cell = Cell()
+    for i, v in enumerate(A.ravel()):
+        cell.A[i] = float(v)
+    sh = (ShellDesc * len(shells))()
+    for i, s in enumerate(shells):
+        e = np.ascontiguousarray(s.exps, dtype=np.float64)
+        c = np.ascontiguousarray(s.coefs, dtype=np.float64)
+        keep += [e, c]
+        sh[i] = ShellDesc(int(s.centre), int(s.l), 1 if s.spherical else 0, int(len(e)),
+                          e.ctypes.data_as(_dp), c.ctypes.data_as(_dp))
+    keep.append(sh)
+    basis = BasisDesc(int(xyz.shape[0]), xyz.ctypes.data_as(_dp), len(shells), sh)
+    return cell, basis
+
+
+def _params_of(w, precision=FTCJ_PREC_FP64, max_dens=None, chunk_points=0, rho_blocks=0):
+    return Params(float(w.omega), float(w.gcut), float(w.eps_g), float(w.pair_thresh), int(precision),
+                  int(max_dens or w.ndens), int(chunk_points), int(rho_blocks))
+
+
+def autotune(w, precision=FTCJ_PREC_FP64):
+    """ftcj_autotune for one workload: (chunk_points, rho_blocks, best_ms)."""
+    keep = []
+    cell, basis = _describe(w.A, w.xyz, w.shells, keep)
+    km = (ctypes.c_int * 3)(*[int(k) for k in w.kmesh])
+    pin = _params_of(w, precision)
+    pout = Params()
+    ms = ctypes.c_double()
+    _check(lib().ftcj_autotune(ctypes.byref(cell), ctypes.byref(basis), km, ctypes.byref(pin), ctypes.byref(pout),
+                               ctypes.byref(ms)), "ftcj_autotune")
+    return pout.chunk_points, pout.rho_blocks, ms.value
+
+
+class Batch:
+    """Independent cells built together (ftcj_batch_*), optionally autotuned,
+    optionally captured into one CUDA graph and replayed."""
+
+    def __init__(self, workloads, precision=FTCJ_PREC_FP64, autotune=False):
+        L = lib()
+        self._keep = []
+        n = len(workloads)
+        cells = (Cell * n)()
+        bases = (BasisDesc * n)()
+        prms = (Params * n)()
+        km = (ctypes.c_int * (3 * n))()
+        for i, w in enumerate(workloads):
+            c, b = _describe(w.A, w.xyz, w.shells, self._keep)
+            cells[i] = c
+            bases[i] = b
+            prms[i] = _params_of(w, precision)
+            for j in range(3):
+                km[3 * i + j] = int(w.kmesh[j])
+        self._keep += [cells, bases, prms, km]
+        h = _c_void_p()
+        _check(L.ftcj_batch_create(n, cells, bases, km, prms, FTCJ_BATCH_AUTOTUNE if autotune else 0,
+                                   ctypes.byref(h)), "ftcj_batch_create")
+        self._h = h
+        self.n = n
+        self.infos = []
+        for i in range(n):
+            inf = Info()
+            _check(L.ftcj_batch_info(self._h, i, ctypes.byref(inf)), "ftcj_batch_info")
+            self.infos.append(inf.as_dict())
+
+    def _arrays(self, Dks, Jks, EJs):
+        import torch
+        n = self.n
+        nd = (ctypes.c_int * n)()
+        a = (_c_void_p * n)()
+        b = (_c_void_p * n)()
+        c = (_c_void_p * n)()
+        for i in range(n):
+            inf = self.infos[i]
+            d = int(Dks[i].shape[0])
+            shp = (d, inf["nk"], inf["nao"], inf["nao"])
+            nd[i] = d
+            a[i] = _dev_ptr(Dks[i], torch.complex128, shp, f"Dk[{i}]").value
+            b[i] = _dev_ptr(Jks[i], torch.complex128, shp, f"Jk[{i}]").value
+            c[i] = _dev_ptr(EJs[i], torch.float64, (d,), f"EJ[{i}]").value
+        self._last = (nd, a, b, c)
+        return nd, a, b, c
+
+    def outputs_like(self, Dks):
+        import torch
+        Jks = [torch.empty_like(D) for D in Dks]
+        EJs = [torch.empty(D.shape[0], dtype=torch.float64, device=D.device) for D in Dks]
+        return Jks, EJs
+
+    def jbuild(self, Dks, Jks=None, EJs=None, stream=None):
+        if Jks is None:
+            Jks, EJs = self.outputs_like(Dks)
+        nd, a, b, c = self._arrays(Dks, Jks, EJs)
+        _check(lib().ftcj_batch_jbuild(self._h, nd, a, b, c, _stream_ptr(stream)), "ftcj_batch_jbuild")
+        return Jks, EJs
+
+    def capture(self, Dks, Jks, EJs, stream):
+        nd, a, b, c = self._arrays(Dks, Jks, EJs)
+        _check(lib().ftcj_batch_capture(self._h, nd, a, b, c, _stream_ptr(stream)), "ftcj_batch_capture")
+
+    def replay(self, stream=None):
+        _check(lib().ftcj_batch_replay(self._h, _stream_ptr(stream)), "ftcj_batch_replay")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().ftcj_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Plan:
     """A plan for one cell, basis and k-mesh (ftcj_plan_create)."""
 
     def __init__(self, A, xyz, shells, kmesh, omega, eps_g=1e-14, gcut=0.0, pair_thresh=1e-12,
-                 precision=FTCJ_PREC_FP64, max_dens=1):
+                 precision=FTCJ_PREC_FP64, max_dens=1, chunk_points=0, rho_blocks=0):
         L = lib()
         self._keep = []
-        A = np.ascontiguousarray(A, dtype=np.float64).reshape(3, 3)
-        xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
-        self._keep += [A, xyz]
-        cell = Cell()
-        for i, v in enumerate(A.ravel()):
-            cell.A[i] = float(v)
-        sh = (ShellDesc * len(shells))()
-        for i, s in enumerate(shells):
-            e = np.ascontiguousarray(s.exps, dtype=np.float64)
-            c = np.ascontiguousarray(s.coefs, dtype=np.float64)
-            self._keep += [e, c]
-            sh[i] = ShellDesc(int(s.centre), int(s.l), 1 if s.spherical else 0, int(len(e)),
-                              e.ctypes.data_as(_dp), c.ctypes.data_as(_dp))
-        basis = BasisDesc(int(xyz.shape[0]), xyz.ctypes.data_as(_dp), len(shells), sh)
+        cell, basis = _describe(A, xyz, shells, self._keep)
         km = (ctypes.c_int * 3)(*[int(k) for k in kmesh])
-        prm = Params(float(omega), float(gcut), float(eps_g), float(pair_thresh), int(precision), int(max_dens))
+        prm = Params(float(omega), float(gcut), float(eps_g), float(pair_thresh), int(precision), int(max_dens),
+                     int(chunk_points), int(rho_blocks))
         h = _c_void_p()
         _check(L.ftcj_plan_create(ctypes.byref(cell), ctypes.byref(basis), km, ctypes.byref(prm), ctypes.byref(h)),
                "ftcj_plan_create")
@@ -183,9 +304,10 @@ class Plan:
         self.ng_half = int(inf.ng_half)
 
     @classmethod
-    def from_workload(cls, w, max_dens=None, precision=FTCJ_PREC_FP64):
+    def from_workload(cls, w, max_dens=None, precision=FTCJ_PREC_FP64, chunk_points=0, rho_blocks=0):
         return cls(w.A, w.xyz, w.shells, w.kmesh, w.omega, eps_g=w.eps_g, gcut=w.gcut, pair_thresh=w.pair_thresh,
-                   precision=precision, max_dens=max_dens or w.ndens)
+                   precision=precision, max_dens=max_dens or w.ndens, chunk_points=chunk_points,
+                   rho_blocks=rho_blocks)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
