@@ -202,6 +202,17 @@ int ftcj_jback(ftcj_plan* plan, int ndens, const double* W, double* J0n, void* s
  * ndens <= max_dens. */
 int ftcj_unfold_j(ftcj_plan* plan, int ndens, const double* J0n, double* Jk, void* stream);
 
+/* Nuclear gradient of the long-range energy with D^k held fixed (the
+ * derivatives of the pair transforms with respect to their two centres,
+ * from d/dA [(x-A)^i e^{-a(x-A)^2}] = 2a (x-A)^{i+1} e^{..} - i (x-A)^{i-1} e^{..}
+ * applied to Eq. "FT of cart Gaussians" and the Gaussian product):
+ *   grad[d][C][x] = dE_J[d]/dR_{C,x}  (device double [ndens][ncentre][3]),
+ *   EJ[d]          (device double [ndens]).
+ * The derivative of E_J with respect to D^k is J^k/Nk (ftcj_jbuild).
+ * Runs a2..a5 and a back-contraction one degree higher than the build's, in
+ * FP64 whatever the plan's precision.  Asynchronous on `stream`. */
+int ftcj_grad(ftcj_plan* plan, int ndens, const double* Dk, double* EJ, double* grad, void* stream);
+
 /* Largest |Im D^{0n}| and largest |D^{0n}_{mu nu} - D^{0,-n}_{nu mu}| of
  * the input (host doubles out), i.e. how far D^k is from the precondition.
  * Synchronises `stream`.  ndens <= max_dens. */

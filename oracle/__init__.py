@@ -63,6 +63,9 @@ def _declare(L):
     L.orc_rho_at.argtypes = basis + [_ip, ctypes.c_double, ctypes.c_int, _dp, ctypes.c_int, _ip, _dp,
                                      ctypes.c_int]
     L.orc_rho_at.restype = ctypes.c_int
+    L.orc_grad.argtypes = basis + [_ip, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp,
+                                   ctypes.c_int]
+    L.orc_grad.restype = ctypes.c_int
     L.orc_solid_harmonic.argtypes = [ctypes.c_int, ctypes.c_int, _dp]
     L.orc_solid_harmonic.restype = ctypes.c_int
     L.orc_norms.argtypes = basis + [ctypes.c_int, ctypes.c_int, _dp]
@@ -190,4 +193,17 @@ def norms(w, s, k=0):
     b = _Basis(w.A, w.xyz, w.flat_basis())
     out = np.zeros(w.shells[s].nfunc)
     assert lib().orc_norms(*b.args(), int(s), int(k), _d(out)) == 0
+    return out
+
+
+def grad(w, Dk=None, nthreads: int = 0):
+    """dE_J/dR_C [ndens][ncentre][3] (D^k held fixed)."""
+    b = _Basis(w.A, w.xyz, w.flat_basis())
+    Dk = np.ascontiguousarray(w.Dk if Dk is None else Dk, dtype=np.complex128)
+    out = np.zeros((Dk.shape[0], b.xyz.shape[0], 3))
+    km = np.ascontiguousarray(w.kmesh, dtype=np.int32)
+    rc = lib().orc_grad(*b.args(), _i(km), float(w.omega), gcut_of(w), float(w.pair_thresh), int(Dk.shape[0]),
+                        Dk.ctypes.data_as(_dp), _d(out), int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"orc_grad failed: {rc}")
     return out

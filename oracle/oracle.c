@@ -288,6 +288,82 @@ static void factors1d(int la, int lb, double a, double Ax, double b, double Bx, 
         }
 }
 
+/* d/dA of the 1D factors: d/dA [(x-A)^i e^{-a(x-A)^2}] = 2a (x-A)^{i+1} e^{..} - i (x-A)^{i-1} e^{..},
+ * so dF[i][j]/dA = 2a F[i+1][j] - i F[i-1][j] (same for B with b and j). */
+static void factors1d_deriv(int la, int lb, double a, double Ax, double b, double Bx, double g,
+                            cplx dA[ORC_LMAX + 1][ORC_LMAX + 1], cplx dB[ORC_LMAX + 1][ORC_LMAX + 1])
+{
+    cplx F[ORC_LMAX + 2][ORC_LMAX + 2]; /* factors up to one extra power on either side */
+    {
+        double p = a + b;
+        double mu = a * b / p;
+        double Px = (a * Ax + b * Bx) / p;
+        double PA = Px - Ax, PB = Px - Bx;
+        double H[2 * ORC_LMAX + 4];
+        int n = la + lb + 2;
+        double sp = sqrt(p);
+        hermite(n, g / (2.0 * sp), H);
+        cplx base = exp(-mu * (Ax - Bx) * (Ax - Bx)) * sqrt(M_PI / p) * exp(-g * g / (4.0 * p)) * cexp(-I * g * Px);
+        cplx Tk[2 * ORC_LMAX + 4];
+        cplx fac = 1.0;
+        for (int k = 0; k <= n; ++k) {
+            Tk[k] = base * fac * H[k];
+            fac *= -I / (2.0 * sp);
+        }
+        for (int i = 0; i <= la + 1; ++i)
+            for (int j = 0; j <= lb + 1; ++j) {
+                cplx s = 0.0;
+                for (int r = 0; r <= i; ++r)
+                    for (int t = 0; t <= j; ++t)
+                        s += binom(i, r) * binom(j, t) * ipow(PA, i - r) * ipow(PB, j - t) * Tk[r + t];
+                F[i][j] = s;
+            }
+    }
+    for (int i = 0; i <= la; ++i)
+        for (int j = 0; j <= lb; ++j) {
+            dA[i][j] = 2.0 * a * F[i + 1][j] - (i > 0 ? i * F[i - 1][j] : 0.0);
+            dB[i][j] = 2.0 * b * F[i][j + 1] - (j > 0 ? j * F[i][j - 1] : 0.0);
+        }
+}
+
+/* d/dA_x and d/dB'_x (x = 0,1,2) of one primitive pair's transform block:
+ * outA/outB [3][nfa*nfb]. */
+static void prim_pair_ft_grad(const OShell* sa, int ka, const double* A, const OShell* sb, int kb, const double* Bs,
+                              const double G[3], cplx* outA, cplx* outB, int nfab)
+{
+    double a = sa->ex[ka], b = sb->ex[kb];
+    cplx F[3][ORC_LMAX + 1][ORC_LMAX + 1], dA[3][ORC_LMAX + 1][ORC_LMAX + 1], dB[3][ORC_LMAX + 1][ORC_LMAX + 1];
+    for (int x = 0; x < 3; ++x) {
+        factors1d(sa->l, sb->l, a, A[x], b, Bs[x], G[x], F[x]);
+        factors1d_deriv(sa->l, sb->l, a, A[x], b, Bs[x], G[x], dA[x], dB[x]);
+    }
+    double dd = sa->co[ka] * sb->co[kb];
+    for (int dir = 0; dir < 3; ++dir)
+        for (int side = 0; side < 2; ++side) {
+            cplx C[ORC_MAXC][ORC_MAXC];
+            for (int ca = 0; ca < sa->nc; ++ca)
+                for (int cb = 0; cb < sb->nc; ++cb) {
+                    cplx v = 1.0;
+                    for (int x = 0; x < 3; ++x) {
+                        int i = sa->cx[ca][x], j = sb->cx[cb][x];
+                        v *= (x == dir) ? (side == 0 ? dA[x][i][j] : dB[x][i][j]) : F[x][i][j];
+                    }
+                    C[ca][cb] = v;
+                }
+            cplx* out = (side == 0 ? outA : outB) + (size_t)dir * nfab;
+            for (int fa = 0; fa < sa->nf; ++fa)
+                for (int fb = 0; fb < sb->nf; ++fb) {
+                    cplx sum = 0.0;
+                    for (int ca = 0; ca < sa->nc; ++ca) {
+                        if (sa->U[fa][ca] == 0.0) continue;
+                        for (int cb = 0; cb < sb->nc; ++cb)
+                            if (sb->U[fb][cb] != 0.0) sum += sa->U[fa][ca] * sb->U[fb][cb] * C[ca][cb];
+                    }
+                    out[fa * sb->nf + fb] += dd * sa->nrm[ka * sa->nf + fa] * sb->nrm[kb * sb->nf + fb] * sum;
+                }
+        }
+}
+
 /* transform of one primitive pair: out[fa*nfb + fb] += d_a d_b N N int ... */
 static void prim_pair_ft(const OShell* sa, int ka, const double* A, const OShell* sb, int kb, const double* Bs,
                          const double G[3], cplx* out /* [nfa][nfb] */)
@@ -815,6 +891,144 @@ int orc_norms(ORC_BASIS_ARGS, int s, int k, double* out)
     OSys S;
     if (build_system(&S, ORC_BASIS_PASS)) return -1;
     for (int f = 0; f < S.sh[s].nf; ++f) out[f] = S.sh[s].nrm[k * S.sh[s].nf + f];
+    free_system(&S);
+    return 0;
+}
+
+/* Nuclear gradient of the long-range energy, dE_J/dR_C for every centre C
+ * (D^k fixed):  E_J = 1/2 sum_G v(G) rho(G) rho(-G), so
+ *   dE_J/dR = 1/2 sum_G v(G) [drho(G)/dR rho(-G) + rho(G) drho(-G)/dR],
+ * with drho/dR from the derivatives of the pair transforms with respect to
+ * their two centres (the b centre sits at R_B + R_L).  grad_out: [ndens][ncen][3]. */
+int orc_grad(ORC_BASIS_ARGS, const int* kmesh, double omega, double gcut, double pair_thresh, int ndens,
+             const double* Dk_in, double* grad_out, int nthreads)
+{
+    OSys S;
+    int rc = build_system(&S, ORC_BASIS_PASS);
+    if (rc) return rc;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    int nao = S.nao;
+    int nk = kmesh[0] * kmesh[1] * kmesh[2];
+    size_t nn = (size_t)nao * nao;
+    cplx* D0n = (cplx*)malloc(sizeof(cplx) * (size_t)ndens * nk * nn);
+    fold_density(ndens, kmesh, nao, (const cplx*)Dk_in, D0n);
+    int* gl = NULL;
+    long nG = enumerate_g(&S, gcut, &gl);
+    double* Gc = (double*)malloc(sizeof(double) * 3 * (size_t)(nG > 0 ? nG : 1));
+    double* vG = (double*)malloc(sizeof(double) * (size_t)(nG > 0 ? nG : 1));
+    long* neg = (long*)malloc(sizeof(long) * (size_t)(nG > 0 ? nG : 1));
+    for (long g = 0; g < nG; ++g) {
+        gvec(&S, gl + 3 * g, Gc + 3 * g);
+        double g2 = gnorm2(&S, gl + 3 * g);
+        vG[g] = 4.0 * M_PI * exp(-g2 / (4.0 * omega * omega)) / (S.vol * g2);
+        neg[g] = -1;
+        for (long h = 0; h < nG; ++h)
+            if (gl[3 * h] == -gl[3 * g] && gl[3 * h + 1] == -gl[3 * g + 1] && gl[3 * h + 2] == -gl[3 * g + 2]) {
+                neg[g] = h;
+                break;
+            }
+    }
+    OPair* P = NULL;
+    long np_all = enumerate_pairs(&S, pair_thresh, &P);
+    /* rho(G) first (plain pair loop, as in orc_lrj) */
+    cplx* rho = (cplx*)calloc((size_t)ndens * (size_t)(nG > 0 ? nG : 1), sizeof(cplx));
+    for (long ip = 0; ip < np_all; ++ip) {
+        const OPair* q = &P[ip];
+        const OShell* ha = &S.sh[q->sa];
+        const OShell* hb = &S.sh[q->sb];
+        const double* Ac = xyz + 3 * ha->cen;
+        double Bs[3];
+        for (int x = 0; x < 3; ++x)
+            Bs[x] = xyz[3 * hb->cen + x] + q->L[0] * S.A[0][x] + q->L[1] * S.A[1][x] + q->L[2] * S.A[2][x];
+        int cell = (wrap(q->L[0], kmesh[0]) * kmesh[1] + wrap(q->L[1], kmesh[1])) * kmesh[2] + wrap(q->L[2], kmesh[2]);
+        cplx blk[(2 * ORC_LMAX + 1) * (2 * ORC_LMAX + 1) + ORC_MAXC * ORC_MAXC];
+        for (long g = 0; g < nG; ++g) {
+            memset(blk, 0, sizeof(cplx) * (size_t)(ha->nf * hb->nf));
+            prim_pair_ft(ha, q->ka, Ac, hb, q->kb, Bs, Gc + 3 * g, blk);
+            for (int d = 0; d < ndens; ++d) {
+                const cplx* Dc = D0n + ((size_t)d * nk + cell) * nn;
+                cplx s = 0.0;
+                for (int fa = 0; fa < ha->nf; ++fa)
+                    for (int fb = 0; fb < hb->nf; ++fb)
+                        s += Dc[(size_t)(ha->ao0 + fa) * nao + hb->ao0 + fb] * blk[fa * hb->nf + fb];
+                rho[(size_t)d * nG + g] += s;
+            }
+        }
+    }
+    int ncent = S.ncen;
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+#endif
+    double* gt = (double*)calloc((size_t)nthr * ndens * ncent * 3, sizeof(double));
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double* my = gt + (size_t)tid * ndens * ncent * 3;
+        cplx dA[3 * ((2 * ORC_LMAX + 1) * (2 * ORC_LMAX + 1) + ORC_MAXC * ORC_MAXC)];
+        cplx dB[3 * ((2 * ORC_LMAX + 1) * (2 * ORC_LMAX + 1) + ORC_MAXC * ORC_MAXC)];
+#pragma omp for schedule(static)
+        for (long ip = 0; ip < np_all; ++ip) {
+            const OPair* q = &P[ip];
+            const OShell* ha = &S.sh[q->sa];
+            const OShell* hb = &S.sh[q->sb];
+            const double* Ac = xyz + 3 * ha->cen;
+            double Bs[3];
+            for (int x = 0; x < 3; ++x)
+                Bs[x] = xyz[3 * hb->cen + x] + q->L[0] * S.A[0][x] + q->L[1] * S.A[1][x] + q->L[2] * S.A[2][x];
+            int cell = (wrap(q->L[0], kmesh[0]) * kmesh[1] + wrap(q->L[1], kmesh[1])) * kmesh[2] +
+                       wrap(q->L[2], kmesh[2]);
+            int nfab = ha->nf * hb->nf;
+            for (long g = 0; g < nG; ++g) {
+                memset(dA, 0, sizeof(cplx) * 3 * (size_t)nfab);
+                memset(dB, 0, sizeof(cplx) * 3 * (size_t)nfab);
+                prim_pair_ft_grad(ha, q->ka, Ac, hb, q->kb, Bs, Gc + 3 * g, dA, dB, nfab);
+                /* the same derivatives at -G are the complex conjugates only for real functions;
+                   evaluate -G explicitly */
+                double Gm[3] = {-Gc[3 * g], -Gc[3 * g + 1], -Gc[3 * g + 2]};
+                cplx eA[3 * ((2 * ORC_LMAX + 1) * (2 * ORC_LMAX + 1) + ORC_MAXC * ORC_MAXC)];
+                cplx eB[3 * ((2 * ORC_LMAX + 1) * (2 * ORC_LMAX + 1) + ORC_MAXC * ORC_MAXC)];
+                memset(eA, 0, sizeof(cplx) * 3 * (size_t)nfab);
+                memset(eB, 0, sizeof(cplx) * 3 * (size_t)nfab);
+                prim_pair_ft_grad(ha, q->ka, Ac, hb, q->kb, Bs, Gm, eA, eB, nfab);
+                for (int d = 0; d < ndens; ++d) {
+                    const cplx* Dc = D0n + ((size_t)d * nk + cell) * nn;
+                    cplx rp = rho[(size_t)d * nG + g], rm = rho[(size_t)d * nG + neg[g]];
+                    for (int dir = 0; dir < 3; ++dir) {
+                        cplx sa_ = 0.0, sb_ = 0.0, ta = 0.0, tb = 0.0;
+                        for (int fa = 0; fa < ha->nf; ++fa)
+                            for (int fb = 0; fb < hb->nf; ++fb) {
+                                cplx Dv = Dc[(size_t)(ha->ao0 + fa) * nao + hb->ao0 + fb];
+                                int e = dir * nfab + fa * hb->nf + fb;
+                                sa_ += Dv * dA[e];
+                                sb_ += Dv * dB[e];
+                                ta += Dv * eA[e];
+                                tb += Dv * eB[e];
+                            }
+                        /* 1/2 v [drho(G) rho(-G) + rho(G) drho(-G)] */
+                        my[((size_t)d * ncent + ha->cen) * 3 + dir] += 0.5 * vG[g] * creal(sa_ * rm + rp * ta);
+                        my[((size_t)d * ncent + hb->cen) * 3 + dir] += 0.5 * vG[g] * creal(sb_ * rm + rp * tb);
+                    }
+                }
+            }
+        }
+    }
+    memset(grad_out, 0, sizeof(double) * (size_t)ndens * ncent * 3);
+    for (int t = 0; t < nthr; ++t)
+        for (size_t e = 0; e < (size_t)ndens * ncent * 3; ++e) grad_out[e] += gt[(size_t)t * ndens * ncent * 3 + e];
+    free(gt);
+    free(rho);
+    free(P);
+    free(neg);
+    free(vG);
+    free(Gc);
+    free(gl);
+    free(D0n);
     free_system(&S);
     return 0;
 }

@@ -139,6 +139,24 @@ int ftcj_jbuild_host(ftcj_plan* P, int ndens, const double* Dk_host, double* Jk_
     return FTCJ_OK;
 }
 
+int ftcj_grad(ftcj_plan* P, int ndens, const double* Dk, double* EJ, double* grad, void* stream) {
+    int rc = check(P, ndens, false);
+    if (rc) return rc;
+    if (!Dk || !EJ || !grad) return fail(FTCJ_EINVAL, "null buffer");
+    cudaStream_t s = as_stream(stream);
+    size_t per = (size_t)P->nk * P->nao * P->nao * 2;
+    for (int b0 = 0; b0 < ndens; b0 += P->max_dens) {
+        const int nd = std::min(P->max_dens, ndens - b0);
+        if ((rc = launch_fold(P, nd, Dk + b0 * per, P->d_D0n, s))) return rc;
+        if ((rc = launch_hermite(P, nd, P->d_D0n, s))) return rc;
+        if ((rc = rho_walk(P, nd, s))) return rc;
+        if ((rc = launch_rho_reduce(P, nd, P->d_rho, P->d_W, EJ + b0, nullptr, s))) return rc;
+        if ((rc = launch_j_walk_grad(P, nd, P->d_W, s))) return rc;
+        if ((rc = launch_grad_assemble(P, nd, P->d_D0n, grad + (size_t)b0 * P->ncentre * 3, s))) return rc;
+    }
+    return FTCJ_OK;
+}
+
 int ftcj_check_density(ftcj_plan* P, int ndens, const double* Dk, double* max_imag, double* max_asym,
                        void* stream) {
     int rc = check(P, ndens, true);

@@ -103,7 +103,7 @@ struct ftcj_plan {
     ftcj_params params;
     int max_dens;
     // basis
-    int nao, nshell, ngroup, nmember;
+    int nao, nshell, ngroup, nmember, ncentre;
     std::vector<ftcj::GroupDev> groups;
     std::vector<ftcj::MemberDev> members;
     std::vector<int> member_shell, member_prim, member_group;
@@ -120,6 +120,8 @@ struct ftcj_plan {
     int64_t class_start[ftcj::kNclass + 1];
     int64_t term_base[ftcj::kNclass];  // SoA offset of each class in a per-density term array
     int64_t total_terms;
+    int64_t term_base_g[ftcj::kNclass];  // gradient: terms of degree class + 1
+    int64_t total_terms_g;
     std::vector<ftcj::Tile> tiles;  // ordered by decreasing class
     int npb;                         // rho pass: blocks per (chunk, density)
     int num_sms;
@@ -141,6 +143,7 @@ struct ftcj_plan {
     double* d_cbuf1 = nullptr;
     double* d_Dp = nullptr;          // [max_dens][total_terms]
     double* d_Jp = nullptr;          // [max_dens][nchunks][total_terms]
+    double* d_Jg = nullptr;          // [max_dens][nchunks][total_terms_g] (gradient sums)
     double* d_rho_part = nullptr;    // complex [max_dens][npb][ng_half]
     double* d_rho = nullptr;         // complex [max_dens][ng_half]
     double* d_W = nullptr;           // complex [max_dens][ng_half]
@@ -192,6 +195,7 @@ int fused_fold_supported(const ftcj_plan* P);
 int upload_hermite_tables(ftcj_plan* P);
 int launch_hermite(ftcj_plan* P, int ndens, const double* D0n, cudaStream_t s);
 int launch_jtransform(ftcj_plan* P, int ndens, double* J0n, cudaStream_t s);
+int launch_grad_assemble(ftcj_plan* P, int ndens, const double* D0n, double* grad, cudaStream_t s);
 
 // --- G walks (walk.cu) ---
 int upload_walk_tables(ftcj_plan* P);
@@ -200,6 +204,7 @@ int launch_rho_walk(ftcj_plan* P, int ndens, cudaStream_t s);
 int launch_rho_reduce(ftcj_plan* P, int ndens, double* rho_out, double* W_out, double* EJ_out,
                       const double* rho_in, cudaStream_t s);
 int launch_j_walk(ftcj_plan* P, int ndens, const double* W, cudaStream_t s);
+int launch_j_walk_grad(ftcj_plan* P, int ndens, const double* W, cudaStream_t s);
 int rho_walk_blocks_per_sm(ftcj_plan* P, int* out);
 
 // --- split-precision walks (walk_split.cu) ---

@@ -22,11 +22,12 @@
 namespace ftcj {
 namespace {
 
-constexpr int kTmatSize = 1 + 9 + 36 + 100 + 225;  // sum over lambda <= 4 of nmono^2
+constexpr int kLgrad = kLpair + 1;                        // degree of the gradient sums
+constexpr int kTmatSize = 1 + 9 + 36 + 100 + 225 + 441;  // sum over lambda <= 5 of nmono^2
 
 __constant__ double c_U[kLmax + 1][2][kNcartMax][kNcartMax];  // [l][sph][function][cart]
 __constant__ int c_cart[kLmax + 1][kNcartMax][3];
-__constant__ int c_Toff[kLpair + 1];
+__constant__ int c_Toff[kLgrad + 1];
 
 struct Layout {
     long long start[kNclass + 1];
@@ -241,6 +242,150 @@ __global__ void __launch_bounds__(128) k_jtransform(const PairDev* __restrict__ 
     }
 }
 
+// E^{ij}_t for i <= la1 <= 3, j <= lb1 <= 3 (MD recurrences), for the gradient
+__device__ void ecoef_g(double PA, double PB, double a2p, int la1, int lb1, double E[4][4][7]) {
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j)
+            for (int t = 0; t < 7; ++t) E[i][j][t] = 0.0;
+    E[0][0][0] = 1.0;
+    for (int i = 1; i <= la1; ++i)
+        for (int t = 0; t <= i; ++t)
+            E[i][0][t] = (t > 0 ? a2p * E[i - 1][0][t - 1] : 0.0) + PA * E[i - 1][0][t] +
+                         (t + 1) * E[i - 1][0][t + 1];
+    for (int i = 0; i <= la1; ++i)
+        for (int j = 1; j <= lb1; ++j)
+            for (int t = 0; t <= i + j && t < 7; ++t)
+                E[i][j][t] = (t > 0 ? a2p * E[i][j - 1][t - 1] : 0.0) + PB * E[i][j - 1][t] +
+                             (t + 1 < 7 ? (t + 1) * E[i][j - 1][t + 1] : 0.0);
+}
+
+// sum_tuv E^x_t(a0,b0) E^y_u(a1,b1) E^z_v(a2,b2) J_tuv for Cartesian exponent triples a, b
+__device__ __forceinline__ double cart_contract(const double (*Ex)[4][7], const double (*Ey)[4][7],
+                                                const double (*Ez)[4][7], const int* a, const int* b,
+                                                const double* jt) {
+    double s = 0.0;
+    for (int t = 0; t <= a[0] + b[0]; ++t)
+        for (int u = 0; u <= a[1] + b[1]; ++u) {
+            const double exy = Ex[a[0]][b[0]][t] * Ey[a[1]][b[1]][u];
+            for (int v = 0; v <= a[2] + b[2]; ++v) {
+                const int lam = t + u + v;
+                s += exy * Ez[a[2]][b[2]][v] * jt[lam_offset(lam) + mono_index(lam, t, u)];
+            }
+        }
+    return s;
+}
+
+// Nuclear gradient of E_J, one pair record per thread:
+//   dE/dA_x = sum_{ca,cb} Dcart[ca][cb] (2 alpha S(ca + x, cb) - ca_x S(ca - x, cb)),
+//   dE/dB_x = sum_{ca,cb} Dcart[ca][cb] (2 beta  S(ca, cb + x) - cb_x S(ca, cb - x)),
+// from d/dA [(x-A)^i e^{-alpha (x-A)^2}] = 2 alpha (x-A)^{i+1} e^{..} - i (x-A)^{i-1} e^{..},
+// with S(a, b) the Cartesian contraction of the degree-(L+1) sums J_tuv
+// (= K Re sum_half W g ph (-iG)^tuv).  Dcart is the combined density of the
+// record and its mirror, as in k_hermite, so the mirror's derivative is included.
+__global__ void __launch_bounds__(128) k_grad_assemble(const PairDev* __restrict__ pairs,
+                                                       const GroupDev* __restrict__ G,
+                                                       const MemberDev* __restrict__ mem,
+                                                       const double* __restrict__ D0n,
+                                                       const double* __restrict__ Jg, int nchunks, int nao, int nk,
+                                                       Layout lay, double* __restrict__ grad, int ncentre,
+                                                       const double* __restrict__ Tm, CellConst cc) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int d = blockIdx.y;
+    if (i >= lay.start[kNclass]) return;
+    const PairDev pr = pairs[i];
+    const int L = pr.cls, Lg = L + 1;
+    const long long cnt = lay.start[L + 1] - lay.start[L];
+    const long long loc = i - lay.start[L];
+    double jp[nterms(kLgrad)];
+    const int NT = nterms(Lg);
+    for (int t = 0; t < NT; ++t) {
+        double s = 0.0;
+        for (int c = 0; c < nchunks; ++c)
+            s += Jg[((long long)d * nchunks + c) * lay.total + lay.base[L] + (long long)t * cnt + loc];
+        jp[t] = s;
+    }
+    double jt[nterms(kLgrad)];
+    for (int lam = 0; lam <= Lg; ++lam) {
+        const int nm = nmono(lam), o = lam_offset(lam);
+        const double* T = Tm + c_Toff[lam];
+        for (int a = 0; a < nm; ++a) {
+            double s = 0.0;
+            for (int b = 0; b < nm; ++b) s += T[a * nm + b] * jp[o + b];
+            jt[o + a] = pr.K * s;
+        }
+    }
+    const GroupDev A = G[pr.ga];
+    const GroupDev B = G[pr.gb];
+    double E[3][4][4][7];
+    {
+        const double Av[3] = {A.x, A.y, A.z};
+        const double Bv[3] = {B.x, B.y, B.z};
+        const double a2p = 0.5 / pr.p;
+        for (int x = 0; x < 3; ++x) {
+            const double Bs = Bv[x] + pr.L[0] * cc.A[x] + pr.L[1] * cc.A[3 + x] + pr.L[2] * cc.A[6 + x];
+            ecoef_g(pr.P[x] - Av[x], pr.P[x] - Bs, a2p, A.lmax + 1, B.lmax + 1, E[x]);
+        }
+    }
+    double gA[3] = {0.0, 0.0, 0.0}, gB[3] = {0.0, 0.0, 0.0};
+    const long long nn = (long long)nao * nao;
+    const double* Dc = D0n + ((long long)d * nk + pr.cell) * nn;
+    const double* Dm = D0n + ((long long)d * nk + pr.mcell) * nn;
+    for (int ia = A.mem0; ia < A.mem1; ++ia) {
+        const MemberDev ma = mem[ia];
+        const int nfa = nfunc(ma.l, ma.sph), nca = (ma.l + 1) * (ma.l + 2) / 2;
+        for (int ib = B.mem0; ib < B.mem1; ++ib) {
+            const MemberDev mb = mem[ib];
+            const int nfb = nfunc(mb.l, mb.sph), ncb = (mb.l + 1) * (mb.l + 2) / 2;
+            double tmp[kNcartMax][kNcartMax];
+            for (int f = 0; f < nfa; ++f)
+                for (int cb = 0; cb < ncb; ++cb) {
+                    double s = 0.0;
+                    for (int q = 0; q < nfb; ++q) {
+                        const double u = c_U[mb.l][mb.sph][q][cb];
+                        if (u == 0.0) continue;
+                        double dv = Dc[(long long)(ma.ao + f) * nao + mb.ao + q];
+                        if (pr.weight == 2) dv += Dm[(long long)(mb.ao + q) * nao + ma.ao + f];
+                        s += u * dv;
+                    }
+                    tmp[f][cb] = s;
+                }
+            const double coef = ma.coef * mb.coef;
+            for (int ca = 0; ca < nca; ++ca) {
+                const int* xa = c_cart[ma.l][ca];
+                for (int cb = 0; cb < ncb; ++cb) {
+                    double dcart = 0.0;
+                    for (int f = 0; f < nfa; ++f) dcart += c_U[ma.l][ma.sph][f][ca] * tmp[f][cb];
+                    dcart *= coef;
+                    if (dcart == 0.0) continue;
+                    const int* xb = c_cart[mb.l][cb];
+                    for (int x = 0; x < 3; ++x) {
+                        int a2[3] = {xa[0], xa[1], xa[2]};
+                        int b2[3] = {xb[0], xb[1], xb[2]};
+                        a2[x] += 1;
+                        double s = 2.0 * A.alpha * cart_contract(E[0], E[1], E[2], a2, xb, jt);
+                        if (xa[x] > 0) {
+                            a2[x] -= 2;
+                            s -= xa[x] * cart_contract(E[0], E[1], E[2], a2, xb, jt);
+                        }
+                        gA[x] += dcart * s;
+                        b2[x] += 1;
+                        double t = 2.0 * B.alpha * cart_contract(E[0], E[1], E[2], xa, b2, jt);
+                        if (xb[x] > 0) {
+                            b2[x] -= 2;
+                            t -= xb[x] * cart_contract(E[0], E[1], E[2], xa, b2, jt);
+                        }
+                        gB[x] += dcart * t;
+                    }
+                }
+            }
+        }
+    }
+    for (int x = 0; x < 3; ++x) {
+        atomicAdd(grad + ((long long)d * ncentre + A.centre) * 3 + x, gA[x]);
+        atomicAdd(grad + ((long long)d * ncentre + B.centre) * 3 + x, gB[x]);
+    }
+}
+
 Layout make_layout(const ftcj_plan* P) {
     Layout l;
     for (int c = 0; c <= kNclass; ++c) l.start[c] = P->class_start[c];
@@ -308,9 +453,9 @@ int upload_hermite_tables(ftcj_plan* P) {
     if (need_const) FTCJ_CUDA(cudaMemcpyToSymbol(c_U, U, sizeof(U)));
     // G_x^t G_y^u G_z^v with G_x = sum_i n_i B[i][x]: expand as polynomials in (n1, n2, n3)
     std::vector<double> T(kTmatSize, 0.0);
-    int Toff[kLpair + 1];
+    int Toff[kLgrad + 1];
     int off = 0;
-    for (int lam = 0; lam <= kLpair; ++lam) {
+    for (int lam = 0; lam <= kLgrad; ++lam) {
         Toff[lam] = off;
         int nm = nmono(lam);
         for (int t = lam; t >= 0; --t)
@@ -361,6 +506,19 @@ int launch_hermite(ftcj_plan* P, int ndens, const double* D0n, cudaStream_t s) {
     else
         k_hermite<false><<<g, 128, 0, s>>>(P->d_pairs, P->d_groups, P->d_members, D0n, P->nao, P->nk,
                                            make_layout(P), P->d_Dp, P->d_Tmat, P->cc);
+    FTCJ_CUDA(cudaGetLastError());
+    return FTCJ_OK;
+}
+
+int launch_grad_assemble(ftcj_plan* P, int ndens, const double* D0n, double* grad, cudaStream_t s) {
+    FTCJ_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * (size_t)ndens * P->ncentre * 3, s));
+    if (P->npairs == 0) return FTCJ_OK;
+    Layout lg = make_layout(P);
+    for (int c = 0; c < kNclass; ++c) lg.base[c] = P->term_base_g[c];
+    lg.total = P->total_terms_g;
+    dim3 g((unsigned)((P->npairs + 127) / 128), ndens);
+    k_grad_assemble<<<g, 128, 0, s>>>(P->d_pairs, P->d_groups, P->d_members, D0n, P->d_Jg, (int)P->chunks.size(),
+                                      P->nao, P->nk, lg, grad, P->ncentre, P->d_Tmat, P->cc);
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }

@@ -201,7 +201,7 @@ void free_device(ftcj_plan* P) {
     void* ptrs[] = {P->d_groups, P->d_members, P->d_pairs, P->d_walk, P->d_lines, P->d_chunks, P->d_tiles,
                     P->d_gvec, P->d_vg, P->d_tw, P->d_Tmat, P->d_D0n, P->d_J0n, P->d_cbuf0, P->d_cbuf1,
                     P->d_Dp, P->d_Jp, P->d_rho_part, P->d_rho, P->d_W, P->d_Epart, P->d_Dk_stage,
-                    P->d_Jk_stage, P->d_EJ_stage, P->d_check, P->d_split_init, P->d_split_const};
+                    P->d_Jk_stage, P->d_EJ_stage, P->d_check, P->d_split_init, P->d_split_const, P->d_Jg};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -273,6 +273,7 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     for (int i = 0; i < 3 * basis->ncentre; ++i)
         if (!finite(basis->xyz[i])) return fail(FTCJ_EINVAL, "non-finite centre");
     P->nshell = basis->nshell;
+    P->ncentre = basis->ncentre;
     int ao = 0;
     double amin = 1e300;
     struct Mem {
@@ -358,9 +359,12 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
 
     // per-class SoA layout of the Hermite terms
     P->total_terms = 0;
+    P->total_terms_g = 0;
     for (int c = 0; c < kNclass; ++c) {
         P->term_base[c] = P->total_terms;
         P->total_terms += (P->class_start[c + 1] - P->class_start[c]) * nterms(c);
+        P->term_base_g[c] = P->total_terms_g;
+        P->total_terms_g += (P->class_start[c + 1] - P->class_start[c]) * nterms(c + 1);
     }
     P->tiles.clear();
     for (int c = kNclass - 1; c >= 0; --c)
@@ -390,6 +394,7 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     if ((rc = dalloc(P, &P->d_cbuf1, 2 * md * P->nk * nn))) return rc;
     if ((rc = dalloc(P, &P->d_Dp, md * (size_t)P->total_terms))) return rc;
     if ((rc = dalloc(P, &P->d_Jp, md * (size_t)nch * (size_t)P->total_terms))) return rc;
+    if ((rc = dalloc(P, &P->d_Jg, md * (size_t)nch * (size_t)P->total_terms_g))) return rc;
     if ((rc = dalloc(P, &P->d_rho_part, 2 * md * (size_t)P->npb * (size_t)P->ng_half))) return rc;
     if ((rc = dalloc(P, &P->d_rho, 2 * md * (size_t)P->ng_half))) return rc;
     if ((rc = dalloc(P, &P->d_W, 2 * md * (size_t)P->ng_half))) return rc;

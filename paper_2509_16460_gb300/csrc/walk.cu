@@ -35,6 +35,8 @@ struct Layout {
     long long total;
 };
 
+constexpr int kPw = kLpair + 2;  // powers n1^0..n1^(L+1) in the J walks' table
+
 struct WalkState {
     double gC, TF, RF0, RB0, rF0, rB0, phCr, phCi;  // plane centre (0, 0, n3)
     double gL, Rd, rF, rB, phLr, phLi;              // line centre (0, n2, n3)
@@ -368,6 +370,8 @@ __global__ void __launch_bounds__(256) k_energy_final(const double* __restrict__
 
 // ---- J -------------------------------------------------------------------
 
+// L is the polynomial degree walked (the record's class, or class + 1 for the
+// gradient); the term layout is that of the record's class tl.cls.
 template <int L>
 __device__ void j_tile(const double* M6, const Tile& tl, const Layout& lay, const PairWalk* __restrict__ walk,
                        const WLine* __restrict__ lines, const WChunk ch, const double2* __restrict__ wsm,
@@ -376,8 +380,8 @@ __device__ void j_tile(const double* M6, const Tile& tl, const Layout& lay, cons
     const int tid = threadIdx.x;
     const bool valid = tid < tl.count;
     const long long pi = (long long)tl.first + tid;
-    const long long cnt = lay.start[L + 1] - lay.start[L];
-    const long long loc = pi - lay.start[L];
+    const long long cnt = lay.start[tl.cls + 1] - lay.start[tl.cls];
+    const long long loc = pi - lay.start[tl.cls];
     const PairWalk w = valid ? walk[pi] : idle_walk();
     double J[NT];
 #pragma unroll
@@ -403,7 +407,7 @@ __device__ void j_tile(const double* M6, const Tile& tl, const Layout& lay, cons
                     const double tr = gr * W.x - gi * W.y, ti = gr * W.y + gi * W.x;
                     Ar[0] += tr;
                     Ai[0] += ti;
-                    const double* pwm = pw + (m - n1min) * 5;
+                    const double* pwm = pw + (m - n1min) * kPw;
 #pragma unroll
                     for (int i = 1; i <= L; ++i) {
                         Ar[i] = fma(tr, pwm[i], Ar[i]);
@@ -425,7 +429,7 @@ __device__ void j_tile(const double* M6, const Tile& tl, const Layout& lay, cons
                     const double tr = gr * W.x - gi * W.y, ti = gr * W.y + gi * W.x;
                     Ar[0] += tr;
                     Ai[0] += ti;
-                    const double* pwm = pw + (m - n1min) * 5;
+                    const double* pwm = pw + (m - n1min) * kPw;
 #pragma unroll
                     for (int i = 1; i <= L; ++i) {
                         Ar[i] = fma(tr, pwm[i], Ar[i]);
@@ -461,10 +465,13 @@ __device__ void j_tile(const double* M6, const Tile& tl, const Layout& lay, cons
     }
     if (valid) {
 #pragma unroll
-        for (int t = 0; t < NT; ++t) Jp_dc[lay.base[L] + (long long)t * cnt + loc] = J[t];
+        for (int t = 0; t < NT; ++t) Jp_dc[lay.base[tl.cls] + (long long)t * cnt + loc] = J[t];
     }
 }
 
+// EXTRA = 0: the back-contraction of degree L; EXTRA = 1: degree L + 1, the
+// sums the nuclear gradient needs (one more power of G from d/dR).
+template <int EXTRA>
 __global__ void __launch_bounds__(kTile) k_j_walk(const Tile* __restrict__ tiles, Layout lay,
                                                   const PairWalk* __restrict__ walk, const WLine* __restrict__ lines,
                                                   const WChunk* __restrict__ chunks, int nchunks,
@@ -478,21 +485,24 @@ __global__ void __launch_bounds__(kTile) k_j_walk(const Tile* __restrict__ tiles
     double* pw = reinterpret_cast<double*>(smem + max_chunk_pts);
     const double2* Wd = W + (long long)d * ng_half + ch.p0;
     for (int i = threadIdx.x; i < npts; i += blockDim.x) wsm[i] = Wd[i];
-    for (int i = threadIdx.x; i < n1cnt * 5; i += blockDim.x) {
-        const double x = (double)(n1min + i / 5);
+    for (int i = threadIdx.x; i < n1cnt * kPw; i += blockDim.x) {
+        const double x = (double)(n1min + i / kPw);
         double v = 1.0;
-        for (int e = 0; e < i % 5; ++e) v *= x;
+        for (int e = 0; e < i % kPw; ++e) v *= x;
         pw[i] = v;
     }
     __syncthreads();
     const Tile tl = tiles[tix];
     double* Jp_dc = Jp + ((long long)d * nchunks + cidx) * lay.total;
-    switch (tl.cls) {
+    switch (tl.cls + EXTRA) {
         case 0: j_tile<0>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
         case 1: j_tile<1>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
         case 2: j_tile<2>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
         case 3: j_tile<3>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
-        default: j_tile<4>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
+        case 4: j_tile<4>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
+        default:
+            if (EXTRA) j_tile<5>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc);
+            break;
     }
 }
 
@@ -513,13 +523,21 @@ Layout make_layout(const ftcj_plan* P) {
     return l;
 }
 
+Layout make_grad_layout(const ftcj_plan* P) {
+    Layout l;
+    for (int c = 0; c <= kNclass; ++c) l.start[c] = P->class_start[c];
+    for (int c = 0; c < kNclass; ++c) l.base[c] = P->term_base_g[c];
+    l.total = P->total_terms_g;
+    return l;
+}
+
 size_t rho_smem_bytes(const ftcj_plan* P) {
     return sizeof(double2) * ((size_t)kBatch * (kTile + 1) + kTile + (size_t)std::max(P->max_chunk_pts, 1));
 }
 
 size_t j_smem_bytes(const ftcj_plan* P) {
     int n1cnt = P->n1_max - P->n1_min + 1;
-    return sizeof(double2) * (size_t)std::max(P->max_chunk_pts, 1) + sizeof(double) * 5 * (size_t)n1cnt;
+    return sizeof(double2) * (size_t)std::max(P->max_chunk_pts, 1) + sizeof(double) * kPw * (size_t)n1cnt;
 }
 
 }  // namespace
@@ -527,7 +545,9 @@ size_t j_smem_bytes(const ftcj_plan* P) {
 int upload_walk_tables(ftcj_plan* P) {
     int rc = allow_dynamic_smem((const void*)k_rho_walk, rho_smem_bytes(P));
     if (rc) return rc;
-    return allow_dynamic_smem((const void*)k_j_walk, j_smem_bytes(P));
+    rc = allow_dynamic_smem((const void*)k_j_walk<0>, j_smem_bytes(P));
+    if (rc) return rc;
+    return allow_dynamic_smem((const void*)k_j_walk<1>, j_smem_bytes(P));
 }
 
 int rho_walk_blocks_per_sm(ftcj_plan* P, int* out) {
@@ -589,9 +609,30 @@ int launch_j_walk(ftcj_plan* P, int ndens, const double* W, cudaStream_t s) {
     }
     dim3 g((unsigned)P->tiles.size(), nch, ndens);
     int n1cnt = P->n1_max - P->n1_min + 1;
-    k_j_walk<<<g, kTile, j_smem_bytes(P), s>>>(P->d_tiles, make_layout(P), P->d_walk, P->d_lines, P->d_chunks, nch,
+    k_j_walk<0><<<g, kTile, j_smem_bytes(P), s>>>(P->d_tiles, make_layout(P), P->d_walk, P->d_lines, P->d_chunks, nch,
                                                reinterpret_cast<const double2*>(W), P->ng_half, P->n1_min, n1cnt,
                                                P->max_chunk_pts, P->d_Jp, P->cc);
+    FTCJ_CUDA(cudaGetLastError());
+    return FTCJ_OK;
+}
+
+}  // namespace ftcj
+
+namespace ftcj {
+
+// the degree-(L+1) back-contraction sums of the nuclear gradient, into d_Jg
+int launch_j_walk_grad(ftcj_plan* P, int ndens, const double* W, cudaStream_t s) {
+    int nch = (int)P->chunks.size();
+    if (P->tiles.empty()) return FTCJ_OK;
+    if (P->ng_half == 0) {
+        FTCJ_CUDA(cudaMemsetAsync(P->d_Jg, 0, sizeof(double) * (size_t)ndens * std::max(nch, 1) * P->total_terms_g, s));
+        return FTCJ_OK;
+    }
+    dim3 g((unsigned)P->tiles.size(), nch, ndens);
+    int n1cnt = P->n1_max - P->n1_min + 1;
+    k_j_walk<1><<<g, kTile, j_smem_bytes(P), s>>>(P->d_tiles, make_grad_layout(P), P->d_walk, P->d_lines,
+                                                  P->d_chunks, nch, reinterpret_cast<const double2*>(W), P->ng_half,
+                                                  P->n1_min, n1cnt, P->max_chunk_pts, P->d_Jg, P->cc);
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }

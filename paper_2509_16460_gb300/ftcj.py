@@ -62,7 +62,7 @@ EXPORTED = [
     "ftcj_get_gvectors", "ftcj_get_pairs", "ftcj_get_groups", "ftcj_strerror", "ftcj_last_error",
     "ftcj_profile_enable", "ftcj_profile_read", "ftcj_launches_per_batch", "ftcj_probe_fma_peak",
     "ftcj_potential_noalloc", "ftcj_batch_create", "ftcj_batch_info", "ftcj_batch_jbuild", "ftcj_batch_capture",
-    "ftcj_batch_replay", "ftcj_batch_destroy", "ftcj_autotune",
+    "ftcj_batch_replay", "ftcj_batch_destroy", "ftcj_autotune", "ftcj_grad",
 ]
 
 FTCJ_BATCH_AUTOTUNE = 1
@@ -125,6 +125,7 @@ def _declare(L):
     L.ftcj_batch_destroy.restype = None
     L.ftcj_autotune.argtypes = [ctypes.POINTER(Cell), ctypes.POINTER(BasisDesc), _ip, ctypes.POINTER(Params),
                                 ctypes.POINTER(Params), _dp]
+    L.ftcj_grad.argtypes = [P, _c_int, P, P, P, P]
     L.ftcj_strerror.argtypes = [_c_int]
     L.ftcj_strerror.restype = ctypes.c_char_p
     L.ftcj_last_error.argtypes = []
@@ -302,6 +303,8 @@ class Plan:
         self.nao = inf.nao
         self.nk = inf.nk
         self.ng_half = int(inf.ng_half)
+        self.ncentre = int(np.asarray(xyz).reshape(-1, 3).shape[0])
+        self.xyz = np.array(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
 
     @classmethod
     def from_workload(cls, w, max_dens=None, precision=FTCJ_PREC_FP64, chunk_points=0, rho_blocks=0):
@@ -407,6 +410,21 @@ class Plan:
                                    _dev_ptr(Jk, torch.complex128, shp, "Jk"), _stream_ptr(stream)), "ftcj_unfold_j")
         return Jk
 
+    def grad(self, Dk, EJ=None, grad=None, stream=None):
+        """(E_J, dE_J/dR_C) with D^k fixed: device tensors [ndens], [ndens, ncentre, 3]."""
+        import torch
+        nd = Dk.shape[0]
+        shp = (nd, self.nk, self.nao, self.nao)
+        nc = self.ncentre
+        if EJ is None:
+            EJ = torch.empty(nd, dtype=torch.float64, device=Dk.device)
+        if grad is None:
+            grad = torch.empty((nd, nc, 3), dtype=torch.float64, device=Dk.device)
+        _check(lib().ftcj_grad(self._h, nd, _dev_ptr(Dk, torch.complex128, shp, "Dk"),
+                               _dev_ptr(EJ, torch.float64, (nd,), "EJ"),
+                               _dev_ptr(grad, torch.float64, (nd, nc, 3), "grad"), _stream_ptr(stream)), "ftcj_grad")
+        return EJ, grad
+
     def check_density(self, Dk, stream=None):
         import torch
         nd = Dk.shape[0]
@@ -483,3 +501,52 @@ def potential_noalloc(A, omega, gvec, rho, W=None, EJ=None, stream=None):
                                         _dev_ptr(EJ, torch.float64, (nd,), "EJ"), _stream_ptr(stream)),
            "ftcj_potential_noalloc")
     return W, EJ
+
+
+def _autograd_function():
+    import torch
+
+    class LongRangeCoulomb(torch.autograd.Function):
+        """E_J(D^k, R) of a plan, differentiable in both arguments.
+
+        forward(Dk, xyz, plan) -> E_J [ndens]; the plan must have been made for
+        the centres xyz (positions are not rebuilt here).
+        backward: dE/dD^k = J^k / Nk (the PyTorch gradient d/dRe + i d/dIm of
+        the real energy), dE/dR from ftcj_grad (summed over densities with the
+        incoming weights)."""
+
+        @staticmethod
+        def forward(ctx, Dk, xyz, plan):
+            if not np.allclose(xyz.detach().cpu().numpy(), plan.xyz, rtol=0, atol=1e-12):
+                raise FtcjError("xyz differs from the geometry the plan was made for")
+            Jk, EJ = plan.jbuild(Dk)
+            ctx.plan = plan
+            ctx.xyz_device = xyz.device
+            ctx.xyz_dtype = xyz.dtype
+            ctx.save_for_backward(Dk, Jk)
+            return EJ
+
+        @staticmethod
+        def backward(ctx, gE):
+            Dk, Jk = ctx.saved_tensors
+            plan = ctx.plan
+            gD = gx = None
+            if ctx.needs_input_grad[0]:
+                gD = gE.to(Jk.dtype).view(-1, 1, 1, 1) * Jk / plan.nk
+            if ctx.needs_input_grad[1]:
+                _, g = plan.grad(Dk)
+                gx = (gE.view(-1, 1, 1) * g).sum(0).to(device=ctx.xyz_device, dtype=ctx.xyz_dtype)
+            return gD, gx, None
+
+    return LongRangeCoulomb
+
+
+_LRC = None
+
+
+def long_range_energy(Dk, xyz, plan):
+    """Differentiable E_J (see LongRangeCoulomb): torch.autograd gives dE/dD^k and dE/dR."""
+    global _LRC
+    if _LRC is None:
+        _LRC = _autograd_function()
+    return _LRC.apply(Dk, xyz, plan)

@@ -1,0 +1,102 @@
+"""Nuclear gradient (ftcj_grad) and the autograd.Function on the GPU, against
+the oracle's analytic gradient and central finite differences."""
+import numpy as np
+import pytest
+
+from paper_2509_16460_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2509_16460_gb300 import build
+    build.build()
+    from paper_2509_16460_gb300 import ftcj
+    return ftcj
+
+
+def dk(w):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(w.Dk)).cuda()
+
+
+SYSTEMS = {
+    "tiny-triclinic": lambda: W.tiny(seed=61, A=np.array([[5.0, 0.0, 0.0], [0.9, 5.3, 0.0], [-0.4, 0.6, 5.6]]),
+                                     kmesh=(2, 1, 1), centres=[[0.1, 0.2, 0.3], [1.5, 0.7, -0.5]], ndens=2),
+    "cfg1": lambda: W.cfg1(),
+    "cartesian-multishell": lambda: W.tiny(seed=62, A=np.diag([5.2, 4.9, 5.5]), kmesh=(1, 2, 1), spherical=False,
+                                           shell_spec=[(0, 0, [1.2]), (0, 1, [1.2]), (0, 2, [0.8]),
+                                                       (1, 1, [0.6]), (1, 2, [1.4])]),
+}
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_gradient_matches_oracle(orc, F, name):
+    import torch
+    w = SYSTEMS[name]()
+    ref = orc.grad(w)
+    for prec in (F.FTCJ_PREC_FP64, F.FTCJ_PREC_SPLIT):
+        p = F.Plan.from_workload(w, precision=prec)
+        E, g = p.grad(dk(w))
+        torch.cuda.synchronize()
+        g = g.cpu().numpy()
+        scale = max(1.0, np.abs(ref).max())
+        assert np.abs(g - ref).max() <= 1e-10 * scale, (name, prec, np.abs(g - ref).max())
+        assert np.abs(g.sum(axis=1)).max() <= 1e-10 * scale  # translational invariance
+        p.close()
+
+
+def test_gradient_central_differences_of_gpu_energy(F):
+    """dE/dR from ftcj_grad against (E(R+h) - E(R-h)) / 2h of GPU builds at displaced
+    geometries (new plans), h = 1e-4 bohr."""
+    import torch
+    w = SYSTEMS["tiny-triclinic"]()
+    p = F.Plan.from_workload(w)
+    _, g = p.grad(dk(w))
+    g = g.cpu().numpy()
+    p.close()
+    h = 1e-4
+    x0 = w.xyz.copy()
+    for c in range(2):
+        for d in range(3):
+            e = []
+            for sgn in (1, -1):
+                w.xyz = x0.copy()
+                w.xyz[c, d] += sgn * h
+                q = F.Plan.from_workload(w)
+                _, E = q.jbuild(dk(w))
+                torch.cuda.synchronize()
+                e.append(E.cpu().numpy())
+                q.close()
+            fd = (e[0] - e[1]) / (2 * h)
+            assert np.abs(fd - g[:, c, d]).max() <= 1e-7 * max(1.0, np.abs(fd).max()), (c, d, fd, g[:, c, d])
+    w.xyz = x0
+
+
+def test_autograd_function(F):
+    """torch.autograd through long_range_energy: dE/dD^k = J^k/Nk checked by a
+    directional central difference (exact for the quadratic E_J), dE/dR by ftcj_grad."""
+    import torch
+    w = SYSTEMS["tiny-triclinic"]()
+    p = F.Plan.from_workload(w)
+    D = dk(w).requires_grad_(True)
+    xyz = torch.tensor(w.xyz, dtype=torch.float64, requires_grad=True)
+    E = F.long_range_energy(D, xyz, p)
+    (E * torch.tensor([1.0, 0.5], dtype=torch.float64, device=E.device)).sum().backward()
+    rng = np.random.default_rng(3)
+    dirn = torch.from_numpy(rng.normal(size=w.Dk.shape) + 1j * rng.normal(size=w.Dk.shape)).cuda()
+    h = 1e-3
+    with torch.no_grad():
+        _, Ep = p.jbuild((D + h * dirn).contiguous())
+        _, Em = p.jbuild((D - h * dirn).contiguous())
+        fd = float(((Ep - Em) / (2 * h) * torch.tensor([1.0, 0.5], device=Ep.device, dtype=torch.float64)).sum())
+    an = float((torch.conj(D.grad) * dirn).real.sum())
+    assert abs(fd - an) <= 1e-9 * max(1.0, abs(fd)), (fd, an)
+    _, g = p.grad(D.detach())
+    gref = (g[0] + 0.5 * g[1]).cpu()
+    assert float((xyz.grad - gref).abs().max()) <= 1e-12 * max(1.0, float(gref.abs().max()))
+    p.close()
