@@ -40,7 +40,7 @@ int build_batch(ftcj_plan* P, int nd, const double* Dk, double* Jk, double* EJ, 
     if ((rc = mark(0))) return rc;
     if ((rc = launch_fold(P, nd, Dk, P->d_D0n, s))) return rc;
     if ((rc = mark(1))) return rc;
-    if ((rc = launch_hermite(P, nd, P->d_D0n, s))) return rc;
+    if ((rc = launch_hermite_map(P, nd, P->d_D0n, s))) return rc;
     if ((rc = mark(2))) return rc;
     if ((rc = rho_walk(P, nd, s))) return rc;
     if ((rc = mark(3))) return rc;
@@ -48,7 +48,7 @@ int build_batch(ftcj_plan* P, int nd, const double* Dk, double* Jk, double* EJ, 
     if ((rc = mark(4))) return rc;
     if ((rc = j_walk(P, nd, P->d_W, s))) return rc;
     if ((rc = mark(5))) return rc;
-    if ((rc = launch_jtransform(P, nd, P->d_J0n, s))) return rc;
+    if ((rc = launch_jtransform_map(P, nd, P->d_J0n, s))) return rc;
     if ((rc = mark(6))) return rc;
     if ((rc = launch_unfold(P, nd, P->d_J0n, Jk, s))) return rc;
     if ((rc = mark(7))) return rc;
@@ -71,7 +71,7 @@ int ftcj_rho(ftcj_plan* P, int ndens, const double* D0n, double* rho, void* stre
     if (rc) return rc;
     if (!D0n || !rho) return fail(FTCJ_EINVAL, "null buffer");
     cudaStream_t s = as_stream(stream);
-    if ((rc = launch_hermite(P, ndens, D0n, s))) return rc;
+    if ((rc = launch_hermite_map(P, ndens, D0n, s))) return rc;
     if ((rc = rho_walk(P, ndens, s))) return rc;
     return launch_rho_reduce(P, ndens, rho, nullptr, nullptr, nullptr, s);
 }
@@ -96,7 +96,7 @@ int ftcj_jback(ftcj_plan* P, int ndens, const double* W, double* J0n, void* stre
     if (!W || !J0n) return fail(FTCJ_EINVAL, "null buffer");
     cudaStream_t s = as_stream(stream);
     if ((rc = j_walk(P, ndens, W, s))) return rc;
-    return launch_jtransform(P, ndens, J0n, s);
+    return launch_jtransform_map(P, ndens, J0n, s);
 }
 
 int ftcj_unfold_j(ftcj_plan* P, int ndens, const double* J0n, double* Jk, void* stream) {
@@ -148,7 +148,7 @@ int ftcj_grad(ftcj_plan* P, int ndens, const double* Dk, double* EJ, double* gra
     for (int b0 = 0; b0 < ndens; b0 += P->max_dens) {
         const int nd = std::min(P->max_dens, ndens - b0);
         if ((rc = launch_fold(P, nd, Dk + b0 * per, P->d_D0n, s))) return rc;
-        if ((rc = launch_hermite(P, nd, P->d_D0n, s))) return rc;
+        if ((rc = launch_hermite_map(P, nd, P->d_D0n, s))) return rc;
         if ((rc = rho_walk(P, nd, s))) return rc;
         if ((rc = launch_rho_reduce(P, nd, P->d_rho, P->d_W, EJ + b0, nullptr, s))) return rc;
         if ((rc = launch_j_walk_grad(P, nd, P->d_W, s))) return rc;

@@ -81,6 +81,21 @@ struct Tile {
     int cls, first, count, pad;  // pairs [first, first+count) of one class
 };
 
+// Per-class layout of the Hermite-term arrays (SoA within each class).
+struct MapLayout {
+    long long start[kNclass + 1];
+    long long base[kNclass];
+    long long total;
+};
+
+// Flattened thread ranges of a per-record kernel: class c owns threads
+// [tstart[c], tstart[c+1]), slots[c] threads per record from record rstart[c].
+struct MapThreads {
+    long long tstart[kNclass + 1];
+    long long rstart[kNclass];
+    int slots[kNclass];
+};
+
 // Per-cell constants, passed to kernels by value (so plans of different cells
 // can be alive and used together).
 struct CellConst {
@@ -144,6 +159,10 @@ struct ftcj_plan {
     double* d_Dp = nullptr;          // [max_dens][total_terms]
     double* d_Jp = nullptr;          // [max_dens][nchunks][total_terms]
     double* d_Jg = nullptr;          // [max_dens][nchunks][total_terms_g] (gradient sums)
+    double* d_maps = nullptr;        // per-record maps AO block -> D'_ijk, see hmap.cu
+    long long* d_map_off = nullptr;  // [npairs + 1]
+    long long map_doubles = 0;
+    ftcj::MapThreads mt_terms, mt_outs;
     double* d_rho_part = nullptr;    // complex [max_dens][npb][ng_half]
     double* d_rho = nullptr;         // complex [max_dens][ng_half]
     double* d_W = nullptr;           // complex [max_dens][ng_half]
@@ -193,9 +212,13 @@ int fused_fold_supported(const ftcj_plan* P);
 
 // --- Hermite densities and J back-transform (hermite.cu) ---
 int upload_hermite_tables(ftcj_plan* P);
-int launch_hermite(ftcj_plan* P, int ndens, const double* D0n, cudaStream_t s);
-int launch_jtransform(ftcj_plan* P, int ndens, double* J0n, cudaStream_t s);
 int launch_grad_assemble(ftcj_plan* P, int ndens, const double* D0n, double* grad, cudaStream_t s);
+void host_hermite_tables(const ftcj_plan* P, std::vector<double>& U, std::vector<int>& cart, std::vector<int>& Toff);
+
+// --- per-record maps of the Hermite-density contraction (hmap.cu) ---
+int build_maps(ftcj_plan* P);
+int launch_hermite_map(ftcj_plan* P, int ndens, const double* D0n, cudaStream_t s);
+int launch_jtransform_map(ftcj_plan* P, int ndens, double* J0n, cudaStream_t s);
 
 // --- G walks (walk.cu) ---
 int upload_walk_tables(ftcj_plan* P);

@@ -37,211 +37,6 @@ struct Layout {
 
 __device__ __forceinline__ int nfunc(int l, int sph) { return sph ? 2 * l + 1 : (l + 1) * (l + 2) / 2; }
 
-// E^{ij}_t for i <= 2, j <= 2, t <= 4 along one axis (MD recurrences)
-__device__ void ecoef(double PA, double PB, double a2p, int la, int lb, double E[3][3][5]) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-            for (int t = 0; t < 5; ++t) E[i][j][t] = 0.0;
-    E[0][0][0] = 1.0;
-    for (int i = 1; i <= la; ++i)
-        for (int t = 0; t <= i; ++t)
-            E[i][0][t] = (t > 0 ? a2p * E[i - 1][0][t - 1] : 0.0) + PA * E[i - 1][0][t] +
-                         (t + 1) * E[i - 1][0][t + 1];
-    for (int i = 0; i <= la; ++i)
-        for (int j = 1; j <= lb; ++j)
-            for (int t = 0; t <= i + j; ++t)
-                E[i][j][t] = (t > 0 ? a2p * E[i][j - 1][t - 1] : 0.0) + PB * E[i][j - 1][t] +
-                             (t + 1 <= 4 ? (t + 1) * E[i][j - 1][t + 1] : 0.0);
-}
-
-struct PairGeom {
-    double E[3][3][3][5];  // [axis][i][j][t]
-};
-
-__device__ void pair_geom(const PairDev& pr, const GroupDev& A, const GroupDev& B, const double* Acell, PairGeom& g) {
-    double Av[3] = {A.x, A.y, A.z};
-    double Bv[3] = {B.x, B.y, B.z};
-    double a2p = 0.5 / pr.p;
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-        double Bs = Bv[x] + pr.L[0] * Acell[x] + pr.L[1] * Acell[3 + x] + pr.L[2] * Acell[6 + x];
-        ecoef(pr.P[x] - Av[x], pr.P[x] - Bs, a2p, A.lmax, B.lmax, g.E[x]);
-    }
-}
-
-// OUT_DF: store D'_ijk as double-float pairs (split form) instead of FP64
-template <bool OUT_DF>
-__global__ void __launch_bounds__(128) k_hermite(const PairDev* __restrict__ pairs, const GroupDev* __restrict__ G,
-                                                 const MemberDev* __restrict__ mem, const double* __restrict__ D0n,
-                                                 int nao, int nk, Layout lay, double* __restrict__ Dp,
-                                                 const double* __restrict__ Tm, CellConst cc) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int d = blockIdx.y;
-    if (i >= lay.start[kNclass]) return;
-    PairDev pr = pairs[i];
-    GroupDev A = G[pr.ga];
-    GroupDev B = G[pr.gb];
-    PairGeom g;
-    pair_geom(pr, A, B, cc.A, g);
-    double h[kMaxTerms];
-#pragma unroll
-    for (int t = 0; t < kMaxTerms; ++t) h[t] = 0.0;
-    long long nn = (long long)nao * nao;
-    const double* Dc = D0n + ((long long)d * nk + pr.cell) * nn;
-    const double* Dm = D0n + ((long long)d * nk + pr.mcell) * nn;
-    for (int ia = A.mem0; ia < A.mem1; ++ia) {
-        MemberDev ma = mem[ia];
-        int nfa = nfunc(ma.l, ma.sph), nca = (ma.l + 1) * (ma.l + 2) / 2;
-        for (int ib = B.mem0; ib < B.mem1; ++ib) {
-            MemberDev mb = mem[ib];
-            int nfb = nfunc(mb.l, mb.sph), ncb = (mb.l + 1) * (mb.l + 2) / 2;
-            double tmp[kNcartMax][kNcartMax];  // [f][cb]
-            for (int f = 0; f < nfa; ++f)
-                for (int cb = 0; cb < ncb; ++cb) {
-                    double s = 0.0;
-                    for (int q = 0; q < nfb; ++q) {
-                        double u = c_U[mb.l][mb.sph][q][cb];
-                        if (u == 0.0) continue;
-                        double dv = Dc[(long long)(ma.ao + f) * nao + mb.ao + q];
-                        if (pr.weight == 2) dv += Dm[(long long)(mb.ao + q) * nao + ma.ao + f];
-                        s += u * dv;
-                    }
-                    tmp[f][cb] = s;
-                }
-            double coef = ma.coef * mb.coef;
-            for (int ca = 0; ca < nca; ++ca) {
-                const int* xa = c_cart[ma.l][ca];
-                for (int cb = 0; cb < ncb; ++cb) {
-                    double dcart = 0.0;
-                    for (int f = 0; f < nfa; ++f) dcart += c_U[ma.l][ma.sph][f][ca] * tmp[f][cb];
-                    dcart *= coef;
-                    if (dcart == 0.0) continue;
-                    const int* xb = c_cart[mb.l][cb];
-                    const double* ex = g.E[0][xa[0]][xb[0]];
-                    const double* ey = g.E[1][xa[1]][xb[1]];
-                    const double* ez = g.E[2][xa[2]][xb[2]];
-                    for (int t = 0; t <= xa[0] + xb[0]; ++t)
-                        for (int u = 0; u <= xa[1] + xb[1]; ++u) {
-                            double exy = dcart * ex[t] * ey[u];
-                            for (int v = 0; v <= xa[2] + xb[2]; ++v) {
-                                int lam = t + u + v;
-                                h[lam_offset(lam) + mono_index(lam, t, u)] += exy * ez[v];
-                            }
-                        }
-                }
-            }
-        }
-    }
-    // relative coordinates: D'_b = sum_a T[a][b] h_a within each lambda, times K
-    int L = pr.cls;
-    long long cnt = lay.start[L + 1] - lay.start[L];
-    long long loc = i - lay.start[L];
-    const long long off = (long long)d * lay.total + lay.base[L] + loc;
-    for (int lam = 0; lam <= L; ++lam) {
-        int nm = nmono(lam), o = lam_offset(lam);
-        const double* T = Tm + c_Toff[lam];
-        for (int b = 0; b < nm; ++b) {
-            double s = 0.0;
-            for (int a = 0; a < nm; ++a) s += T[a * nm + b] * h[o + a];
-            const double v = pr.K * s;
-            if (OUT_DF) {
-                const float hi = (float)v;
-                reinterpret_cast<float2*>(Dp)[off + (long long)(o + b) * cnt] = make_float2(hi, (float)(v - (double)hi));
-            } else {
-                Dp[off + (long long)(o + b) * cnt] = v;
-            }
-        }
-    }
-}
-
-// a7: J'_ijk summed over chunks -> J_tuv -> AO block, scattered with atomics
-__global__ void __launch_bounds__(128) k_jtransform(const PairDev* __restrict__ pairs,
-                                                    const GroupDev* __restrict__ G,
-                                                    const MemberDev* __restrict__ mem,
-                                                    const double* __restrict__ Jp, int nchunks, int nao, int nk,
-                                                    Layout lay, double* __restrict__ J0n,
-                                                    const double* __restrict__ Tm, CellConst cc) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int d = blockIdx.y;
-    if (i >= lay.start[kNclass]) return;
-    PairDev pr = pairs[i];
-    int L = pr.cls;
-    long long cnt = lay.start[L + 1] - lay.start[L];
-    long long loc = i - lay.start[L];
-    double jp[kMaxTerms];
-    int NT = nterms(L);
-    for (int t = 0; t < NT; ++t) {
-        double s = 0.0;
-        for (int c = 0; c < nchunks; ++c)
-            s += Jp[((long long)d * nchunks + c) * lay.total + lay.base[L] + (long long)t * cnt + loc];
-        jp[t] = s;
-    }
-    double jt[kMaxTerms];
-    for (int lam = 0; lam <= L; ++lam) {
-        int nm = nmono(lam), o = lam_offset(lam);
-        const double* T = Tm + c_Toff[lam];
-        for (int a = 0; a < nm; ++a) {
-            double s = 0.0;
-            for (int b = 0; b < nm; ++b) s += T[a * nm + b] * jp[o + b];
-            jt[o + a] = pr.K * s;
-        }
-    }
-    GroupDev A = G[pr.ga];
-    GroupDev B = G[pr.gb];
-    PairGeom g;
-    pair_geom(pr, A, B, cc.A, g);
-    long long nn = (long long)nao * nao;
-    double* Jc = J0n + ((long long)d * nk + pr.cell) * nn;
-    double* Jm = J0n + ((long long)d * nk + pr.mcell) * nn;
-    for (int ia = A.mem0; ia < A.mem1; ++ia) {
-        MemberDev ma = mem[ia];
-        int nfa = nfunc(ma.l, ma.sph), nca = (ma.l + 1) * (ma.l + 2) / 2;
-        for (int ib = B.mem0; ib < B.mem1; ++ib) {
-            MemberDev mb = mem[ib];
-            int nfb = nfunc(mb.l, mb.sph), ncb = (mb.l + 1) * (mb.l + 2) / 2;
-            double jc[kNcartMax][kNcartMax];
-            for (int ca = 0; ca < nca; ++ca) {
-                const int* xa = c_cart[ma.l][ca];
-                for (int cb = 0; cb < ncb; ++cb) {
-                    const int* xb = c_cart[mb.l][cb];
-                    const double* ex = g.E[0][xa[0]][xb[0]];
-                    const double* ey = g.E[1][xa[1]][xb[1]];
-                    const double* ez = g.E[2][xa[2]][xb[2]];
-                    double s = 0.0;
-                    for (int t = 0; t <= xa[0] + xb[0]; ++t)
-                        for (int u = 0; u <= xa[1] + xb[1]; ++u) {
-                            double exy = ex[t] * ey[u];
-                            for (int v = 0; v <= xa[2] + xb[2]; ++v) {
-                                int lam = t + u + v;
-                                s += exy * ez[v] * jt[lam_offset(lam) + mono_index(lam, t, u)];
-                            }
-                        }
-                    jc[ca][cb] = s;
-                }
-            }
-            double coef = ma.coef * mb.coef;
-            for (int f = 0; f < nfa; ++f) {
-                double tmp[kNcartMax];
-                for (int cb = 0; cb < ncb; ++cb) {
-                    double s = 0.0;
-                    for (int ca = 0; ca < nca; ++ca) s += c_U[ma.l][ma.sph][f][ca] * jc[ca][cb];
-                    tmp[cb] = s;
-                }
-                for (int q = 0; q < nfb; ++q) {
-                    double s = 0.0;
-                    for (int cb = 0; cb < ncb; ++cb) s += c_U[mb.l][mb.sph][q][cb] * tmp[cb];
-                    s *= coef;
-                    atomicAdd(Jc + (long long)(ma.ao + f) * nao + mb.ao + q, s);
-                    if (pr.weight == 2) atomicAdd(Jm + (long long)(mb.ao + q) * nao + ma.ao + f, s);
-                }
-            }
-        }
-    }
-}
-
 // E^{ij}_t for i <= la1 <= 3, j <= lb1 <= 3 (MD recurrences), for the gradient
 __device__ void ecoef_g(double PA, double PB, double a2p, int la1, int lb1, double E[4][4][7]) {
     for (int i = 0; i < 4; ++i)
@@ -281,7 +76,7 @@ __device__ __forceinline__ double cart_contract(const double (*Ex)[4][7], const 
 // from d/dA [(x-A)^i e^{-alpha (x-A)^2}] = 2 alpha (x-A)^{i+1} e^{..} - i (x-A)^{i-1} e^{..},
 // with S(a, b) the Cartesian contraction of the degree-(L+1) sums J_tuv
 // (= K Re sum_half W g ph (-iG)^tuv).  Dcart is the combined density of the
-// record and its mirror, as in k_hermite, so the mirror's derivative is included.
+// record and its mirror, as in the Hermite-density step, so the mirror's derivative is included.
 __global__ void __launch_bounds__(128) k_grad_assemble(const PairDev* __restrict__ pairs,
                                                        const GroupDev* __restrict__ G,
                                                        const MemberDev* __restrict__ mem,
@@ -403,53 +198,72 @@ Layout make_layout(const ftcj_plan* P) {
 static std::mutex g_table_mutex;
 static bool g_tables_on_device[64] = {};
 
-int upload_hermite_tables(ftcj_plan* P) {
-    int dev = 0;
-    FTCJ_CUDA(cudaGetDevice(&dev));
-    std::lock_guard<std::mutex> lock(g_table_mutex);
-    const bool need_const = dev < 0 || dev >= 64 || !g_tables_on_device[dev];
-    int cart[kLmax + 1][kNcartMax][3] = {};
+// Cartesian exponents [l][c][3], AO -> Cartesian matrices [l][sph][f][c] (kNcartMax
+// strides) and the per-lambda offsets of the relative-coordinate transforms.
+void host_hermite_tables(const ftcj_plan* P, std::vector<double>& Uv, std::vector<int>& cartv, std::vector<int>& Toffv) {
+    (void)P;
+    cartv.assign((kLmax + 1) * kNcartMax * 3, 0);
     for (int l = 0; l <= kLmax; ++l) {
         int n = 0;
         for (int lx = l; lx >= 0; --lx)
             for (int ly = l - lx; ly >= 0; --ly) {
-                cart[l][n][0] = lx;
-                cart[l][n][1] = ly;
-                cart[l][n][2] = l - lx - ly;
+                cartv[(l * kNcartMax + n) * 3 + 0] = lx;
+                cartv[(l * kNcartMax + n) * 3 + 1] = ly;
+                cartv[(l * kNcartMax + n) * 3 + 2] = l - lx - ly;
                 ++n;
             }
     }
-    if (need_const) FTCJ_CUDA(cudaMemcpyToSymbol(c_cart, cart, sizeof(cart)));
-    double U[kLmax + 1][2][kNcartMax][kNcartMax] = {};
-    // Cartesian: component c scaled by 1/sqrt((2lx-1)!!(2ly-1)!!(2lz-1)!!)
+    Uv.assign((kLmax + 1) * 2 * kNcartMax * kNcartMax, 0.0);
+    auto U = [&](int l, int sph, int f, int c) -> double& { return Uv[((l * 2 + sph) * kNcartMax + f) * kNcartMax + c]; };
     auto dfact = [](int n) {
         double r = 1.0;
         for (int k = n; k > 1; k -= 2) r *= k;
         return r;
     };
     for (int l = 0; l <= kLmax; ++l) {
-        int nc = (l + 1) * (l + 2) / 2;
-        for (int c = 0; c < nc; ++c)
-            U[l][0][c][c] = 1.0 / std::sqrt(dfact(2 * cart[l][c][0] - 1) * dfact(2 * cart[l][c][1] - 1) *
-                                            dfact(2 * cart[l][c][2] - 1));
+        const int nc = (l + 1) * (l + 2) / 2;
+        for (int c = 0; c < nc; ++c) {
+            const int* x = &cartv[(l * kNcartMax + c) * 3];
+            U(l, 0, c, c) = 1.0 / std::sqrt(dfact(2 * x[0] - 1) * dfact(2 * x[1] - 1) * dfact(2 * x[2] - 1));
+        }
     }
-    // spherical (real solid harmonics over unit-normalised radial factor; l <= 2)
-    U[0][1][0][0] = 1.0;
-    U[1][1][0][0] = 1.0;  // x
-    U[1][1][1][1] = 1.0;  // y
-    U[1][1][2][2] = 1.0;  // z
+    U(0, 1, 0, 0) = 1.0;
+    U(1, 1, 0, 0) = 1.0;  // x
+    U(1, 1, 1, 1) = 1.0;  // y
+    U(1, 1, 2, 2) = 1.0;  // z
     {
-        // d: cart order xx, xy, xz, yy, yz, zz; functions m = -2..2 = xy, yz, z2, xz, x2-y2
+        // d: Cartesian order xx, xy, xz, yy, yz, zz; functions m = -2..2 = xy, yz, z2, xz, x2-y2
         const double r3 = 1.0 / std::sqrt(3.0);
-        U[2][1][0][1] = 1.0;        // xy
-        U[2][1][1][4] = 1.0;        // yz
-        U[2][1][2][0] = -0.5 * r3;  // z2 = (2zz - xx - yy)/2, over sqrt(3)
-        U[2][1][2][3] = -0.5 * r3;
-        U[2][1][2][5] = r3;
-        U[2][1][3][2] = 1.0;   // xz
-        U[2][1][4][0] = 0.5;   // (xx - yy) sqrt(3)/2, over sqrt(3)
-        U[2][1][4][3] = -0.5;
+        U(2, 1, 0, 1) = 1.0;        // xy
+        U(2, 1, 1, 4) = 1.0;        // yz
+        U(2, 1, 2, 0) = -0.5 * r3;  // z2 = (2zz - xx - yy)/2, over sqrt(3)
+        U(2, 1, 2, 3) = -0.5 * r3;
+        U(2, 1, 2, 5) = r3;
+        U(2, 1, 3, 2) = 1.0;  // xz
+        U(2, 1, 4, 0) = 0.5;  // (xx - yy) sqrt(3)/2, over sqrt(3)
+        U(2, 1, 4, 3) = -0.5;
     }
+    Toffv.assign(kLgrad + 1, 0);
+    int off = 0;
+    for (int lam = 0; lam <= kLgrad; ++lam) {
+        Toffv[lam] = off;
+        off += nmono(lam) * nmono(lam);
+    }
+}
+
+int upload_hermite_tables(ftcj_plan* P) {
+    int dev = 0;
+    FTCJ_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(g_table_mutex);
+    const bool need_const = dev < 0 || dev >= 64 || !g_tables_on_device[dev];
+    std::vector<double> Uh;
+    std::vector<int> carth, Toffh;
+    host_hermite_tables(P, Uh, carth, Toffh);
+    int cart[kLmax + 1][kNcartMax][3] = {};
+    std::copy(carth.begin(), carth.end(), &cart[0][0][0]);
+    if (need_const) FTCJ_CUDA(cudaMemcpyToSymbol(c_cart, cart, sizeof(cart)));
+    double U[kLmax + 1][2][kNcartMax][kNcartMax] = {};
+    std::copy(Uh.begin(), Uh.end(), &U[0][0][0][0]);
     if (need_const) FTCJ_CUDA(cudaMemcpyToSymbol(c_U, U, sizeof(U)));
     // G_x^t G_y^u G_z^v with G_x = sum_i n_i B[i][x]: expand as polynomials in (n1, n2, n3)
     std::vector<double> T(kTmatSize, 0.0);
@@ -497,19 +311,6 @@ int upload_hermite_tables(ftcj_plan* P) {
     return FTCJ_OK;
 }
 
-int launch_hermite(ftcj_plan* P, int ndens, const double* D0n, cudaStream_t s) {
-    if (P->npairs == 0) return FTCJ_OK;
-    dim3 g((unsigned)((P->npairs + 127) / 128), ndens);
-    if (P->precision == FTCJ_PREC_SPLIT)
-        k_hermite<true><<<g, 128, 0, s>>>(P->d_pairs, P->d_groups, P->d_members, D0n, P->nao, P->nk, make_layout(P),
-                                          P->d_Dp, P->d_Tmat, P->cc);
-    else
-        k_hermite<false><<<g, 128, 0, s>>>(P->d_pairs, P->d_groups, P->d_members, D0n, P->nao, P->nk,
-                                           make_layout(P), P->d_Dp, P->d_Tmat, P->cc);
-    FTCJ_CUDA(cudaGetLastError());
-    return FTCJ_OK;
-}
-
 int launch_grad_assemble(ftcj_plan* P, int ndens, const double* D0n, double* grad, cudaStream_t s) {
     FTCJ_CUDA(cudaMemsetAsync(grad, 0, sizeof(double) * (size_t)ndens * P->ncentre * 3, s));
     if (P->npairs == 0) return FTCJ_OK;
@@ -519,17 +320,6 @@ int launch_grad_assemble(ftcj_plan* P, int ndens, const double* D0n, double* gra
     dim3 g((unsigned)((P->npairs + 127) / 128), ndens);
     k_grad_assemble<<<g, 128, 0, s>>>(P->d_pairs, P->d_groups, P->d_members, D0n, P->d_Jg, (int)P->chunks.size(),
                                       P->nao, P->nk, lg, grad, P->ncentre, P->d_Tmat, P->cc);
-    FTCJ_CUDA(cudaGetLastError());
-    return FTCJ_OK;
-}
-
-int launch_jtransform(ftcj_plan* P, int ndens, double* J0n, cudaStream_t s) {
-    size_t bytes = sizeof(double) * (size_t)ndens * P->nk * P->nao * P->nao;
-    FTCJ_CUDA(cudaMemsetAsync(J0n, 0, bytes, s));
-    if (P->npairs == 0) return FTCJ_OK;
-    dim3 g((unsigned)((P->npairs + 127) / 128), ndens);
-    k_jtransform<<<g, 128, 0, s>>>(P->d_pairs, P->d_groups, P->d_members, P->d_Jp, (int)P->chunks.size(), P->nao,
-                                   P->nk, make_layout(P), J0n, P->d_Tmat, P->cc);
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }

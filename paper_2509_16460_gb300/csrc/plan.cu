@@ -201,7 +201,8 @@ void free_device(ftcj_plan* P) {
     void* ptrs[] = {P->d_groups, P->d_members, P->d_pairs, P->d_walk, P->d_lines, P->d_chunks, P->d_tiles,
                     P->d_gvec, P->d_vg, P->d_tw, P->d_Tmat, P->d_D0n, P->d_J0n, P->d_cbuf0, P->d_cbuf1,
                     P->d_Dp, P->d_Jp, P->d_rho_part, P->d_rho, P->d_W, P->d_Epart, P->d_Dk_stage,
-                    P->d_Jk_stage, P->d_EJ_stage, P->d_check, P->d_split_init, P->d_split_const, P->d_Jg};
+                    P->d_Jk_stage, P->d_EJ_stage, P->d_check, P->d_split_init, P->d_split_const, P->d_Jg,
+                    P->d_maps, P->d_map_off};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -375,6 +376,7 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     if ((rc = upload(P, &P->d_tiles, P->tiles))) return rc;
     if ((rc = upload_walk_tables(P))) return rc;
     if ((rc = upload_hermite_tables(P))) return rc;
+    if ((rc = build_maps(P))) return rc;
     if (P->precision == FTCJ_PREC_SPLIT && (rc = setup_split(P))) return rc;
     int bps = 1;
     if (P->precision == FTCJ_PREC_SPLIT) {
@@ -398,7 +400,7 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     if ((rc = dalloc(P, &P->d_rho_part, 2 * md * (size_t)P->npb * (size_t)P->ng_half))) return rc;
     if ((rc = dalloc(P, &P->d_rho, 2 * md * (size_t)P->ng_half))) return rc;
     if ((rc = dalloc(P, &P->d_W, 2 * md * (size_t)P->ng_half))) return rc;
-    P->nEblocks = (int)std::max<int64_t>(1, (P->ng_half + 255) / 256);
+    P->nEblocks = (int)std::max<int64_t>(1, (P->ng_half + 31) / 32);
     if ((rc = dalloc(P, &P->d_Epart, md * (size_t)P->nEblocks))) return rc;
     if ((rc = dalloc(P, &P->d_Dk_stage, 2 * md * P->nk * nn))) return rc;
     if ((rc = dalloc(P, &P->d_Jk_stage, 2 * md * P->nk * nn))) return rc;

@@ -22,6 +22,8 @@
 namespace ftcj {
 namespace {
 
+constexpr int kSBatch = 16;  // points per reduction batch of the split rho walk
+
 
 struct Layout {
     long long start[kNclass + 1];
@@ -190,7 +192,7 @@ __device__ __forceinline__ cdf unpack(float4 v) { return cdf{{v.x, v.y}, {v.z, v
 __device__ __forceinline__ void split_flush(float4* buf, float4* red, float4* row, int rbase, int nvalid) {
     __syncthreads();
     const int tid = threadIdx.x, j = tid & 31, wv = tid >> 5;
-    if (j < nvalid) {
+    if (j < nvalid) {  // nvalid <= kSBatch
         cdf s{{0.f, 0.f}, {0.f, 0.f}};
         const float4* b = buf + j * (kTile + 1) + wv * 32;
 #pragma unroll 4
@@ -210,19 +212,18 @@ template <int L>
 __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* __restrict__ Dp_d,
                                const SConst* __restrict__ cst, const SState* __restrict__ init_c,
                                const WLine* __restrict__ lines, const WChunk ch, float4* buf, float4* red,
-                               float4* row) {
+                               float4* row, float2* Dsm) {
     constexpr int NT = nterms(L);
     const int tid = threadIdx.x;
     const bool valid = tid < tl.count;
     const long long pi = (long long)tl.first + tid;
     const long long cnt = lay.start[L + 1] - lay.start[L];
     const long long loc = pi - lay.start[L];
-    df D[NT];
+    // the record's coefficients live in a thread-private shared-memory slice
+    // (read once per line), keeping registers for the per-point recurrences
 #pragma unroll
-    for (int t = 0; t < NT; ++t) {
-        float2 v = valid ? Dp_d[lay.base[L] + (long long)t * cnt + loc] : make_float2(0.f, 0.f);
-        D[t] = df{v.x, v.y};
-    }
+    for (int t = 0; t < NT; ++t)
+        Dsm[t * kTile + tid] = valid ? Dp_d[lay.base[L] + (long long)t * cnt + loc] : make_float2(0.f, 0.f);
     const SConst k = valid ? cst[pi] : idle_const();
     const SState* init_p = init_c + (valid ? pi : 0);
     SState s;
@@ -245,7 +246,8 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
 #pragma unroll
                     for (int j = lam - i; j >= 0; --j) {
                         const int kk = lam - i - j;
-                        const df v = df_mulf(D[t], pq[j][kk]);
+                        const float2 dv = Dsm[t * kTile + tid];
+                        const df v = df_mulf(df{dv.x, dv.y}, pq[j][kk]);
                         switch (lam & 3) {
                             case 0: c[i].re = df_add(c[i].re, v); break;
                             case 1: c[i].im = df_sub(c[i].im, v); break;
@@ -283,9 +285,9 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
                         a = cdf{df_add(df_mulf(a.re, x), c[i].re), df_add(df_mulf(a.im, x), c[i].im)};
                     const cdf z = cdf_mul(gp, a);
                     buf[slot * (kTile + 1) + tid] = make_float4(z.re.hi, z.re.lo, z.im.hi, z.im.lo);
-                    if (++slot == kBatch) {
-                        split_flush(buf, red, row, rbase, kBatch);
-                        rbase += kBatch;
+                    if (++slot == kSBatch) {
+                        split_flush(buf, red, row, rbase, kSBatch);
+                        rbase += kSBatch;
                         slot = 0;
                     }
                 }
@@ -299,7 +301,7 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kTile) k_rho_walk_split(const Tile* __restrict__ tiles, int ntiles, Layout lay,
+__global__ void __launch_bounds__(kTile, 3) k_rho_walk_split(const Tile* __restrict__ tiles, int ntiles, Layout lay,
                                                           const float2* __restrict__ Dp,
                                                           const SConst* __restrict__ cst,
                                                           const SState* __restrict__ init, long long npairs,
@@ -311,8 +313,9 @@ __global__ void __launch_bounds__(kTile) k_rho_walk_split(const Tile* __restrict
     const WChunk ch = chunks[cidx];
     const int npts = ch.p1 - ch.p0;
     float4* buf = ssm;
-    float4* red = buf + kBatch * (kTile + 1);
-    float4* row = red + kTile;
+    float4* red = buf + kSBatch * (kTile + 1);
+    float2* Dsm = reinterpret_cast<float2*>(red + kTile);
+    float4* row = reinterpret_cast<float4*>(Dsm + kMaxTerms * kTile);
     for (int i = threadIdx.x; i < npts; i += blockDim.x) row[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     const float2* Dp_d = Dp + (long long)d * lay.total;
@@ -320,11 +323,11 @@ __global__ void __launch_bounds__(kTile) k_rho_walk_split(const Tile* __restrict
     for (int t = b; t < ntiles; t += npb) {
         const Tile tl = tiles[t];
         switch (tl.cls) {
-            case 0: rho_tile_split<0>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row); break;
-            case 1: rho_tile_split<1>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row); break;
-            case 2: rho_tile_split<2>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row); break;
-            case 3: rho_tile_split<3>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row); break;
-            default: rho_tile_split<4>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row); break;
+            case 0: rho_tile_split<0>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm); break;
+            case 1: rho_tile_split<1>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm); break;
+            case 2: rho_tile_split<2>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm); break;
+            case 3: rho_tile_split<3>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm); break;
+            default: rho_tile_split<4>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm); break;
         }
     }
     __syncthreads();
@@ -341,7 +344,7 @@ template <int L>
 __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __restrict__ cst,
                              const SState* __restrict__ init_c, const WLine* __restrict__ lines, const WChunk ch,
                              const float4* __restrict__ wsm, const float* __restrict__ pw, int n1min,
-                             double* __restrict__ Jp_dc) {
+                             double* __restrict__ Jp_dc, float2* Jsm) {
     constexpr int NT = nterms(L);
     const int tid = threadIdx.x;
     const bool valid = tid < tl.count;
@@ -350,9 +353,10 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
     const long long loc = pi - lay.start[L];
     const SConst k = valid ? cst[pi] : idle_const();
     const SState* init_p = init_c + (valid ? pi : 0);
-    df J[NT];
+    // the record's J' accumulators live in a thread-private shared-memory slice
+    // (updated once per line)
 #pragma unroll
-    for (int t = 0; t < NT; ++t) J[t] = df{0.f, 0.f};
+    for (int t = 0; t < NT; ++t) Jsm[t * kTile + tid] = make_float2(0.f, 0.f);
     SState s;
     for (int li = ch.l0; li < ch.l1; ++li) {
         const WLine ln = lines[li];
@@ -414,17 +418,22 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
                         case 2: a = df_neg(A[i].re); break;
                         default: a = df_neg(A[i].im); break;
                     }
-                    J[t] = df_add(J[t], df_mulf(a, pq[j][kk]));
+                    const float2 jv = Jsm[t * kTile + tid];
+                    const df r = df_add(df{jv.x, jv.y}, df_mulf(a, pq[j][kk]));
+                    Jsm[t * kTile + tid] = make_float2(r.hi, r.lo);
                     ++t;
                 }
     }
     if (valid) {
 #pragma unroll
-        for (int t = 0; t < NT; ++t) Jp_dc[lay.base[L] + (long long)t * cnt + loc] = (double)J[t].hi + (double)J[t].lo;
+        for (int t = 0; t < NT; ++t) {
+            const float2 jv = Jsm[t * kTile + tid];
+            Jp_dc[lay.base[L] + (long long)t * cnt + loc] = (double)jv.x + (double)jv.y;
+        }
     }
 }
 
-__global__ void __launch_bounds__(kTile) k_j_walk_split(const Tile* __restrict__ tiles, Layout lay,
+__global__ void __launch_bounds__(kTile, 3) k_j_walk_split(const Tile* __restrict__ tiles, Layout lay,
                                                         const SConst* __restrict__ cst,
                                                         const SState* __restrict__ init, long long npairs,
                                                         const WLine* __restrict__ lines,
@@ -436,7 +445,8 @@ __global__ void __launch_bounds__(kTile) k_j_walk_split(const Tile* __restrict__
     const WChunk ch = chunks[cidx];
     const int npts = ch.p1 - ch.p0;
     float4* wsm = ssm;
-    float* pw = reinterpret_cast<float*>(ssm + max_chunk_pts);
+    float2* Jsm = reinterpret_cast<float2*>(ssm + max_chunk_pts);
+    float* pw = reinterpret_cast<float*>(Jsm + kMaxTerms * kTile);
     const double2* Wd = W + (long long)d * ng_half + ch.p0;
     for (int i = threadIdx.x; i < npts; i += blockDim.x) {
         const double2 v = Wd[i];
@@ -454,11 +464,11 @@ __global__ void __launch_bounds__(kTile) k_j_walk_split(const Tile* __restrict__
     double* Jp_dc = Jp + ((long long)d * nchunks + cidx) * lay.total;
     const SState* init_c = init + (long long)cidx * npairs;
     switch (tl.cls) {
-        case 0: j_tile_split<0>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc); break;
-        case 1: j_tile_split<1>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc); break;
-        case 2: j_tile_split<2>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc); break;
-        case 3: j_tile_split<3>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc); break;
-        default: j_tile_split<4>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc); break;
+        case 0: j_tile_split<0>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm); break;
+        case 1: j_tile_split<1>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm); break;
+        case 2: j_tile_split<2>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm); break;
+        case 3: j_tile_split<3>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm); break;
+        default: j_tile_split<4>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm); break;
     }
 }
 
@@ -471,12 +481,14 @@ Layout make_layout(const ftcj_plan* P) {
 }
 
 size_t rho_smem(const ftcj_plan* P) {
-    return sizeof(float4) * ((size_t)kBatch * (kTile + 1) + kTile + (size_t)std::max(P->max_chunk_pts, 1));
+    return sizeof(float4) * ((size_t)kSBatch * (kTile + 1) + kTile + (size_t)std::max(P->max_chunk_pts, 1)) +
+           sizeof(float2) * (size_t)kMaxTerms * kTile;
 }
 
 size_t j_smem(const ftcj_plan* P) {
     const int n1cnt = P->n1_max - P->n1_min + 1;
-    return sizeof(float4) * (size_t)std::max(P->max_chunk_pts, 1) + sizeof(float) * 5 * (size_t)n1cnt;
+    return sizeof(float4) * (size_t)std::max(P->max_chunk_pts, 1) + sizeof(float2) * (size_t)kMaxTerms * kTile +
+           sizeof(float) * 5 * (size_t)n1cnt;
 }
 
 }  // namespace
