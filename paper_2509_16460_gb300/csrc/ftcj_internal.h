@@ -174,6 +174,7 @@ struct ftcj_plan {
     void* d_split_init = nullptr;    // split form: walk state at each chunk start, [nchunks][npairs]
     void* d_split_const = nullptr;   // split form: recurrence multipliers, [npairs]
     int precision = FTCJ_PREC_FP64;
+    bool ortho = false;  // reciprocal metric diagonal (orthorhombic cell)
     ftcj::CellConst cc;
     int nEblocks = 0;
     size_t device_bytes = 0;

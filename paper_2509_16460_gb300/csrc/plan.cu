@@ -239,6 +239,7 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
         const double m6[6] = {P->M[0], P->M[4], P->M[8], P->M[1], P->M[2], P->M[5]};
         for (int i = 0; i < 6; ++i) P->cc.M6[i] = m6[i];
         for (int i = 0; i < 3; ++i) P->cc.bn[i] = std::sqrt(P->M[4 * i]);
+        P->ortho = m6[3] == 0.0 && m6[4] == 0.0 && m6[5] == 0.0;
     }
     // k mesh
     P->nk = 1;

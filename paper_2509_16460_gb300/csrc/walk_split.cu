@@ -189,30 +189,63 @@ __device__ __forceinline__ void powers23f(int n2, int n3, float pq[L + 1][L + 1]
 
 __device__ __forceinline__ cdf unpack(float4 v) { return cdf{{v.x, v.y}, {v.z, v.w}}; }
 
+// Sums the batch's contributions over the block's 128 records: warp w, lanes
+// j and j+16 add the two halves of point j's column of warp w's 32 records,
+// join with one shuffle, and the four warp sums are added into the row.
 __device__ __forceinline__ void split_flush(float4* buf, float4* red, float4* row, int rbase, int nvalid) {
     __syncthreads();
-    const int tid = threadIdx.x, j = tid & 31, wv = tid >> 5;
-    if (j < nvalid) {  // nvalid <= kSBatch
-        cdf s{{0.f, 0.f}, {0.f, 0.f}};
-        const float4* b = buf + j * (kTile + 1) + wv * 32;
+    const int tid = threadIdx.x, lane = tid & 31, wv = tid >> 5;
+    const int j = lane & (kSBatch - 1), half = lane / kSBatch;
+    cdf s{{0.f, 0.f}, {0.f, 0.f}};
+    if (j < nvalid) {
+        const float4* b = buf + j * (kTile + 1) + wv * 32 + half * 16;
 #pragma unroll 4
-        for (int k = 0; k < 32; ++k) s = cdf_add(s, unpack(b[k]));
+        for (int k = 0; k < 16; ++k) s = cdf_add(s, unpack(b[k]));
+    }
+    cdf o;
+    o.re.hi = __shfl_down_sync(0xffffffffu, s.re.hi, 16);
+    o.re.lo = __shfl_down_sync(0xffffffffu, s.re.lo, 16);
+    o.im.hi = __shfl_down_sync(0xffffffffu, s.im.hi, 16);
+    o.im.lo = __shfl_down_sync(0xffffffffu, s.im.lo, 16);
+    if (half == 0 && j < nvalid) {
+        s = cdf_add(s, o);
         red[wv * 32 + j] = make_float4(s.re.hi, s.re.lo, s.im.hi, s.im.lo);
     }
     __syncthreads();
     if (tid < nvalid) {
-        cdf s = unpack(row[rbase + tid]);
+        cdf r = unpack(row[rbase + tid]);
 #pragma unroll
-        for (int q = 0; q < kTile / 32; ++q) s = cdf_add(s, unpack(red[q * 32 + tid]));
-        row[rbase + tid] = make_float4(s.re.hi, s.re.lo, s.im.hi, s.im.lo);
+        for (int q = 0; q < kTile / 32; ++q) r = cdf_add(r, unpack(red[q * 32 + tid]));
+        row[rbase + tid] = make_float4(r.re.hi, r.re.lo, r.im.hi, r.im.lo);
     }
 }
 
-template <int L>
+// Builds the record's table X(n1) = exp(-c M11 n1^2) exp(-2 pi i f1 n1),
+// n1 in [n1min, n1min + n1cnt), from n1 = 0 outwards with the line-independent
+// ratios of an orthorhombic cell (the first line's RfL, RbL and q1).
+__device__ __forceinline__ void build_xtab(const SState& s0, const df q1, int n1min, int n1cnt, float4* Xs, int tid) {
+    const int i0 = -n1min;
+    cdf x{{1.f, 0.f}, {0.f, 0.f}};
+    cdf R = s0.RfL;
+    for (int n = 0; n < n1cnt - i0; ++n) {
+        Xs[(i0 + n) * kTile + tid] = make_float4(x.re.hi, x.re.lo, x.im.hi, x.im.lo);
+        x = cdf_mul(x, R);
+        R = cdf_scale(R, q1);
+    }
+    x = cdf{{1.f, 0.f}, {0.f, 0.f}};
+    R = s0.RbL;
+    for (int n = 1; n <= i0; ++n) {
+        x = cdf_mul(x, R);
+        R = cdf_scale(R, q1);
+        Xs[(i0 - n) * kTile + tid] = make_float4(x.re.hi, x.re.lo, x.im.hi, x.im.lo);
+    }
+}
+
+template <int L, bool ORTHO>
 __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* __restrict__ Dp_d,
                                const SConst* __restrict__ cst, const SState* __restrict__ init_c,
                                const WLine* __restrict__ lines, const WChunk ch, float4* buf, float4* red,
-                               float4* row, float2* Dsm) {
+                               float4* row, float2* Dsm, float4* Xs, int n1min, int n1cnt) {
     constexpr int NT = nterms(L);
     const int tid = threadIdx.x;
     const bool valid = tid < tl.count;
@@ -226,6 +259,7 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
         Dsm[t * kTile + tid] = valid ? Dp_d[lay.base[L] + (long long)t * cnt + loc] : make_float2(0.f, 0.f);
     const SConst k = valid ? cst[pi] : idle_const();
     const SState* init_p = init_c + (valid ? pi : 0);
+    if (ORTHO) build_xtab(valid ? *init_p : idle_state(), k.q1, n1min, n1cnt, Xs, tid);
     SState s;
     int slot = 0, rbase = 0;
     for (int li = ch.l0; li < ch.l1; ++li) {
@@ -257,6 +291,11 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
                         ++t;
                     }
         }
+        if (ORTHO) {
+            // the line value gp(0) goes into the coefficients; X(n1) carries the rest
+#pragma unroll
+            for (int i = 0; i <= L; ++i) c[i] = cdf_mul(s.gpL, c[i]);
+        }
 #pragma unroll
         for (int dir = 0; dir < 2; ++dir) {
             int m0, m1, step;
@@ -266,15 +305,19 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
                 m0 = 0;
                 m1 = ln.hi;
                 step = 1;
-                gp = s.gpL;
-                R = s.RfL;
+                if (!ORTHO) {
+                    gp = s.gpL;
+                    R = s.RfL;
+                }
             } else {
                 if (ln.lo > -1) continue;
                 m0 = -1;
                 m1 = ln.lo;
                 step = -1;
-                gp = cdf_mul(s.gpL, s.RbL);
-                R = cdf_scale(s.RbL, k.q1);
+                if (!ORTHO) {
+                    gp = cdf_mul(s.gpL, s.RbL);
+                    R = cdf_scale(s.RbL, k.q1);
+                }
             }
             for (int m = m0;; m += step) {
                 if (m >= ln.lo && m <= ln.hi) {
@@ -283,7 +326,7 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
 #pragma unroll
                     for (int i = L - 1; i >= 0; --i)
                         a = cdf{df_add(df_mulf(a.re, x), c[i].re), df_add(df_mulf(a.im, x), c[i].im)};
-                    const cdf z = cdf_mul(gp, a);
+                    const cdf z = ORTHO ? cdf_mul(unpack(Xs[(m - n1min) * kTile + tid]), a) : cdf_mul(gp, a);
                     buf[slot * (kTile + 1) + tid] = make_float4(z.re.hi, z.re.lo, z.im.hi, z.im.lo);
                     if (++slot == kSBatch) {
                         split_flush(buf, red, row, rbase, kSBatch);
@@ -292,8 +335,10 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
                     }
                 }
                 if (m == m1) break;
-                gp = cdf_mul(gp, R);
-                R = cdf_scale(R, k.q1);
+                if (!ORTHO) {
+                    gp = cdf_mul(gp, R);
+                    R = cdf_scale(R, k.q1);
+                }
             }
         }
     }
@@ -301,13 +346,15 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
     __syncthreads();
 }
 
+template <bool ORTHO>
 __global__ void __launch_bounds__(kTile, 3) k_rho_walk_split(const Tile* __restrict__ tiles, int ntiles, Layout lay,
                                                           const float2* __restrict__ Dp,
                                                           const SConst* __restrict__ cst,
                                                           const SState* __restrict__ init, long long npairs,
                                                           const WLine* __restrict__ lines,
                                                           const WChunk* __restrict__ chunks, int npb,
-                                                          double2* __restrict__ rho_part, long long ng_half) {
+                                                          double2* __restrict__ rho_part, long long ng_half,
+                                                          int n1min, int n1cnt) {
     extern __shared__ float4 ssm[];
     const int b = blockIdx.x, cidx = blockIdx.y, d = blockIdx.z;
     const WChunk ch = chunks[cidx];
@@ -315,7 +362,8 @@ __global__ void __launch_bounds__(kTile, 3) k_rho_walk_split(const Tile* __restr
     float4* buf = ssm;
     float4* red = buf + kSBatch * (kTile + 1);
     float2* Dsm = reinterpret_cast<float2*>(red + kTile);
-    float4* row = reinterpret_cast<float4*>(Dsm + kMaxTerms * kTile);
+    float4* Xs = reinterpret_cast<float4*>(Dsm + kMaxTerms * kTile);
+    float4* row = Xs + (ORTHO ? n1cnt * kTile : 0);
     for (int i = threadIdx.x; i < npts; i += blockDim.x) row[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     const float2* Dp_d = Dp + (long long)d * lay.total;
@@ -323,11 +371,11 @@ __global__ void __launch_bounds__(kTile, 3) k_rho_walk_split(const Tile* __restr
     for (int t = b; t < ntiles; t += npb) {
         const Tile tl = tiles[t];
         switch (tl.cls) {
-            case 0: rho_tile_split<0>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm); break;
-            case 1: rho_tile_split<1>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm); break;
-            case 2: rho_tile_split<2>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm); break;
-            case 3: rho_tile_split<3>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm); break;
-            default: rho_tile_split<4>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm); break;
+            case 0: rho_tile_split<0, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, n1min, n1cnt); break;
+            case 1: rho_tile_split<1, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, n1min, n1cnt); break;
+            case 2: rho_tile_split<2, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, n1min, n1cnt); break;
+            case 3: rho_tile_split<3, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, n1min, n1cnt); break;
+            default: rho_tile_split<4, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, n1min, n1cnt); break;
         }
     }
     __syncthreads();
@@ -340,11 +388,11 @@ __global__ void __launch_bounds__(kTile, 3) k_rho_walk_split(const Tile* __restr
 
 // ---- J -------------------------------------------------------------------
 
-template <int L>
+template <int L, bool ORTHO>
 __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __restrict__ cst,
                              const SState* __restrict__ init_c, const WLine* __restrict__ lines, const WChunk ch,
                              const float4* __restrict__ wsm, const float* __restrict__ pw, int n1min,
-                             double* __restrict__ Jp_dc, float2* Jsm) {
+                             double* __restrict__ Jp_dc, float2* Jsm, float4* Xs, int n1cnt) {
     constexpr int NT = nterms(L);
     const int tid = threadIdx.x;
     const bool valid = tid < tl.count;
@@ -357,6 +405,7 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
     // (updated once per line)
 #pragma unroll
     for (int t = 0; t < NT; ++t) Jsm[t * kTile + tid] = make_float2(0.f, 0.f);
+    if (ORTHO) build_xtab(valid ? *init_p : idle_state(), k.q1, n1min, n1cnt, Xs, tid);
     SState s;
     for (int li = ch.l0; li < ch.l1; ++li) {
         const WLine ln = lines[li];
@@ -375,19 +424,24 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
                 m0 = 0;
                 m1 = ln.hi;
                 step = 1;
-                gp = s.gpL;
-                R = s.RfL;
+                if (!ORTHO) {
+                    gp = s.gpL;
+                    R = s.RfL;
+                }
             } else {
                 if (ln.lo > -1) continue;
                 m0 = -1;
                 m1 = ln.lo;
                 step = -1;
-                gp = cdf_mul(s.gpL, s.RbL);
-                R = cdf_scale(s.RbL, k.q1);
+                if (!ORTHO) {
+                    gp = cdf_mul(s.gpL, s.RbL);
+                    R = cdf_scale(s.RbL, k.q1);
+                }
             }
             for (int m = m0;; m += step) {
                 if (m >= ln.lo && m <= ln.hi) {
-                    const cdf t = cdf_mul(gp, unpack(wsm[q++]));
+                    const cdf w = unpack(wsm[q++]);
+                    const cdf t = ORTHO ? cdf_mul(unpack(Xs[(m - n1min) * kTile + tid]), w) : cdf_mul(gp, w);
                     A[0] = cdf_add(A[0], t);
                     const float* pwm = pw + (m - n1min) * 5;
 #pragma unroll
@@ -397,9 +451,15 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
                     }
                 }
                 if (m == m1) break;
-                gp = cdf_mul(gp, R);
-                R = cdf_scale(R, k.q1);
+                if (!ORTHO) {
+                    gp = cdf_mul(gp, R);
+                    R = cdf_scale(R, k.q1);
+                }
             }
+        }
+        if (ORTHO) {
+#pragma unroll
+            for (int i = 0; i <= L; ++i) A[i] = cdf_mul(s.gpL, A[i]);
         }
         float pq[L + 1][L + 1];
         powers23f<L>(ln.n2, ln.n3, pq);
@@ -433,6 +493,7 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
     }
 }
 
+template <bool ORTHO>
 __global__ void __launch_bounds__(kTile, 3) k_j_walk_split(const Tile* __restrict__ tiles, Layout lay,
                                                         const SConst* __restrict__ cst,
                                                         const SState* __restrict__ init, long long npairs,
@@ -446,7 +507,8 @@ __global__ void __launch_bounds__(kTile, 3) k_j_walk_split(const Tile* __restric
     const int npts = ch.p1 - ch.p0;
     float4* wsm = ssm;
     float2* Jsm = reinterpret_cast<float2*>(ssm + max_chunk_pts);
-    float* pw = reinterpret_cast<float*>(Jsm + kMaxTerms * kTile);
+    float4* Xs = reinterpret_cast<float4*>(Jsm + kMaxTerms * kTile);
+    float* pw = reinterpret_cast<float*>(Xs + (ORTHO ? n1cnt * kTile : 0));
     const double2* Wd = W + (long long)d * ng_half + ch.p0;
     for (int i = threadIdx.x; i < npts; i += blockDim.x) {
         const double2 v = Wd[i];
@@ -464,11 +526,11 @@ __global__ void __launch_bounds__(kTile, 3) k_j_walk_split(const Tile* __restric
     double* Jp_dc = Jp + ((long long)d * nchunks + cidx) * lay.total;
     const SState* init_c = init + (long long)cidx * npairs;
     switch (tl.cls) {
-        case 0: j_tile_split<0>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm); break;
-        case 1: j_tile_split<1>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm); break;
-        case 2: j_tile_split<2>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm); break;
-        case 3: j_tile_split<3>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm); break;
-        default: j_tile_split<4>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm); break;
+        case 0: j_tile_split<0, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, n1cnt); break;
+        case 1: j_tile_split<1, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, n1cnt); break;
+        case 2: j_tile_split<2, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, n1cnt); break;
+        case 3: j_tile_split<3, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, n1cnt); break;
+        default: j_tile_split<4, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, n1cnt); break;
     }
 }
 
@@ -480,15 +542,20 @@ Layout make_layout(const ftcj_plan* P) {
     return l;
 }
 
+// orthorhombic cells with a short enough n1 range use the per-record X(n1) table
+bool use_xtab(const ftcj_plan* P) { return P->ortho && (P->n1_max - P->n1_min + 1) <= 40; }
+
 size_t rho_smem(const ftcj_plan* P) {
+    const size_t xt = use_xtab(P) ? sizeof(float4) * (size_t)(P->n1_max - P->n1_min + 1) * kTile : 0;
     return sizeof(float4) * ((size_t)kSBatch * (kTile + 1) + kTile + (size_t)std::max(P->max_chunk_pts, 1)) +
-           sizeof(float2) * (size_t)kMaxTerms * kTile;
+           sizeof(float2) * (size_t)kMaxTerms * kTile + xt;
 }
 
 size_t j_smem(const ftcj_plan* P) {
     const int n1cnt = P->n1_max - P->n1_min + 1;
+    const size_t xt = use_xtab(P) ? sizeof(float4) * (size_t)n1cnt * kTile : 0;
     return sizeof(float4) * (size_t)std::max(P->max_chunk_pts, 1) + sizeof(float2) * (size_t)kMaxTerms * kTile +
-           sizeof(float) * 5 * (size_t)n1cnt;
+           sizeof(float) * 5 * (size_t)n1cnt + xt;
 }
 
 }  // namespace
@@ -507,14 +574,19 @@ int setup_split(ftcj_plan* P) {
                                   reinterpret_cast<SConst*>(P->d_split_const), P->cc);
         FTCJ_CUDA(cudaGetLastError());
     }
-    int rc = allow_dynamic_smem((const void*)k_rho_walk_split, rho_smem(P));
+    int rc = use_xtab(P) ? allow_dynamic_smem((const void*)k_rho_walk_split<true>, rho_smem(P))
+                         : allow_dynamic_smem((const void*)k_rho_walk_split<false>, rho_smem(P));
     if (rc) return rc;
-    return allow_dynamic_smem((const void*)k_j_walk_split, j_smem(P));
+    return use_xtab(P) ? allow_dynamic_smem((const void*)k_j_walk_split<true>, j_smem(P))
+                       : allow_dynamic_smem((const void*)k_j_walk_split<false>, j_smem(P));
 }
 
 int rho_walk_split_blocks_per_sm(ftcj_plan* P, int* out) {
     int n = 0;
-    FTCJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rho_walk_split, kTile, rho_smem(P)));
+    if (use_xtab(P))
+        FTCJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rho_walk_split<true>, kTile, rho_smem(P)));
+    else
+        FTCJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rho_walk_split<false>, kTile, rho_smem(P)));
     *out = n > 0 ? n : 1;
     return FTCJ_OK;
 }
@@ -525,10 +597,14 @@ int launch_rho_walk_split(ftcj_plan* P, int ndens, cudaStream_t s) {
         return FTCJ_OK;
     }
     dim3 g(P->npb, (unsigned)P->chunks.size(), ndens);
-    k_rho_walk_split<<<g, kTile, rho_smem(P), s>>>(
-        P->d_tiles, (int)P->tiles.size(), make_layout(P), reinterpret_cast<const float2*>(P->d_Dp),
-        reinterpret_cast<const SConst*>(P->d_split_const), reinterpret_cast<const SState*>(P->d_split_init),
-        P->npairs, P->d_lines, P->d_chunks, P->npb, reinterpret_cast<double2*>(P->d_rho_part), P->ng_half);
+    const int n1cnt = P->n1_max - P->n1_min + 1;
+    auto* kern = use_xtab(P) ? k_rho_walk_split<true> : k_rho_walk_split<false>;
+    kern<<<g, kTile, rho_smem(P), s>>>(P->d_tiles, (int)P->tiles.size(), make_layout(P),
+                                       reinterpret_cast<const float2*>(P->d_Dp),
+                                       reinterpret_cast<const SConst*>(P->d_split_const),
+                                       reinterpret_cast<const SState*>(P->d_split_init), P->npairs, P->d_lines,
+                                       P->d_chunks, P->npb, reinterpret_cast<double2*>(P->d_rho_part), P->ng_half,
+                                       P->n1_min, n1cnt);
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }
@@ -542,7 +618,8 @@ int launch_j_walk_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s
     }
     dim3 g((unsigned)P->tiles.size(), nch, ndens);
     const int n1cnt = P->n1_max - P->n1_min + 1;
-    k_j_walk_split<<<g, kTile, j_smem(P), s>>>(P->d_tiles, make_layout(P),
+    auto* kern = use_xtab(P) ? k_j_walk_split<true> : k_j_walk_split<false>;
+    kern<<<g, kTile, j_smem(P), s>>>(P->d_tiles, make_layout(P),
                                                reinterpret_cast<const SConst*>(P->d_split_const),
                                                reinterpret_cast<const SState*>(P->d_split_init), P->npairs,
                                                P->d_lines, P->d_chunks, nch, reinterpret_cast<const double2*>(W),
