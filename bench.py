@@ -109,10 +109,18 @@ def walk_flops(info, ndens, form):
     pass; both have the same count).  Per (pair record of class L, half-sphere G):
     FP64 form: 4L + 14 flops (an (L+1)-term complex Horner, prefactor x phase
     and the accumulation); split form: the same arithmetic evaluated in
-    double-float on the FP32 pipe, 38L + 142 FP32 flops (two complex
-    double-float products of 50, one complex-by-real product of 20, L Horner
-    or accumulation steps of 38, and one complex double-float sum of 22)."""
-    per = (lambda L: 4 * L + 14) if form == "fp64" else (lambda L: 38 * L + 142)
+    double-float on the FP32 pipe (an FMA counts two): L Horner or accumulation
+    steps of 38, one complex double-float product of 50 (prefactor x
+    polynomial) and one complex double-float sum of 22; where the n1 recurrence
+    runs (no per-record X(n1) table) each point also advances the prefactor and
+    its ratio, another complex product of 50 and a complex-by-real one of 20.
+    So 38L + 72 with the table, 38L + 142 without."""
+    if form == "fp64":
+        per = lambda L: 4 * L + 14
+    elif info.get("n1_table", 0) > 0:
+        per = lambda L: 38 * L + 72
+    else:
+        per = lambda L: 38 * L + 142
     return ndens * sum(n * info["ng_half"] * per(L) for L, n in enumerate(info["pairs_by_class"]))
 
 
@@ -214,6 +222,7 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     peaks = {"fp64": ftcj.probe_fma_peak(0), "split": ftcj.probe_fma_peak(1)}
     forms = {}
+    infos = {}
     results = {}
     for form, prec in (("split", ftcj.FTCJ_PREC_SPLIT), ("fp64", ftcj.FTCJ_PREC_FP64)):
         plan = ftcj.Plan.from_workload(w, precision=prec)
@@ -286,11 +295,14 @@ def main():
                                "h2d_bytes_per_step": Dk_h.numel() * 16,
                                "d2h_bytes_per_step": Jk_h.numel() * 16 + EJ_h.numel() * 8},
                        "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks,
-                       "wall_s_timed_region": t_wall}
+                       "wall_s_timed_region": t_wall,
+                       "walk_shape": {"rho_blocks": info["rho_blocks"], "n1_table": info["n1_table"]}}
+        infos[form] = info
         results[form] = (Jk.cpu().numpy(), EJ.cpu().numpy())
         plan.close()
 
     head = forms["split"]
+    info = infos["split"]
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -298,6 +310,8 @@ def main():
         "config": {"workload": WORKLOAD, "form": "split", "pair_g_units_per_step": units,
                    "npairs_ordered": info["npairs_ordered"], "pair_records": info["npairs"],
                    "ng_full": info["ng_full"], "nao": info["nao"], "nk": info["nk"],
+                   "records_by_class": info["pairs_by_class"], "rho_blocks": info["rho_blocks"],
+                   "n1_table": info["n1_table"],
                    "l2": f"{L2_FLUSH_BYTES >> 20} MB buffer written between timed steps",
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
         "e2e": {k: head["e2e"][k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")},

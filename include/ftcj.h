@@ -111,6 +111,9 @@ typedef struct {
     double gcut;
     double volume;
     size_t device_bytes;      /* device memory held by the plan */
+    int rho_blocks;           /* persistent blocks of the structure-factor walk */
+    int n1_table;             /* split form, orthorhombic cell: entries of the per-record
+                                 X(n1) table (0: the n1 walk runs the recurrence) */
 } ftcj_info;
 
 typedef struct ftcj_plan ftcj_plan;

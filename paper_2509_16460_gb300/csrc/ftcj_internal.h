@@ -148,6 +148,8 @@ struct ftcj_plan {
     ftcj::WLine* d_lines = nullptr;
     ftcj::WChunk* d_chunks = nullptr;
     ftcj::Tile* d_tiles = nullptr;
+    int* d_sched = nullptr;
+    std::vector<int> rho_sched;  // rho pass: npb+1 offsets, then tile ids grouped by block
     int* d_gvec = nullptr;
     double* d_vg = nullptr;          // v(G) on the half sphere
     double* d_tw = nullptr;          // twiddles, [3][16][16] complex
@@ -233,6 +235,7 @@ int rho_walk_blocks_per_sm(ftcj_plan* P, int* out);
 
 // --- split-precision walks (walk_split.cu) ---
 int setup_split(ftcj_plan* P);
+int split_xtab_entries(const ftcj_plan* P);  // 0 when the split walks run the n1 recurrence
 int rho_walk_split_blocks_per_sm(ftcj_plan* P, int* out);
 int launch_rho_walk_split(ftcj_plan* P, int ndens, cudaStream_t s);
 int launch_j_walk_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s);

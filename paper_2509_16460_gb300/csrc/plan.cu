@@ -4,6 +4,7 @@
 // half G sphere as lines along b_1 (Sec. 2.5, Eq. "G-space root finding"),
 // device allocation, and the device-side pair screening.
 #include <algorithm>
+#include <queue>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -197,12 +198,54 @@ int upload(ftcj_plan* P, T** ptr, const std::vector<T>& v) {
     return FTCJ_OK;
 }
 
+// Longest-processing-time assignment of the rho pass's tiles to its npb
+// persistent blocks (each block sums its tiles into its own row, so the
+// assignment is fixed at plan time and the sums stay deterministic).  A tile
+// walks every point of the chunk, so its cost is set by its class L: per point
+// the split form spends about 38L + 100 FP32 operations (polynomial, phase
+// product, batch reduction), the FP64 form about 4L + 24 FP64 operations.
+int build_rho_schedule(ftcj_plan* P) {
+    const int nt = (int)P->tiles.size(), nb = std::max(1, P->npb);
+    auto cost = [&](int t) {
+        const double L = (double)P->tiles[t].cls;
+        return P->precision == FTCJ_PREC_SPLIT ? 38.0 * L + 100.0 : 4.0 * L + 24.0;
+    };
+    std::vector<int> order(nt);
+    for (int t = 0; t < nt; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    using Slot = std::pair<double, int>;  // (load, block): ties go to the lower block
+    std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+    for (int b = 0; b < nb; ++b) heap.push({0.0, b});
+    std::vector<std::vector<int>> lists(nb);
+    for (int t : order) {
+        Slot s = heap.top();
+        heap.pop();
+        lists[s.second].push_back(t);
+        heap.push({s.first + cost(t), s.second});
+    }
+    std::vector<int> sched;
+    sched.reserve((size_t)nb + 1 + nt);
+    int off = 0;
+    for (int b = 0; b < nb; ++b) {
+        sched.push_back(off);
+        off += (int)lists[b].size();
+    }
+    sched.push_back(off);
+    for (int b = 0; b < nb; ++b) sched.insert(sched.end(), lists[b].begin(), lists[b].end());
+    P->rho_sched = sched;
+    if (P->d_sched) {
+        cudaFree(P->d_sched);
+        P->d_sched = nullptr;
+    }
+    return upload(P, &P->d_sched, P->rho_sched);
+}
+
 void free_device(ftcj_plan* P) {
     void* ptrs[] = {P->d_groups, P->d_members, P->d_pairs, P->d_walk, P->d_lines, P->d_chunks, P->d_tiles,
                     P->d_gvec, P->d_vg, P->d_tw, P->d_Tmat, P->d_D0n, P->d_J0n, P->d_cbuf0, P->d_cbuf1,
                     P->d_Dp, P->d_Jp, P->d_rho_part, P->d_rho, P->d_W, P->d_Epart, P->d_Dk_stage,
                     P->d_Jk_stage, P->d_EJ_stage, P->d_check, P->d_split_init, P->d_split_const, P->d_Jg,
-                    P->d_maps, P->d_map_off};
+                    P->d_maps, P->d_map_off, P->d_sched};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -388,6 +431,7 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     int nch = std::max<int>(1, (int)P->chunks.size());
     P->npb = std::max(1, std::min<int>((int)std::max<size_t>(1, P->tiles.size()), P->num_sms * bps / nch));
     if (prm->rho_blocks > 0) P->npb = std::min<int>(prm->rho_blocks, (int)std::max<size_t>(1, P->tiles.size()));
+    if ((rc = build_rho_schedule(P))) return rc;
 
     size_t nn = (size_t)P->nao * P->nao;
     size_t md = (size_t)P->max_dens;
@@ -476,6 +520,8 @@ int ftcj_plan_info(const ftcj_plan* P, ftcj_info* o) {
     o->gcut = P->gcut;
     o->volume = P->vol;
     o->device_bytes = P->device_bytes;
+    o->rho_blocks = P->npb;
+    o->n1_table = P->precision == FTCJ_PREC_SPLIT ? split_xtab_entries(P) : 0;
     return FTCJ_OK;
 }
 

@@ -292,7 +292,8 @@ __global__ void __launch_bounds__(kTile) k_rho_walk(const Tile* __restrict__ til
                                                     const double* __restrict__ Dp, const PairWalk* __restrict__ walk,
                                                     const WLine* __restrict__ lines,
                                                     const WChunk* __restrict__ chunks, int npb,
-                                                    double2* __restrict__ rho_part, long long ng_half, CellConst cc) {
+                                                    double2* __restrict__ rho_part, long long ng_half, CellConst cc,
+                                                    const int* __restrict__ sched) {
     extern __shared__ double2 smem[];
     const int b = blockIdx.x, cidx = blockIdx.y, d = blockIdx.z;
     const WChunk ch = chunks[cidx];
@@ -303,8 +304,9 @@ __global__ void __launch_bounds__(kTile) k_rho_walk(const Tile* __restrict__ til
     for (int i = threadIdx.x; i < npts; i += blockDim.x) row[i] = make_double2(0.0, 0.0);
     __syncthreads();
     const double* Dp_d = Dp + (long long)d * lay.total;
-    for (int t = b; t < ntiles; t += npb) {
-        const Tile tl = tiles[t];
+    // this block's tiles: sched[b] .. sched[b+1] index the list after the npb+1 offsets
+    for (int j = sched[b]; j < sched[b + 1]; ++j) {
+        const Tile tl = tiles[sched[npb + 1 + j]];
         switch (tl.cls) {
             case 0: rho_tile<0>(cc.M6, tl, lay, Dp_d, walk, lines, ch, buf, red, row); break;
             case 1: rho_tile<1>(cc.M6, tl, lay, Dp_d, walk, lines, ch, buf, red, row); break;
@@ -590,7 +592,8 @@ int launch_rho_walk(ftcj_plan* P, int ndens, cudaStream_t s) {
     dim3 g(P->npb, (unsigned)P->chunks.size(), ndens);
     k_rho_walk<<<g, kTile, rho_smem_bytes(P), s>>>(P->d_tiles, (int)P->tiles.size(), make_layout(P), P->d_Dp,
                                                    P->d_walk, P->d_lines, P->d_chunks, P->npb,
-                                                   reinterpret_cast<double2*>(P->d_rho_part), P->ng_half, P->cc);
+                                                   reinterpret_cast<double2*>(P->d_rho_part), P->ng_half, P->cc,
+                                                   P->d_sched);
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }

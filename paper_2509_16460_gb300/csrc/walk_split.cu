@@ -22,7 +22,7 @@
 namespace ftcj {
 namespace {
 
-constexpr int kSBatch = 16;  // points per reduction batch of the split rho walk
+constexpr int kSBatch = 8;  // points per reduction batch of the split rho walk (4 lanes per point)
 
 
 struct Layout {
@@ -189,28 +189,30 @@ __device__ __forceinline__ void powers23f(int n2, int n3, float pq[L + 1][L + 1]
 
 __device__ __forceinline__ cdf unpack(float4 v) { return cdf{{v.x, v.y}, {v.z, v.w}}; }
 
-// Sums the batch's contributions over the block's 128 records: warp w, lanes
-// j and j+16 add the two halves of point j's column of warp w's 32 records,
-// join with one shuffle, and the four warp sums are added into the row.
+// Sums the batch's contributions over the block's 128 records: in warp w the
+// four lanes j, j+8, j+16, j+24 each add a quarter of point j's column of the
+// warp's 32 records, two shuffles join the quarters, and the four warp sums
+// are added into the row.
 __device__ __forceinline__ void split_flush(float4* buf, float4* red, float4* row, int rbase, int nvalid) {
     __syncthreads();
     const int tid = threadIdx.x, lane = tid & 31, wv = tid >> 5;
-    const int j = lane & (kSBatch - 1), half = lane / kSBatch;
+    const int j = lane & (kSBatch - 1), quarter = lane / kSBatch;
     cdf s{{0.f, 0.f}, {0.f, 0.f}};
     if (j < nvalid) {
-        const float4* b = buf + j * (kTile + 1) + wv * 32 + half * 16;
-#pragma unroll 4
-        for (int k = 0; k < 16; ++k) s = cdf_add(s, unpack(b[k]));
+        const float4* b = buf + j * (kTile + 1) + wv * 32 + quarter * 8;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s = cdf_add(s, unpack(b[k]));
     }
-    cdf o;
-    o.re.hi = __shfl_down_sync(0xffffffffu, s.re.hi, 16);
-    o.re.lo = __shfl_down_sync(0xffffffffu, s.re.lo, 16);
-    o.im.hi = __shfl_down_sync(0xffffffffu, s.im.hi, 16);
-    o.im.lo = __shfl_down_sync(0xffffffffu, s.im.lo, 16);
-    if (half == 0 && j < nvalid) {
+#pragma unroll
+    for (int off = 16; off >= kSBatch; off >>= 1) {
+        cdf o;
+        o.re.hi = __shfl_down_sync(0xffffffffu, s.re.hi, off);
+        o.re.lo = __shfl_down_sync(0xffffffffu, s.re.lo, off);
+        o.im.hi = __shfl_down_sync(0xffffffffu, s.im.hi, off);
+        o.im.lo = __shfl_down_sync(0xffffffffu, s.im.lo, off);
         s = cdf_add(s, o);
-        red[wv * 32 + j] = make_float4(s.re.hi, s.re.lo, s.im.hi, s.im.lo);
     }
+    if (quarter == 0 && j < nvalid) red[wv * 32 + j] = make_float4(s.re.hi, s.re.lo, s.im.hi, s.im.lo);
     __syncthreads();
     if (tid < nvalid) {
         cdf r = unpack(row[rbase + tid]);
@@ -220,32 +222,32 @@ __device__ __forceinline__ void split_flush(float4* buf, float4* red, float4* ro
     }
 }
 
-// Builds the record's table X(n1) = exp(-c M11 n1^2) exp(-2 pi i f1 n1),
-// n1 in [n1min, n1min + n1cnt), from n1 = 0 outwards with the line-independent
-// ratios of an orthorhombic cell (the first line's RfL, RbL and q1).
-__device__ __forceinline__ void build_xtab(const SState& s0, const df q1, int n1min, int n1cnt, float4* Xs, int tid) {
-    const int i0 = -n1min;
+// Builds the record's table X(n1) = exp(-c M11 n1^2) exp(-2 pi i f1 n1) for
+// n1 in [0, nx) with the line-independent ratios of an orthorhombic cell (the
+// first line's RfL and q1).  There the backward ratio is the conjugate of the
+// forward one, so X(-n1) = conj X(n1) and the half table serves both ends.
+__device__ __forceinline__ void build_xtab(const SState& s0, const df q1, int nx, float4* Xs, int tid) {
     cdf x{{1.f, 0.f}, {0.f, 0.f}};
     cdf R = s0.RfL;
-    for (int n = 0; n < n1cnt - i0; ++n) {
-        Xs[(i0 + n) * kTile + tid] = make_float4(x.re.hi, x.re.lo, x.im.hi, x.im.lo);
+    for (int n = 0; n < nx; ++n) {
+        Xs[n * kTile + tid] = make_float4(x.re.hi, x.re.lo, x.im.hi, x.im.lo);
         x = cdf_mul(x, R);
         R = cdf_scale(R, q1);
     }
-    x = cdf{{1.f, 0.f}, {0.f, 0.f}};
-    R = s0.RbL;
-    for (int n = 1; n <= i0; ++n) {
-        x = cdf_mul(x, R);
-        R = cdf_scale(R, q1);
-        Xs[(i0 - n) * kTile + tid] = make_float4(x.re.hi, x.re.lo, x.im.hi, x.im.lo);
-    }
+}
+
+// X(m) from the half table: conj X(-m) for m < 0 (dir 1 walks m < 0)
+template <int DIR>
+__device__ __forceinline__ cdf xtab_at(const float4* Xs, int m, int tid) {
+    const cdf x = unpack(Xs[(DIR == 0 ? m : -m) * kTile + tid]);
+    return DIR == 0 ? x : cdf_conj(x);
 }
 
 template <int L, bool ORTHO>
 __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* __restrict__ Dp_d,
                                const SConst* __restrict__ cst, const SState* __restrict__ init_c,
                                const WLine* __restrict__ lines, const WChunk ch, float4* buf, float4* red,
-                               float4* row, float2* Dsm, float4* Xs, int n1min, int n1cnt) {
+                               float4* row, float2* Dsm, float4* Xs, int nx) {
     constexpr int NT = nterms(L);
     const int tid = threadIdx.x;
     const bool valid = tid < tl.count;
@@ -259,7 +261,7 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
         Dsm[t * kTile + tid] = valid ? Dp_d[lay.base[L] + (long long)t * cnt + loc] : make_float2(0.f, 0.f);
     const SConst k = valid ? cst[pi] : idle_const();
     const SState* init_p = init_c + (valid ? pi : 0);
-    if (ORTHO) build_xtab(valid ? *init_p : idle_state(), k.q1, n1min, n1cnt, Xs, tid);
+    if (ORTHO) build_xtab(valid ? *init_p : idle_state(), k.q1, nx, Xs, tid);
     SState s;
     int slot = 0, rbase = 0;
     for (int li = ch.l0; li < ch.l1; ++li) {
@@ -326,7 +328,8 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
 #pragma unroll
                     for (int i = L - 1; i >= 0; --i)
                         a = cdf{df_add(df_mulf(a.re, x), c[i].re), df_add(df_mulf(a.im, x), c[i].im)};
-                    const cdf z = ORTHO ? cdf_mul(unpack(Xs[(m - n1min) * kTile + tid]), a) : cdf_mul(gp, a);
+                    const cdf z = ORTHO ? cdf_mul(dir == 0 ? xtab_at<0>(Xs, m, tid) : xtab_at<1>(Xs, m, tid), a)
+                                        : cdf_mul(gp, a);
                     buf[slot * (kTile + 1) + tid] = make_float4(z.re.hi, z.re.lo, z.im.hi, z.im.lo);
                     if (++slot == kSBatch) {
                         split_flush(buf, red, row, rbase, kSBatch);
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(kTile, 3) k_rho_walk_split(const Tile* __restr
                                                           const WLine* __restrict__ lines,
                                                           const WChunk* __restrict__ chunks, int npb,
                                                           double2* __restrict__ rho_part, long long ng_half,
-                                                          int n1min, int n1cnt) {
+                                                          const int* __restrict__ sched, int nx) {
     extern __shared__ float4 ssm[];
     const int b = blockIdx.x, cidx = blockIdx.y, d = blockIdx.z;
     const WChunk ch = chunks[cidx];
@@ -363,19 +366,20 @@ __global__ void __launch_bounds__(kTile, 3) k_rho_walk_split(const Tile* __restr
     float4* red = buf + kSBatch * (kTile + 1);
     float2* Dsm = reinterpret_cast<float2*>(red + kTile);
     float4* Xs = reinterpret_cast<float4*>(Dsm + kMaxTerms * kTile);
-    float4* row = Xs + (ORTHO ? n1cnt * kTile : 0);
+    float4* row = Xs + (ORTHO ? nx * kTile : 0);
     for (int i = threadIdx.x; i < npts; i += blockDim.x) row[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     const float2* Dp_d = Dp + (long long)d * lay.total;
     const SState* init_c = init + (long long)cidx * npairs;
-    for (int t = b; t < ntiles; t += npb) {
-        const Tile tl = tiles[t];
+    // this block's tiles: sched[b] .. sched[b+1] index the list after the npb+1 offsets
+    for (int j = sched[b]; j < sched[b + 1]; ++j) {
+        const Tile tl = tiles[sched[npb + 1 + j]];
         switch (tl.cls) {
-            case 0: rho_tile_split<0, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, n1min, n1cnt); break;
-            case 1: rho_tile_split<1, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, n1min, n1cnt); break;
-            case 2: rho_tile_split<2, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, n1min, n1cnt); break;
-            case 3: rho_tile_split<3, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, n1min, n1cnt); break;
-            default: rho_tile_split<4, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, n1min, n1cnt); break;
+            case 0: rho_tile_split<0, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx); break;
+            case 1: rho_tile_split<1, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx); break;
+            case 2: rho_tile_split<2, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx); break;
+            case 3: rho_tile_split<3, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx); break;
+            default: rho_tile_split<4, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx); break;
         }
     }
     __syncthreads();
@@ -392,7 +396,7 @@ template <int L, bool ORTHO>
 __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __restrict__ cst,
                              const SState* __restrict__ init_c, const WLine* __restrict__ lines, const WChunk ch,
                              const float4* __restrict__ wsm, const float* __restrict__ pw, int n1min,
-                             double* __restrict__ Jp_dc, float2* Jsm, float4* Xs, int n1cnt) {
+                             double* __restrict__ Jp_dc, float2* Jsm, float4* Xs, int nx) {
     constexpr int NT = nterms(L);
     const int tid = threadIdx.x;
     const bool valid = tid < tl.count;
@@ -405,7 +409,7 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
     // (updated once per line)
 #pragma unroll
     for (int t = 0; t < NT; ++t) Jsm[t * kTile + tid] = make_float2(0.f, 0.f);
-    if (ORTHO) build_xtab(valid ? *init_p : idle_state(), k.q1, n1min, n1cnt, Xs, tid);
+    if (ORTHO) build_xtab(valid ? *init_p : idle_state(), k.q1, nx, Xs, tid);
     SState s;
     for (int li = ch.l0; li < ch.l1; ++li) {
         const WLine ln = lines[li];
@@ -441,7 +445,8 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
             for (int m = m0;; m += step) {
                 if (m >= ln.lo && m <= ln.hi) {
                     const cdf w = unpack(wsm[q++]);
-                    const cdf t = ORTHO ? cdf_mul(unpack(Xs[(m - n1min) * kTile + tid]), w) : cdf_mul(gp, w);
+                    const cdf t = ORTHO ? cdf_mul(dir == 0 ? xtab_at<0>(Xs, m, tid) : xtab_at<1>(Xs, m, tid), w)
+                                        : cdf_mul(gp, w);
                     A[0] = cdf_add(A[0], t);
                     const float* pwm = pw + (m - n1min) * 5;
 #pragma unroll
@@ -500,7 +505,8 @@ __global__ void __launch_bounds__(kTile, 3) k_j_walk_split(const Tile* __restric
                                                         const WLine* __restrict__ lines,
                                                         const WChunk* __restrict__ chunks, int nchunks,
                                                         const double2* __restrict__ W, long long ng_half, int n1min,
-                                                        int n1cnt, int max_chunk_pts, double* __restrict__ Jp) {
+                                                        int n1cnt, int nx, int max_chunk_pts,
+                                                        double* __restrict__ Jp) {
     extern __shared__ float4 ssm[];
     const int tix = blockIdx.x, cidx = blockIdx.y, d = blockIdx.z;
     const WChunk ch = chunks[cidx];
@@ -508,7 +514,7 @@ __global__ void __launch_bounds__(kTile, 3) k_j_walk_split(const Tile* __restric
     float4* wsm = ssm;
     float2* Jsm = reinterpret_cast<float2*>(ssm + max_chunk_pts);
     float4* Xs = reinterpret_cast<float4*>(Jsm + kMaxTerms * kTile);
-    float* pw = reinterpret_cast<float*>(Xs + (ORTHO ? n1cnt * kTile : 0));
+    float* pw = reinterpret_cast<float*>(Xs + (ORTHO ? nx * kTile : 0));
     const double2* Wd = W + (long long)d * ng_half + ch.p0;
     for (int i = threadIdx.x; i < npts; i += blockDim.x) {
         const double2 v = Wd[i];
@@ -526,11 +532,11 @@ __global__ void __launch_bounds__(kTile, 3) k_j_walk_split(const Tile* __restric
     double* Jp_dc = Jp + ((long long)d * nchunks + cidx) * lay.total;
     const SState* init_c = init + (long long)cidx * npairs;
     switch (tl.cls) {
-        case 0: j_tile_split<0, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, n1cnt); break;
-        case 1: j_tile_split<1, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, n1cnt); break;
-        case 2: j_tile_split<2, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, n1cnt); break;
-        case 3: j_tile_split<3, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, n1cnt); break;
-        default: j_tile_split<4, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, n1cnt); break;
+        case 0: j_tile_split<0, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, nx); break;
+        case 1: j_tile_split<1, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, nx); break;
+        case 2: j_tile_split<2, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, nx); break;
+        case 3: j_tile_split<3, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, nx); break;
+        default: j_tile_split<4, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, nx); break;
     }
 }
 
@@ -542,23 +548,30 @@ Layout make_layout(const ftcj_plan* P) {
     return l;
 }
 
+// entries of the half X(n1) table, n1 = 0 .. max(|n1_min|, n1_max)
+int xtab_entries(const ftcj_plan* P) { return std::max(-P->n1_min, P->n1_max) + 1; }
+
 // orthorhombic cells with a short enough n1 range use the per-record X(n1) table
-bool use_xtab(const ftcj_plan* P) { return P->ortho && (P->n1_max - P->n1_min + 1) <= 40; }
+bool use_xtab(const ftcj_plan* P) { return P->ortho && xtab_entries(P) <= 24; }
+
+size_t xtab_bytes(const ftcj_plan* P) {
+    return use_xtab(P) ? sizeof(float4) * (size_t)xtab_entries(P) * kTile : 0;
+}
 
 size_t rho_smem(const ftcj_plan* P) {
-    const size_t xt = use_xtab(P) ? sizeof(float4) * (size_t)(P->n1_max - P->n1_min + 1) * kTile : 0;
     return sizeof(float4) * ((size_t)kSBatch * (kTile + 1) + kTile + (size_t)std::max(P->max_chunk_pts, 1)) +
-           sizeof(float2) * (size_t)kMaxTerms * kTile + xt;
+           sizeof(float2) * (size_t)kMaxTerms * kTile + xtab_bytes(P);
 }
 
 size_t j_smem(const ftcj_plan* P) {
     const int n1cnt = P->n1_max - P->n1_min + 1;
-    const size_t xt = use_xtab(P) ? sizeof(float4) * (size_t)n1cnt * kTile : 0;
     return sizeof(float4) * (size_t)std::max(P->max_chunk_pts, 1) + sizeof(float2) * (size_t)kMaxTerms * kTile +
-           sizeof(float) * 5 * (size_t)n1cnt + xt;
+           sizeof(float) * 5 * (size_t)n1cnt + xtab_bytes(P);
 }
 
 }  // namespace
+
+int split_xtab_entries(const ftcj_plan* P) { return use_xtab(P) ? xtab_entries(P) : 0; }
 
 int setup_split(ftcj_plan* P) {
     const size_t nch = P->chunks.size();
@@ -597,14 +610,14 @@ int launch_rho_walk_split(ftcj_plan* P, int ndens, cudaStream_t s) {
         return FTCJ_OK;
     }
     dim3 g(P->npb, (unsigned)P->chunks.size(), ndens);
-    const int n1cnt = P->n1_max - P->n1_min + 1;
+    const int nx = use_xtab(P) ? xtab_entries(P) : 0;
     auto* kern = use_xtab(P) ? k_rho_walk_split<true> : k_rho_walk_split<false>;
     kern<<<g, kTile, rho_smem(P), s>>>(P->d_tiles, (int)P->tiles.size(), make_layout(P),
                                        reinterpret_cast<const float2*>(P->d_Dp),
                                        reinterpret_cast<const SConst*>(P->d_split_const),
                                        reinterpret_cast<const SState*>(P->d_split_init), P->npairs, P->d_lines,
                                        P->d_chunks, P->npb, reinterpret_cast<double2*>(P->d_rho_part), P->ng_half,
-                                       P->n1_min, n1cnt);
+                                       P->d_sched, nx);
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }
@@ -618,12 +631,13 @@ int launch_j_walk_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s
     }
     dim3 g((unsigned)P->tiles.size(), nch, ndens);
     const int n1cnt = P->n1_max - P->n1_min + 1;
+    const int nx = use_xtab(P) ? xtab_entries(P) : 0;
     auto* kern = use_xtab(P) ? k_j_walk_split<true> : k_j_walk_split<false>;
     kern<<<g, kTile, j_smem(P), s>>>(P->d_tiles, make_layout(P),
                                                reinterpret_cast<const SConst*>(P->d_split_const),
                                                reinterpret_cast<const SState*>(P->d_split_init), P->npairs,
                                                P->d_lines, P->d_chunks, nch, reinterpret_cast<const double2*>(W),
-                                               P->ng_half, P->n1_min, n1cnt, P->max_chunk_pts, P->d_Jp);
+                                               P->ng_half, P->n1_min, n1cnt, nx, P->max_chunk_pts, P->d_Jp);
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }

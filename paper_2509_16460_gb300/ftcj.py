@@ -48,7 +48,8 @@ class Info(ctypes.Structure):
                 ("npairs", ctypes.c_int64), ("npairs_ordered", ctypes.c_int64), ("ng_half", ctypes.c_int64),
                 ("ng_full", ctypes.c_int64), ("pair_g_units", ctypes.c_int64),
                 ("pairs_by_class", ctypes.c_int64 * 5), ("nlines", _c_int), ("nchunks", _c_int),
-                ("gcut", _c_double), ("volume", _c_double), ("device_bytes", ctypes.c_size_t)]
+                ("gcut", _c_double), ("volume", _c_double), ("device_bytes", ctypes.c_size_t),
+                ("rho_blocks", _c_int), ("n1_table", _c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
