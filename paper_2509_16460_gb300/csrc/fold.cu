@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "df.cuh"
 #include "ftcj_internal.h"
 
 namespace ftcj {
@@ -218,6 +219,188 @@ __global__ void __launch_bounds__(kFusedT) k_unfold_fused(const double* __restri
     }
 }
 
+// ---- split-precision fused transform -------------------------------------
+// The same transform with the column in complex double-float (hi + lo FP32
+// pairs, ~48 bits): the butterflies run on the FP32 pipe.  Doubles are split
+// and rebuilt from their exponent and mantissa fields with integer operations,
+// so that only one FP64 addition per output value touches GB300's narrow FP64
+// pipe.  Magnitudes below 2^-126 (the normal FP32 range) are dropped on input
+// and output: an absolute error below 2^-126.
+
+// hi = x truncated to 24 significant bits, lo = the remaining 29 bits rounded
+// to 24 (a subnormal FP32 number when x is below about 2^-74)
+__device__ __forceinline__ df split_double(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(u >> 63) << 31;
+    const int e = (int)((u >> 52) & 0x7ff) - 1023;
+    const unsigned long long m = u & 0xfffffffffffffULL;
+    if (e < -126) return df{__uint_as_float(sign), 0.f};
+    if (e > 127) return df{__uint_as_float(sign | 0x7f800000u | (m ? 0x400000u : 0u)), 0.f};
+    const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
+    const unsigned r = (unsigned)(m & 0x1fffffffULL);
+    float lo = 0.f;
+    if (r != 0u) {
+        // r 2^(e-52) by power-of-two factors that are normal FP32 numbers: the
+        // first product is exact, the second rounds once into the subnormals
+        const int sc = e - 52;
+        const float rf = __uint2float_rn(r);
+        lo = sc >= -126 ? rf * __uint_as_float((unsigned)(sc + 127) << 23)
+                        : (rf * __uint_as_float((unsigned)(sc + 64 + 127) << 23)) * 5.421010862427522e-20f;  // 2^-64
+        lo = __uint_as_float(__float_as_uint(lo) | sign);
+    }
+    return df{hi, lo};
+}
+
+// the double with the value of a normal (or zero, inf, nan) float, built from its fields
+__device__ __forceinline__ double widen(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned long long s = (unsigned long long)(b >> 31) << 63;
+    const unsigned ex = (b >> 23) & 0xffu;
+    const unsigned long long mant = (unsigned long long)(b & 0x7fffffu) << 29;
+    if (ex == 0u) return __longlong_as_double((long long)s);
+    if (ex == 0xffu) return __longlong_as_double((long long)(s | 0x7ff0000000000000ULL | mant));
+    return __longlong_as_double((long long)(s | ((unsigned long long)(ex - 127u + 1023u) << 52) | mant));
+}
+
+__device__ __forceinline__ double join_df(df a) { return widen(a.hi) + widen(a.lo); }
+
+__device__ __forceinline__ cdf cdf_sub(cdf a, cdf b) { return cdf{df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
+
+// -i v (forward twiddle of a length-4 axis) and +i v (inverse)
+__device__ __forceinline__ cdf mul_mi(cdf v) { return cdf{v.im, df_neg(v.re)}; }
+__device__ __forceinline__ cdf mul_pi(cdf v) { return cdf{df_neg(v.im), v.re}; }
+
+// in-register DFT of v[base + m*stride], m < N (N = 1, 2, 4), in natural order
+template <int N, bool INV>
+__device__ __forceinline__ void dft_reg(cdf* v, int base, int stride) {
+    if (N == 2) {
+        const cdf x0 = v[base], x1 = v[base + stride];
+        v[base] = cdf_add(x0, x1);
+        v[base + stride] = cdf_sub(x0, x1);
+    } else if (N == 4) {
+        const cdf x0 = v[base], x1 = v[base + stride], x2 = v[base + 2 * stride], x3 = v[base + 3 * stride];
+        const cdf a = cdf_add(x0, x2), b = cdf_sub(x0, x2), c = cdf_add(x1, x3), d = cdf_sub(x1, x3);
+        const cdf wd = INV ? mul_pi(d) : mul_mi(d);  // y1 = b + w d, y3 = b - w d
+        v[base] = cdf_add(a, c);
+        v[base + 2 * stride] = cdf_sub(a, c);
+        v[base + stride] = cdf_add(b, wd);
+        v[base + 3 * stride] = cdf_sub(b, wd);
+    }
+}
+
+__device__ __forceinline__ cdf shfl_xor_cdf(cdf v, int mask) {
+    return cdf{{__shfl_xor_sync(0xffffffffu, v.re.hi, mask), __shfl_xor_sync(0xffffffffu, v.re.lo, mask)},
+               {__shfl_xor_sync(0xffffffffu, v.im.hi, mask), __shfl_xor_sync(0xffffffffu, v.im.lo, mask)}};
+}
+
+// Axis-1 DFT across the N1 lanes of a column group (lane j holds x_j);
+// returns the output of index out_index(j).  N1 = 2: y_j.  N1 = 4: two
+// radix-2 exchanges; lane j ends with y of the bit-reversed index.
+template <bool INV>
+__device__ __forceinline__ cdf dft_lanes(cdf x, int j, int N1) {
+    if (N1 == 2) {
+        const cdf o = shfl_xor_cdf(x, 1);
+        return j == 0 ? cdf_add(x, o) : cdf_sub(o, x);
+    }
+    if (N1 == 4) {
+        // lanes 0,1: a_j = x_j + x_{j+2}; lanes 2,3: b_{j-2} = x_{j-2} - x_j
+        cdf o = shfl_xor_cdf(x, 2);
+        const cdf t = j < 2 ? cdf_add(x, o) : cdf_sub(o, x);
+        // y0 = a0 + a1, y2 = a0 - a1, y1 = b0 + w b1, y3 = b0 - w b1
+        o = shfl_xor_cdf(t, 1);
+        switch (j) {
+            case 0: return cdf_add(t, o);
+            case 1: return cdf_sub(o, t);
+            case 2: return cdf_add(t, INV ? mul_pi(o) : mul_mi(o));
+            default: return cdf_sub(o, INV ? mul_pi(t) : mul_mi(t));
+        }
+    }
+    return x;
+}
+
+__device__ __forceinline__ int out_index(int j, int N1) { return N1 == 4 ? ((j & 1) << 1) | (j >> 1) : j; }
+
+constexpr int kRegBlock = 128;
+
+// Split-form transforms for meshes whose axes are 1, 2 or 4 long (the
+// twiddles are +-1, +-i, so the transform is additions only), in complex
+// double-float on the FP32 pipe.  N1 consecutive lanes share one AO-pair
+// column of one density; lane j holds the i1 = j plane of N2 x N3 values in
+// registers, transforms it along axes 3 and 2, and the axis-1 transform runs
+// across the lanes with shuffles.  MODE 0: fold, D^{0n} = Re (1/nk) sum_k
+// exp(-i k.R_n) D^k; MODE 1: unfold, J^k = sum_n exp(+i k.R_n) J^{0n}.
+template <int MODE, int N2, int N3>
+__global__ void __launch_bounds__(kRegBlock) k_fold_reg(const void* __restrict__ in, void* __restrict__ out,
+                                                        long long E, int N1, df inv_nk) {
+    constexpr int P = N2 * N3;
+    constexpr bool INV = MODE == 1;
+    const int j = threadIdx.x % N1;
+    const long long e = (long long)blockIdx.x * (kRegBlock / N1) + threadIdx.x / N1;
+    const long long d = blockIdx.y;
+    const int nk = N1 * P;
+    const bool valid = e < E;
+    cdf v[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        const long long idx = (d * nk + (long long)j * P + q) * E + e;
+        if (MODE == 0) {
+            const double2 x = valid ? static_cast<const double2*>(in)[idx] : make_double2(0.0, 0.0);
+            v[q] = cdf{split_double(x.x), split_double(x.y)};
+        } else {
+            const double x = valid ? static_cast<const double*>(in)[idx] : 0.0;
+            v[q] = cdf{split_double(x), {0.f, 0.f}};
+        }
+    }
+#pragma unroll
+    for (int i2 = 0; i2 < N2; ++i2) dft_reg<N3, INV>(v, i2 * N3, 1);
+#pragma unroll
+    for (int i3 = 0; i3 < N3; ++i3) dft_reg<N2, INV>(v, i3, N3);
+#pragma unroll
+    for (int q = 0; q < P; ++q) v[q] = dft_lanes<INV>(v[q], j, N1);
+    if (!valid) return;
+    const long long base = (d * nk + (long long)out_index(j, N1) * P) * E + e;
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        if (MODE == 0)
+            static_cast<double*>(out)[base + (long long)q * E] = join_df(df_mul(v[q].re, inv_nk));
+        else
+            static_cast<double2*>(out)[base + (long long)q * E] = make_double2(join_df(v[q].re), join_df(v[q].im));
+    }
+}
+
+int axis_code(int n) { return n == 1 ? 0 : (n == 2 ? 1 : (n == 4 ? 2 : -1)); }
+
+template <int MODE>
+int launch_fold_reg(const ftcj_plan* P, int ndens, const void* in, void* out, cudaStream_t s) {
+    const long long E = (long long)P->nao * P->nao;
+    const int N1 = P->km[0];
+    dim3 g(nblocks(E * N1, kRegBlock), ndens);
+    const df inv = df_from_double(1.0 / P->nk);
+    const int code = axis_code(P->km[1]) * 3 + axis_code(P->km[2]);
+#define FTCJ_REG_CASE(c, n2, n3) \
+    case c: k_fold_reg<MODE, n2, n3><<<g, kRegBlock, 0, s>>>(in, out, E, N1, inv); break;
+    switch (code) {
+        FTCJ_REG_CASE(0, 1, 1)
+        FTCJ_REG_CASE(1, 1, 2)
+        FTCJ_REG_CASE(2, 1, 4)
+        FTCJ_REG_CASE(3, 2, 1)
+        FTCJ_REG_CASE(4, 2, 2)
+        FTCJ_REG_CASE(5, 2, 4)
+        FTCJ_REG_CASE(6, 4, 1)
+        FTCJ_REG_CASE(7, 4, 2)
+        default: k_fold_reg<MODE, 4, 4><<<g, kRegBlock, 0, s>>>(in, out, E, N1, inv); break;
+    }
+#undef FTCJ_REG_CASE
+    FTCJ_CUDA(cudaGetLastError());
+    return FTCJ_OK;
+}
+
+// the split form's register transform covers meshes with every axis 1, 2 or 4 long
+bool reg_fold_supported(const ftcj_plan* P) {
+    return P->precision == FTCJ_PREC_SPLIT && P->nk > 1 && axis_code(P->km[0]) >= 0 && axis_code(P->km[1]) >= 0 &&
+           axis_code(P->km[2]) >= 0;
+}
+
 }  // namespace
 
 int launch_twiddles(ftcj_plan* P) {
@@ -283,11 +466,12 @@ int fused_fold_supported(const ftcj_plan* P) { return P->nk > 1 && P->nk <= kFus
 int setup_fold(ftcj_plan* P) {
     if (!fused_fold_supported(P)) return FTCJ_OK;
     int rc = allow_dynamic_smem((const void*)k_fold_fused, fused_smem(P));
-    if (rc) return rc;
-    return allow_dynamic_smem((const void*)k_unfold_fused, fused_smem(P));
+    if (!rc) rc = allow_dynamic_smem((const void*)k_unfold_fused, fused_smem(P));
+    return rc;
 }
 
 int launch_fold(ftcj_plan* P, int ndens, const double* Dk, double* D0n, cudaStream_t s) {
+    if (reg_fold_supported(P)) return launch_fold_reg<0>(P, ndens, Dk, D0n, s);
     if (!fused_fold_supported(P)) return run_stages(P, ndens, Dk, D0n, 0, s);
     long long E = (long long)P->nao * P->nao;
     dim3 g(nblocks(E, kFusedT), ndens);
@@ -298,6 +482,7 @@ int launch_fold(ftcj_plan* P, int ndens, const double* Dk, double* D0n, cudaStre
 }
 
 int launch_unfold(ftcj_plan* P, int ndens, const double* J0n, double* Jk, cudaStream_t s) {
+    if (reg_fold_supported(P)) return launch_fold_reg<1>(P, ndens, J0n, Jk, s);
     if (!fused_fold_supported(P)) return run_stages(P, ndens, J0n, Jk, 1, s);
     long long E = (long long)P->nao * P->nao;
     dim3 g(nblocks(E, kFusedT), ndens);

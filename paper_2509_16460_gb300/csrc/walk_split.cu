@@ -192,8 +192,9 @@ __device__ __forceinline__ cdf unpack(float4 v) { return cdf{{v.x, v.y}, {v.z, v
 // Sums the batch's contributions over the block's 128 records: in warp w the
 // four lanes j, j+8, j+16, j+24 each add a quarter of point j's column of the
 // warp's 32 records, two shuffles join the quarters, and the four warp sums
-// are added into the row.
-__device__ __forceinline__ void split_flush(float4* buf, float4* red, float4* row, int rbase, int nvalid) {
+// are added into the row.  Not inlined: one copy serves every call site of
+// the five record classes, which keeps the walk inside the instruction cache.
+__device__ __noinline__ void split_flush(float4* buf, float4* red, float4* row, int rbase, int nvalid) {
     __syncthreads();
     const int tid = threadIdx.x, lane = tid & 31, wv = tid >> 5;
     const int j = lane & (kSBatch - 1), quarter = lane / kSBatch;
@@ -237,10 +238,10 @@ __device__ __forceinline__ void build_xtab(const SState& s0, const df q1, int nx
 }
 
 // X(m) from the half table: conj X(-m) for m < 0 (dir 1 walks m < 0)
-template <int DIR>
-__device__ __forceinline__ cdf xtab_at(const float4* Xs, int m, int tid) {
-    const cdf x = unpack(Xs[(DIR == 0 ? m : -m) * kTile + tid]);
-    return DIR == 0 ? x : cdf_conj(x);
+__device__ __forceinline__ cdf xtab_at(const float4* Xs, int m, int dir, int tid) {
+    const float4 v = Xs[(dir == 0 ? m : -m) * kTile + tid];
+    const float sg = dir == 0 ? 1.f : -1.f;
+    return cdf{{v.x, v.y}, {sg * v.z, sg * v.w}};
 }
 
 template <int L, bool ORTHO>
@@ -298,7 +299,8 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
 #pragma unroll
             for (int i = 0; i <= L; ++i) c[i] = cdf_mul(s.gpL, c[i]);
         }
-#pragma unroll
+        // not unrolled: the walk's instruction footprint (five classes) stays in the instruction cache
+#pragma unroll 1
         for (int dir = 0; dir < 2; ++dir) {
             int m0, m1, step;
             cdf gp, R;
@@ -328,8 +330,9 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
 #pragma unroll
                     for (int i = L - 1; i >= 0; --i)
                         a = cdf{df_add(df_mulf(a.re, x), c[i].re), df_add(df_mulf(a.im, x), c[i].im)};
-                    const cdf z = ORTHO ? cdf_mul(dir == 0 ? xtab_at<0>(Xs, m, tid) : xtab_at<1>(Xs, m, tid), a)
-                                        : cdf_mul(gp, a);
+                    cdf xv;
+                    if (ORTHO) xv = xtab_at(Xs, m, dir, tid);
+                    const cdf z = ORTHO ? cdf_mul(xv, a) : cdf_mul(gp, a);
                     buf[slot * (kTile + 1) + tid] = make_float4(z.re.hi, z.re.lo, z.im.hi, z.im.lo);
                     if (++slot == kSBatch) {
                         split_flush(buf, red, row, rbase, kSBatch);
@@ -445,8 +448,9 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
             for (int m = m0;; m += step) {
                 if (m >= ln.lo && m <= ln.hi) {
                     const cdf w = unpack(wsm[q++]);
-                    const cdf t = ORTHO ? cdf_mul(dir == 0 ? xtab_at<0>(Xs, m, tid) : xtab_at<1>(Xs, m, tid), w)
-                                        : cdf_mul(gp, w);
+                    cdf xv;
+                    if (ORTHO) xv = xtab_at(Xs, m, dir, tid);
+                    const cdf t = ORTHO ? cdf_mul(xv, w) : cdf_mul(gp, w);
                     A[0] = cdf_add(A[0], t);
                     const float* pwm = pw + (m - n1min) * 5;
 #pragma unroll
