@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batch and molecular-crystal legs")
     return ap.parse_args()
 
 
@@ -104,6 +105,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (the time of the slowest replica); x itself
+    without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_replica, seconds):
+    """Units of all replicas per second of the slowest one."""
+    return world * units_per_replica / seconds
+
+
 def walk_flops(info, ndens, form):
     """Algorithmic flops of one walk launch (structure-factor or back-contraction
     pass; both have the same count).  Per (pair record of class L, half-sphere G):
@@ -154,6 +171,89 @@ def cpu_oracle_run(w, pair_stride):
         pass
     units = r["units"] * w.ndens
     return r, units, threads
+
+
+def time_events(fn, steps, flush, stream):
+    """Mean device ms of fn() over `steps` calls, L2 flushed before each."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        fn()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+
+def batch_leg(ftcj, W, torch, flush, steps):
+    """The uneven batch: 64 independent triclinic cells, walk shapes picked by
+    the autotuner, the whole batch captured once into a CUDA graph and
+    replayed; beside it the same cells built one after another on one stream."""
+    import numpy as np
+    cells = W.cfg4()
+    Dks = [torch.from_numpy(np.ascontiguousarray(w.Dk)).cuda() for w in cells]
+    out = {"workload": "64 seeded triclinic cells, edges 6-16 bohr, 2-24 centres (H/C/O/Mg-like templates), "
+                       "k-meshes 1..3 per axis, omega 0.3-0.5",
+           "ncell": len(cells)}
+    t0 = time.perf_counter()
+    B = ftcj.Batch(cells, precision=ftcj.FTCJ_PREC_SPLIT, autotune=True)
+    out["setup_s_with_autotune"] = time.perf_counter() - t0
+    units = sum(float(i["pair_g_units"]) * w.ndens for i, w in zip(B.infos, cells))
+    out["pair_g_units_per_step"] = units
+    s = torch.cuda.Stream()
+    Jg, Eg = B.outputs_like(Dks)
+    torch.cuda.synchronize()
+    B.capture(Dks, Jg, Eg, stream=s)
+    for _ in range(3):
+        B.replay(stream=s)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        ms = time_events(lambda: B.replay(stream=s), steps, flush, s)
+    out["graph_replay"] = {"ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT}
+    stream = torch.cuda.current_stream()
+    plans = [ftcj.Plan.from_workload(w, precision=ftcj.FTCJ_PREC_SPLIT) for w in cells]
+    outs = [p.jbuild(D) for p, D in zip(plans, Dks)]
+
+    def serial():
+        for p, D, (J, E) in zip(plans, Dks, outs):
+            p.jbuild(D, J, E)
+    for _ in range(3):
+        serial()
+    ms_serial = time_events(serial, steps, flush, stream)
+    out["serial_one_stream"] = {"ms_per_step": ms_serial, "value": units / (ms_serial * 1e-3), "unit": UNIT}
+    out["max_abs_dJ_graph_vs_serial"] = max(float((a - b[0]).abs().max()) for a, b in zip(Jg, outs))
+    for p in plans:
+        p.close()
+    B.close()
+    return out
+
+
+def cfg3_leg(ftcj, W, torch, flush, steps):
+    """The molecular-crystal cell (1056 AOs, k 2x2x2, 2 spin densities in one
+    call), split and FP64 forms."""
+    import numpy as np
+    w = W.cfg3()
+    Dk = torch.from_numpy(np.ascontiguousarray(w.Dk)).cuda()
+    out = {"workload": "orthorhombic 14.0x17.8x12.9 bohr, 4 six-rings (24 C-like, 24 H-like), 1056 spherical AOs, "
+                       "k 2x2x2, 2 spin densities x 8 D^k, omega 0.5", "ndens": w.ndens}
+    stream = torch.cuda.current_stream()
+    res = {}
+    for form, prec in (("split", ftcj.FTCJ_PREC_SPLIT), ("fp64", ftcj.FTCJ_PREC_FP64)):
+        p = ftcj.Plan.from_workload(w, precision=prec)
+        units = float(p.info["pair_g_units"]) * w.ndens
+        J, E = p.jbuild(Dk)
+        for _ in range(2):
+            p.jbuild(Dk, J, E)
+        ms = time_events(lambda: p.jbuild(Dk, J, E), steps, flush, stream)
+        out[form] = {"ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT}
+        out["pair_g_units_per_step"] = units
+        res[form] = (J.clone(), E.clone())
+        p.close()
+    out["split_vs_fp64_max_abs_dJ"] = float((res["split"][0] - res["fp64"][0]).abs().max())
+    out["split_vs_fp64_abs_dEJ"] = float((res["split"][1] - res["fp64"][1]).abs().max())
+    out["split_speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["split"]["ms_per_step"]
+    return out
 
 
 def run_reference(args, world, rank):
@@ -252,12 +352,8 @@ def main():
         step_ms = [a.elapsed_time(b) for a, b in ev]
         phase_ms, batches, launches = plan.profile_read()
         plan.profile_enable(0)
-        ms = statistics.mean(step_ms)
-        if dist is not None:
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        value = world * units / (ms * 1e-3)
+        ms = max_over_ranks(statistics.mean(step_ms), dist, "cuda")
+        value = whole_job_rate(world, units, ms * 1e-3)
         # end to end through the host-buffer entry point
         Dk_h = torch.from_numpy(np.ascontiguousarray(w.Dk)).pin_memory()
         Jk_h = torch.empty(Dk_h.shape, dtype=torch.complex128).pin_memory()
@@ -271,11 +367,7 @@ def main():
             t0 = time.perf_counter()
             plan.jbuild_host(Dk_h, Jk_h, EJ_h)
             e2e_t.append(time.perf_counter() - t0)
-        e2e_s = statistics.mean(e2e_t)
-        if dist is not None:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(statistics.mean(e2e_t), dist, "cuda")
         # roofline of the dominant kernel: FP64 pipe (fp64) or FP32 pipe (split)
         suffix = "_split" if form == "split" else ""
         walks = {"k_rho_walk" + suffix: phase_ms["rho_walk"], "k_j_walk" + suffix: phase_ms["j_walk"]}
@@ -291,7 +383,8 @@ def main():
                     "nominal_peak": 152 * 2 * 2.07e9 * (2 if form == "fp64" else 128) / 1e12,
                     "phase_ms_per_step": {k: v / max(batches, 1) for k, v in phase_ms.items()}}
         forms[form] = {"value": value, "unit": UNIT, "ms_per_step": ms, "step_ms_min": min(step_ms),
-                       "e2e": {"value": world * units / e2e_s, "unit": UNIT, "ms_per_step": e2e_s * 1e3,
+                       "e2e": {"value": whole_job_rate(world, units, e2e_s), "unit": UNIT,
+                               "ms_per_step": e2e_s * 1e3,
                                "h2d_bytes_per_step": Dk_h.numel() * 16,
                                "d2h_bytes_per_step": Jk_h.numel() * 16 + EJ_h.numel() * 8},
                        "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks,
@@ -322,6 +415,10 @@ def main():
         "split_speedup_vs_fp64": forms["fp64"]["ms_per_step"] / head["ms_per_step"],
     }
 
+    if rank == 0 and not args.no_extra:
+        extra_steps = max(3, min(args.steps, 10))
+        line["batch"] = batch_leg(ftcj, W, torch, flush, extra_steps)
+        line["workloads"] = {"molecular_crystal": cfg3_leg(ftcj, W, torch, flush, extra_steps)}
     if rank == 0 and not args.no_cpu_baseline:
         # the whole oracle on the host cores: the CPU baseline and the accuracy of this run
         r, cu, threads = cpu_oracle_run(w, 1)
