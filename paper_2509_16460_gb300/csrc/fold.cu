@@ -219,50 +219,8 @@ __global__ void __launch_bounds__(kFusedT) k_unfold_fused(const double* __restri
     }
 }
 
-// ---- split-precision fused transform -------------------------------------
-// The same transform with the column in complex double-float (hi + lo FP32
-// pairs, ~48 bits): the butterflies run on the FP32 pipe.  Doubles are split
-// and rebuilt from their exponent and mantissa fields with integer operations,
-// so that only one FP64 addition per output value touches GB300's narrow FP64
-// pipe.  Magnitudes below 2^-126 (the normal FP32 range) are dropped on input
-// and output: an absolute error below 2^-126.
+// ---- split-precision register transform ----------------------------------
 
-// hi = x truncated to 24 significant bits, lo = the remaining 29 bits rounded
-// to 24 (a subnormal FP32 number when x is below about 2^-74)
-__device__ __forceinline__ df split_double(double x) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-    const unsigned sign = (unsigned)(u >> 63) << 31;
-    const int e = (int)((u >> 52) & 0x7ff) - 1023;
-    const unsigned long long m = u & 0xfffffffffffffULL;
-    if (e < -126) return df{__uint_as_float(sign), 0.f};
-    if (e > 127) return df{__uint_as_float(sign | 0x7f800000u | (m ? 0x400000u : 0u)), 0.f};
-    const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
-    const unsigned r = (unsigned)(m & 0x1fffffffULL);
-    float lo = 0.f;
-    if (r != 0u) {
-        // r 2^(e-52) by power-of-two factors that are normal FP32 numbers: the
-        // first product is exact, the second rounds once into the subnormals
-        const int sc = e - 52;
-        const float rf = __uint2float_rn(r);
-        lo = sc >= -126 ? rf * __uint_as_float((unsigned)(sc + 127) << 23)
-                        : (rf * __uint_as_float((unsigned)(sc + 64 + 127) << 23)) * 5.421010862427522e-20f;  // 2^-64
-        lo = __uint_as_float(__float_as_uint(lo) | sign);
-    }
-    return df{hi, lo};
-}
-
-// the double with the value of a normal (or zero, inf, nan) float, built from its fields
-__device__ __forceinline__ double widen(float f) {
-    const unsigned b = __float_as_uint(f);
-    const unsigned long long s = (unsigned long long)(b >> 31) << 63;
-    const unsigned ex = (b >> 23) & 0xffu;
-    const unsigned long long mant = (unsigned long long)(b & 0x7fffffu) << 29;
-    if (ex == 0u) return __longlong_as_double((long long)s);
-    if (ex == 0xffu) return __longlong_as_double((long long)(s | 0x7ff0000000000000ULL | mant));
-    return __longlong_as_double((long long)(s | ((unsigned long long)(ex - 127u + 1023u) << 52) | mant));
-}
-
-__device__ __forceinline__ double join_df(df a) { return widen(a.hi) + widen(a.lo); }
 
 __device__ __forceinline__ cdf cdf_sub(cdf a, cdf b) { return cdf{df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
 

@@ -19,6 +19,7 @@ constexpr int kMaxTerms = (kLpair + 1) * (kLpair + 2) * (kLpair + 3) / 6;  // 35
 constexpr int kTile = 128;                 // pair records per walker block
 constexpr int kBatch = 32;                 // points per rho reduction batch
 constexpr int kChunkMax = 4096;            // G points per walk chunk
+constexpr int kRedPoints = 4;  // G points per block of the rho row reduction
 constexpr int kSortTile = 1024;            // candidates per sort tile
 
 __host__ __device__ constexpr int nterms(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
@@ -96,6 +97,18 @@ struct MapThreads {
     int slots[kNclass];
 };
 
+// Record-major blocks of one class (the split form's map kernels): class c
+// owns blocks [bstart[c], bstart[c+1]), each holding `per` whole records of
+// `width` threads and `stage` shared values per record.
+struct RecBlocks {
+    long long rstart[kNclass];
+    long long rcount[kNclass];
+    int bstart[kNclass + 1];
+    int per[kNclass];
+    int width[kNclass];
+    int stage[kNclass];
+};
+
 // Per-cell constants, passed to kernels by value (so plans of different cells
 // can be alive and used together).
 struct CellConst {
@@ -165,6 +178,9 @@ struct ftcj_plan {
     long long* d_map_off = nullptr;  // [npairs + 1]
     long long map_doubles = 0;
     ftcj::MapThreads mt_terms, mt_outs;
+    ftcj::RecBlocks rb_terms, rb_outs;  // a3 / a7 blocks of the double-float maps
+    bool maps_df = false;               // maps stored as double-float (split form)
+    size_t rb_terms_smem = 0, rb_outs_smem = 0;
     double* d_rho_part = nullptr;    // complex [max_dens][npb][ng_half]
     double* d_rho = nullptr;         // complex [max_dens][ng_half]
     double* d_W = nullptr;           // complex [max_dens][ng_half]

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "df.cuh"
 #include "ftcj_internal.h"
 
 namespace ftcj {
@@ -230,6 +231,173 @@ __global__ void __launch_bounds__(256) k_jtransform_map(const PairDev* __restric
         atomicAdd(J0n + ((long long)d * nk + pr.mcell) * nn + (long long)(mb.ao + q) * nao + ma.ao + f, s);
 }
 
+// ---- split form: double-float maps, record-major blocks --------------------
+// A block holds whole records of one class.  a3 stages each record's combined
+// density elements (D^{0[L]}_{fq} + D^{0[-L]}_{qf}, split into double-float)
+// once in shared memory and gives every term its own thread; a7 stages each
+// record's J'_t (summed over the walk chunks) and gives every output element
+// its own thread.  Arithmetic in double-float on the FP32 pipe.
+
+// AO row and column of element e of a record (member pairs in order, then f, q)
+__device__ __forceinline__ bool entry_ao(const GroupDev& A, const GroupDev& B, const MemberDev* __restrict__ mem,
+                                         int e, int& row, int& col) {
+    for (int ia = A.mem0; ia < A.mem1; ++ia) {
+        const MemberDev ma = mem[ia];
+        const int nfa = nfunc_d(ma.l, ma.sph);
+        for (int ib = B.mem0; ib < B.mem1; ++ib) {
+            const MemberDev mb = mem[ib];
+            const int nfb = nfunc_d(mb.l, mb.sph);
+            if (e < nfa * nfb) {
+                row = ma.ao + e / nfb;
+                col = mb.ao + e % nfb;
+                return true;
+            }
+            e -= nfa * nfb;
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ int entries_of(const GroupDev& A, const GroupDev& B, const MemberDev* __restrict__ mem) {
+    int n = 0;
+    for (int ia = A.mem0; ia < A.mem1; ++ia)
+        for (int ib = B.mem0; ib < B.mem1; ++ib)
+            n += nfunc_d(mem[ia].l, mem[ia].sph) * nfunc_d(mem[ib].l, mem[ib].sph);
+    return n;
+}
+
+__device__ __forceinline__ int block_class(const RecBlocks& rb) {
+    int c = 0;
+    while (c < kNclass - 1 && (int)blockIdx.x >= rb.bstart[c + 1]) ++c;
+    return c;
+}
+
+__global__ void __launch_bounds__(256) k_hermite_map_df(const PairDev* __restrict__ pairs,
+                                                        const GroupDev* __restrict__ G,
+                                                        const MemberDev* __restrict__ mem,
+                                                        const long long* __restrict__ moff,
+                                                        const float2* __restrict__ maps,
+                                                        const double* __restrict__ D0n, int nao, int nk,
+                                                        MapLayout lay, RecBlocks rb, float2* __restrict__ Dp) {
+    extern __shared__ float2 stage[];
+    const int d = blockIdx.y;
+    const int c = block_class(rb);
+    const int NT = nterms(c), E = rb.stage[c], R = rb.per[c];
+    const long long r0 = rb.rstart[c] + (long long)(blockIdx.x - rb.bstart[c]) * R;
+    const long long rend = rb.rstart[c] + rb.rcount[c];
+    const long long nn = (long long)nao * nao;
+    for (int idx = threadIdx.x; idx < R * E; idx += blockDim.x) {
+        const long long i = r0 + idx / E;
+        df v{0.f, 0.f};
+        int row, col;
+        if (i < rend) {
+            const PairDev pr = pairs[i];
+            if (entry_ao(G[pr.ga], G[pr.gb], mem, idx % E, row, col)) {
+                v = split_double(__ldg(D0n + ((long long)d * nk + pr.cell) * nn + (long long)row * nao + col));
+                if (pr.weight == 2)
+                    v = df_add(v, split_double(__ldg(D0n + ((long long)d * nk + pr.mcell) * nn +
+                                                     (long long)col * nao + row)));
+            }
+        }
+        stage[idx] = make_float2(v.hi, v.lo);
+    }
+    __syncthreads();
+    const int r = threadIdx.x / NT, t = threadIdx.x % NT;
+    const long long i = r0 + r;
+    if (r >= R || i >= rend) return;
+    const PairDev pr = pairs[i];
+    const int ne = entries_of(G[pr.ga], G[pr.gb], mem);
+    const float2* M = maps + moff[i] + t;
+    const float2* v = stage + r * E;
+    df acc{0.f, 0.f};
+    for (int e = 0; e < ne; ++e) {
+        const float2 m = __ldg(M + (long long)e * NT);
+        const float2 x = v[e];
+        acc = df_add(acc, df_mul(df{m.x, m.y}, df{x.x, x.y}));
+    }
+    const long long off = (long long)d * lay.total + lay.base[c] + (i - lay.start[c]) +
+                          (long long)t * (lay.start[c + 1] - lay.start[c]);
+    Dp[off] = make_float2(acc.hi, acc.lo);
+}
+
+__global__ void __launch_bounds__(256) k_jtransform_map_df(const PairDev* __restrict__ pairs,
+                                                           const GroupDev* __restrict__ G,
+                                                           const MemberDev* __restrict__ mem,
+                                                           const long long* __restrict__ moff,
+                                                           const float2* __restrict__ maps,
+                                                           const double* __restrict__ Jp, int nchunks, int nao,
+                                                           int nk, MapLayout lay, RecBlocks rb,
+                                                           double* __restrict__ J0n) {
+    extern __shared__ float2 stage[];
+    const int d = blockIdx.y;
+    const int c = block_class(rb);
+    const int NT = nterms(c), E = rb.width[c], R = rb.per[c];
+    const long long r0 = rb.rstart[c] + (long long)(blockIdx.x - rb.bstart[c]) * R;
+    const long long rend = rb.rstart[c] + rb.rcount[c];
+    const long long cnt = lay.start[c + 1] - lay.start[c];
+    for (int idx = threadIdx.x; idx < R * NT; idx += blockDim.x) {
+        const long long i = r0 + idx / NT;
+        const int t = idx % NT;
+        df s{0.f, 0.f};
+        if (i < rend) {
+            const long long loc = i - lay.start[c];
+            for (int ch = 0; ch < nchunks; ++ch)
+                s = df_add(s, split_double(__ldg(Jp + ((long long)d * nchunks + ch) * lay.total + lay.base[c] +
+                                                 (long long)t * cnt + loc)));
+        }
+        stage[idx] = make_float2(s.hi, s.lo);
+    }
+    __syncthreads();
+    const int r = threadIdx.x / E, e = threadIdx.x % E;
+    const long long i = r0 + r;
+    if (r >= R || i >= rend) return;
+    const PairDev pr = pairs[i];
+    int row, col;
+    if (!entry_ao(G[pr.ga], G[pr.gb], mem, e, row, col)) return;
+    const float2* M = maps + moff[i] + (long long)e * NT;
+    const float2* jt = stage + r * NT;
+    df s{0.f, 0.f};
+    for (int t = 0; t < NT; ++t) {
+        const float2 m = __ldg(M + t);
+        const float2 x = jt[t];
+        s = df_add(s, df_mul(df{m.x, m.y}, df{x.x, x.y}));
+    }
+    const double v = join_df(s);
+    const long long nn = (long long)nao * nao;
+    atomicAdd(J0n + ((long long)d * nk + pr.cell) * nn + (long long)row * nao + col, v);
+    if (pr.weight == 2) atomicAdd(J0n + ((long long)d * nk + pr.mcell) * nn + (long long)col * nao + row, v);
+}
+
+// the geometry-only maps, rewritten in place as double-float
+__global__ void k_maps_to_df(double* __restrict__ maps, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const df v = split_double(maps[i]);
+    reinterpret_cast<float2*>(maps)[i] = make_float2(v.hi, v.lo);
+}
+
+RecBlocks make_rec_blocks(const ftcj_plan* P, const long long* width, const long long* stage, int bdim) {
+    RecBlocks rb;
+    rb.bstart[0] = 0;
+    for (int c = 0; c < kNclass; ++c) {
+        rb.rstart[c] = P->class_start[c];
+        rb.rcount[c] = P->class_start[c + 1] - P->class_start[c];
+        rb.width[c] = (int)std::max<long long>(width[c], 1);
+        rb.stage[c] = (int)std::max<long long>(stage[c], 1);
+        rb.per[c] = std::max(1, bdim / rb.width[c]);
+        const long long nb = rb.rcount[c] > 0 ? (rb.rcount[c] + rb.per[c] - 1) / rb.per[c] : 0;
+        rb.bstart[c + 1] = rb.bstart[c] + (int)nb;
+    }
+    return rb;
+}
+
+size_t rec_blocks_smem(const RecBlocks& rb) {
+    size_t m = 0;
+    for (int c = 0; c < kNclass; ++c)
+        if (rb.rcount[c] > 0) m = std::max(m, sizeof(float2) * (size_t)rb.per[c] * rb.stage[c]);
+    return m;
+}
+
 MapLayout make_map_layout(const ftcj_plan* P) {
     MapLayout l;
     for (int c = 0; c <= kNclass; ++c) l.start[c] = P->class_start[c];
@@ -301,11 +469,42 @@ int build_maps(ftcj_plan* P) {
     cudaFree(dC);
     cudaFree(dT);
     if (e != cudaSuccess) return cuda_fail(e, "k_map_build");
+    // split form: double-float maps and record-major blocks, when every record's
+    // outputs fit one block
+    P->maps_df = false;
+    if (P->precision == FTCJ_PREC_SPLIT) {
+        long long nt[kNclass];
+        for (int c = 0; c < kNclass; ++c) nt[c] = nterms(c);
+        bool fits = true;
+        for (int c = 0; c < kNclass; ++c) fits = fits && maxout[c] <= 256;
+        if (fits) {
+            P->rb_terms = make_rec_blocks(P, nt, maxout, 256);
+            P->rb_outs = make_rec_blocks(P, maxout, nt, 256);
+            P->rb_terms_smem = rec_blocks_smem(P->rb_terms);
+            P->rb_outs_smem = rec_blocks_smem(P->rb_outs);
+            int rc = allow_dynamic_smem((const void*)k_hermite_map_df, P->rb_terms_smem);
+            if (!rc) rc = allow_dynamic_smem((const void*)k_jtransform_map_df, P->rb_outs_smem);
+            if (rc) return rc;
+            k_maps_to_df<<<(unsigned)((P->map_doubles + 255) / 256), 256>>>(P->d_maps, P->map_doubles);
+            FTCJ_CUDA(cudaGetLastError());
+            FTCJ_CUDA(cudaDeviceSynchronize());
+            P->maps_df = true;
+        }
+    }
     return FTCJ_OK;
 }
 
 int launch_hermite_map(ftcj_plan* P, int ndens, const double* D0n, cudaStream_t s) {
     if (P->npairs == 0) return FTCJ_OK;
+    if (P->maps_df) {
+        dim3 g((unsigned)P->rb_terms.bstart[kNclass], ndens);
+        k_hermite_map_df<<<g, 256, P->rb_terms_smem, s>>>(P->d_pairs, P->d_groups, P->d_members, P->d_map_off,
+                                                          reinterpret_cast<const float2*>(P->d_maps), D0n, P->nao,
+                                                          P->nk, make_map_layout(P), P->rb_terms,
+                                                          reinterpret_cast<float2*>(P->d_Dp));
+        FTCJ_CUDA(cudaGetLastError());
+        return FTCJ_OK;
+    }
     const long long n = P->mt_terms.tstart[kNclass];
     dim3 g((unsigned)((n + 255) / 256), ndens);
     if (P->precision == FTCJ_PREC_SPLIT)
@@ -322,6 +521,15 @@ int launch_jtransform_map(ftcj_plan* P, int ndens, double* J0n, cudaStream_t s) 
     const size_t bytes = sizeof(double) * (size_t)ndens * P->nk * P->nao * P->nao;
     FTCJ_CUDA(cudaMemsetAsync(J0n, 0, bytes, s));
     if (P->npairs == 0) return FTCJ_OK;
+    if (P->maps_df) {
+        dim3 g((unsigned)P->rb_outs.bstart[kNclass], ndens);
+        k_jtransform_map_df<<<g, 256, P->rb_outs_smem, s>>>(P->d_pairs, P->d_groups, P->d_members, P->d_map_off,
+                                                            reinterpret_cast<const float2*>(P->d_maps), P->d_Jp,
+                                                            (int)P->chunks.size(), P->nao, P->nk,
+                                                            make_map_layout(P), P->rb_outs, J0n);
+        FTCJ_CUDA(cudaGetLastError());
+        return FTCJ_OK;
+    }
     const long long n = P->mt_outs.tstart[kNclass];
     dim3 g((unsigned)((n + 255) / 256), ndens);
     k_jtransform_map<<<g, 256, 0, s>>>(P->d_pairs, P->d_groups, P->d_members, P->d_map_off, P->d_maps, P->d_Jp,

@@ -445,7 +445,7 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     if ((rc = dalloc(P, &P->d_rho_part, 2 * md * (size_t)P->npb * (size_t)P->ng_half))) return rc;
     if ((rc = dalloc(P, &P->d_rho, 2 * md * (size_t)P->ng_half))) return rc;
     if ((rc = dalloc(P, &P->d_W, 2 * md * (size_t)P->ng_half))) return rc;
-    P->nEblocks = (int)std::max<int64_t>(1, (P->ng_half + 31) / 32);
+    P->nEblocks = (int)std::max<int64_t>(1, (P->ng_half + kRedPoints - 1) / kRedPoints);
     if ((rc = dalloc(P, &P->d_Epart, md * (size_t)P->nEblocks))) return rc;
     if ((rc = dalloc(P, &P->d_Dk_stage, 2 * md * P->nk * nn))) return rc;
     if ((rc = dalloc(P, &P->d_Jk_stage, 2 * md * P->nk * nn))) return rc;

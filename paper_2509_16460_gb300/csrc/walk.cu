@@ -321,41 +321,52 @@ __global__ void __launch_bounds__(kTile) k_rho_walk(const Tile* __restrict__ til
 }
 
 // rho = sum over the block rows; optional W = 2 v conj(rho) and per-block
-// partial sums of v |rho|^2.  A block takes 32 points (one per lane, coalesced)
-// and 32 row groups (one per warp, rows w, w+32, ...); the warps' sums are
-// added in a fixed tree, so the result does not depend on scheduling.  With
-// nparts = 1 and part = rho this is the potential step on a given rho.
-__global__ void __launch_bounds__(1024) k_rho_reduce(const double2* __restrict__ part, int nparts,
-                                                     long long ng_half, const double* __restrict__ vg,
-                                                     double2* __restrict__ rho_out, double2* __restrict__ W_out,
-                                                     double* __restrict__ Epart, int nEblocks) {
-    __shared__ double2 sred[32][33];
-    __shared__ double se[32];
+// partial sums of v |rho|^2.  A block takes kRedPoints consecutive points and
+// 256 / kRedPoints row groups (group g sums rows g, g + groups, ... with two
+// accumulators); the groups are added in a fixed tree, so the result does not
+// depend on scheduling.  With nparts = 1 and part = rho this is the potential
+// step on a given rho.
+__global__ void __launch_bounds__(256) k_rho_reduce(const double2* __restrict__ part, int nparts,
+                                                    long long ng_half, const double* __restrict__ vg,
+                                                    double2* __restrict__ rho_out, double2* __restrict__ W_out,
+                                                    double* __restrict__ Epart, int nEblocks) {
+    constexpr int kGroups = 256 / kRedPoints;
+    __shared__ double2 sred[kGroups][kRedPoints];
+    __shared__ double se[kRedPoints];
     const int d = blockIdx.y;
-    const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5;
-    const long long p = (long long)blockIdx.x * 32 + lane;
-    double sr = 0.0, si = 0.0;
+    const int pt = threadIdx.x % kRedPoints, g = threadIdx.x / kRedPoints;
+    const long long p = (long long)blockIdx.x * kRedPoints + pt;
+    double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
     if (p < ng_half) {
         const double2* src = part + (long long)d * nparts * ng_half + p;
-        for (int q = wv; q < nparts; q += 32) {
-            const double2 v = src[(long long)q * ng_half];
-            sr += v.x;
-            si += v.y;
+        int q = g;
+        for (; q + kGroups < nparts; q += 2 * kGroups) {
+            const double2 u = src[(long long)q * ng_half];
+            const double2 v = src[(long long)(q + kGroups) * ng_half];
+            ar += u.x;
+            ai += u.y;
+            br += v.x;
+            bi += v.y;
+        }
+        if (q < nparts) {
+            const double2 u = src[(long long)q * ng_half];
+            ar += u.x;
+            ai += u.y;
         }
     }
-    sred[wv][lane] = make_double2(sr, si);
+    sred[g][pt] = make_double2(ar + br, ai + bi);
     __syncthreads();
-    for (int o = 16; o > 0; o >>= 1) {
-        if (wv < o) {
-            const double2 a = sred[wv][lane], b = sred[wv + o][lane];
-            sred[wv][lane] = make_double2(a.x + b.x, a.y + b.y);
+    for (int o = kGroups / 2; o > 0; o >>= 1) {
+        if (g < o) {
+            const double2 a = sred[g][pt], b = sred[g + o][pt];
+            sred[g][pt] = make_double2(a.x + b.x, a.y + b.y);
         }
         __syncthreads();
     }
-    if (wv == 0) {
+    if (g == 0) {
         double e = 0.0;
         if (p < ng_half) {
-            const double2 r = sred[0][lane];
+            const double2 r = sred[0][pt];
             if (rho_out) rho_out[(long long)d * ng_half + p] = r;
             if (W_out) {
                 const double v = vg[p];
@@ -363,13 +374,13 @@ __global__ void __launch_bounds__(1024) k_rho_reduce(const double2* __restrict__
                 e = v * (r.x * r.x + r.y * r.y);
             }
         }
-        se[lane] = e;
-        __syncwarp();
-        if (lane == 0 && Epart) {
-            double t = 0.0;
-            for (int k = 0; k < 32; ++k) t += se[k];
-            Epart[(long long)d * nEblocks + blockIdx.x] = t;
-        }
+        se[pt] = e;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && Epart) {
+        double t = 0.0;
+        for (int k = 0; k < kRedPoints; ++k) t += se[k];
+        Epart[(long long)d * nEblocks + blockIdx.x] = t;
     }
 }
 
@@ -605,7 +616,7 @@ int launch_rho_reduce(ftcj_plan* P, int ndens, double* rho_out, double* W_out, d
     int nparts = rho_in ? 1 : P->npb;
     if (P->ng_half > 0) {
         dim3 g(P->nEblocks, ndens);
-        k_rho_reduce<<<g, 1024, 0, s>>>(part, nparts, P->ng_half, P->d_vg, reinterpret_cast<double2*>(rho_out),
+        k_rho_reduce<<<g, 256, 0, s>>>(part, nparts, P->ng_half, P->d_vg, reinterpret_cast<double2*>(rho_out),
                                        reinterpret_cast<double2*>(W_out), EJ_out ? P->d_Epart : nullptr,
                                        P->nEblocks);
         FTCJ_CUDA(cudaGetLastError());
