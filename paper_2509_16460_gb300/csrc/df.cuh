@@ -106,6 +106,70 @@ __device__ __forceinline__ cdf cdf_add(cdf a, cdf b) { return cdf{df_add(a.re, b
 
 __device__ __forceinline__ cdf cdf_conj(cdf a) { return cdf{a.re, df_neg(a.im)}; }
 
+// ---- deferred renormalisation --------------------------------------------
+// The "_u" forms leave out the closing FastTwoSum: hi + lo is the same value
+// to the same accuracy, but |lo| may exceed ulp(hi)/2 by a few units.  Every
+// operation above accepts such operands (TwoSum of the high parts is exact for
+// any inputs; the products carry a.lo b.hi and a.hi b.lo), so chains of a few
+// steps in a hot loop renormalise once, with df_norm, before a value is kept.
+__device__ __forceinline__ df df_norm(df a) { return fast_two_sum(a.hi, a.lo); }
+
+__device__ __forceinline__ df df_add_u(df a, df b) {
+    const df s = two_sum(a.hi, b.hi);
+    return df{s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
+}
+
+__device__ __forceinline__ df df_mulf_u(df a, float b) {
+    const float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return df{p, e};
+}
+
+__device__ __forceinline__ df df_mul_u(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df{p, e};
+}
+
+__device__ __forceinline__ df df_mul_sub_u(df a, df b, df c, df d) {
+    const float p1 = __fmul_rn(a.hi, b.hi);
+    const float e1 = __fmaf_rn(a.hi, b.hi, -p1);
+    const float p2 = __fmul_rn(c.hi, d.hi);
+    const float e2 = __fmaf_rn(c.hi, d.hi, -p2);
+    const df s = two_sum(p1, -p2);
+    float e = __fadd_rn(s.lo, __fsub_rn(e1, e2));
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    e = __fmaf_rn(-c.hi, d.lo, e);
+    e = __fmaf_rn(-c.lo, d.hi, e);
+    return df{s.hi, e};
+}
+
+__device__ __forceinline__ df df_mul_add_u(df a, df b, df c, df d) {
+    const float p1 = __fmul_rn(a.hi, b.hi);
+    const float e1 = __fmaf_rn(a.hi, b.hi, -p1);
+    const float p2 = __fmul_rn(c.hi, d.hi);
+    const float e2 = __fmaf_rn(c.hi, d.hi, -p2);
+    const df s = two_sum(p1, p2);
+    float e = __fadd_rn(s.lo, __fadd_rn(e1, e2));
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    e = __fmaf_rn(c.hi, d.lo, e);
+    e = __fmaf_rn(c.lo, d.hi, e);
+    return df{s.hi, e};
+}
+
+__device__ __forceinline__ cdf cdf_mul_u(cdf a, cdf b) {
+    return cdf{df_mul_sub_u(a.re, b.re, a.im, b.im), df_mul_add_u(a.re, b.im, a.im, b.re)};
+}
+
+__device__ __forceinline__ cdf cdf_add_u(cdf a, cdf b) { return cdf{df_add_u(a.re, b.re), df_add_u(a.im, b.im)}; }
+
+__device__ __forceinline__ cdf cdf_norm(cdf a) { return cdf{df_norm(a.re), df_norm(a.im)}; }
+
 // ---- conversions that keep off the FP64 pipe ----------------------------
 // GB300 issues FP64 (conversions included) at 2 lanes per clock per SM, so
 // doubles are split into double-float and rebuilt from their exponent and

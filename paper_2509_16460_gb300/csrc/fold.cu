@@ -222,7 +222,11 @@ __global__ void __launch_bounds__(kFusedT) k_unfold_fused(const double* __restri
 // ---- split-precision register transform ----------------------------------
 
 
-__device__ __forceinline__ cdf cdf_sub(cdf a, cdf b) { return cdf{df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
+// The transform's sums are at most 6 additions deep (three axes of length 4),
+// so they run without renormalisation (df.cuh "_u" forms); the outputs are
+// rebuilt as exact double sums of both parts.
+__device__ __forceinline__ cdf cadd(cdf a, cdf b) { return cdf_add_u(a, b); }
+__device__ __forceinline__ cdf csub(cdf a, cdf b) { return cdf{df_add_u(a.re, df_neg(b.re)), df_add_u(a.im, df_neg(b.im))}; }
 
 // -i v (forward twiddle of a length-4 axis) and +i v (inverse)
 __device__ __forceinline__ cdf mul_mi(cdf v) { return cdf{v.im, df_neg(v.re)}; }
@@ -233,16 +237,16 @@ template <int N, bool INV>
 __device__ __forceinline__ void dft_reg(cdf* v, int base, int stride) {
     if (N == 2) {
         const cdf x0 = v[base], x1 = v[base + stride];
-        v[base] = cdf_add(x0, x1);
-        v[base + stride] = cdf_sub(x0, x1);
+        v[base] = cadd(x0, x1);
+        v[base + stride] = csub(x0, x1);
     } else if (N == 4) {
         const cdf x0 = v[base], x1 = v[base + stride], x2 = v[base + 2 * stride], x3 = v[base + 3 * stride];
-        const cdf a = cdf_add(x0, x2), b = cdf_sub(x0, x2), c = cdf_add(x1, x3), d = cdf_sub(x1, x3);
+        const cdf a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = csub(x1, x3);
         const cdf wd = INV ? mul_pi(d) : mul_mi(d);  // y1 = b + w d, y3 = b - w d
-        v[base] = cdf_add(a, c);
-        v[base + 2 * stride] = cdf_sub(a, c);
-        v[base + stride] = cdf_add(b, wd);
-        v[base + 3 * stride] = cdf_sub(b, wd);
+        v[base] = cadd(a, c);
+        v[base + 2 * stride] = csub(a, c);
+        v[base + stride] = cadd(b, wd);
+        v[base + 3 * stride] = csub(b, wd);
     }
 }
 
@@ -258,19 +262,19 @@ template <bool INV>
 __device__ __forceinline__ cdf dft_lanes(cdf x, int j, int N1) {
     if (N1 == 2) {
         const cdf o = shfl_xor_cdf(x, 1);
-        return j == 0 ? cdf_add(x, o) : cdf_sub(o, x);
+        return j == 0 ? cadd(x, o) : csub(o, x);
     }
     if (N1 == 4) {
         // lanes 0,1: a_j = x_j + x_{j+2}; lanes 2,3: b_{j-2} = x_{j-2} - x_j
         cdf o = shfl_xor_cdf(x, 2);
-        const cdf t = j < 2 ? cdf_add(x, o) : cdf_sub(o, x);
+        const cdf t = j < 2 ? cadd(x, o) : csub(o, x);
         // y0 = a0 + a1, y2 = a0 - a1, y1 = b0 + w b1, y3 = b0 - w b1
         o = shfl_xor_cdf(t, 1);
         switch (j) {
-            case 0: return cdf_add(t, o);
-            case 1: return cdf_sub(o, t);
-            case 2: return cdf_add(t, INV ? mul_pi(o) : mul_mi(o));
-            default: return cdf_sub(o, INV ? mul_pi(t) : mul_mi(t));
+            case 0: return cadd(t, o);
+            case 1: return csub(o, t);
+            case 2: return cadd(t, INV ? mul_pi(o) : mul_mi(o));
+            default: return csub(o, INV ? mul_pi(t) : mul_mi(t));
         }
     }
     return x;

@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(256) k_hermite_map_df(const PairDev* __restric
     for (int e = 0; e < ne; ++e) {
         const float2 m = __ldg(M + (long long)e * NT);
         const float2 x = v[e];
-        acc = df_add(acc, df_mul(df{m.x, m.y}, df{x.x, x.y}));
+        acc = df_add(acc, df_mul_u(df{m.x, m.y}, df{x.x, x.y}));
     }
     const long long off = (long long)d * lay.total + lay.base[c] + (i - lay.start[c]) +
                           (long long)t * (lay.start[c + 1] - lay.start[c]);
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(256) k_jtransform_map_df(const PairDev* __rest
     for (int t = 0; t < NT; ++t) {
         const float2 m = __ldg(M + t);
         const float2 x = jt[t];
-        s = df_add(s, df_mul(df{m.x, m.y}, df{x.x, x.y}));
+        s = df_add(s, df_mul_u(df{m.x, m.y}, df{x.x, x.y}));
     }
     const double v = join_df(s);
     const long long nn = (long long)nao * nao;

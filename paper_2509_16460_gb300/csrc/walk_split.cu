@@ -202,7 +202,7 @@ __device__ __noinline__ void split_flush(float4* buf, float4* red, float4* row, 
     if (j < nvalid) {
         const float4* b = buf + j * (kTile + 1) + wv * 32 + quarter * 8;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) s = cdf_add(s, unpack(b[k]));
+        for (int k = 0; k < 8; ++k) s = cdf_add_u(s, unpack(b[k]));
     }
 #pragma unroll
     for (int off = 16; off >= kSBatch; off >>= 1) {
@@ -211,14 +211,15 @@ __device__ __noinline__ void split_flush(float4* buf, float4* red, float4* row, 
         o.re.lo = __shfl_down_sync(0xffffffffu, s.re.lo, off);
         o.im.hi = __shfl_down_sync(0xffffffffu, s.im.hi, off);
         o.im.lo = __shfl_down_sync(0xffffffffu, s.im.lo, off);
-        s = cdf_add(s, o);
+        s = cdf_add_u(s, o);
     }
     if (quarter == 0 && j < nvalid) red[wv * 32 + j] = make_float4(s.re.hi, s.re.lo, s.im.hi, s.im.lo);
     __syncthreads();
     if (tid < nvalid) {
         cdf r = unpack(row[rbase + tid]);
 #pragma unroll
-        for (int q = 0; q < kTile / 32; ++q) r = cdf_add(r, unpack(red[q * 32 + tid]));
+        for (int q = 0; q < kTile / 32; ++q) r = cdf_add_u(r, unpack(red[q * 32 + tid]));
+        r = cdf_norm(r);
         row[rbase + tid] = make_float4(r.re.hi, r.re.lo, r.im.hi, r.im.lo);
     }
 }
@@ -329,10 +330,10 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
                     cdf a = c[L];
 #pragma unroll
                     for (int i = L - 1; i >= 0; --i)
-                        a = cdf{df_add(df_mulf(a.re, x), c[i].re), df_add(df_mulf(a.im, x), c[i].im)};
+                        a = cdf{df_add_u(df_mulf_u(a.re, x), c[i].re), df_add_u(df_mulf_u(a.im, x), c[i].im)};
                     cdf xv;
                     if (ORTHO) xv = xtab_at(Xs, m, dir, tid);
-                    const cdf z = ORTHO ? cdf_mul(xv, a) : cdf_mul(gp, a);
+                    const cdf z = ORTHO ? cdf_mul_u(xv, a) : cdf_mul_u(gp, a);
                     buf[slot * (kTile + 1) + tid] = make_float4(z.re.hi, z.re.lo, z.im.hi, z.im.lo);
                     if (++slot == kSBatch) {
                         split_flush(buf, red, row, rbase, kSBatch);
@@ -450,13 +451,13 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
                     const cdf w = unpack(wsm[q++]);
                     cdf xv;
                     if (ORTHO) xv = xtab_at(Xs, m, dir, tid);
-                    const cdf t = ORTHO ? cdf_mul(xv, w) : cdf_mul(gp, w);
-                    A[0] = cdf_add(A[0], t);
+                    const cdf t = ORTHO ? cdf_mul_u(xv, w) : cdf_mul_u(gp, w);
+                    A[0] = cdf_add_u(A[0], t);
                     const float* pwm = pw + (m - n1min) * 5;
 #pragma unroll
                     for (int i = 1; i <= L; ++i) {
                         const float p = pwm[i];
-                        A[i] = cdf{df_add(A[i].re, df_mulf(t.re, p)), df_add(A[i].im, df_mulf(t.im, p))};
+                        A[i] = cdf{df_add_u(A[i].re, df_mulf_u(t.re, p)), df_add_u(A[i].im, df_mulf_u(t.im, p))};
                     }
                 }
                 if (m == m1) break;
@@ -466,6 +467,8 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
                 }
             }
         }
+#pragma unroll
+        for (int i = 0; i <= L; ++i) A[i] = cdf_norm(A[i]);
         if (ORTHO) {
 #pragma unroll
             for (int i = 0; i <= L; ++i) A[i] = cdf_mul(s.gpL, A[i]);
