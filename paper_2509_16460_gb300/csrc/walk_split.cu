@@ -131,6 +131,10 @@ __device__ __forceinline__ SState idle_state() {
     return s;
 }
 
+// One transition of the walk program.  With ORTHO (the per-record X(n1)
+// table serves every line) the n1 ratios RfL, RbL, rF0c, rB0c are not used
+// and not advanced.
+template <bool ORTHO>
 __device__ __forceinline__ void split_step(const SConst& k, int op, SState& s, const SState* init_p, bool valid) {
     switch (op) {
         case OP_FIRST:
@@ -139,28 +143,36 @@ __device__ __forceinline__ void split_step(const SConst& k, int op, SState& s, c
         case OP_N2F:
             s.gpL = cdf_mul(s.gpL, s.Sd);
             s.Sd = cdf_scale(s.Sd, k.q2);
-            s.RfL = cdf_scale(s.RfL, k.x12);
-            s.RbL = cdf_scale(s.RbL, k.y12);
+            if (!ORTHO) {
+                s.RfL = cdf_scale(s.RfL, k.x12);
+                s.RbL = cdf_scale(s.RbL, k.y12);
+            }
             break;
         case OP_NEGSTART:
             s.gpL = cdf_mul(s.gpC, s.RB0c);
             s.Sd = cdf_scale(s.RB0c, k.q2);
-            s.RfL = cdf_scale(s.rF0c, k.y12);
-            s.RbL = cdf_scale(s.rB0c, k.x12);
+            if (!ORTHO) {
+                s.RfL = cdf_scale(s.rF0c, k.y12);
+                s.RbL = cdf_scale(s.rB0c, k.x12);
+            }
             break;
         case OP_N2B:
             s.gpL = cdf_mul(s.gpL, s.Sd);
             s.Sd = cdf_scale(s.Sd, k.q2);
-            s.RfL = cdf_scale(s.RfL, k.y12);
-            s.RbL = cdf_scale(s.RbL, k.x12);
+            if (!ORTHO) {
+                s.RfL = cdf_scale(s.RfL, k.y12);
+                s.RbL = cdf_scale(s.RbL, k.x12);
+            }
             break;
         default:  // OP_N3
             s.gpC = cdf_mul(s.gpC, s.Tc);
             s.Tc = cdf_scale(s.Tc, k.q3);
             s.RF0c = cdf_scale(s.RF0c, k.x23);
             s.RB0c = cdf_scale(s.RB0c, k.y23);
-            s.rF0c = cdf_scale(s.rF0c, k.x13);
-            s.rB0c = cdf_scale(s.rB0c, k.y13);
+            if (!ORTHO) {
+                s.rF0c = cdf_scale(s.rF0c, k.x13);
+                s.rB0c = cdf_scale(s.rB0c, k.y13);
+            }
             s.gpL = s.gpC;
             s.Sd = s.RF0c;
             s.RfL = s.rF0c;
@@ -268,7 +280,7 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
     int slot = 0, rbase = 0;
     for (int li = ch.l0; li < ch.l1; ++li) {
         const WLine ln = lines[li];
-        split_step(k, ln.op, s, init_p, valid);
+        split_step<ORTHO>(k, ln.op, s, init_p, valid);
         if (ln.lo > ln.hi) continue;
         cdf c[L + 1];
         {
@@ -285,12 +297,12 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
                     for (int j = lam - i; j >= 0; --j) {
                         const int kk = lam - i - j;
                         const float2 dv = Dsm[t * kTile + tid];
-                        const df v = df_mulf(df{dv.x, dv.y}, pq[j][kk]);
+                        const df v = df_mulf_u(df{dv.x, dv.y}, pq[j][kk]);
                         switch (lam & 3) {
-                            case 0: c[i].re = df_add(c[i].re, v); break;
-                            case 1: c[i].im = df_sub(c[i].im, v); break;
-                            case 2: c[i].re = df_sub(c[i].re, v); break;
-                            default: c[i].im = df_add(c[i].im, v); break;
+                            case 0: c[i].re = df_add_u(c[i].re, v); break;
+                            case 1: c[i].im = df_add_u(c[i].im, df_neg(v)); break;
+                            case 2: c[i].re = df_add_u(c[i].re, df_neg(v)); break;
+                            default: c[i].im = df_add_u(c[i].im, v); break;
                         }
                         ++t;
                     }
@@ -324,9 +336,15 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
                     R = cdf_scale(s.RbL, k.q1);
                 }
             }
-            for (int m = m0;; m += step) {
-                if (m >= ln.lo && m <= ln.hi) {
-                    const float x = (float)m;
+            if (ORTHO) {
+                // no recurrence to carry: visit exactly the line's points of this direction
+                m0 = dir == 0 ? max(ln.lo, 0) : min(ln.hi, -1);
+                if ((m1 - m0) * step < 0) continue;
+            }
+            float x = (float)m0;
+            const float xstep = (float)step;
+            for (int m = m0;; m += step, x += xstep) {
+                if (ORTHO || (m >= ln.lo && m <= ln.hi)) {
                     cdf a = c[L];
 #pragma unroll
                     for (int i = L - 1; i >= 0; --i)
@@ -399,7 +417,7 @@ __global__ void __launch_bounds__(kTile, 3) k_rho_walk_split(const Tile* __restr
 template <int L, bool ORTHO>
 __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __restrict__ cst,
                              const SState* __restrict__ init_c, const WLine* __restrict__ lines, const WChunk ch,
-                             const float4* __restrict__ wsm, const float* __restrict__ pw, int n1min,
+                             const float4* __restrict__ wsm,
                              double* __restrict__ Jp_dc, float2* Jsm, float4* Xs, int nx) {
     constexpr int NT = nterms(L);
     const int tid = threadIdx.x;
@@ -417,7 +435,7 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
     SState s;
     for (int li = ch.l0; li < ch.l1; ++li) {
         const WLine ln = lines[li];
-        split_step(k, ln.op, s, init_p, valid);
+        split_step<ORTHO>(k, ln.op, s, init_p, valid);
         if (ln.lo > ln.hi) continue;
         cdf A[L + 1];
 #pragma unroll
@@ -446,17 +464,24 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
                     R = cdf_scale(s.RbL, k.q1);
                 }
             }
-            for (int m = m0;; m += step) {
-                if (m >= ln.lo && m <= ln.hi) {
+            if (ORTHO) {
+                // no recurrence to carry: visit exactly the line's points of this direction
+                m0 = dir == 0 ? max(ln.lo, 0) : min(ln.hi, -1);
+                if ((m1 - m0) * step < 0) continue;
+            }
+            float x = (float)m0;
+            const float xstep = (float)step;
+            for (int m = m0;; m += step, x += xstep) {
+                if (ORTHO || (m >= ln.lo && m <= ln.hi)) {
                     const cdf w = unpack(wsm[q++]);
                     cdf xv;
                     if (ORTHO) xv = xtab_at(Xs, m, dir, tid);
                     const cdf t = ORTHO ? cdf_mul_u(xv, w) : cdf_mul_u(gp, w);
                     A[0] = cdf_add_u(A[0], t);
-                    const float* pwm = pw + (m - n1min) * 5;
+                    float p = 1.f;
 #pragma unroll
                     for (int i = 1; i <= L; ++i) {
-                        const float p = pwm[i];
+                        p *= x;  // n1^i, exact (|n1|^4 < 2^24)
                         A[i] = cdf{df_add_u(A[i].re, df_mulf_u(t.re, p)), df_add_u(A[i].im, df_mulf_u(t.im, p))};
                     }
                 }
@@ -491,7 +516,7 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
                         default: a = df_neg(A[i].im); break;
                     }
                     const float2 jv = Jsm[t * kTile + tid];
-                    const df r = df_add(df{jv.x, jv.y}, df_mulf(a, pq[j][kk]));
+                    const df r = df_add(df{jv.x, jv.y}, df_mulf_u(a, pq[j][kk]));
                     Jsm[t * kTile + tid] = make_float2(r.hi, r.lo);
                     ++t;
                 }
@@ -511,9 +536,8 @@ __global__ void __launch_bounds__(kTile, 3) k_j_walk_split(const Tile* __restric
                                                         const SState* __restrict__ init, long long npairs,
                                                         const WLine* __restrict__ lines,
                                                         const WChunk* __restrict__ chunks, int nchunks,
-                                                        const double2* __restrict__ W, long long ng_half, int n1min,
-                                                        int n1cnt, int nx, int max_chunk_pts,
-                                                        double* __restrict__ Jp) {
+                                                        const double2* __restrict__ W, long long ng_half, int nx,
+                                                        int max_chunk_pts, double* __restrict__ Jp) {
     extern __shared__ float4 ssm[];
     const int tix = blockIdx.x, cidx = blockIdx.y, d = blockIdx.z;
     const WChunk ch = chunks[cidx];
@@ -521,29 +545,22 @@ __global__ void __launch_bounds__(kTile, 3) k_j_walk_split(const Tile* __restric
     float4* wsm = ssm;
     float2* Jsm = reinterpret_cast<float2*>(ssm + max_chunk_pts);
     float4* Xs = reinterpret_cast<float4*>(Jsm + kMaxTerms * kTile);
-    float* pw = reinterpret_cast<float*>(Xs + (ORTHO ? nx * kTile : 0));
     const double2* Wd = W + (long long)d * ng_half + ch.p0;
     for (int i = threadIdx.x; i < npts; i += blockDim.x) {
         const double2 v = Wd[i];
         const df re = df_from_double(v.x), im = df_from_double(v.y);
         wsm[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
     }
-    for (int i = threadIdx.x; i < n1cnt * 5; i += blockDim.x) {
-        const float x = (float)(n1min + i / 5);
-        float v = 1.f;
-        for (int e = 0; e < i % 5; ++e) v *= x;
-        pw[i] = v;
-    }
     __syncthreads();
     const Tile tl = tiles[tix];
     double* Jp_dc = Jp + ((long long)d * nchunks + cidx) * lay.total;
     const SState* init_c = init + (long long)cidx * npairs;
     switch (tl.cls) {
-        case 0: j_tile_split<0, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, nx); break;
-        case 1: j_tile_split<1, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, nx); break;
-        case 2: j_tile_split<2, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, nx); break;
-        case 3: j_tile_split<3, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, nx); break;
-        default: j_tile_split<4, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, pw, n1min, Jp_dc, Jsm, Xs, nx); break;
+        case 0: j_tile_split<0, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+        case 1: j_tile_split<1, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+        case 2: j_tile_split<2, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+        case 3: j_tile_split<3, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+        default: j_tile_split<4, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
     }
 }
 
@@ -571,9 +588,8 @@ size_t rho_smem(const ftcj_plan* P) {
 }
 
 size_t j_smem(const ftcj_plan* P) {
-    const int n1cnt = P->n1_max - P->n1_min + 1;
     return sizeof(float4) * (size_t)std::max(P->max_chunk_pts, 1) + sizeof(float2) * (size_t)kMaxTerms * kTile +
-           sizeof(float) * 5 * (size_t)n1cnt + xtab_bytes(P);
+           xtab_bytes(P);
 }
 
 }  // namespace
@@ -637,14 +653,13 @@ int launch_j_walk_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s
         return FTCJ_OK;
     }
     dim3 g((unsigned)P->tiles.size(), nch, ndens);
-    const int n1cnt = P->n1_max - P->n1_min + 1;
     const int nx = use_xtab(P) ? xtab_entries(P) : 0;
     auto* kern = use_xtab(P) ? k_j_walk_split<true> : k_j_walk_split<false>;
     kern<<<g, kTile, j_smem(P), s>>>(P->d_tiles, make_layout(P),
                                                reinterpret_cast<const SConst*>(P->d_split_const),
                                                reinterpret_cast<const SState*>(P->d_split_init), P->npairs,
                                                P->d_lines, P->d_chunks, nch, reinterpret_cast<const double2*>(W),
-                                               P->ng_half, P->n1_min, n1cnt, nx, P->max_chunk_pts, P->d_Jp);
+                                               P->ng_half, nx, P->max_chunk_pts, P->d_Jp);
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }
