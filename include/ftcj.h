@@ -93,6 +93,11 @@ typedef struct {
     int max_dens;       /* densities per device batch (scratch is sized for it); <= 0: 1 */
     int chunk_points;   /* G points per walk chunk, 64..4096; <= 0: 4096 */
     int rho_blocks;     /* persistent blocks of the structure-factor walk; <= 0: fill the GPU */
+    double pair_gcut_eps; /* > 0: per-pair G cutoffs (Sec. 2.5, Eq. "AFT screening obj"): each pair
+                             record is evaluated only for |G| below the radius where its
+                             screening estimate 8 pi eta G (4 pi/G^2) e^{-G^2/4w^2} |rho_ab(G)|
+                             falls under this value (split form only; EUNSUPPORTED with FP64;
+                             ftcj_grad ignores it).  0: every pair over the whole sphere. */
 } ftcj_params;
 
 typedef struct {
@@ -114,6 +119,11 @@ typedef struct {
     int rho_blocks;           /* persistent blocks of the structure-factor walk */
     int n1_table;             /* split form, orthorhombic cell: entries of the per-record
                                  X(n1) table (0: the n1 walk runs the recurrence) */
+    int64_t pair_g_units_screened; /* with pair_gcut_eps > 0: ordered pairs x G (full sphere)
+                                      inside each record's own cutoff; else = pair_g_units */
+    int64_t pair_g_units_walked;   /* record x G evaluations the walks perform (both passes
+                                      count once), x4 for the (+-G, mirror) symmetries: the
+                                      work actually done in the units of pair_g_units */
 } ftcj_info;
 
 typedef struct ftcj_plan ftcj_plan;

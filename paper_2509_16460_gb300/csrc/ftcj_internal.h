@@ -73,13 +73,15 @@ struct PairWalk {
 enum : int { OP_FIRST = 0, OP_N2F = 1, OP_NEGSTART = 2, OP_N2B = 3, OP_N3 = 4 };
 struct WLine {
     int n2, n3, lo, hi, op, pt;  // pt: index of the line's first stored point
+    float qa, qb, qc;            // |G|^2 = qa n1^2 + 2 qb n1 + qc along the line
 };
 struct WChunk {
     int l0, l1, p0, p1;  // lines [l0,l1), points [p0,p1)
 };
 
 struct Tile {
-    int cls, first, count, pad;  // pairs [first, first+count) of one class
+    int cls, first, count;  // pairs [first, first+count) of one class
+    float gcut2;            // squared G radius the tile walks (per-pair cutoffs), else +inf
 };
 
 // Per-class layout of the Hermite-term arrays (SoA within each class).
@@ -163,6 +165,9 @@ struct ftcj_plan {
     ftcj::Tile* d_tiles = nullptr;
     int* d_sched = nullptr;
     std::vector<int> rho_sched;  // rho pass: npb+1 offsets, then tile ids grouped by block
+    float* d_rec_gcut = nullptr;     // per-record G cutoff (pair_gcut_eps > 0)
+    int64_t units_screened = 0, units_walked = 0;
+    std::vector<int64_t> tile_npts;  // half-sphere points inside each tile's radius (cutoffs on)
     int* d_gvec = nullptr;
     double* d_vg = nullptr;          // v(G) on the half sphere
     double* d_tw = nullptr;          // twiddles, [3][16][16] complex
@@ -252,6 +257,8 @@ int rho_walk_blocks_per_sm(ftcj_plan* P, int* out);
 // --- split-precision walks (walk_split.cu) ---
 int setup_split(ftcj_plan* P);
 int split_xtab_entries(const ftcj_plan* P);  // 0 when the split walks run the n1 recurrence
+int launch_pair_gcut(ftcj_plan* P);      // per-record cutoffs from the (double) maps, in build_maps
+int apply_pair_cutoffs(ftcj_plan* P);    // sort records by cutoff within each class, radius per tile
 int rho_walk_split_blocks_per_sm(ftcj_plan* P, int* out);
 int launch_rho_walk_split(ftcj_plan* P, int ndens, cudaStream_t s);
 int launch_j_walk_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s);

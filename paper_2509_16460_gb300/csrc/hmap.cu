@@ -15,6 +15,7 @@
 // threads read neighbouring map entries and share the record's density block
 // (or J' terms) through broadcast loads.
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "df.cuh"
@@ -368,6 +369,70 @@ __global__ void __launch_bounds__(256) k_jtransform_map_df(const PairDev* __rest
     if (pr.weight == 2) atomicAdd(J0n + ((long long)d * nk + pr.mcell) * nn + (long long)col * nao + row, v);
 }
 
+// Per-record G cutoff (Sec. 2.5, Eq. "AFT screening obj"): the radius beyond
+// which 8 pi eta G (4 pi / G^2) e^{-G^2/4w^2} B(G) stays below eps, with
+// eta = (1/p + 1/w^2)^{-1} and B(G) = e^{-G^2/4p} max_{fq} sum_term |M_fq,term|
+// (G a_max / 2 pi)^deg(term), an upper bound of every component of the
+// record's exact pair transform at |G| = G in any direction (the map M holds
+// the normalisation, contraction, E coefficients, K and (pi/p)^{3/2}; the
+// relative coordinates obey |n_i| <= G |a_i| / 2 pi).  Searched in the log
+// domain in FP32 (a screening estimate): a 64-point scan down from the
+// sphere's radius, then 16 bisections of the bracket; the upper end is kept.
+__global__ void k_pair_gcut(const PairDev* __restrict__ pairs, const GroupDev* __restrict__ G,
+                            const MemberDev* __restrict__ mem, const long long* __restrict__ moff,
+                            const double* __restrict__ maps, long long npairs, float gmax, float amax_2pi,
+                            float omega, float log_eps, float* __restrict__ gcut) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npairs) return;
+    const PairDev pr = pairs[i];
+    const int L = pr.cls, NT = nterms(L);
+    const int ne = entries_of(G[pr.ga], G[pr.gb], mem);
+    const double* M = maps + moff[i];
+    float c[kLpair + 1];
+    for (int l = 0; l <= kLpair; ++l) c[l] = 0.f;
+    for (int e = 0; e < ne; ++e) {
+        int t = 0;
+        for (int lam = 0; lam <= L; ++lam) {
+            float s = 0.f;
+            for (int b = 0; b < nmono(lam); ++b, ++t) s += (float)fabs(M[(long long)e * NT + t]);
+            c[lam] = fmaxf(c[lam], s);
+        }
+    }
+    const float p = (float)pr.p;
+    const float eta = 1.f / (1.f / p + 1.f / (omega * omega));
+    const float decay = 0.25f / (omega * omega) + 0.25f / p;
+    const float lpref = logf(32.f * 9.8696044f * eta);
+    auto logf_at = [&](float g) {
+        float poly = 0.f, x = 1.f;
+        for (int lam = 0; lam <= L; ++lam) {
+            poly += c[lam] * x;
+            x *= g * amax_2pi;
+        }
+        return poly > 0.f ? lpref - logf(g) - g * g * decay + logf(poly) : -INFINITY;
+    };
+    constexpr int kScan = 64;
+    const float dg = gmax / kScan;
+    float cut = dg;
+    if (logf_at(gmax) >= log_eps) {
+        cut = gmax;
+    } else {
+        for (int k = kScan - 1; k >= 1; --k) {
+            const float g = k * dg;
+            if (logf_at(g) >= log_eps) {
+                float lo = g, hi = g + dg;
+                for (int it = 0; it < 16; ++it) {
+                    const float mid = 0.5f * (lo + hi);
+                    if (logf_at(mid) >= log_eps) lo = mid;
+                    else hi = mid;
+                }
+                cut = hi;
+                break;
+            }
+        }
+    }
+    gcut[i] = fminf(cut * 1.000001f, gmax * 1.000001f);
+}
+
 // the geometry-only maps, rewritten in place as double-float
 __global__ void k_maps_to_df(double* __restrict__ maps, long long n) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -471,6 +536,10 @@ int build_maps(ftcj_plan* P) {
     if (e != cudaSuccess) return cuda_fail(e, "k_map_build");
     // split form: double-float maps and record-major blocks, when every record's
     // outputs fit one block
+    if (P->params.pair_gcut_eps > 0.0) {
+        int rc = launch_pair_gcut(P);
+        if (rc) return rc;
+    }
     P->maps_df = false;
     if (P->precision == FTCJ_PREC_SPLIT) {
         long long nt[kNclass];
@@ -491,6 +560,22 @@ int build_maps(ftcj_plan* P) {
             P->maps_df = true;
         }
     }
+    return FTCJ_OK;
+}
+
+int launch_pair_gcut(ftcj_plan* P) {
+    if (P->npairs == 0) return FTCJ_OK;
+    FTCJ_CUDA(cudaMalloc(&P->d_rec_gcut, sizeof(float) * (size_t)P->npairs));
+    P->device_bytes += sizeof(float) * (size_t)P->npairs;
+    double amax = 0.0;
+    for (int r = 0; r < 3; ++r)
+        amax = std::max(amax, std::sqrt(P->A[3 * r] * P->A[3 * r] + P->A[3 * r + 1] * P->A[3 * r + 1] +
+                                        P->A[3 * r + 2] * P->A[3 * r + 2]));
+    k_pair_gcut<<<(unsigned)((P->npairs + 127) / 128), 128>>>(
+        P->d_pairs, P->d_groups, P->d_members, P->d_map_off, P->d_maps, P->npairs, (float)P->gcut,
+        (float)(amax / (2.0 * M_PI)), (float)P->params.omega, (float)std::log(P->params.pair_gcut_eps), P->d_rec_gcut);
+    FTCJ_CUDA(cudaGetLastError());
+    FTCJ_CUDA(cudaDeviceSynchronize());
     return FTCJ_OK;
 }
 

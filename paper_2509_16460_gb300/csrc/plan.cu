@@ -27,12 +27,18 @@ int cuda_fail(cudaError_t e, const char* what) {
     return FTCJ_ECUDA;
 }
 
+// Raises the kernel's dynamic shared-memory limit to what the device allows
+// beside its static shared memory (the attribute is per kernel and global, so
+// it is set to the maximum once rather than to one plan's need).
 int allow_dynamic_smem(const void* func, size_t need) {
     int dev = 0, optin = 0;
     FTCJ_CUDA(cudaGetDevice(&dev));
     FTCJ_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (need > (size_t)optin) return fail(FTCJ_EUNSUPPORTED, "shared memory of a walk chunk above the device limit");
-    FTCJ_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    cudaFuncAttributes fa;
+    FTCJ_CUDA(cudaFuncGetAttributes(&fa, func));
+    const size_t room = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    if (need > room) return fail(FTCJ_EUNSUPPORTED, "shared memory of a walk chunk above the device limit");
+    FTCJ_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)room));
     return FTCJ_OK;
 }
 
@@ -149,7 +155,9 @@ int build_walk(ftcj_plan* P) {
             cur = 0;
         }
         int o = (i == (size_t)l0) ? OP_FIRST : op[i];
-        P->lines.push_back({raw[i].n2, raw[i].n3, raw[i].lo, raw[i].hi, o, pt});
+        const double qb = M[1] * raw[i].n2 + M[2] * raw[i].n3;
+        P->lines.push_back({raw[i].n2, raw[i].n3, raw[i].lo, raw[i].hi, o, pt, (float)M[0], (float)qb,
+                            (float)qform(M, 0, raw[i].n2, raw[i].n3)});
         if (npts > 0) {
             for (int n1 = std::max(raw[i].lo, 0); n1 <= raw[i].hi; ++n1) {
                 P->gvec.push_back(n1);
@@ -208,7 +216,8 @@ int build_rho_schedule(ftcj_plan* P) {
     const int nt = (int)P->tiles.size(), nb = std::max(1, P->npb);
     auto cost = [&](int t) {
         const double L = (double)P->tiles[t].cls;
-        return P->precision == FTCJ_PREC_SPLIT ? 38.0 * L + 100.0 : 4.0 * L + 24.0;
+        const double pts = P->tile_npts.empty() ? 1.0 : (double)P->tile_npts[t] + 1.0;  // radius-limited tiles
+        return (P->precision == FTCJ_PREC_SPLIT ? 38.0 * L + 100.0 : 4.0 * L + 24.0) * pts;
     };
     std::vector<int> order(nt);
     for (int t = 0; t < nt; ++t) order[t] = t;
@@ -245,7 +254,7 @@ void free_device(ftcj_plan* P) {
                     P->d_gvec, P->d_vg, P->d_tw, P->d_Tmat, P->d_D0n, P->d_J0n, P->d_cbuf0, P->d_cbuf1,
                     P->d_Dp, P->d_Jp, P->d_rho_part, P->d_rho, P->d_W, P->d_Epart, P->d_Dk_stage,
                     P->d_Jk_stage, P->d_EJ_stage, P->d_check, P->d_split_init, P->d_split_const, P->d_Jg,
-                    P->d_maps, P->d_map_off, P->d_sched};
+                    P->d_maps, P->d_map_off, P->d_sched, P->d_rec_gcut};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -298,6 +307,10 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     if (prm->precision != FTCJ_PREC_FP64 && prm->precision != FTCJ_PREC_SPLIT)
         return fail(FTCJ_EUNSUPPORTED, "precision must be FTCJ_PREC_FP64 or FTCJ_PREC_SPLIT");
     P->precision = prm->precision;
+    if (!(prm->pair_gcut_eps >= 0.0) || !finite(prm->pair_gcut_eps))
+        return fail(FTCJ_EINVAL, "pair_gcut_eps must be a finite number >= 0");
+    if (prm->pair_gcut_eps > 0.0 && prm->precision != FTCJ_PREC_SPLIT)
+        return fail(FTCJ_EUNSUPPORTED, "per-pair G cutoffs are implemented in the split form's walks");
     if (!(prm->pair_thresh > 0.0 && prm->pair_thresh < 1.0)) return fail(FTCJ_EINVAL, "pair_thresh in (0,1)");
     P->omega = prm->omega;
     P->cc.vpar[0] = 4.0 * M_PI / P->vol;
@@ -415,12 +428,13 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     for (int c = kNclass - 1; c >= 0; --c)
         for (int64_t f = P->class_start[c]; f < P->class_start[c + 1]; f += kTile) {
             int cnt = (int)std::min<int64_t>(kTile, P->class_start[c + 1] - f);
-            P->tiles.push_back({c, (int)f, cnt, 0});
+            P->tiles.push_back({c, (int)f, cnt, INFINITY});
         }
     if ((rc = upload(P, &P->d_tiles, P->tiles))) return rc;
     if ((rc = upload_walk_tables(P))) return rc;
     if ((rc = upload_hermite_tables(P))) return rc;
     if ((rc = build_maps(P))) return rc;
+    if (prm->pair_gcut_eps > 0.0 && (rc = apply_pair_cutoffs(P))) return rc;
     if (P->precision == FTCJ_PREC_SPLIT && (rc = setup_split(P))) return rc;
     int bps = 1;
     if (P->precision == FTCJ_PREC_SPLIT) {
@@ -522,6 +536,8 @@ int ftcj_plan_info(const ftcj_plan* P, ftcj_info* o) {
     o->device_bytes = P->device_bytes;
     o->rho_blocks = P->npb;
     o->n1_table = P->precision == FTCJ_PREC_SPLIT ? split_xtab_entries(P) : 0;
+    o->pair_g_units_screened = P->d_rec_gcut ? P->units_screened : o->pair_g_units;
+    o->pair_g_units_walked = P->d_rec_gcut ? P->units_walked : o->pair_g_units;
     return FTCJ_OK;
 }
 

@@ -206,7 +206,8 @@ __device__ __forceinline__ cdf unpack(float4 v) { return cdf{{v.x, v.y}, {v.z, v
 // warp's 32 records, two shuffles join the quarters, and the four warp sums
 // are added into the row.  Not inlined: one copy serves every call site of
 // the five record classes, which keeps the walk inside the instruction cache.
-__device__ __noinline__ void split_flush(float4* buf, float4* red, float4* row, int rbase, int nvalid) {
+__device__ __noinline__ void split_flush(float4* buf, float4* red, float4* row, const int* pidx, int rbase,
+                                        int nvalid) {
     __syncthreads();
     const int tid = threadIdx.x, lane = tid & 31, wv = tid >> 5;
     const int j = lane & (kSBatch - 1), quarter = lane / kSBatch;
@@ -228,11 +229,12 @@ __device__ __noinline__ void split_flush(float4* buf, float4* red, float4* row, 
     if (quarter == 0 && j < nvalid) red[wv * 32 + j] = make_float4(s.re.hi, s.re.lo, s.im.hi, s.im.lo);
     __syncthreads();
     if (tid < nvalid) {
-        cdf r = unpack(row[rbase + tid]);
+        const int pr = pidx ? pidx[tid] : rbase + tid;  // point indices given, or consecutive points
+        cdf r = unpack(row[pr]);
 #pragma unroll
         for (int q = 0; q < kTile / 32; ++q) r = cdf_add_u(r, unpack(red[q * 32 + tid]));
         r = cdf_norm(r);
-        row[rbase + tid] = make_float4(r.re.hi, r.re.lo, r.im.hi, r.im.lo);
+        row[pr] = make_float4(r.re.hi, r.re.lo, r.im.hi, r.im.lo);
     }
 }
 
@@ -257,11 +259,38 @@ __device__ __forceinline__ cdf xtab_at(const float4* Xs, int m, int dir, int tid
     return cdf{{v.x, v.y}, {sg * v.z, sg * v.w}};
 }
 
-template <int L, bool ORTHO>
+// The tile's part of a line under its G radius (per-pair cutoffs): the n1
+// with qa n1^2 + 2 qb n1 + qc < R2, intersected with [lo, hi].  FP32: points
+// within rounding of the radius may fall either side, where the screening
+// estimate is already at its threshold.
+__device__ __forceinline__ void tile_line_range(const WLine& ln, float R2, int& lo, int& hi) {
+    const float disc = ln.qb * ln.qb - ln.qa * (ln.qc - R2);
+    if (!(disc >= 0.f)) {
+        lo = 1;
+        hi = 0;
+        return;
+    }
+    const float x0 = -ln.qb / ln.qa, h = sqrtf(disc) / ln.qa;
+    lo = max(lo, (int)ceilf(x0 - h));
+    hi = min(hi, (int)floorf(x0 + h));
+}
+
+// Index within the chunk of the first point visited in direction dir of line
+// ln (stored order: n1 = max(lo,0) .. hi, then min(hi,-1) .. lo; the tile
+// visits first = max(tile lo, 0) resp. min(tile hi, -1)); the following
+// points of the direction have the next indices.
+__device__ __forceinline__ int first_index(const WLine& ln, int p0, int dir, int first) {
+    const int f = max(ln.lo, 0);
+    if (dir == 0) return ln.pt - p0 + (first - f);
+    const int n0 = ln.hi >= f ? ln.hi - f + 1 : 0;
+    return ln.pt - p0 + n0 + (min(ln.hi, -1) - first);
+}
+
+template <int L, bool ORTHO, bool CUT>
 __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* __restrict__ Dp_d,
                                const SConst* __restrict__ cst, const SState* __restrict__ init_c,
                                const WLine* __restrict__ lines, const WChunk ch, float4* buf, float4* red,
-                               float4* row, float2* Dsm, float4* Xs, int nx) {
+                               float4* row, float2* Dsm, float4* Xs, int nx, int* spt) {
     constexpr int NT = nterms(L);
     const int tid = threadIdx.x;
     const bool valid = tid < tl.count;
@@ -277,11 +306,13 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
     const SState* init_p = init_c + (valid ? pi : 0);
     if (ORTHO) build_xtab(valid ? *init_p : idle_state(), k.q1, nx, Xs, tid);
     SState s;
-    int slot = 0, rbase = 0;
+    int slot = 0, par = 0, rbase = 0;
     for (int li = ch.l0; li < ch.l1; ++li) {
         const WLine ln = lines[li];
         split_step<ORTHO>(k, ln.op, s, init_p, valid);
-        if (ln.lo > ln.hi) continue;
+        int lo = ln.lo, hi = ln.hi;
+        if (CUT) tile_line_range(ln, tl.gcut2, lo, hi);
+        if (lo > hi) continue;
         cdf c[L + 1];
         {
             float pq[L + 1][L + 1];
@@ -318,18 +349,18 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
             int m0, m1, step;
             cdf gp, R;
             if (dir == 0) {
-                if (ln.hi < 0) continue;
+                if (hi < 0) continue;
                 m0 = 0;
-                m1 = ln.hi;
+                m1 = hi;
                 step = 1;
                 if (!ORTHO) {
                     gp = s.gpL;
                     R = s.RfL;
                 }
             } else {
-                if (ln.lo > -1) continue;
+                if (lo > -1) continue;
                 m0 = -1;
-                m1 = ln.lo;
+                m1 = lo;
                 step = -1;
                 if (!ORTHO) {
                     gp = cdf_mul(s.gpL, s.RbL);
@@ -338,13 +369,14 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
             }
             if (ORTHO) {
                 // no recurrence to carry: visit exactly the line's points of this direction
-                m0 = dir == 0 ? max(ln.lo, 0) : min(ln.hi, -1);
+                m0 = dir == 0 ? max(lo, 0) : min(hi, -1);
                 if ((m1 - m0) * step < 0) continue;
             }
+            int q = CUT ? first_index(ln, ch.p0, dir, dir == 0 ? max(lo, 0) : min(hi, -1)) : 0;
             float x = (float)m0;
             const float xstep = (float)step;
             for (int m = m0;; m += step, x += xstep) {
-                if (ORTHO || (m >= ln.lo && m <= ln.hi)) {
+                if (ORTHO || (m >= lo && m <= hi)) {
                     cdf a = c[L];
 #pragma unroll
                     for (int i = L - 1; i >= 0; --i)
@@ -353,8 +385,13 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
                     if (ORTHO) xv = xtab_at(Xs, m, dir, tid);
                     const cdf z = ORTHO ? cdf_mul_u(xv, a) : cdf_mul_u(gp, a);
                     buf[slot * (kTile + 1) + tid] = make_float4(z.re.hi, z.re.lo, z.im.hi, z.im.lo);
+                    if (CUT) {
+                        if (tid == 0) spt[par * kSBatch + slot] = q;
+                        ++q;
+                    }
                     if (++slot == kSBatch) {
-                        split_flush(buf, red, row, rbase, kSBatch);
+                        split_flush(buf, red, row, CUT ? spt + par * kSBatch : nullptr, rbase, kSBatch);
+                        par ^= 1;  // the next batch's indices go to the other half
                         rbase += kSBatch;
                         slot = 0;
                     }
@@ -367,11 +404,11 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
             }
         }
     }
-    if (slot > 0) split_flush(buf, red, row, rbase, slot);
+    if (slot > 0) split_flush(buf, red, row, CUT ? spt + par * kSBatch : nullptr, rbase, slot);
     __syncthreads();
 }
 
-template <bool ORTHO>
+template <bool ORTHO, bool CUT>
 __global__ void __launch_bounds__(kTile, 3) k_rho_walk_split(const Tile* __restrict__ tiles, int ntiles, Layout lay,
                                                           const float2* __restrict__ Dp,
                                                           const SConst* __restrict__ cst,
@@ -381,6 +418,7 @@ __global__ void __launch_bounds__(kTile, 3) k_rho_walk_split(const Tile* __restr
                                                           double2* __restrict__ rho_part, long long ng_half,
                                                           const int* __restrict__ sched, int nx) {
     extern __shared__ float4 ssm[];
+    __shared__ int spt[2 * kSBatch];  // point indices of the current and the previous batch
     const int b = blockIdx.x, cidx = blockIdx.y, d = blockIdx.z;
     const WChunk ch = chunks[cidx];
     const int npts = ch.p1 - ch.p0;
@@ -397,11 +435,11 @@ __global__ void __launch_bounds__(kTile, 3) k_rho_walk_split(const Tile* __restr
     for (int j = sched[b]; j < sched[b + 1]; ++j) {
         const Tile tl = tiles[sched[npb + 1 + j]];
         switch (tl.cls) {
-            case 0: rho_tile_split<0, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx); break;
-            case 1: rho_tile_split<1, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx); break;
-            case 2: rho_tile_split<2, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx); break;
-            case 3: rho_tile_split<3, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx); break;
-            default: rho_tile_split<4, ORTHO>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx); break;
+            case 0: rho_tile_split<0, ORTHO, CUT>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx, spt); break;
+            case 1: rho_tile_split<1, ORTHO, CUT>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx, spt); break;
+            case 2: rho_tile_split<2, ORTHO, CUT>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx, spt); break;
+            case 3: rho_tile_split<3, ORTHO, CUT>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx, spt); break;
+            default: rho_tile_split<4, ORTHO, CUT>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx, spt); break;
         }
     }
     __syncthreads();
@@ -414,7 +452,7 @@ __global__ void __launch_bounds__(kTile, 3) k_rho_walk_split(const Tile* __restr
 
 // ---- J -------------------------------------------------------------------
 
-template <int L, bool ORTHO>
+template <int L, bool ORTHO, bool CUT>
 __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __restrict__ cst,
                              const SState* __restrict__ init_c, const WLine* __restrict__ lines, const WChunk ch,
                              const float4* __restrict__ wsm,
@@ -436,28 +474,30 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
     for (int li = ch.l0; li < ch.l1; ++li) {
         const WLine ln = lines[li];
         split_step<ORTHO>(k, ln.op, s, init_p, valid);
-        if (ln.lo > ln.hi) continue;
+        int lo = ln.lo, hi = ln.hi;
+        if (CUT) tile_line_range(ln, tl.gcut2, lo, hi);
+        if (lo > hi) continue;
         cdf A[L + 1];
 #pragma unroll
         for (int i = 0; i <= L; ++i) A[i] = cdf{{0.f, 0.f}, {0.f, 0.f}};
-        int q = ln.pt - ch.p0;
+        int qs = ln.pt - ch.p0;  // without cutoffs the line's points are visited in stored order
 #pragma unroll
         for (int dir = 0; dir < 2; ++dir) {
             int m0, m1, step;
             cdf gp, R;
             if (dir == 0) {
-                if (ln.hi < 0) continue;
+                if (hi < 0) continue;
                 m0 = 0;
-                m1 = ln.hi;
+                m1 = hi;
                 step = 1;
                 if (!ORTHO) {
                     gp = s.gpL;
                     R = s.RfL;
                 }
             } else {
-                if (ln.lo > -1) continue;
+                if (lo > -1) continue;
                 m0 = -1;
-                m1 = ln.lo;
+                m1 = lo;
                 step = -1;
                 if (!ORTHO) {
                     gp = cdf_mul(s.gpL, s.RbL);
@@ -466,13 +506,14 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
             }
             if (ORTHO) {
                 // no recurrence to carry: visit exactly the line's points of this direction
-                m0 = dir == 0 ? max(ln.lo, 0) : min(ln.hi, -1);
+                m0 = dir == 0 ? max(lo, 0) : min(hi, -1);
                 if ((m1 - m0) * step < 0) continue;
             }
+            int q = CUT ? first_index(ln, ch.p0, dir, dir == 0 ? max(lo, 0) : min(hi, -1)) : qs;
             float x = (float)m0;
             const float xstep = (float)step;
             for (int m = m0;; m += step, x += xstep) {
-                if (ORTHO || (m >= ln.lo && m <= ln.hi)) {
+                if (ORTHO || (m >= lo && m <= hi)) {
                     const cdf w = unpack(wsm[q++]);
                     cdf xv;
                     if (ORTHO) xv = xtab_at(Xs, m, dir, tid);
@@ -491,6 +532,7 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
                     R = cdf_scale(R, k.q1);
                 }
             }
+            qs = q;
         }
 #pragma unroll
         for (int i = 0; i <= L; ++i) A[i] = cdf_norm(A[i]);
@@ -530,7 +572,7 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
     }
 }
 
-template <bool ORTHO>
+template <bool ORTHO, bool CUT>
 __global__ void __launch_bounds__(kTile, 3) k_j_walk_split(const Tile* __restrict__ tiles, Layout lay,
                                                         const SConst* __restrict__ cst,
                                                         const SState* __restrict__ init, long long npairs,
@@ -556,11 +598,11 @@ __global__ void __launch_bounds__(kTile, 3) k_j_walk_split(const Tile* __restric
     double* Jp_dc = Jp + ((long long)d * nchunks + cidx) * lay.total;
     const SState* init_c = init + (long long)cidx * npairs;
     switch (tl.cls) {
-        case 0: j_tile_split<0, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
-        case 1: j_tile_split<1, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
-        case 2: j_tile_split<2, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
-        case 3: j_tile_split<3, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
-        default: j_tile_split<4, ORTHO>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+        case 0: j_tile_split<0, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+        case 1: j_tile_split<1, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+        case 2: j_tile_split<2, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+        case 3: j_tile_split<3, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+        default: j_tile_split<4, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
     }
 }
 
@@ -592,6 +634,22 @@ size_t j_smem(const ftcj_plan* P) {
            xtab_bytes(P);
 }
 
+// the walk kernels for the plan's shape: X(n1) table or recurrence, with or without per-pair cutoffs
+using RhoKernel = decltype(&k_rho_walk_split<true, true>);
+using JKernel = decltype(&k_j_walk_split<true, true>);
+
+RhoKernel rho_kernel(const ftcj_plan* P) {
+    const bool c = P->d_rec_gcut != nullptr;
+    if (use_xtab(P)) return c ? k_rho_walk_split<true, true> : k_rho_walk_split<true, false>;
+    return c ? k_rho_walk_split<false, true> : k_rho_walk_split<false, false>;
+}
+
+JKernel j_kernel(const ftcj_plan* P) {
+    const bool c = P->d_rec_gcut != nullptr;
+    if (use_xtab(P)) return c ? k_j_walk_split<true, true> : k_j_walk_split<true, false>;
+    return c ? k_j_walk_split<false, true> : k_j_walk_split<false, false>;
+}
+
 }  // namespace
 
 int split_xtab_entries(const ftcj_plan* P) { return use_xtab(P) ? xtab_entries(P) : 0; }
@@ -610,19 +668,14 @@ int setup_split(ftcj_plan* P) {
                                   reinterpret_cast<SConst*>(P->d_split_const), P->cc);
         FTCJ_CUDA(cudaGetLastError());
     }
-    int rc = use_xtab(P) ? allow_dynamic_smem((const void*)k_rho_walk_split<true>, rho_smem(P))
-                         : allow_dynamic_smem((const void*)k_rho_walk_split<false>, rho_smem(P));
+    int rc = allow_dynamic_smem((const void*)rho_kernel(P), rho_smem(P));
     if (rc) return rc;
-    return use_xtab(P) ? allow_dynamic_smem((const void*)k_j_walk_split<true>, j_smem(P))
-                       : allow_dynamic_smem((const void*)k_j_walk_split<false>, j_smem(P));
+    return allow_dynamic_smem((const void*)j_kernel(P), j_smem(P));
 }
 
 int rho_walk_split_blocks_per_sm(ftcj_plan* P, int* out) {
     int n = 0;
-    if (use_xtab(P))
-        FTCJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rho_walk_split<true>, kTile, rho_smem(P)));
-    else
-        FTCJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rho_walk_split<false>, kTile, rho_smem(P)));
+    FTCJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rho_kernel(P), kTile, rho_smem(P)));
     *out = n > 0 ? n : 1;
     return FTCJ_OK;
 }
@@ -634,7 +687,7 @@ int launch_rho_walk_split(ftcj_plan* P, int ndens, cudaStream_t s) {
     }
     dim3 g(P->npb, (unsigned)P->chunks.size(), ndens);
     const int nx = use_xtab(P) ? xtab_entries(P) : 0;
-    auto* kern = use_xtab(P) ? k_rho_walk_split<true> : k_rho_walk_split<false>;
+    auto* kern = rho_kernel(P);
     kern<<<g, kTile, rho_smem(P), s>>>(P->d_tiles, (int)P->tiles.size(), make_layout(P),
                                        reinterpret_cast<const float2*>(P->d_Dp),
                                        reinterpret_cast<const SConst*>(P->d_split_const),
@@ -654,7 +707,7 @@ int launch_j_walk_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s
     }
     dim3 g((unsigned)P->tiles.size(), nch, ndens);
     const int nx = use_xtab(P) ? xtab_entries(P) : 0;
-    auto* kern = use_xtab(P) ? k_j_walk_split<true> : k_j_walk_split<false>;
+    auto* kern = j_kernel(P);
     kern<<<g, kTile, j_smem(P), s>>>(P->d_tiles, make_layout(P),
                                                reinterpret_cast<const SConst*>(P->d_split_const),
                                                reinterpret_cast<const SState*>(P->d_split_init), P->npairs,

@@ -40,7 +40,8 @@ class BasisDesc(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("omega", _c_double), ("gcut", _c_double), ("eps_g", _c_double), ("pair_thresh", _c_double),
-                ("precision", _c_int), ("max_dens", _c_int), ("chunk_points", _c_int), ("rho_blocks", _c_int)]
+                ("precision", _c_int), ("max_dens", _c_int), ("chunk_points", _c_int), ("rho_blocks", _c_int),
+                ("pair_gcut_eps", _c_double)]
 
 
 class Info(ctypes.Structure):
@@ -49,7 +50,8 @@ class Info(ctypes.Structure):
                 ("ng_full", ctypes.c_int64), ("pair_g_units", ctypes.c_int64),
                 ("pairs_by_class", ctypes.c_int64 * 5), ("nlines", _c_int), ("nchunks", _c_int),
                 ("gcut", _c_double), ("volume", _c_double), ("device_bytes", ctypes.c_size_t),
-                ("rho_blocks", _c_int), ("n1_table", _c_int)]
+                ("rho_blocks", _c_int), ("n1_table", _c_int), ("pair_g_units_screened", ctypes.c_int64),
+                ("pair_g_units_walked", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -183,9 +185,9 @@ def _describe(A, xyz, shells, keep):
     return cell, basis
 
 
-def _params_of(w, precision=FTCJ_PREC_FP64, max_dens=None, chunk_points=0, rho_blocks=0):
+def _params_of(w, precision=FTCJ_PREC_FP64, max_dens=None, chunk_points=0, rho_blocks=0, pair_gcut_eps=0.0):
     return Params(float(w.omega), float(w.gcut), float(w.eps_g), float(w.pair_thresh), int(precision),
-                  int(max_dens or w.ndens), int(chunk_points), int(rho_blocks))
+                  int(max_dens or w.ndens), int(chunk_points), int(rho_blocks), float(pair_gcut_eps))
 
 
 def autotune(w, precision=FTCJ_PREC_FP64):
@@ -286,13 +288,13 @@ class Plan:
     """A plan for one cell, basis and k-mesh (ftcj_plan_create)."""
 
     def __init__(self, A, xyz, shells, kmesh, omega, eps_g=1e-14, gcut=0.0, pair_thresh=1e-12,
-                 precision=FTCJ_PREC_FP64, max_dens=1, chunk_points=0, rho_blocks=0):
+                 precision=FTCJ_PREC_FP64, max_dens=1, chunk_points=0, rho_blocks=0, pair_gcut_eps=0.0):
         L = lib()
         self._keep = []
         cell, basis = _describe(A, xyz, shells, self._keep)
         km = (ctypes.c_int * 3)(*[int(k) for k in kmesh])
         prm = Params(float(omega), float(gcut), float(eps_g), float(pair_thresh), int(precision), int(max_dens),
-                     int(chunk_points), int(rho_blocks))
+                     int(chunk_points), int(rho_blocks), float(pair_gcut_eps))
         h = _c_void_p()
         _check(L.ftcj_plan_create(ctypes.byref(cell), ctypes.byref(basis), km, ctypes.byref(prm), ctypes.byref(h)),
                "ftcj_plan_create")
@@ -308,9 +310,11 @@ class Plan:
         self.xyz = np.array(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
 
     @classmethod
-    def from_workload(cls, w, max_dens=None, precision=FTCJ_PREC_FP64, chunk_points=0, rho_blocks=0):
+    def from_workload(cls, w, max_dens=None, precision=FTCJ_PREC_FP64, chunk_points=0, rho_blocks=0,
+                      pair_gcut_eps=0.0):
         return cls(w.A, w.xyz, w.shells, w.kmesh, w.omega, eps_g=w.eps_g, gcut=w.gcut, pair_thresh=w.pair_thresh,
                    precision=precision, max_dens=max_dens or w.ndens, chunk_points=chunk_points,
+                   pair_gcut_eps=pair_gcut_eps,
                    rho_blocks=rho_blocks)
 
     def close(self):

@@ -129,3 +129,37 @@ def test_split_fold_and_unfold_steps(orc, F, kmesh):
     cmax = np.abs(J0n).max(axis=1, keepdims=True)
     assert (np.abs(Jk - Jref) <= 1e-13 * nk * cmax + 1e-36).all()
     plan.close()
+
+
+@pytest.mark.parametrize("eps", [1e-12, 1e-10])
+def test_pair_cutoffs_against_the_whole_sphere(orc, F, eps):
+    """Per-pair G cutoffs (Sec. 2.5, screening objective): each record is
+    evaluated only inside its own radius, so the result differs from the full
+    sum (the oracle) by the screened-out terms; with eps = 1e-12 that stays
+    inside the split form's 1e-8 Eh bound on J and E_J.  The work counters must
+    be ordered: screened <= walked <= all."""
+    import torch
+    cells = [W.cfg1(),
+             W.tiny(seed=34, A=np.array([[5.1, 0.0, 0.0], [1.7, 4.9, 0.0], [-0.9, 0.6, 5.4]]), kmesh=(2, 1, 2)),
+             W.cfg2()]
+    for w in cells:
+        ref = orc.lrj(w, want_j0n=False)
+        plan = F.Plan.from_workload(w, precision=F.FTCJ_PREC_SPLIT, pair_gcut_eps=eps)
+        info = plan.info
+        assert 0 < info["pair_g_units_screened"] <= info["pair_g_units_walked"] <= info["pair_g_units"]
+        J, E = plan.jbuild(torch.from_numpy(np.ascontiguousarray(w.Dk)).cuda())
+        torch.cuda.synchronize()
+        dJ = float(np.abs(J.cpu().numpy() - ref["Jk"]).max())
+        dE = float(np.abs(E.cpu().numpy() - ref["EJ"]).max())
+        frac = info["pair_g_units_walked"] / info["pair_g_units"]
+        print(f"{w.name} eps={eps:g}: walked {frac:.3f} of the units, max|dJ|={dJ:.2e} |dE|={dE:.2e}")
+        if eps <= 1e-12:
+            assert dJ <= SPLIT_J_TOL and dE <= SPLIT_E_TOL, (w.name, dJ, dE)
+        else:
+            assert dJ <= 1e-6 and dE <= 1e-6, (w.name, dJ, dE)
+        plan.close()
+
+
+def test_pair_cutoffs_need_the_split_form(F):
+    with pytest.raises(F.FtcjError, match="split form"):
+        F.Plan.from_workload(W.cfg1(), precision=F.FTCJ_PREC_FP64, pair_gcut_eps=1e-12)
