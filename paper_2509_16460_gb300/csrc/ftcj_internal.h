@@ -257,6 +257,7 @@ int rho_walk_blocks_per_sm(ftcj_plan* P, int* out);
 // --- split-precision walks (walk_split.cu) ---
 int setup_split(ftcj_plan* P);
 int split_xtab_entries(const ftcj_plan* P);  // 0 when the split walks run the n1 recurrence
+size_t split_rho_smem(const ftcj_plan* P);  // shared memory of one split structure-factor block
 int launch_pair_gcut(ftcj_plan* P);      // per-record cutoffs from the (double) maps, in build_maps
 int apply_pair_cutoffs(ftcj_plan* P);    // sort records by cutoff within each class, radius per tile
 int rho_walk_split_blocks_per_sm(ftcj_plan* P, int* out);

@@ -184,6 +184,35 @@ int build_walk(ftcj_plan* P) {
     return FTCJ_OK;
 }
 
+// Default walk chunk of the split form: the structure-factor block keeps one
+// chunk's rho row (16 B per point) in shared memory beside chunk-independent
+// staging, so the chunk sets its occupancy.  Take the largest power of two
+// (<= 4096 points) that lets three blocks share an SM, or else two, with at
+// least 1024 resp. 512 points; the walk program is rebuilt for it.
+int default_split_chunk(ftcj_plan* P) {
+    int dev = 0, per_sm = 0;
+    FTCJ_CUDA(cudaGetDevice(&dev));
+    FTCJ_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    const int keep = P->max_chunk_pts;
+    P->max_chunk_pts = 0;
+    const size_t fixed = split_rho_smem(P);
+    P->max_chunk_pts = keep;
+    int chunk = 256;
+    for (int target = 3; target >= 1; --target) {
+        const long long room = (long long)per_sm / target - 1024 - (long long)fixed;
+        const long long pts = room / 16;
+        const long long need = target == 3 ? 1024 : (target == 2 ? 512 : 0);
+        if (pts >= need && pts >= 64) {
+            chunk = 64;
+            while (chunk * 2 <= std::min<long long>(pts, kChunkMax)) chunk *= 2;
+            break;
+        }
+    }
+    if (chunk >= P->chunk_max) return FTCJ_OK;
+    P->chunk_max = chunk;
+    return build_walk(P);
+}
+
 template <class T>
 int dalloc(ftcj_plan* P, T** ptr, size_t count) {
     if (count == 0) count = 1;
@@ -399,6 +428,7 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
         return fail(FTCJ_EUNSUPPORTED, "Gcut^2/(4 p_min) above 600: exponents too diffuse for this Gcut");
     int rc = build_walk(P);
     if (rc) return rc;
+    if (prm->chunk_points <= 0 && P->precision == FTCJ_PREC_SPLIT && (rc = default_split_chunk(P))) return rc;
 
     FTCJ_CUDA(cudaFree(0));
     int dev = 0;

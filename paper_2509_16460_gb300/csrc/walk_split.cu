@@ -275,6 +275,30 @@ __device__ __forceinline__ void tile_line_range(const WLine& ln, float R2, int& 
     hi = min(hi, (int)floorf(x0 + h));
 }
 
+// Skipping state of a radius-limited tile in an orthorhombic cell, where the
+// smallest |G| of a line grows with |n2| inside a plane and the smallest |G|
+// of a plane grows with n3: once a line lies wholly outside the radius, so do
+// the rest of its direction in that plane (and, for a plane's centre line,
+// every later plane), and the walk jumps to the next transition that starts
+// from the plane values (OP_NEGSTART, OP_N3, or a chunk's OP_FIRST).
+enum { kWalkOn = 0, kSkipPos = 1, kSkipNeg = 2, kSkipRest = 3 };
+
+__device__ __forceinline__ bool line_outside(const WLine& ln, float R2) {
+    return !(ln.qb * ln.qb - ln.qa * (ln.qc - R2) >= 0.f);
+}
+
+// true: skip this line without advancing the walk state
+__device__ __forceinline__ bool skip_line(int& mode, int op) {
+    if (mode == kSkipPos && op != OP_NEGSTART && op != OP_N3 && op != OP_FIRST) return true;
+    if (mode == kSkipNeg && op != OP_N3 && op != OP_FIRST) return true;
+    mode = kWalkOn;
+    return false;
+}
+
+__device__ __forceinline__ int skip_mode_after(const WLine& ln) {
+    return ln.n2 == 0 ? kSkipRest : (ln.n2 > 0 ? kSkipPos : kSkipNeg);
+}
+
 // Index within the chunk of the first point visited in direction dir of line
 // ln (stored order: n1 = max(lo,0) .. hi, then min(hi,-1) .. lo; the tile
 // visits first = max(tile lo, 0) resp. min(tile hi, -1)); the following
@@ -306,12 +330,22 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
     const SState* init_p = init_c + (valid ? pi : 0);
     if (ORTHO) build_xtab(valid ? *init_p : idle_state(), k.q1, nx, Xs, tid);
     SState s;
-    int slot = 0, par = 0, rbase = 0;
+    int slot = 0, par = 0, rbase = 0, mode = kWalkOn;
     for (int li = ch.l0; li < ch.l1; ++li) {
         const WLine ln = lines[li];
+        if (ORTHO && CUT) {
+            if (mode == kSkipRest) break;
+            if (skip_line(mode, ln.op)) continue;
+        }
         split_step<ORTHO>(k, ln.op, s, init_p, valid);
         int lo = ln.lo, hi = ln.hi;
-        if (CUT) tile_line_range(ln, tl.gcut2, lo, hi);
+        if (CUT) {
+            if (ORTHO && line_outside(ln, tl.gcut2)) {
+                mode = skip_mode_after(ln);
+                continue;
+            }
+            tile_line_range(ln, tl.gcut2, lo, hi);
+        }
         if (lo > hi) continue;
         cdf c[L + 1];
         {
@@ -471,11 +505,22 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
     for (int t = 0; t < NT; ++t) Jsm[t * kTile + tid] = make_float2(0.f, 0.f);
     if (ORTHO) build_xtab(valid ? *init_p : idle_state(), k.q1, nx, Xs, tid);
     SState s;
+    int mode = kWalkOn;
     for (int li = ch.l0; li < ch.l1; ++li) {
         const WLine ln = lines[li];
+        if (ORTHO && CUT) {
+            if (mode == kSkipRest) break;
+            if (skip_line(mode, ln.op)) continue;
+        }
         split_step<ORTHO>(k, ln.op, s, init_p, valid);
         int lo = ln.lo, hi = ln.hi;
-        if (CUT) tile_line_range(ln, tl.gcut2, lo, hi);
+        if (CUT) {
+            if (ORTHO && line_outside(ln, tl.gcut2)) {
+                mode = skip_mode_after(ln);
+                continue;
+            }
+            tile_line_range(ln, tl.gcut2, lo, hi);
+        }
         if (lo > hi) continue;
         cdf A[L + 1];
 #pragma unroll
@@ -653,6 +698,8 @@ JKernel j_kernel(const ftcj_plan* P) {
 }  // namespace
 
 int split_xtab_entries(const ftcj_plan* P) { return use_xtab(P) ? xtab_entries(P) : 0; }
+
+size_t split_rho_smem(const ftcj_plan* P) { return rho_smem(P); }
 
 int setup_split(ftcj_plan* P) {
     const size_t nch = P->chunks.size();
