@@ -36,6 +36,7 @@ UNIT = "pair*G/s"
 WORKLOAD = ("diamond-like cubic a=6.74 bohr, 8 C-like centres, spherical s8p4d2 (240 AOs), "
             "k 4x4x4 (64 D^k, 16 occupied), omega 0.4, exp(-G^2/4w^2)>1e-14, pair overlap>1e-12")
 L2_FLUSH_BYTES = 512 << 20
+PAIR_GCUT_EPS = 1e-12  # the per-pair G cutoff variant (screening threshold of Sec. 2.5)
 
 
 def parse():
@@ -239,17 +240,22 @@ def cfg3_leg(ftcj, W, torch, flush, steps):
                        "k 2x2x2, 2 spin densities x 8 D^k, omega 0.5", "ndens": w.ndens}
     stream = torch.cuda.current_stream()
     res = {}
-    for form, prec in (("split", ftcj.FTCJ_PREC_SPLIT), ("fp64", ftcj.FTCJ_PREC_FP64)):
-        p = ftcj.Plan.from_workload(w, precision=prec)
+    for form, prec, eps in (("split", ftcj.FTCJ_PREC_SPLIT, 0.0), ("fp64", ftcj.FTCJ_PREC_FP64, 0.0),
+                            ("split_pair_gcut", ftcj.FTCJ_PREC_SPLIT, PAIR_GCUT_EPS)):
+        p = ftcj.Plan.from_workload(w, precision=prec, pair_gcut_eps=eps)
         units = float(p.info["pair_g_units"]) * w.ndens
         J, E = p.jbuild(Dk)
         for _ in range(2):
             p.jbuild(Dk, J, E)
         ms = time_events(lambda: p.jbuild(Dk, J, E), steps, flush, stream)
         out[form] = {"ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT}
+        if eps > 0:
+            out[form]["pair_gcut_eps"] = eps
+            out[form]["walked_fraction_of_units"] = p.info["pair_g_units_walked"] / p.info["pair_g_units"]
         out["pair_g_units_per_step"] = units
         res[form] = (J.clone(), E.clone())
         p.close()
+    out["split_pair_gcut_vs_fp64_max_abs_dJ"] = float((res["split_pair_gcut"][0] - res["fp64"][0]).abs().max())
     out["split_vs_fp64_max_abs_dJ"] = float((res["split"][0] - res["fp64"][0]).abs().max())
     out["split_vs_fp64_abs_dEJ"] = float((res["split"][1] - res["fp64"][1]).abs().max())
     out["split_speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["split"]["ms_per_step"]
@@ -324,8 +330,9 @@ def main():
     forms = {}
     infos = {}
     results = {}
-    for form, prec in (("split", ftcj.FTCJ_PREC_SPLIT), ("fp64", ftcj.FTCJ_PREC_FP64)):
-        plan = ftcj.Plan.from_workload(w, precision=prec)
+    for form, prec, eps in (("split", ftcj.FTCJ_PREC_SPLIT, 0.0), ("fp64", ftcj.FTCJ_PREC_FP64, 0.0),
+                            ("split_pair_gcut", ftcj.FTCJ_PREC_SPLIT, PAIR_GCUT_EPS)):
+        plan = ftcj.Plan.from_workload(w, precision=prec, pair_gcut_eps=eps)
         info = plan.info
         units = float(info["pair_g_units"]) * w.ndens
         Jk = torch.empty_like(Dk)
@@ -369,19 +376,24 @@ def main():
             e2e_t.append(time.perf_counter() - t0)
         e2e_s = max_over_ranks(statistics.mean(e2e_t), dist, "cuda")
         # roofline of the dominant kernel: FP64 pipe (fp64) or FP32 pipe (split)
-        suffix = "_split" if form == "split" else ""
+        pipe_form = "fp64" if form == "fp64" else "split"
+        suffix = "_split" if pipe_form == "split" else ""
         walks = {"k_rho_walk" + suffix: phase_ms["rho_walk"], "k_j_walk" + suffix: phase_ms["j_walk"]}
         kname = max(walks, key=walks.get)
         per_launch_ms = walks[kname] / max(batches, 1)
-        achieved = walk_flops(info, w.ndens, form) / (per_launch_ms * 1e-3)
-        peak = peaks[form]
+        # with per-pair cutoffs the walks evaluate only the walked share of the units
+        walked = info["pair_g_units_walked"] / info["pair_g_units"]
+        achieved = walk_flops(info, w.ndens, pipe_form) * walked / (per_launch_ms * 1e-3)
+        peak = peaks[pipe_form]
         roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": traffic_from_profile(kname), "kernel": kname,
-                    "pipe": "FP64" if form == "fp64" else "FP32",
-                    "peak_source": f"measured {'FP64' if form == 'fp64' else 'FP32'} FMA throughput "
+                    "frac": achieved / peak, "traffic": traffic_from_profile(kname) if eps == 0 else None,
+                    "kernel": kname, "pipe": "FP64" if pipe_form == "fp64" else "FP32",
+                    "peak_source": f"measured {'FP64' if pipe_form == 'fp64' else 'FP32'} FMA throughput "
                                    "(ftcj_probe_fma_peak) on this GPU",
-                    "nominal_peak": 152 * 2 * 2.07e9 * (2 if form == "fp64" else 128) / 1e12,
+                    "nominal_peak": 152 * 2 * 2.07e9 * (2 if pipe_form == "fp64" else 128) / 1e12,
                     "phase_ms_per_step": {k: v / max(batches, 1) for k, v in phase_ms.items()}}
+        if eps > 0:
+            roofline["flops_note"] = "algorithmic flops scaled by the walked fraction of the units (per-class mix ignored)"
         forms[form] = {"value": value, "unit": UNIT, "ms_per_step": ms, "step_ms_min": min(step_ms),
                        "e2e": {"value": whole_job_rate(world, units, e2e_s), "unit": UNIT,
                                "ms_per_step": e2e_s * 1e3,
@@ -389,7 +401,12 @@ def main():
                                "d2h_bytes_per_step": Jk_h.numel() * 16 + EJ_h.numel() * 8},
                        "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks,
                        "wall_s_timed_region": t_wall,
-                       "walk_shape": {"rho_blocks": info["rho_blocks"], "n1_table": info["n1_table"]}}
+                       "walk_shape": {"rho_blocks": info["rho_blocks"], "n1_table": info["n1_table"],
+                                      "nchunks": info["nchunks"]}}
+        if eps > 0:
+            forms[form]["pair_gcut_eps"] = eps
+            forms[form]["walked_fraction_of_units"] = walked
+            forms[form]["screened_fraction_of_units"] = info["pair_g_units_screened"] / info["pair_g_units"]
         infos[form] = info
         results[form] = (Jk.cpu().numpy(), EJ.cpu().numpy())
         plan.close()
