@@ -201,6 +201,26 @@ __device__ __forceinline__ void powers23f(int n2, int n3, float pq[L + 1][L + 1]
 
 __device__ __forceinline__ cdf unpack(float4 v) { return cdf{{v.x, v.y}, {v.z, v.w}}; }
 
+// sum_i c_i x^i for an integer-valued x (|x|^L exact in FP32): the terms are
+// independent products added in a pairwise tree, which gives the warp more
+// independent instructions than Horner's serial chain at the same count
+template <int L>
+__device__ __forceinline__ cdf poly_at(const cdf* c, float x) {
+    float p[L + 1];
+    p[0] = 1.f;
+#pragma unroll
+    for (int i = 1; i <= L; ++i) p[i] = p[i - 1] * x;
+    cdf t[L + 1];
+    t[0] = c[0];
+#pragma unroll
+    for (int i = 1; i <= L; ++i) t[i] = cdf{df_mulf_u(c[i].re, p[i]), df_mulf_u(c[i].im, p[i])};
+#pragma unroll
+    for (int w = 1; w <= L; w *= 2)
+#pragma unroll
+        for (int i = 0; i + w <= L; i += 2 * w) t[i] = cdf_add_u(t[i], t[i + w]);
+    return t[0];
+}
+
 // Sums the batch's contributions over the block's 128 records: in warp w the
 // four lanes j, j+8, j+16, j+24 each add a quarter of point j's column of the
 // warp's 32 records, two shuffles join the quarters, and the four warp sums
@@ -214,8 +234,10 @@ __device__ __noinline__ void split_flush(float4* buf, float4* red, float4* row, 
     cdf s{{0.f, 0.f}, {0.f, 0.f}};
     if (j < nvalid) {
         const float4* b = buf + j * (kTile + 1) + wv * 32 + quarter * 8;
+        cdf t[4];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) s = cdf_add_u(s, unpack(b[k]));
+        for (int k = 0; k < 8; k += 2) t[k / 2] = cdf_add_u(unpack(b[k]), unpack(b[k + 1]));
+        s = cdf_add_u(cdf_add_u(t[0], t[1]), cdf_add_u(t[2], t[3]));  // pairwise: depth 3, not 8
     }
 #pragma unroll
     for (int off = 16; off >= kSBatch; off >>= 1) {
@@ -411,10 +433,7 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
             const float xstep = (float)step;
             for (int m = m0;; m += step, x += xstep) {
                 if (ORTHO || (m >= lo && m <= hi)) {
-                    cdf a = c[L];
-#pragma unroll
-                    for (int i = L - 1; i >= 0; --i)
-                        a = cdf{df_add_u(df_mulf_u(a.re, x), c[i].re), df_add_u(df_mulf_u(a.im, x), c[i].im)};
+                    const cdf a = poly_at<L>(c, x);
                     cdf xv;
                     if (ORTHO) xv = xtab_at(Xs, m, dir, tid);
                     const cdf z = ORTHO ? cdf_mul_u(xv, a) : cdf_mul_u(gp, a);
