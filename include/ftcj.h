@@ -153,10 +153,12 @@ void ftcj_plan_destroy(ftcj_plan* plan);
  * Asynchronous: returns after enqueueing.  Errors: EINVAL, ECUDA. */
 int ftcj_jbuild(ftcj_plan* plan, int ndens, const double* Dk, double* Jk, double* EJ, void* stream);
 
-/* The same build on HOST buffers (same layouts): copies D^k in, runs the
- * build, copies J^k and E_J out, and synchronises `stream`.  Staging uses
- * plan-owned device buffers sized at plan creation for max_dens densities;
- * ndens may exceed it (batched). */
+/* The same build on HOST buffers (same layouts), synchronising `stream`
+ * before it returns.  A page-locked (cudaHostAlloc / cudaHostRegister) or
+ * managed D^k or J^k is read or written by the k-mesh transform kernels
+ * directly over the host link, so its transfer overlaps that kernel; a
+ * pageable buffer is copied through plan-owned staging sized at plan creation
+ * for max_dens densities.  ndens may exceed max_dens (batched). */
 int ftcj_jbuild_host(ftcj_plan* plan, int ndens, const double* Dk_host, double* Jk_host, double* EJ_host,
                      void* stream);
 

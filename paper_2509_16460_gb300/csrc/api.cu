@@ -7,6 +7,20 @@ using namespace ftcj;
 
 namespace {
 
+// The device address of a host buffer the device can dereference (page-locked
+// or managed memory), else nullptr (pageable memory goes through staging).
+void* device_alias(const void* host) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();  // clear the non-sticky error of an unknown pointer
+        return nullptr;
+    }
+    if ((a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeManaged) && a.devicePointer)
+        return a.devicePointer;
+    return nullptr;
+}
+
+
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 int rho_walk(ftcj_plan* P, int nd, cudaStream_t s) {
@@ -126,13 +140,22 @@ int ftcj_jbuild_host(ftcj_plan* P, int ndens, const double* Dk_host, double* Jk_
     if (!Dk_host || !Jk_host || !EJ_host) return fail(FTCJ_EINVAL, "null buffer");
     cudaStream_t s = as_stream(stream);
     size_t per = (size_t)P->nk * P->nao * P->nao * 2;
+    // Page-locked (or managed) buffers are reached from the device over the
+    // host link: the k-mesh transforms read D^k and write J^k there directly,
+    // so the transfers run inside those kernels instead of as separate copies.
+    const double* Dk_dev = static_cast<const double*>(device_alias(Dk_host));
+    double* Jk_dev = static_cast<double*>(device_alias(Jk_host));
     for (int b0 = 0; b0 < ndens; b0 += P->max_dens) {
         int nd = std::min(P->max_dens, ndens - b0);
-        FTCJ_CUDA(cudaMemcpyAsync(P->d_Dk_stage, Dk_host + b0 * per, sizeof(double) * nd * per,
-                                  cudaMemcpyHostToDevice, s));
-        if ((rc = build_batch(P, nd, P->d_Dk_stage, P->d_Jk_stage, P->d_EJ_stage, s))) return rc;
-        FTCJ_CUDA(cudaMemcpyAsync(Jk_host + b0 * per, P->d_Jk_stage, sizeof(double) * nd * per,
-                                  cudaMemcpyDeviceToHost, s));
+        const double* din = Dk_dev ? Dk_dev + b0 * per : P->d_Dk_stage;
+        double* jout = Jk_dev ? Jk_dev + b0 * per : P->d_Jk_stage;
+        if (!Dk_dev)
+            FTCJ_CUDA(cudaMemcpyAsync(P->d_Dk_stage, Dk_host + b0 * per, sizeof(double) * nd * per,
+                                      cudaMemcpyHostToDevice, s));
+        if ((rc = build_batch(P, nd, din, jout, P->d_EJ_stage, s))) return rc;
+        if (!Jk_dev)
+            FTCJ_CUDA(cudaMemcpyAsync(Jk_host + b0 * per, P->d_Jk_stage, sizeof(double) * nd * per,
+                                      cudaMemcpyDeviceToHost, s));
         FTCJ_CUDA(cudaMemcpyAsync(EJ_host + b0, P->d_EJ_stage, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
     }
     FTCJ_CUDA(cudaStreamSynchronize(s));

@@ -343,16 +343,17 @@ class Plan:
         return Jk, EJ
 
     def jbuild_host(self, Dk, Jk=None, EJ=None, stream=None):
-        """Host buffers in and out (numpy or pinned CPU torch tensors)."""
+        """Host buffers in and out (numpy or CPU torch tensors; pinned ones are
+        read and written by the device directly, the outputs are allocated pinned)."""
         import torch
         nd = Dk.shape[0]
         shp = (nd, self.nk, self.nao, self.nao)
         if isinstance(Dk, np.ndarray):
             Dk = torch.from_numpy(np.ascontiguousarray(Dk, dtype=np.complex128))
         if Jk is None:
-            Jk = torch.empty(shp, dtype=torch.complex128)
+            Jk = torch.empty(shp, dtype=torch.complex128, pin_memory=True)
         if EJ is None:
-            EJ = torch.empty(nd, dtype=torch.float64)
+            EJ = torch.empty(nd, dtype=torch.float64, pin_memory=True)
         for t, name, dt, s in ((Dk, "Dk", torch.complex128, shp), (Jk, "Jk", torch.complex128, shp),
                                (EJ, "EJ", torch.float64, (nd,))):
             if t.is_cuda or t.dtype != dt or tuple(t.shape) != tuple(s) or not t.is_contiguous():

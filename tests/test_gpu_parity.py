@@ -188,6 +188,33 @@ def test_host_buffer_variant(orc, F, torch_cuda):
     plan.close()
 
 
+def test_host_buffer_paths_agree(F, torch_cuda):
+    """Pinned host buffers are used by the device directly, pageable ones go
+    through staging copies: every mix gives the device-buffer result (up to the
+    order of the J -> AO atomic additions)."""
+    torch = torch_cuda
+    w = W.tiny(seed=29, kmesh=(2, 2, 1), ndens=2)
+    for prec in (F.FTCJ_PREC_FP64, F.FTCJ_PREC_SPLIT):
+        plan = F.Plan.from_workload(w, precision=prec)
+        Dd = torch.from_numpy(np.ascontiguousarray(w.Dk)).cuda()
+        Jd, Ed = plan.jbuild(Dd)
+        torch.cuda.synchronize()
+        Jd, Ed = Jd.cpu(), Ed.cpu()
+        shp = tuple(Dd.shape)
+        for pin_in in (True, False):
+            for pin_out in (True, False):
+                Dh = torch.from_numpy(np.ascontiguousarray(w.Dk))
+                if pin_in:
+                    Dh = Dh.pin_memory()
+                Jh = torch.full(shp, float("nan"), dtype=torch.complex128, pin_memory=pin_out)
+                Eh = torch.empty(shp[0], dtype=torch.float64, pin_memory=pin_out)
+                plan.jbuild_host(Dh, Jh, Eh)
+                scale = float(Jd.abs().max())
+                assert float((Jh - Jd).abs().max()) <= 1e-13 * scale, (prec, pin_in, pin_out)
+                assert float((Eh - Ed).abs().max()) <= 1e-13 * float(Ed.abs().max()), (prec, pin_in, pin_out)
+        plan.close()
+
+
 def test_check_density_flags_broken_input(F, torch_cuda):
     torch = torch_cuda
     w = W.tiny(seed=28, kmesh=(2, 1, 1))
