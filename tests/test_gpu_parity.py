@@ -282,3 +282,30 @@ def test_cfg3_sampled_rho_and_invariants(orc, F, torch_cuda):
         herm = np.abs(Jk[d] - np.conj(np.transpose(Jk[d], (0, 2, 1)))).max()
         assert herm <= 1e-12 * np.abs(Jk[d]).max()
     plan.close()
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "split"])
+def test_cfg5_slab_sampled_rho_and_invariants(orc, F, torch_cuda, prec_name):
+    """Slab + adsorbate cell (~940 AOs, k 3x3x1, 20 bohr vacuum) at full size, in
+    the launch shape the library picks: rho at sampled G against the oracle one
+    by one, E_J against (1/2Nk) sum_k Tr(D^k J^k), Hermiticity of J^k."""
+    torch = torch_cuda
+    w = W.cfg5()
+    prec = F.FTCJ_PREC_FP64 if prec_name == "fp64" else F.FTCJ_PREC_SPLIT
+    plan = F.Plan.from_workload(w, precision=prec)
+    Dk = torch.from_numpy(np.ascontiguousarray(w.Dk)).cuda()
+    Jk, EJ = plan.jbuild(Dk)
+    rho = plan.rho(plan.fold_density(Dk)).cpu().numpy()
+    Gh = plan.gvectors()
+    rng = np.random.default_rng(5)
+    sel = np.concatenate([[0], rng.choice(len(Gh), size=5, replace=False)])
+    ref = orc.rho_at(w, Gh[sel])
+    scale = np.abs(ref).max()
+    np.testing.assert_allclose(rho[:, sel], ref, atol=(1e-11 if prec_name == "fp64" else 1e-10) * scale, rtol=0)
+    Jk = Jk.cpu().numpy()
+    EJ = EJ.cpu().numpy()
+    tr = sum(np.trace(w.Dk[0, k] @ Jk[0, k]) for k in range(w.nk)) / (2 * w.nk)
+    assert abs(tr.real - EJ[0]) <= 1e-9 * abs(EJ[0])
+    herm = np.abs(Jk[0] - np.conj(np.transpose(Jk[0], (0, 2, 1)))).max()
+    assert herm <= 1e-12 * np.abs(Jk[0]).max()
+    plan.close()
