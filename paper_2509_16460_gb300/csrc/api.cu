@@ -52,7 +52,7 @@ int build_batch(ftcj_plan* P, int nd, const double* Dk, double* Jk, double* EJ, 
         return FTCJ_OK;
     };
     if ((rc = mark(0))) return rc;
-    if ((rc = launch_fold(P, nd, Dk, P->d_D0n, s))) return rc;
+    if ((rc = launch_fold_build(P, nd, Dk, P->d_D0n, s))) return rc;
     if ((rc = mark(1))) return rc;
     if ((rc = launch_hermite_map(P, nd, P->d_D0n, s))) return rc;
     if ((rc = mark(2))) return rc;
@@ -170,7 +170,7 @@ int ftcj_grad(ftcj_plan* P, int ndens, const double* Dk, double* EJ, double* gra
     size_t per = (size_t)P->nk * P->nao * P->nao * 2;
     for (int b0 = 0; b0 < ndens; b0 += P->max_dens) {
         const int nd = std::min(P->max_dens, ndens - b0);
-        if ((rc = launch_fold(P, nd, Dk + b0 * per, P->d_D0n, s))) return rc;
+        if ((rc = launch_fold_build(P, nd, Dk + b0 * per, P->d_D0n, s))) return rc;
         if ((rc = launch_hermite_map(P, nd, P->d_D0n, s))) return rc;
         if ((rc = rho_walk(P, nd, s))) return rc;
         if ((rc = launch_rho_reduce(P, nd, P->d_rho, P->d_W, EJ + b0, nullptr, s))) return rc;

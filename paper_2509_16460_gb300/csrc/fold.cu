@@ -330,6 +330,64 @@ __global__ void __launch_bounds__(kRegBlock) k_fold_reg(const void* __restrict__
     }
 }
 
+// (mu, nu), mu <= nu, of the t-th element of the row-major upper triangle of an
+// n x n matrix (row mu starts at mu n - mu (mu - 1) / 2); FP32 estimate, then
+// integer correction
+__device__ __forceinline__ void tri_index(long long t, int n, int& mu, int& nu) {
+    const float b = 2.f * n + 1.f;
+    int m = (int)floorf(0.5f * (b - sqrtf(fmaxf(b * b - 8.f * (float)t, 0.f))));
+    m = min(max(m, 0), n - 1);
+    auto start = [n](int r) { return (long long)r * n - (long long)r * (r - 1) / 2; };
+    while (m > 0 && start(m) > t) --m;
+    while (m + 1 < n && start(m + 1) <= t) ++m;
+    mu = m;
+    nu = m + (int)(t - start(m));
+}
+
+// The fold of a Hermitian D^k (D^k_{nu mu} = conj D^k_{mu nu}): then
+// D^{0n}_{nu mu} = D^{0,-n}_{mu nu}, so only the upper triangle mu <= nu is read
+// and transformed, and each result is also written, transposed, at cell -n.
+// Same arithmetic and lane layout as k_fold_reg<0, N2, N3>.
+template <int N2, int N3>
+__global__ void __launch_bounds__(kRegBlock) k_fold_reg_herm(const double2* __restrict__ in, double* __restrict__ out,
+                                                             int nao, long long T, int N1, df inv_nk) {
+    constexpr int P = N2 * N3;
+    const int j = threadIdx.x % N1;
+    const long long t = (long long)blockIdx.x * (kRegBlock / N1) + threadIdx.x / N1;
+    const long long d = blockIdx.y;
+    const int nk = N1 * P;
+    const long long E = (long long)nao * nao;
+    const bool valid = t < T;
+    int mu = 0, nu = 0;
+    if (valid) tri_index(t, nao, mu, nu);
+    const long long e = (long long)mu * nao + nu;
+    cdf v[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        const double2 x = valid ? in[(d * nk + (long long)j * P + q) * E + e] : make_double2(0.0, 0.0);
+        v[q] = cdf{split_double(x.x), split_double(x.y)};
+    }
+#pragma unroll
+    for (int i2 = 0; i2 < N2; ++i2) dft_reg<N3, false>(v, i2 * N3, 1);
+#pragma unroll
+    for (int i3 = 0; i3 < N3; ++i3) dft_reg<N2, false>(v, i3, N3);
+#pragma unroll
+    for (int q = 0; q < P; ++q) v[q] = dft_lanes<false>(v[q], j, N1);
+    if (!valid) return;
+    const int o1 = out_index(j, N1), m1 = (N1 - o1) % N1;
+    const long long et = (long long)nu * nao + mu;
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        const double val = join_df(df_mul(v[q].re, inv_nk));
+        out[(d * nk + (long long)o1 * P + q) * E + e] = val;
+        if (mu != nu) {
+            const int i2 = q / N3, i3 = q % N3;
+            const int qm = ((N2 - i2) % N2) * N3 + (N3 - i3) % N3;
+            out[(d * nk + (long long)m1 * P + qm) * E + et] = val;
+        }
+    }
+}
+
 int axis_code(int n) { return n == 1 ? 0 : (n == 2 ? 1 : (n == 4 ? 2 : -1)); }
 
 template <int MODE>
@@ -353,6 +411,31 @@ int launch_fold_reg(const ftcj_plan* P, int ndens, const void* in, void* out, cu
         default: k_fold_reg<MODE, 4, 4><<<g, kRegBlock, 0, s>>>(in, out, E, N1, inv); break;
     }
 #undef FTCJ_REG_CASE
+    FTCJ_CUDA(cudaGetLastError());
+    return FTCJ_OK;
+}
+
+int launch_fold_herm(const ftcj_plan* P, int ndens, const double* Dk, double* D0n, cudaStream_t s) {
+    const long long T = (long long)P->nao * (P->nao + 1) / 2;
+    const int N1 = P->km[0];
+    dim3 g(nblocks(T * N1, kRegBlock), ndens);
+    const df inv = df_from_double(1.0 / P->nk);
+    const double2* in = reinterpret_cast<const double2*>(Dk);
+    const int code = axis_code(P->km[1]) * 3 + axis_code(P->km[2]);
+#define FTCJ_HERM_CASE(c, n2, n3) \
+    case c: k_fold_reg_herm<n2, n3><<<g, kRegBlock, 0, s>>>(in, D0n, P->nao, T, N1, inv); break;
+    switch (code) {
+        FTCJ_HERM_CASE(0, 1, 1)
+        FTCJ_HERM_CASE(1, 1, 2)
+        FTCJ_HERM_CASE(2, 1, 4)
+        FTCJ_HERM_CASE(3, 2, 1)
+        FTCJ_HERM_CASE(4, 2, 2)
+        FTCJ_HERM_CASE(5, 2, 4)
+        FTCJ_HERM_CASE(6, 4, 1)
+        FTCJ_HERM_CASE(7, 4, 2)
+        default: k_fold_reg_herm<4, 4><<<g, kRegBlock, 0, s>>>(in, D0n, P->nao, T, N1, inv); break;
+    }
+#undef FTCJ_HERM_CASE
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }
@@ -441,6 +524,13 @@ int launch_fold(ftcj_plan* P, int ndens, const double* Dk, double* D0n, cudaStre
                                                    P->km[2], reinterpret_cast<const double2*>(P->d_tw));
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
+}
+
+// The build's fold: D^k is Hermitian by the contract, which the split form's
+// register transform uses to read and transform half of it.
+int launch_fold_build(ftcj_plan* P, int ndens, const double* Dk, double* D0n, cudaStream_t s) {
+    if (reg_fold_supported(P)) return launch_fold_herm(P, ndens, Dk, D0n, s);
+    return launch_fold(P, ndens, Dk, D0n, s);
 }
 
 int launch_unfold(ftcj_plan* P, int ndens, const double* J0n, double* Jk, cudaStream_t s) {

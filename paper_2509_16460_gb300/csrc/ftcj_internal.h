@@ -228,6 +228,7 @@ int screen_and_sort(ftcj_plan* P);  // fills pairs, walk constants, tiles
 
 // --- fold / unfold (fold.cu) ---
 int launch_fold(ftcj_plan* P, int ndens, const double* Dk, double* D0n, cudaStream_t s);
+int launch_fold_build(ftcj_plan* P, int ndens, const double* Dk, double* D0n, cudaStream_t s);  // Hermitian D^k
 int launch_unfold(ftcj_plan* P, int ndens, const double* J0n, double* Jk, cudaStream_t s);
 int launch_check_density(ftcj_plan* P, int ndens, const double* Dk, double* out2, cudaStream_t s);
 int launch_twiddles(ftcj_plan* P);
