@@ -222,8 +222,8 @@ __global__ void __launch_bounds__(kFusedT) k_unfold_fused(const double* __restri
 // ---- split-precision register transform ----------------------------------
 
 
-// The transform's sums are at most 6 additions deep (three axes of length 4),
-// so they run without renormalisation (df.cuh "_u" forms); the outputs are
+// The transform's sums are at most 9 additions deep (three axes of length 3 or
+// 4), so they run without renormalisation (df.cuh "_u" forms); the outputs are
 // rebuilt as exact double sums of both parts.
 __device__ __forceinline__ cdf cadd(cdf a, cdf b) { return cdf_add_u(a, b); }
 __device__ __forceinline__ cdf csub(cdf a, cdf b) { return cdf{df_add_u(a.re, df_neg(b.re)), df_add_u(a.im, df_neg(b.im))}; }
@@ -232,13 +232,35 @@ __device__ __forceinline__ cdf csub(cdf a, cdf b) { return cdf{df_add_u(a.re, df
 __device__ __forceinline__ cdf mul_mi(cdf v) { return cdf{v.im, df_neg(v.re)}; }
 __device__ __forceinline__ cdf mul_pi(cdf v) { return cdf{df_neg(v.im), v.re}; }
 
-// in-register DFT of v[base + m*stride], m < N (N = 1, 2, 4), in natural order
+// sqrt(3)/2 as a double-float (hi = the nearest float, lo = the nearest float to the rest)
+__device__ __forceinline__ df sqrt3_half() { return df{__uint_as_float(1063105495u), __uint_as_float(847611083u)}; }
+
+__device__ __forceinline__ cdf halve(cdf v) {
+    return cdf{{0.5f * v.re.hi, 0.5f * v.re.lo}, {0.5f * v.im.hi, 0.5f * v.im.lo}};  // exact
+}
+
+// Length-3 DFT from t1 = x1 + x2, t2 = x1 - x2: y0 = x0 + t1 and
+// y1, y2 = x0 - t1/2 -+ i (sqrt3/2) t2 (forward; the inverse swaps the signs).
+template <bool INV>
+__device__ __forceinline__ void dft3(cdf x0, cdf x1, cdf x2, cdf& y0, cdf& y1, cdf& y2) {
+    const cdf t1 = cadd(x1, x2), t2 = csub(x1, x2);
+    const df c = sqrt3_half();
+    const cdf is = mul_pi(cdf{df_mul_u(t2.re, c), df_mul_u(t2.im, c)});  // +i (sqrt3/2) t2
+    const cdf m1 = csub(x0, halve(t1));
+    y0 = cadd(x0, t1);
+    y1 = INV ? cadd(m1, is) : csub(m1, is);
+    y2 = INV ? csub(m1, is) : cadd(m1, is);
+}
+
+// in-register DFT of v[base + m*stride], m < N (N = 1, 2, 3, 4), in natural order
 template <int N, bool INV>
 __device__ __forceinline__ void dft_reg(cdf* v, int base, int stride) {
     if (N == 2) {
         const cdf x0 = v[base], x1 = v[base + stride];
         v[base] = cadd(x0, x1);
         v[base + stride] = csub(x0, x1);
+    } else if (N == 3) {
+        dft3<INV>(v[base], v[base + stride], v[base + 2 * stride], v[base], v[base + stride], v[base + 2 * stride]);
     } else if (N == 4) {
         const cdf x0 = v[base], x1 = v[base + stride], x2 = v[base + 2 * stride], x3 = v[base + 3 * stride];
         const cdf a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = csub(x1, x3);
@@ -255,11 +277,23 @@ __device__ __forceinline__ cdf shfl_xor_cdf(cdf v, int mask) {
                {__shfl_xor_sync(0xffffffffu, v.im.hi, mask), __shfl_xor_sync(0xffffffffu, v.im.lo, mask)}};
 }
 
-// Axis-1 DFT across the N1 lanes of a column group (lane j holds x_j);
-// returns the output of index out_index(j).  N1 = 2: y_j.  N1 = 4: two
-// radix-2 exchanges; lane j ends with y of the bit-reversed index.
-template <bool INV>
+__device__ __forceinline__ cdf shfl_cdf(cdf v, int src) {
+    return cdf{{__shfl_sync(0xffffffffu, v.re.hi, src), __shfl_sync(0xffffffffu, v.re.lo, src)},
+               {__shfl_sync(0xffffffffu, v.im.hi, src), __shfl_sync(0xffffffffu, v.im.lo, src)}};
+}
+
+// Axis-1 DFT across the N1 lanes of a column group (lane j of the group holds
+// x_j); returns the output of index out_index(j).  N1 = 2, 3: y_j.  N1 = 4:
+// two radix-2 exchanges; lane j ends with y of the bit-reversed index.  G3
+// (N1 = 3) is a template flag so that the other kernels carry no code for it.
+template <bool INV, bool G3>
 __device__ __forceinline__ cdf dft_lanes(cdf x, int j, int N1) {
+    if (G3) {  // N1 == 3
+        const int g0 = (int)(threadIdx.x & 31) - j;  // lane of x_0
+        cdf y[3];
+        dft3<INV>(shfl_cdf(x, g0), shfl_cdf(x, g0 + 1), shfl_cdf(x, g0 + 2), y[0], y[1], y[2]);
+        return j == 0 ? y[0] : (j == 1 ? y[1] : y[2]);
+    }
     if (N1 == 2) {
         const cdf o = shfl_xor_cdf(x, 1);
         return j == 0 ? cadd(x, o) : csub(o, x);
@@ -284,23 +318,44 @@ __device__ __forceinline__ int out_index(int j, int N1) { return N1 == 4 ? ((j &
 
 constexpr int kRegBlock = 128;
 
-// Split-form transforms for meshes whose axes are 1, 2 or 4 long (the
-// twiddles are +-1, +-i, so the transform is additions only), in complex
-// double-float on the FP32 pipe.  N1 consecutive lanes share one AO-pair
-// column of one density; lane j holds the i1 = j plane of N2 x N3 values in
-// registers, transforms it along axes 3 and 2, and the axis-1 transform runs
-// across the lanes with shuffles.  MODE 0: fold, D^{0n} = Re (1/nk) sum_k
-// exp(-i k.R_n) D^k; MODE 1: unfold, J^k = sum_n exp(+i k.R_n) J^{0n}.
-template <int MODE, int N2, int N3>
+// Lanes of a warp form 32 / N1 groups of N1 (lanes 30, 31 idle when N1 = 3);
+// group g of warp w of block b owns column (b * 4 + w) * (32 / N1) + g.
+struct LaneGroup {
+    long long col;
+    int j;
+    bool live;
+};
+
+__device__ __forceinline__ LaneGroup lane_group(int N1) {
+    const int lane = threadIdx.x & 31, cpw = 32 / N1;
+    const int g = lane / N1;
+    LaneGroup r;
+    r.j = lane - g * N1;
+    r.live = g < cpw;
+    r.col = ((long long)blockIdx.x * (kRegBlock / 32) + (threadIdx.x >> 5)) * cpw + g;
+    return r;
+}
+
+inline unsigned reg_blocks(long long ncol, int N1) { return nblocks(ncol, (kRegBlock / 32) * (32 / N1)); }
+
+// Split-form transforms for meshes whose axes are 1, 2, 3 or 4 long (the
+// twiddles are +-1, +-i and -1/2 +- i sqrt3/2), in complex double-float on
+// the FP32 pipe.  N1 lanes share one AO-pair column of one density; lane j
+// holds the i1 = j plane of N2 x N3 values in registers, transforms it along
+// axes 3 and 2, and the axis-1 transform runs across the lanes with shuffles.
+// MODE 0: fold, D^{0n} = Re (1/nk) sum_k exp(-i k.R_n) D^k; MODE 1: unfold,
+// J^k = sum_n exp(+i k.R_n) J^{0n}.
+template <int MODE, int N2, int N3, bool G3>
 __global__ void __launch_bounds__(kRegBlock) k_fold_reg(const void* __restrict__ in, void* __restrict__ out,
                                                         long long E, int N1, df inv_nk) {
     constexpr int P = N2 * N3;
     constexpr bool INV = MODE == 1;
-    const int j = threadIdx.x % N1;
-    const long long e = (long long)blockIdx.x * (kRegBlock / N1) + threadIdx.x / N1;
+    const LaneGroup lg = lane_group(N1);
+    const int j = lg.j;
+    const long long e = lg.col;
     const long long d = blockIdx.y;
     const int nk = N1 * P;
-    const bool valid = e < E;
+    const bool valid = lg.live && e < E;
     cdf v[P];
 #pragma unroll
     for (int q = 0; q < P; ++q) {
@@ -318,7 +373,7 @@ __global__ void __launch_bounds__(kRegBlock) k_fold_reg(const void* __restrict__
 #pragma unroll
     for (int i3 = 0; i3 < N3; ++i3) dft_reg<N2, INV>(v, i3, N3);
 #pragma unroll
-    for (int q = 0; q < P; ++q) v[q] = dft_lanes<INV>(v[q], j, N1);
+    for (int q = 0; q < P; ++q) v[q] = dft_lanes<INV, G3>(v[q], j, N1);
     if (!valid) return;
     const long long base = (d * nk + (long long)out_index(j, N1) * P) * E + e;
 #pragma unroll
@@ -347,17 +402,18 @@ __device__ __forceinline__ void tri_index(long long t, int n, int& mu, int& nu) 
 // The fold of a Hermitian D^k (D^k_{nu mu} = conj D^k_{mu nu}): then
 // D^{0n}_{nu mu} = D^{0,-n}_{mu nu}, so only the upper triangle mu <= nu is read
 // and transformed, and each result is also written, transposed, at cell -n.
-// Same arithmetic and lane layout as k_fold_reg<0, N2, N3>.
-template <int N2, int N3>
+// Same arithmetic and lane layout as k_fold_reg<0, N2, N3, G3>.
+template <int N2, int N3, bool G3>
 __global__ void __launch_bounds__(kRegBlock) k_fold_reg_herm(const double2* __restrict__ in, double* __restrict__ out,
                                                              int nao, long long T, int N1, df inv_nk) {
     constexpr int P = N2 * N3;
-    const int j = threadIdx.x % N1;
-    const long long t = (long long)blockIdx.x * (kRegBlock / N1) + threadIdx.x / N1;
+    const LaneGroup lg = lane_group(N1);
+    const int j = lg.j;
+    const long long t = lg.col;
     const long long d = blockIdx.y;
     const int nk = N1 * P;
     const long long E = (long long)nao * nao;
-    const bool valid = t < T;
+    const bool valid = lg.live && t < T;
     int mu = 0, nu = 0;
     if (valid) tri_index(t, nao, mu, nu);
     const long long e = (long long)mu * nao + nu;
@@ -372,7 +428,7 @@ __global__ void __launch_bounds__(kRegBlock) k_fold_reg_herm(const double2* __re
 #pragma unroll
     for (int i3 = 0; i3 < N3; ++i3) dft_reg<N2, false>(v, i3, N3);
 #pragma unroll
-    for (int q = 0; q < P; ++q) v[q] = dft_lanes<false>(v[q], j, N1);
+    for (int q = 0; q < P; ++q) v[q] = dft_lanes<false, G3>(v[q], j, N1);
     if (!valid) return;
     const int o1 = out_index(j, N1), m1 = (N1 - o1) % N1;
     const long long et = (long long)nu * nao + mu;
@@ -388,29 +444,68 @@ __global__ void __launch_bounds__(kRegBlock) k_fold_reg_herm(const double2* __re
     }
 }
 
-int axis_code(int n) { return n == 1 ? 0 : (n == 2 ? 1 : (n == 4 ? 2 : -1)); }
+int axis_code(int n) { return n >= 1 && n <= 4 ? n - 1 : -1; }
+
+// runs f.template run<N2, N3>() for the plan's (N2, N3), both in 1..4
+template <class F>
+void by_plane(const ftcj_plan* P, const F& f) {
+    switch (axis_code(P->km[1]) * 4 + axis_code(P->km[2])) {
+        case 0: f.template run<1, 1>(); break;
+        case 1: f.template run<1, 2>(); break;
+        case 2: f.template run<1, 3>(); break;
+        case 3: f.template run<1, 4>(); break;
+        case 4: f.template run<2, 1>(); break;
+        case 5: f.template run<2, 2>(); break;
+        case 6: f.template run<2, 3>(); break;
+        case 7: f.template run<2, 4>(); break;
+        case 8: f.template run<3, 1>(); break;
+        case 9: f.template run<3, 2>(); break;
+        case 10: f.template run<3, 3>(); break;
+        case 11: f.template run<3, 4>(); break;
+        case 12: f.template run<4, 1>(); break;
+        case 13: f.template run<4, 2>(); break;
+        case 14: f.template run<4, 3>(); break;
+        default: f.template run<4, 4>(); break;
+    }
+}
+
+template <int MODE>
+struct RegLaunch {
+    dim3 g;
+    cudaStream_t s;
+    const void* in;
+    void* out;
+    long long E;
+    int N1;
+    df inv;
+    template <int N2, int N3>
+    void run() const {
+        if (N1 == 3) k_fold_reg<MODE, N2, N3, true><<<g, kRegBlock, 0, s>>>(in, out, E, N1, inv);
+        else k_fold_reg<MODE, N2, N3, false><<<g, kRegBlock, 0, s>>>(in, out, E, N1, inv);
+    }
+};
+
+struct HermLaunch {
+    dim3 g;
+    cudaStream_t s;
+    const double2* in;
+    double* out;
+    int nao;
+    long long T;
+    int N1;
+    df inv;
+    template <int N2, int N3>
+    void run() const {
+        if (N1 == 3) k_fold_reg_herm<N2, N3, true><<<g, kRegBlock, 0, s>>>(in, out, nao, T, N1, inv);
+        else k_fold_reg_herm<N2, N3, false><<<g, kRegBlock, 0, s>>>(in, out, nao, T, N1, inv);
+    }
+};
 
 template <int MODE>
 int launch_fold_reg(const ftcj_plan* P, int ndens, const void* in, void* out, cudaStream_t s) {
     const long long E = (long long)P->nao * P->nao;
     const int N1 = P->km[0];
-    dim3 g(nblocks(E * N1, kRegBlock), ndens);
-    const df inv = df_from_double(1.0 / P->nk);
-    const int code = axis_code(P->km[1]) * 3 + axis_code(P->km[2]);
-#define FTCJ_REG_CASE(c, n2, n3) \
-    case c: k_fold_reg<MODE, n2, n3><<<g, kRegBlock, 0, s>>>(in, out, E, N1, inv); break;
-    switch (code) {
-        FTCJ_REG_CASE(0, 1, 1)
-        FTCJ_REG_CASE(1, 1, 2)
-        FTCJ_REG_CASE(2, 1, 4)
-        FTCJ_REG_CASE(3, 2, 1)
-        FTCJ_REG_CASE(4, 2, 2)
-        FTCJ_REG_CASE(5, 2, 4)
-        FTCJ_REG_CASE(6, 4, 1)
-        FTCJ_REG_CASE(7, 4, 2)
-        default: k_fold_reg<MODE, 4, 4><<<g, kRegBlock, 0, s>>>(in, out, E, N1, inv); break;
-    }
-#undef FTCJ_REG_CASE
+    by_plane(P, RegLaunch<MODE>{dim3(reg_blocks(E, N1), ndens), s, in, out, E, N1, df_from_double(1.0 / P->nk)});
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }
@@ -418,29 +513,13 @@ int launch_fold_reg(const ftcj_plan* P, int ndens, const void* in, void* out, cu
 int launch_fold_herm(const ftcj_plan* P, int ndens, const double* Dk, double* D0n, cudaStream_t s) {
     const long long T = (long long)P->nao * (P->nao + 1) / 2;
     const int N1 = P->km[0];
-    dim3 g(nblocks(T * N1, kRegBlock), ndens);
-    const df inv = df_from_double(1.0 / P->nk);
-    const double2* in = reinterpret_cast<const double2*>(Dk);
-    const int code = axis_code(P->km[1]) * 3 + axis_code(P->km[2]);
-#define FTCJ_HERM_CASE(c, n2, n3) \
-    case c: k_fold_reg_herm<n2, n3><<<g, kRegBlock, 0, s>>>(in, D0n, P->nao, T, N1, inv); break;
-    switch (code) {
-        FTCJ_HERM_CASE(0, 1, 1)
-        FTCJ_HERM_CASE(1, 1, 2)
-        FTCJ_HERM_CASE(2, 1, 4)
-        FTCJ_HERM_CASE(3, 2, 1)
-        FTCJ_HERM_CASE(4, 2, 2)
-        FTCJ_HERM_CASE(5, 2, 4)
-        FTCJ_HERM_CASE(6, 4, 1)
-        FTCJ_HERM_CASE(7, 4, 2)
-        default: k_fold_reg_herm<4, 4><<<g, kRegBlock, 0, s>>>(in, D0n, P->nao, T, N1, inv); break;
-    }
-#undef FTCJ_HERM_CASE
+    by_plane(P, HermLaunch{dim3(reg_blocks(T, N1), ndens), s, reinterpret_cast<const double2*>(Dk), D0n, P->nao, T,
+                           N1, df_from_double(1.0 / P->nk)});
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }
 
-// the split form's register transform covers meshes with every axis 1, 2 or 4 long
+// the split form's register transform covers meshes with every axis 1 to 4 long
 bool reg_fold_supported(const ftcj_plan* P) {
     return P->precision == FTCJ_PREC_SPLIT && P->nk > 1 && axis_code(P->km[0]) >= 0 && axis_code(P->km[1]) >= 0 &&
            axis_code(P->km[2]) >= 0;

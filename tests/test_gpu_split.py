@@ -99,10 +99,10 @@ def test_split_cfg3_against_fp64_form(F):
     assert dJ <= SPLIT_J_TOL and dE <= SPLIT_E_TOL
 
 
-@pytest.mark.parametrize("kmesh", [(2, 3, 1), (4, 2, 1), (3, 3, 1), (4, 4, 4)])
+@pytest.mark.parametrize("kmesh", [(2, 3, 1), (4, 2, 1), (3, 3, 1), (4, 4, 4), (3, 2, 3), (1, 3, 4), (3, 3, 3)])
 def test_split_fold_and_unfold_steps(orc, F, kmesh):
-    """The double-float k <-> BvK transforms of the split form (radix-2/4 and
-    direct lengths) against the FP64 definitions, on inputs whose magnitudes
+    """The double-float k <-> BvK transforms of the split form (axes of length
+    1 to 4, lane groups of 2, 3 and 4) against the FP64 definitions, on inputs whose magnitudes
     span 1e-40 .. 1e3 (zeros and signs included), so that the exponent and
     mantissa splitting of doubles is exercised across the range."""
     import torch
