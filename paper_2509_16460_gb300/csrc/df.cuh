@@ -168,6 +168,8 @@ __device__ __forceinline__ cdf cdf_mul_u(cdf a, cdf b) {
 
 __device__ __forceinline__ cdf cdf_add_u(cdf a, cdf b) { return cdf{df_add_u(a.re, b.re), df_add_u(a.im, b.im)}; }
 
+__device__ __forceinline__ cdf cdf_scale_u(cdf a, df s) { return cdf{df_mul_u(a.re, s), df_mul_u(a.im, s)}; }
+
 __device__ __forceinline__ cdf cdf_norm(cdf a) { return cdf{df_norm(a.re), df_norm(a.im)}; }
 
 // ---- conversions that keep off the FP64 pipe ----------------------------

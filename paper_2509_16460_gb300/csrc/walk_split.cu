@@ -133,7 +133,9 @@ __device__ __forceinline__ SState idle_state() {
 
 // One transition of the walk program.  With ORTHO (the per-record X(n1)
 // table serves every line) the n1 ratios RfL, RbL, rF0c, rB0c are not used
-// and not advanced.
+// and not advanced.  Line steps inside a plane use the deferred-renormalisation
+// products (at most one plane's lines deep); plane steps keep the plane values
+// renormalised, and every plane restarts the line values from them.
 template <bool ORTHO>
 __device__ __forceinline__ void split_step(const SConst& k, int op, SState& s, const SState* init_p, bool valid) {
     switch (op) {
@@ -141,27 +143,27 @@ __device__ __forceinline__ void split_step(const SConst& k, int op, SState& s, c
             s = valid ? *init_p : idle_state();
             break;
         case OP_N2F:
-            s.gpL = cdf_mul(s.gpL, s.Sd);
-            s.Sd = cdf_scale(s.Sd, k.q2);
+            s.gpL = cdf_mul_u(s.gpL, s.Sd);
+            s.Sd = cdf_scale_u(s.Sd, k.q2);
             if (!ORTHO) {
-                s.RfL = cdf_scale(s.RfL, k.x12);
-                s.RbL = cdf_scale(s.RbL, k.y12);
+                s.RfL = cdf_scale_u(s.RfL, k.x12);
+                s.RbL = cdf_scale_u(s.RbL, k.y12);
             }
             break;
         case OP_NEGSTART:
-            s.gpL = cdf_mul(s.gpC, s.RB0c);
-            s.Sd = cdf_scale(s.RB0c, k.q2);
+            s.gpL = cdf_mul_u(s.gpC, s.RB0c);
+            s.Sd = cdf_scale_u(s.RB0c, k.q2);
             if (!ORTHO) {
-                s.RfL = cdf_scale(s.rF0c, k.y12);
-                s.RbL = cdf_scale(s.rB0c, k.x12);
+                s.RfL = cdf_scale_u(s.rF0c, k.y12);
+                s.RbL = cdf_scale_u(s.rB0c, k.x12);
             }
             break;
         case OP_N2B:
-            s.gpL = cdf_mul(s.gpL, s.Sd);
-            s.Sd = cdf_scale(s.Sd, k.q2);
+            s.gpL = cdf_mul_u(s.gpL, s.Sd);
+            s.Sd = cdf_scale_u(s.Sd, k.q2);
             if (!ORTHO) {
-                s.RfL = cdf_scale(s.RfL, k.y12);
-                s.RbL = cdf_scale(s.RbL, k.x12);
+                s.RfL = cdf_scale_u(s.RfL, k.y12);
+                s.RbL = cdf_scale_u(s.RbL, k.x12);
             }
             break;
         default:  // OP_N3
@@ -397,7 +399,7 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
         if (ORTHO) {
             // the line value gp(0) goes into the coefficients; X(n1) carries the rest
 #pragma unroll
-            for (int i = 0; i <= L; ++i) c[i] = cdf_mul(s.gpL, c[i]);
+            for (int i = 0; i <= L; ++i) c[i] = cdf_mul_u(s.gpL, c[i]);
         }
         // not unrolled: the walk's instruction footprint (five classes) stays in the instruction cache
 #pragma unroll 1
@@ -419,8 +421,8 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
                 m1 = lo;
                 step = -1;
                 if (!ORTHO) {
-                    gp = cdf_mul(s.gpL, s.RbL);
-                    R = cdf_scale(s.RbL, k.q1);
+                    gp = cdf_mul_u(s.gpL, s.RbL);
+                    R = cdf_scale_u(s.RbL, k.q1);
                 }
             }
             if (ORTHO) {
@@ -451,8 +453,8 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
                 }
                 if (m == m1) break;
                 if (!ORTHO) {
-                    gp = cdf_mul(gp, R);
-                    R = cdf_scale(R, k.q1);
+                    gp = cdf_mul_u(gp, R);
+                    R = cdf_scale_u(R, k.q1);
                 }
             }
         }
@@ -564,8 +566,8 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
                 m1 = lo;
                 step = -1;
                 if (!ORTHO) {
-                    gp = cdf_mul(s.gpL, s.RbL);
-                    R = cdf_scale(s.RbL, k.q1);
+                    gp = cdf_mul_u(s.gpL, s.RbL);
+                    R = cdf_scale_u(s.RbL, k.q1);
                 }
             }
             if (ORTHO) {
@@ -592,17 +594,15 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
                 }
                 if (m == m1) break;
                 if (!ORTHO) {
-                    gp = cdf_mul(gp, R);
-                    R = cdf_scale(R, k.q1);
+                    gp = cdf_mul_u(gp, R);
+                    R = cdf_scale_u(R, k.q1);
                 }
             }
             qs = q;
         }
-#pragma unroll
-        for (int i = 0; i <= L; ++i) A[i] = cdf_norm(A[i]);
         if (ORTHO) {
 #pragma unroll
-            for (int i = 0; i <= L; ++i) A[i] = cdf_mul(s.gpL, A[i]);
+            for (int i = 0; i <= L; ++i) A[i] = cdf_mul_u(s.gpL, A[i]);
         }
         float pq[L + 1][L + 1];
         powers23f<L>(ln.n2, ln.n3, pq);
