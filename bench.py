@@ -398,7 +398,11 @@ def main():
                        "e2e": {"value": whole_job_rate(world, units, e2e_s), "unit": UNIT,
                                "ms_per_step": e2e_s * 1e3,
                                "h2d_bytes_per_step": Dk_h.numel() * 16,
-                               "d2h_bytes_per_step": Jk_h.numel() * 16 + EJ_h.numel() * 8},
+                               "d2h_bytes_per_step": Jk_h.numel() * 16 + EJ_h.numel() * 8,
+                               "transfer": "pinned host buffers read and written by the device over the host link; "
+                                           + ("the split form's fold reads only the upper triangle of the "
+                                              "Hermitian D^k" if pipe_form == "split" else
+                                              "the whole D^k is read")},
                        "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks,
                        "wall_s_timed_region": t_wall,
                        "walk_shape": {"rho_blocks": info["rho_blocks"], "n1_table": info["n1_table"],
