@@ -166,6 +166,9 @@ struct ftcj_plan {
     int* d_sched = nullptr;
     std::vector<int> rho_sched;  // rho pass: npb+1 offsets, then tile ids grouped by block
     float* d_rec_gcut = nullptr;     // per-record G cutoff (pair_gcut_eps > 0)
+    int ntiles_hi = 0;               // leading tiles of classes 3-4 (split J walk launches them apart)
+    cudaStream_t aux = nullptr;      // second stream of the split J walk (fork/join by events)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t units_screened = 0, units_walked = 0;
     std::vector<int64_t> tile_npts;  // half-sphere points inside each tile's radius (cutoffs on)
     int* d_gvec = nullptr;
@@ -268,5 +271,6 @@ int launch_j_walk_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s
 // --- measurement (profile.cu) ---
 void release_profiling(ftcj_plan* P);
 int64_t launches_per_batch(const ftcj_plan* P);
+int split_j_launches(const ftcj_plan* P);  // kernel launches of one split J walk (1 or 2)
 
 }  // namespace ftcj

@@ -286,6 +286,9 @@ void free_device(ftcj_plan* P) {
                     P->d_maps, P->d_map_off, P->d_sched, P->d_rec_gcut};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+    if (P->ev_join) cudaEventDestroy(P->ev_join);
+    if (P->aux) cudaStreamDestroy(P->aux);
 }
 
 int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], const ftcj_params* prm,

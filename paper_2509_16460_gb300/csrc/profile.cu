@@ -24,7 +24,7 @@ int64_t launches_per_batch(const ftcj_plan* P) {
     n += P->npairs > 0 ? 1 : 0;                        // a3
     n += (P->ng_half > 0 && !P->tiles.empty()) ? 1 : 0;  // a4
     n += P->ng_half > 0 ? 2 : 0;                       // a5: reduce + energy
-    n += (P->ng_half > 0 && !P->tiles.empty()) ? 1 : 0;  // a6
+    n += (P->ng_half > 0 && !P->tiles.empty()) ? (P->precision == FTCJ_PREC_SPLIT ? split_j_launches(P) : 1) : 0;  // a6
     n += P->npairs > 0 ? 1 : 0;                        // a7
     n += fold;                                         // a8
     return n;

@@ -636,21 +636,24 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
     }
 }
 
-template <bool ORTHO, bool CUT>
-__global__ void __launch_bounds__(kTile, 3) k_j_walk_split(const Tile* __restrict__ tiles, Layout lay,
-                                                        const SConst* __restrict__ cst,
-                                                        const SState* __restrict__ init, long long npairs,
-                                                        const WLine* __restrict__ lines,
-                                                        const WChunk* __restrict__ chunks, int nchunks,
-                                                        const double2* __restrict__ W, long long ng_half, int nx,
-                                                        int max_chunk_pts, double* __restrict__ Jp) {
+// The back-contraction walk.  PART 0: tiles of every class; PART 1: classes
+// 0-2 only (a 10-term J' slice, sized for four blocks per SM); PART 2: classes
+// 3-4.  Parts 1 and 2 run as two launches side by side where the shared
+// memory of the one-kernel walk (a long chunk's W beside a 35-term J' slice)
+// would hold it below three blocks per SM.
+template <bool ORTHO, bool CUT, int PART>
+__global__ void __launch_bounds__(kTile, PART == 1 ? 4 : 3) k_j_walk_split(
+    const Tile* __restrict__ tiles, int tile0, Layout lay, const SConst* __restrict__ cst,
+    const SState* __restrict__ init, long long npairs, const WLine* __restrict__ lines,
+    const WChunk* __restrict__ chunks, int nchunks, const double2* __restrict__ W, long long ng_half, int nx,
+    int max_chunk_pts, double* __restrict__ Jp) {
     extern __shared__ float4 ssm[];
-    const int tix = blockIdx.x, cidx = blockIdx.y, d = blockIdx.z;
+    const int tix = tile0 + blockIdx.x, cidx = blockIdx.y, d = blockIdx.z;
     const WChunk ch = chunks[cidx];
     const int npts = ch.p1 - ch.p0;
     float4* wsm = ssm;
     float2* Jsm = reinterpret_cast<float2*>(ssm + max_chunk_pts);
-    float4* Xs = reinterpret_cast<float4*>(Jsm + kMaxTerms * kTile);
+    float4* Xs = reinterpret_cast<float4*>(Jsm + nterms(PART == 1 ? 2 : 4) * kTile);
     const double2* Wd = W + (long long)d * ng_half + ch.p0;
     for (int i = threadIdx.x; i < npts; i += blockDim.x) {
         const double2 v = Wd[i];
@@ -661,12 +664,23 @@ __global__ void __launch_bounds__(kTile, 3) k_j_walk_split(const Tile* __restric
     const Tile tl = tiles[tix];
     double* Jp_dc = Jp + ((long long)d * nchunks + cidx) * lay.total;
     const SState* init_c = init + (long long)cidx * npairs;
-    switch (tl.cls) {
-        case 0: j_tile_split<0, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
-        case 1: j_tile_split<1, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
-        case 2: j_tile_split<2, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
-        case 3: j_tile_split<3, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
-        default: j_tile_split<4, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+    if (PART == 1) {
+        switch (tl.cls) {
+            case 0: j_tile_split<0, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+            case 1: j_tile_split<1, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+            default: j_tile_split<2, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+        }
+    } else if (PART == 2) {
+        if (tl.cls == 3) j_tile_split<3, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx);
+        else j_tile_split<4, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx);
+    } else {
+        switch (tl.cls) {
+            case 0: j_tile_split<0, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+            case 1: j_tile_split<1, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+            case 2: j_tile_split<2, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+            case 3: j_tile_split<3, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+            default: j_tile_split<4, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+        }
     }
 }
 
@@ -693,14 +707,15 @@ size_t rho_smem(const ftcj_plan* P) {
            sizeof(float2) * (size_t)kMaxTerms * kTile + xtab_bytes(P);
 }
 
-size_t j_smem(const ftcj_plan* P) {
-    return sizeof(float4) * (size_t)std::max(P->max_chunk_pts, 1) + sizeof(float2) * (size_t)kMaxTerms * kTile +
+size_t j_smem(const ftcj_plan* P, int part) {
+    const int hi = part == 1 ? 2 : 4;
+    return sizeof(float4) * (size_t)std::max(P->max_chunk_pts, 1) + sizeof(float2) * (size_t)nterms(hi) * kTile +
            xtab_bytes(P);
 }
 
 // the walk kernels for the plan's shape: X(n1) table or recurrence, with or without per-pair cutoffs
 using RhoKernel = decltype(&k_rho_walk_split<true, true>);
-using JKernel = decltype(&k_j_walk_split<true, true>);
+using JKernel = decltype(&k_j_walk_split<true, true, 0>);
 
 RhoKernel rho_kernel(const ftcj_plan* P) {
     const bool c = P->d_rec_gcut != nullptr;
@@ -708,10 +723,15 @@ RhoKernel rho_kernel(const ftcj_plan* P) {
     return c ? k_rho_walk_split<false, true> : k_rho_walk_split<false, false>;
 }
 
-JKernel j_kernel(const ftcj_plan* P) {
+template <int PART>
+JKernel j_kernel_part(const ftcj_plan* P) {
     const bool c = P->d_rec_gcut != nullptr;
-    if (use_xtab(P)) return c ? k_j_walk_split<true, true> : k_j_walk_split<true, false>;
-    return c ? k_j_walk_split<false, true> : k_j_walk_split<false, false>;
+    if (use_xtab(P)) return c ? k_j_walk_split<true, true, PART> : k_j_walk_split<true, false, PART>;
+    return c ? k_j_walk_split<false, true, PART> : k_j_walk_split<false, false, PART>;
+}
+
+JKernel j_kernel(const ftcj_plan* P, int part) {
+    return part == 1 ? j_kernel_part<1>(P) : (part == 2 ? j_kernel_part<2>(P) : j_kernel_part<0>(P));
 }
 
 }  // namespace
@@ -736,7 +756,25 @@ int setup_split(ftcj_plan* P) {
     }
     int rc = allow_dynamic_smem((const void*)rho_kernel(P), rho_smem(P));
     if (rc) return rc;
-    return allow_dynamic_smem((const void*)j_kernel(P), j_smem(P));
+    for (int part = 0; part < 3 && !rc; ++part) rc = allow_dynamic_smem((const void*)j_kernel(P, part), j_smem(P, part));
+    if (rc) return rc;
+    // split the walk by class only where shared memory holds the one-kernel walk below three blocks per SM
+    int dev = 0, per_sm = 0;
+    FTCJ_CUDA(cudaGetDevice(&dev));
+    FTCJ_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    int nhi = 0;  // tiles are ordered by decreasing class: classes 3-4 lead
+    while (nhi < (int)P->tiles.size() && P->tiles[nhi].cls >= 3) ++nhi;
+    const bool smem_bound = (size_t)per_sm / (j_smem(P, 0) + 1024) < 3;
+    P->ntiles_hi = smem_bound && nhi > 0 && nhi < (int)P->tiles.size() ? nhi : 0;
+    if (!P->aux) {
+        // the heavy classes' stream has the highest priority, so that their blocks take SM slots first
+        int lo_prio = 0, hi_prio = 0;
+        FTCJ_CUDA(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+        FTCJ_CUDA(cudaStreamCreateWithPriority(&P->aux, cudaStreamNonBlocking, hi_prio));
+        FTCJ_CUDA(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+        FTCJ_CUDA(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+    }
+    return FTCJ_OK;
 }
 
 int rho_walk_split_blocks_per_sm(ftcj_plan* P, int* out) {
@@ -764,6 +802,8 @@ int launch_rho_walk_split(ftcj_plan* P, int ndens, cudaStream_t s) {
     return FTCJ_OK;
 }
 
+int split_j_launches(const ftcj_plan* P) { return P->ntiles_hi > 0 ? 2 : 1; }
+
 int launch_j_walk_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s) {
     const int nch = (int)P->chunks.size();
     if (P->tiles.empty()) return FTCJ_OK;
@@ -771,15 +811,28 @@ int launch_j_walk_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s
         FTCJ_CUDA(cudaMemsetAsync(P->d_Jp, 0, sizeof(double) * (size_t)ndens * std::max(nch, 1) * P->total_terms, s));
         return FTCJ_OK;
     }
-    dim3 g((unsigned)P->tiles.size(), nch, ndens);
     const int nx = use_xtab(P) ? xtab_entries(P) : 0;
-    auto* kern = j_kernel(P);
-    kern<<<g, kTile, j_smem(P), s>>>(P->d_tiles, make_layout(P),
-                                               reinterpret_cast<const SConst*>(P->d_split_const),
-                                               reinterpret_cast<const SState*>(P->d_split_init), P->npairs,
-                                               P->d_lines, P->d_chunks, nch, reinterpret_cast<const double2*>(W),
-                                               P->ng_half, nx, P->max_chunk_pts, P->d_Jp);
-    FTCJ_CUDA(cudaGetLastError());
+    const int nhi = P->ntiles_hi, nlo = (int)P->tiles.size() - nhi;
+    auto go = [&](int part, int tile0, int ntiles, cudaStream_t st) {
+        j_kernel(P, part)<<<dim3((unsigned)ntiles, nch, ndens), kTile, j_smem(P, part), st>>>(
+            P->d_tiles, tile0, make_layout(P), reinterpret_cast<const SConst*>(P->d_split_const),
+            reinterpret_cast<const SState*>(P->d_split_init), P->npairs, P->d_lines, P->d_chunks, nch,
+            reinterpret_cast<const double2*>(W), P->ng_half, nx, P->max_chunk_pts, P->d_Jp);
+    };
+    if (nhi > 0 && nlo > 0) {
+        // classes 3-4 on the plan's second stream, beside classes 0-2 on the caller's (event fork and join)
+        FTCJ_CUDA(cudaEventRecord(P->ev_fork, s));
+        FTCJ_CUDA(cudaStreamWaitEvent(P->aux, P->ev_fork, 0));
+        go(2, 0, nhi, P->aux);
+        FTCJ_CUDA(cudaGetLastError());
+        go(1, nhi, nlo, s);
+        FTCJ_CUDA(cudaGetLastError());
+        FTCJ_CUDA(cudaEventRecord(P->ev_join, P->aux));
+        FTCJ_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));
+    } else {
+        go(0, 0, (int)P->tiles.size(), s);
+        FTCJ_CUDA(cudaGetLastError());
+    }
     return FTCJ_OK;
 }
 
