@@ -167,6 +167,7 @@ struct ftcj_plan {
     std::vector<int> rho_sched;  // rho pass: npb+1 offsets, then tile ids grouped by block
     float* d_rec_gcut = nullptr;     // per-record G cutoff (pair_gcut_eps > 0)
     int ntiles_hi = 0;               // leading tiles of classes 3-4 (split J walk launches them apart)
+    int rho_hi_tiles = 0, npb_hi = 0;  // the same for the split rho walk, and the blocks of its first launch
     cudaStream_t aux = nullptr;      // second stream of the split J walk (fork/join by events)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int64_t units_screened = 0, units_walked = 0;
@@ -261,10 +262,10 @@ int rho_walk_blocks_per_sm(ftcj_plan* P, int* out);
 // --- split-precision walks (walk_split.cu) ---
 int setup_split(ftcj_plan* P);
 int split_xtab_entries(const ftcj_plan* P);  // 0 when the split walks run the n1 recurrence
-size_t split_rho_smem(const ftcj_plan* P);  // shared memory of one split structure-factor block
+size_t split_rho_smem(const ftcj_plan* P, int part);  // shared memory of one split structure-factor block (part: 0 all classes, 1 classes 0-2)
 int launch_pair_gcut(ftcj_plan* P);      // per-record cutoffs from the (double) maps, in build_maps
 int apply_pair_cutoffs(ftcj_plan* P);    // sort records by cutoff within each class, radius per tile
-int rho_walk_split_blocks_per_sm(ftcj_plan* P, int* out);
+int rho_walk_split_blocks_per_sm(ftcj_plan* P, int part, int* out);  // part: 0 all, 1 classes 0-2, 2 classes 3-4
 int launch_rho_walk_split(ftcj_plan* P, int ndens, cudaStream_t s);
 int launch_j_walk_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s);
 

@@ -187,22 +187,29 @@ int build_walk(ftcj_plan* P) {
 // Default walk chunk of the split form: the structure-factor block keeps one
 // chunk's rho row (16 B per point) in shared memory beside chunk-independent
 // staging, so the chunk sets its occupancy.  Take the largest power of two
-// (<= 4096 points) that lets three blocks share an SM, or else two, with at
-// least 1024 resp. 512 points; the walk program is rebuilt for it.
+// (<= 4096 points) that lets three blocks of the one-kernel walk share an SM
+// with at least 1024 points; else three blocks of its classes 0-2 part (the
+// walk then runs in two launches by class) with at least 512; else two blocks
+// of the one-kernel walk.  The walk program is rebuilt for it.
 int default_split_chunk(ftcj_plan* P) {
     int dev = 0, per_sm = 0;
     FTCJ_CUDA(cudaGetDevice(&dev));
     FTCJ_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
     const int keep = P->max_chunk_pts;
     P->max_chunk_pts = 0;
-    const size_t fixed = split_rho_smem(P);
+    const size_t fixed_all = split_rho_smem(P, 0), fixed_low = split_rho_smem(P, 1);
     P->max_chunk_pts = keep;
+    struct Try {
+        int blocks;
+        size_t fixed;
+        long long need;
+    };
+    const Try tries[] = {{3, fixed_all, 1024}, {3, fixed_low, 512}, {2, fixed_all, 512}, {1, fixed_all, 64}};
     int chunk = 256;
-    for (int target = 3; target >= 1; --target) {
-        const long long room = (long long)per_sm / target - 1024 - (long long)fixed;
+    for (const Try& t : tries) {
+        const long long room = (long long)per_sm / t.blocks - 1024 - (long long)t.fixed;
         const long long pts = room / 16;
-        const long long need = target == 3 ? 1024 : (target == 2 ? 512 : 0);
-        if (pts >= need && pts >= 64) {
+        if (pts >= t.need && pts >= 64) {
             chunk = 64;
             while (chunk * 2 <= std::min<long long>(pts, kChunkMax)) chunk *= 2;
             break;
@@ -241,6 +248,9 @@ int upload(ftcj_plan* P, T** ptr, const std::vector<T>& v) {
 // walks every point of the chunk, so its cost is set by its class L: per point
 // the split form spends about 38L + 100 FP32 operations (polynomial, phase
 // product, batch reduction), the FP64 form about 4L + 24 FP64 operations.
+// With the split walk in two launches (rho_hi_tiles > 0) the leading tiles of
+// classes 3-4 go to blocks [0, npb_hi) and the rest to [npb_hi, npb), each
+// group by its own assignment.
 int build_rho_schedule(ftcj_plan* P) {
     const int nt = (int)P->tiles.size(), nb = std::max(1, P->npb);
     auto cost = [&](int t) {
@@ -248,18 +258,26 @@ int build_rho_schedule(ftcj_plan* P) {
         const double pts = P->tile_npts.empty() ? 1.0 : (double)P->tile_npts[t] + 1.0;  // radius-limited tiles
         return (P->precision == FTCJ_PREC_SPLIT ? 38.0 * L + 100.0 : 4.0 * L + 24.0) * pts;
     };
-    std::vector<int> order(nt);
-    for (int t = 0; t < nt; ++t) order[t] = t;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
-    using Slot = std::pair<double, int>;  // (load, block): ties go to the lower block
-    std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
-    for (int b = 0; b < nb; ++b) heap.push({0.0, b});
     std::vector<std::vector<int>> lists(nb);
-    for (int t : order) {
-        Slot s = heap.top();
-        heap.pop();
-        lists[s.second].push_back(t);
-        heap.push({s.first + cost(t), s.second});
+    auto assign = [&](int t0, int t1, int b0, int b1) {
+        std::vector<int> order;
+        for (int t = t0; t < t1; ++t) order.push_back(t);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+        using Slot = std::pair<double, int>;  // (load, block): ties go to the lower block
+        std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+        for (int b = b0; b < b1; ++b) heap.push({0.0, b});
+        for (int t : order) {
+            Slot s = heap.top();
+            heap.pop();
+            lists[s.second].push_back(t);
+            heap.push({s.first + cost(t), s.second});
+        }
+    };
+    if (P->rho_hi_tiles > 0) {
+        assign(0, P->rho_hi_tiles, 0, P->npb_hi);
+        assign(P->rho_hi_tiles, nt, P->npb_hi, nb);
+    } else {
+        assign(0, nt, 0, nb);
     }
     std::vector<int> sched;
     sched.reserve((size_t)nb + 1 + nt);
@@ -471,13 +489,25 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     if (P->precision == FTCJ_PREC_SPLIT && (rc = setup_split(P))) return rc;
     int bps = 1;
     if (P->precision == FTCJ_PREC_SPLIT) {
-        if ((rc = rho_walk_split_blocks_per_sm(P, &bps))) return rc;
+        if ((rc = rho_walk_split_blocks_per_sm(P, 0, &bps))) return rc;
     } else {
         if ((rc = rho_walk_blocks_per_sm(P, &bps))) return rc;
     }
     int nch = std::max<int>(1, (int)P->chunks.size());
     P->npb = std::max(1, std::min<int>((int)std::max<size_t>(1, P->tiles.size()), P->num_sms * bps / nch));
-    if (prm->rho_blocks > 0) P->npb = std::min<int>(prm->rho_blocks, (int)std::max<size_t>(1, P->tiles.size()));
+    if (prm->rho_blocks > 0) {
+        P->npb = std::min<int>(prm->rho_blocks, (int)std::max<size_t>(1, P->tiles.size()));
+        P->rho_hi_tiles = 0;  // an explicit block count keeps the one-launch walk
+    }
+    if (P->rho_hi_tiles > 0) {
+        // two launches, each filling the GPU with its own persistent blocks
+        int bps_hi = 1, bps_lo = 1;
+        if ((rc = rho_walk_split_blocks_per_sm(P, 2, &bps_hi))) return rc;
+        if ((rc = rho_walk_split_blocks_per_sm(P, 1, &bps_lo))) return rc;
+        const int nlo = (int)P->tiles.size() - P->rho_hi_tiles;
+        P->npb_hi = std::max(1, std::min(P->rho_hi_tiles, P->num_sms * bps_hi / nch));
+        P->npb = P->npb_hi + std::max(1, std::min(nlo, P->num_sms * bps_lo / nch));
+    }
     if ((rc = build_rho_schedule(P))) return rc;
 
     size_t nn = (size_t)P->nao * P->nao;

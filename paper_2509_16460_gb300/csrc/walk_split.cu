@@ -463,24 +463,26 @@ __device__ void rho_tile_split(const Tile& tl, const Layout& lay, const float2* 
     __syncthreads();
 }
 
-template <bool ORTHO, bool CUT>
-__global__ void __launch_bounds__(kTile, 3) k_rho_walk_split(const Tile* __restrict__ tiles, int ntiles, Layout lay,
-                                                          const float2* __restrict__ Dp,
-                                                          const SConst* __restrict__ cst,
-                                                          const SState* __restrict__ init, long long npairs,
-                                                          const WLine* __restrict__ lines,
-                                                          const WChunk* __restrict__ chunks, int npb,
-                                                          double2* __restrict__ rho_part, long long ng_half,
-                                                          const int* __restrict__ sched, int nx) {
+// The structure-factor walk, persistent over the plan's tile schedule.  PART
+// 0: tiles of every class; PART 1: classes 0-2 (a 10-term D' slice, sized for
+// four blocks per SM); PART 2: classes 3-4.  Where shared memory holds the
+// one-kernel walk below three blocks per SM, parts 2 and 1 run as two launches
+// in turn, blocks [0, npb_hi) and [npb_hi, npb) of the schedule and the rows.
+template <bool ORTHO, bool CUT, int PART>
+__global__ void __launch_bounds__(kTile, PART == 1 ? 4 : 3) k_rho_walk_split(
+    const Tile* __restrict__ tiles, int b0, Layout lay, const float2* __restrict__ Dp, const SConst* __restrict__ cst,
+    const SState* __restrict__ init, long long npairs, const WLine* __restrict__ lines,
+    const WChunk* __restrict__ chunks, int npb, double2* __restrict__ rho_part, long long ng_half,
+    const int* __restrict__ sched, int nx) {
     extern __shared__ float4 ssm[];
     __shared__ int spt[2 * kSBatch];  // point indices of the current and the previous batch
-    const int b = blockIdx.x, cidx = blockIdx.y, d = blockIdx.z;
+    const int b = b0 + blockIdx.x, cidx = blockIdx.y, d = blockIdx.z;
     const WChunk ch = chunks[cidx];
     const int npts = ch.p1 - ch.p0;
     float4* buf = ssm;
     float4* red = buf + kSBatch * (kTile + 1);
     float2* Dsm = reinterpret_cast<float2*>(red + kTile);
-    float4* Xs = reinterpret_cast<float4*>(Dsm + kMaxTerms * kTile);
+    float4* Xs = reinterpret_cast<float4*>(Dsm + nterms(PART == 1 ? 2 : 4) * kTile);
     float4* row = Xs + (ORTHO ? nx * kTile : 0);
     for (int i = threadIdx.x; i < npts; i += blockDim.x) row[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
@@ -489,13 +491,25 @@ __global__ void __launch_bounds__(kTile, 3) k_rho_walk_split(const Tile* __restr
     // this block's tiles: sched[b] .. sched[b+1] index the list after the npb+1 offsets
     for (int j = sched[b]; j < sched[b + 1]; ++j) {
         const Tile tl = tiles[sched[npb + 1 + j]];
-        switch (tl.cls) {
-            case 0: rho_tile_split<0, ORTHO, CUT>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx, spt); break;
-            case 1: rho_tile_split<1, ORTHO, CUT>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx, spt); break;
-            case 2: rho_tile_split<2, ORTHO, CUT>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx, spt); break;
-            case 3: rho_tile_split<3, ORTHO, CUT>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx, spt); break;
-            default: rho_tile_split<4, ORTHO, CUT>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx, spt); break;
+#define FTCJ_RHO_TILE(Lc) \
+    rho_tile_split<Lc, ORTHO, CUT>(tl, lay, Dp_d, cst, init_c, lines, ch, buf, red, row, Dsm, Xs, nx, spt)
+        if (PART == 1) {
+            if (tl.cls == 0) FTCJ_RHO_TILE(0);
+            else if (tl.cls == 1) FTCJ_RHO_TILE(1);
+            else FTCJ_RHO_TILE(2);
+        } else if (PART == 2) {
+            if (tl.cls == 3) FTCJ_RHO_TILE(3);
+            else FTCJ_RHO_TILE(4);
+        } else {
+            switch (tl.cls) {
+                case 0: FTCJ_RHO_TILE(0); break;
+                case 1: FTCJ_RHO_TILE(1); break;
+                case 2: FTCJ_RHO_TILE(2); break;
+                case 3: FTCJ_RHO_TILE(3); break;
+                default: FTCJ_RHO_TILE(4); break;
+            }
         }
+#undef FTCJ_RHO_TILE
     }
     __syncthreads();
     double2* out = rho_part + ((long long)d * npb + b) * ng_half + ch.p0;
@@ -702,9 +716,9 @@ size_t xtab_bytes(const ftcj_plan* P) {
     return use_xtab(P) ? sizeof(float4) * (size_t)xtab_entries(P) * kTile : 0;
 }
 
-size_t rho_smem(const ftcj_plan* P) {
+size_t rho_smem(const ftcj_plan* P, int part = 0) {
     return sizeof(float4) * ((size_t)kSBatch * (kTile + 1) + kTile + (size_t)std::max(P->max_chunk_pts, 1)) +
-           sizeof(float2) * (size_t)kMaxTerms * kTile + xtab_bytes(P);
+           sizeof(float2) * (size_t)nterms(part == 1 ? 2 : 4) * kTile + xtab_bytes(P);
 }
 
 size_t j_smem(const ftcj_plan* P, int part) {
@@ -714,13 +728,18 @@ size_t j_smem(const ftcj_plan* P, int part) {
 }
 
 // the walk kernels for the plan's shape: X(n1) table or recurrence, with or without per-pair cutoffs
-using RhoKernel = decltype(&k_rho_walk_split<true, true>);
+using RhoKernel = decltype(&k_rho_walk_split<true, true, 0>);
 using JKernel = decltype(&k_j_walk_split<true, true, 0>);
 
-RhoKernel rho_kernel(const ftcj_plan* P) {
+template <int PART>
+RhoKernel rho_kernel_part(const ftcj_plan* P) {
     const bool c = P->d_rec_gcut != nullptr;
-    if (use_xtab(P)) return c ? k_rho_walk_split<true, true> : k_rho_walk_split<true, false>;
-    return c ? k_rho_walk_split<false, true> : k_rho_walk_split<false, false>;
+    if (use_xtab(P)) return c ? k_rho_walk_split<true, true, PART> : k_rho_walk_split<true, false, PART>;
+    return c ? k_rho_walk_split<false, true, PART> : k_rho_walk_split<false, false, PART>;
+}
+
+RhoKernel rho_kernel(const ftcj_plan* P, int part = 0) {
+    return part == 1 ? rho_kernel_part<1>(P) : (part == 2 ? rho_kernel_part<2>(P) : rho_kernel_part<0>(P));
 }
 
 template <int PART>
@@ -738,7 +757,7 @@ JKernel j_kernel(const ftcj_plan* P, int part) {
 
 int split_xtab_entries(const ftcj_plan* P) { return use_xtab(P) ? xtab_entries(P) : 0; }
 
-size_t split_rho_smem(const ftcj_plan* P) { return rho_smem(P); }
+size_t split_rho_smem(const ftcj_plan* P, int part) { return rho_smem(P, part); }
 
 int setup_split(ftcj_plan* P) {
     const size_t nch = P->chunks.size();
@@ -754,7 +773,8 @@ int setup_split(ftcj_plan* P) {
                                   reinterpret_cast<SConst*>(P->d_split_const), P->cc);
         FTCJ_CUDA(cudaGetLastError());
     }
-    int rc = allow_dynamic_smem((const void*)rho_kernel(P), rho_smem(P));
+    int rc = FTCJ_OK;
+    for (int part = 0; part < 3 && !rc; ++part) rc = allow_dynamic_smem((const void*)rho_kernel(P, part), rho_smem(P, part));
     if (rc) return rc;
     for (int part = 0; part < 3 && !rc; ++part) rc = allow_dynamic_smem((const void*)j_kernel(P, part), j_smem(P, part));
     if (rc) return rc;
@@ -766,6 +786,8 @@ int setup_split(ftcj_plan* P) {
     while (nhi < (int)P->tiles.size() && P->tiles[nhi].cls >= 3) ++nhi;
     const bool smem_bound = (size_t)per_sm / (j_smem(P, 0) + 1024) < 3;
     P->ntiles_hi = smem_bound && nhi > 0 && nhi < (int)P->tiles.size() ? nhi : 0;
+    const bool rho_smem_bound = (size_t)per_sm / (rho_smem(P, 0) + 1024) < 3;
+    P->rho_hi_tiles = rho_smem_bound && nhi > 0 && nhi < (int)P->tiles.size() ? nhi : 0;
     if (!P->aux) {
         // the heavy classes' stream has the highest priority, so that their blocks take SM slots first
         int lo_prio = 0, hi_prio = 0;
@@ -777,9 +799,9 @@ int setup_split(ftcj_plan* P) {
     return FTCJ_OK;
 }
 
-int rho_walk_split_blocks_per_sm(ftcj_plan* P, int* out) {
+int rho_walk_split_blocks_per_sm(ftcj_plan* P, int part, int* out) {
     int n = 0;
-    FTCJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rho_kernel(P), kTile, rho_smem(P)));
+    FTCJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rho_kernel(P, part), kTile, rho_smem(P, part)));
     *out = n > 0 ? n : 1;
     return FTCJ_OK;
 }
@@ -789,15 +811,21 @@ int launch_rho_walk_split(ftcj_plan* P, int ndens, cudaStream_t s) {
         FTCJ_CUDA(cudaMemsetAsync(P->d_rho_part, 0, sizeof(double2) * (size_t)ndens * P->npb * P->ng_half, s));
         return FTCJ_OK;
     }
-    dim3 g(P->npb, (unsigned)P->chunks.size(), ndens);
     const int nx = use_xtab(P) ? xtab_entries(P) : 0;
-    auto* kern = rho_kernel(P);
-    kern<<<g, kTile, rho_smem(P), s>>>(P->d_tiles, (int)P->tiles.size(), make_layout(P),
-                                       reinterpret_cast<const float2*>(P->d_Dp),
-                                       reinterpret_cast<const SConst*>(P->d_split_const),
-                                       reinterpret_cast<const SState*>(P->d_split_init), P->npairs, P->d_lines,
-                                       P->d_chunks, P->npb, reinterpret_cast<double2*>(P->d_rho_part), P->ng_half,
-                                       P->d_sched, nx);
+    auto go = [&](int part, int b0, int nblk) {
+        rho_kernel(P, part)<<<dim3((unsigned)nblk, (unsigned)P->chunks.size(), ndens), kTile, rho_smem(P, part), s>>>(
+            P->d_tiles, b0, make_layout(P), reinterpret_cast<const float2*>(P->d_Dp),
+            reinterpret_cast<const SConst*>(P->d_split_const), reinterpret_cast<const SState*>(P->d_split_init),
+            P->npairs, P->d_lines, P->d_chunks, P->npb, reinterpret_cast<double2*>(P->d_rho_part), P->ng_half,
+            P->d_sched, nx);
+    };
+    if (P->rho_hi_tiles > 0) {
+        go(2, 0, P->npb_hi);
+        FTCJ_CUDA(cudaGetLastError());
+        go(1, P->npb_hi, P->npb - P->npb_hi);
+    } else {
+        go(0, 0, P->npb);
+    }
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }
