@@ -265,10 +265,53 @@ def cfg3_leg(ftcj, W, torch, flush, steps):
         p.jbuild(Dk, J, E)
     ms = time_events(lambda: p.jbuild(Dk, J, E), steps, flush, stream)
     out["split_autotuned"] = {"ms_per_step": ms, "value": out["pair_g_units_per_step"] / (ms * 1e-3), "unit": UNIT,
-                              "chunk_points": chunk, "rho_blocks": rb, "autotune_s": tune_s,
+                              "chunk_points": chunk, "rho_blocks": rb, "shape_note": "0 = the plan's own default",
+                              "autotune_s": tune_s,
                               "max_abs_dJ_vs_split_default": float((J - res["split"][0]).abs().max())}
     p.close()
     out["split_pair_gcut_vs_fp64_max_abs_dJ"] = float((res["split_pair_gcut"][0] - res["fp64"][0]).abs().max())
+    out["split_vs_fp64_max_abs_dJ"] = float((res["split"][0] - res["fp64"][0]).abs().max())
+    out["split_vs_fp64_abs_dEJ"] = float((res["split"][1] - res["fp64"][1]).abs().max())
+    out["split_speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["split"]["ms_per_step"]
+    return out
+
+
+def slab_leg(ftcj, W, torch, flush, steps):
+    """The surface slab (rock-salt 2x2 (001), 4 layers + CO, 1270 AOs, k
+    3x3x1): split and FP64 builds, and the split plan's nuclear gradient
+    (dE_J/dR of every centre)."""
+    import numpy as np
+    w = W.cfg5()
+    Dk = torch.from_numpy(np.ascontiguousarray(w.Dk)).cuda()
+    out = {"workload": "rock-salt (001) 2x2 slab, 4 layers (16 Mg-like + 16 O-like) + CO, 20 bohr vacuum, "
+                       f"{w.nao} spherical AOs, k 3x3x1, omega 0.4", "ndens": w.ndens}
+    stream = torch.cuda.current_stream()
+    res = {}
+    for form, prec in (("split", ftcj.FTCJ_PREC_SPLIT), ("fp64", ftcj.FTCJ_PREC_FP64)):
+        p = ftcj.Plan.from_workload(w, precision=prec)
+        units = float(p.info["pair_g_units"]) * w.ndens
+        out["pair_g_units_per_step"] = units
+        J, E = p.jbuild(Dk)
+        for _ in range(2):
+            p.jbuild(Dk, J, E)
+        ms = time_events(lambda: p.jbuild(Dk, J, E), steps, flush, stream)
+        out[form] = {"ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT}
+        res[form] = (J.clone(), E.clone())
+        if form == "split":
+            EJ, G = p.grad(Dk)
+            for _ in range(2):
+                p.grad(Dk, EJ, G)
+            ms = time_events(lambda: p.grad(Dk, EJ, G), steps, flush, stream)
+            torch.cuda.synchronize()
+            out["gradient"] = {"ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT,
+                               "note": "one call: fold, Hermite map and rho pass of the plan's form, the adjoint "
+                                       "walk of degree L+1 (double-float where grad_split is 1), then the FP64 "
+                                       "per-centre assembly",
+                               "grad_split": int(p.info["grad_split"]),
+                               "abs_dEJ_vs_build": float((EJ - E).abs().max()),
+                               "max_abs_force": float(G.abs().max()),
+                               "sum_of_forces_max_abs": float(G.sum(dim=1).abs().max())}
+        p.close()
     out["split_vs_fp64_max_abs_dJ"] = float((res["split"][0] - res["fp64"][0]).abs().max())
     out["split_vs_fp64_abs_dEJ"] = float((res["split"][1] - res["fp64"][1]).abs().max())
     out["split_speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["split"]["ms_per_step"]
@@ -452,7 +495,8 @@ def main():
     if rank == 0 and not args.no_extra:
         extra_steps = max(3, min(args.steps, 10))
         line["batch"] = batch_leg(ftcj, W, torch, flush, extra_steps)
-        line["workloads"] = {"molecular_crystal": cfg3_leg(ftcj, W, torch, flush, extra_steps)}
+        line["workloads"] = {"molecular_crystal": cfg3_leg(ftcj, W, torch, flush, extra_steps),
+                             "slab": slab_leg(ftcj, W, torch, flush, extra_steps)}
     if rank == 0 and not args.no_cpu_baseline:
         # the whole oracle on the host cores: the CPU baseline and the accuracy of this run
         r, cu, threads = cpu_oracle_run(w, 1)

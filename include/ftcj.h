@@ -91,13 +91,20 @@ typedef struct {
     double pair_thresh; /* keep primitive pairs with overlap bound > this */
     int precision;      /* FTCJ_PREC_FP64 or FTCJ_PREC_SPLIT */
     int max_dens;       /* densities per device batch (scratch is sized for it); <= 0: 1 */
-    int chunk_points;   /* G points per walk chunk, 64..4096; <= 0: 4096 */
-    int rho_blocks;     /* persistent blocks of the structure-factor walk; <= 0: fill the GPU */
+    int chunk_points;   /* G points per walk chunk, 64..4096; <= 0: 4096 in the FP64 form; in the
+                           split form the longest power of two (<= 4096) whose structure-factor
+                           walk keeps three blocks per SM in shared memory (one kernel, >= 1024
+                           points; else its classes 0-2 part, >= 512), else two blocks (>= 512),
+                           else one */
+    int rho_blocks;     /* persistent blocks of the structure-factor walk; <= 0: fill the GPU
+                           (the split form then runs classes 3-4 and 0-2 as two launches where
+                           shared memory holds the one-kernel walk below three blocks per SM);
+                           > 0: that many blocks of the one-kernel walk */
     double pair_gcut_eps; /* > 0: per-pair G cutoffs (Sec. 2.5, Eq. "AFT screening obj"): each pair
                              record is evaluated only for |G| below the radius where its
                              screening estimate 8 pi eta G (4 pi/G^2) e^{-G^2/4w^2} |rho_ab(G)|
-                             falls under this value (split form only; EUNSUPPORTED with FP64;
-                             ftcj_grad ignores it).  0: every pair over the whole sphere. */
+                             falls under this value (split form only; EUNSUPPORTED with FP64).
+                             0: every pair over the whole sphere. */
 } ftcj_params;
 
 typedef struct {
@@ -124,6 +131,10 @@ typedef struct {
     int64_t pair_g_units_walked;   /* record x G evaluations the walks perform (both passes
                                       count once), x4 for the (+-G, mirror) symmetries: the
                                       work actually done in the units of pair_g_units */
+    int n_abs_max;            /* largest |n_i| of the sphere's G = sum_i n_i b_i (the split form
+                                 needs <= 63) */
+    int grad_split;           /* 1: ftcj_grad's back-contraction runs in double-float (split
+                                 form with n_abs_max <= 27), 0: in FP64 */
 } ftcj_info;
 
 typedef struct ftcj_plan ftcj_plan;
@@ -224,8 +235,14 @@ int ftcj_unfold_j(ftcj_plan* plan, int ndens, const double* J0n, double* Jk, voi
  *   grad[d][C][x] = dE_J[d]/dR_{C,x}  (device double [ndens][ncentre][3]),
  *   EJ[d]          (device double [ndens]).
  * The derivative of E_J with respect to D^k is J^k/Nk (ftcj_jbuild).
- * Runs a2..a5 and a back-contraction one degree higher than the build's, in
- * FP64 whatever the plan's precision.  Asynchronous on `stream`. */
+ * Runs a2..a5 and a back-contraction one degree higher than the build's,
+ * in the plan's form (split: double-float on the FP32 pipe where every
+ * |n_i| <= 27, so that FP32 holds the fifth powers exactly; else FP64),
+ * followed by an FP64 assembly per centre.  With pair_gcut_eps > 0 the
+ * double-float back-contraction walks the same points as the build's, so the
+ * result is the derivative of the screened energy that ftcj_jbuild returns
+ * (the FP64 one walks the whole sphere).
+ * Asynchronous on `stream`. */
 int ftcj_grad(ftcj_plan* plan, int ndens, const double* Dk, double* EJ, double* grad, void* stream);
 
 /* Largest |Im D^{0n}| and largest |D^{0n}_{mu nu} - D^{0,-n}_{nu mu}| of
@@ -273,8 +290,10 @@ int ftcj_batch_replay(ftcj_batch* batch, void* stream);
 void ftcj_batch_destroy(ftcj_batch* batch);
 
 /* Autotuner of the walk shape: builds the plan for every candidate
- * (chunk_points in {512, 1024, 2048, 4096} that hold the longest G line,
- * rho_blocks in {fill, 2 x fill}), times ftcj_jbuild on a zero density
+ * (chunk_points in {0 = the plan's default, 512, 1024, 2048, 4096} that hold
+ * the longest G line, rho_blocks in {0 = the plan's own count, which fills
+ * the GPU and may split the split-form walk by class, 2 x fill}; an explicit
+ * value equal to the default is not tried twice), times ftcj_jbuild on a zero density
  * (the walks' cost does not depend on the values) with CUDA events, and
  * writes the fastest parameters to *out (and its time to *best_ms, may be
  * NULL).  Allocates and frees its own buffers; synchronises the device. */

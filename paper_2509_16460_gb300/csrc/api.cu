@@ -174,7 +174,10 @@ int ftcj_grad(ftcj_plan* P, int ndens, const double* Dk, double* EJ, double* gra
         if ((rc = launch_hermite_map(P, nd, P->d_D0n, s))) return rc;
         if ((rc = rho_walk(P, nd, s))) return rc;
         if ((rc = launch_rho_reduce(P, nd, P->d_rho, P->d_W, EJ + b0, nullptr, s))) return rc;
-        if ((rc = launch_j_walk_grad(P, nd, P->d_W, s))) return rc;
+        // the degree-(L+1) sums in the plan's form where FP32 holds their powers of n exactly
+        const bool split = P->precision == FTCJ_PREC_SPLIT && split_grad_walk_exact(P);
+        if ((rc = split ? launch_j_walk_grad_split(P, nd, P->d_W, s) : launch_j_walk_grad(P, nd, P->d_W, s)))
+            return rc;
         if ((rc = launch_grad_assemble(P, nd, P->d_D0n, grad + (size_t)b0 * P->ncentre * 3, s))) return rc;
     }
     return FTCJ_OK;

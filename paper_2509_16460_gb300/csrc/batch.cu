@@ -77,7 +77,10 @@ extern "C" {
 int ftcj_autotune(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], const ftcj_params* in,
                   ftcj_params* out, double* best_ms) {
     if (!cell || !basis || !kmesh || !in || !out) return fail(FTCJ_EINVAL, "null argument");
-    const int chunks[] = {512, 1024, 2048, 4096};
+    // 0 = the plan's own default chunk; an explicit chunk equal to it builds
+    // the same plan and is skipped
+    const int chunks[] = {0, 512, 1024, 2048, 4096};
+    int default_chunk = -1;
     ftcj_params best = *in;
     double best_t = 1e300;
     cudaEvent_t e0, e1;
@@ -86,12 +89,15 @@ int ftcj_autotune(const ftcj_cell* cell, const ftcj_basis* basis, const int kmes
     int rc = FTCJ_OK;
     bool any = false;
     for (int ch : chunks) {
+        if (ch == default_chunk) continue;
         int npb_fill = 0;
         for (int mult = 1; mult <= 2; ++mult) {
             ftcj_params p = *in;
             p.max_dens = 1;
             p.chunk_points = ch;
-            p.rho_blocks = mult == 1 ? 0 : 2 * npb_fill;  // the fill count, then twice it
+            // the plan's own count (it fills the GPU, and splits the walk by
+            // class where shared memory calls for it), then twice the fill
+            p.rho_blocks = mult == 1 ? 0 : 2 * npb_fill;
             ftcj_plan* P = nullptr;
             int r = ftcj_plan_create(cell, basis, kmesh, &p, &P);
             if (r == FTCJ_EUNSUPPORTED) break;  // a G line longer than this chunk
@@ -100,7 +106,7 @@ int ftcj_autotune(const ftcj_cell* cell, const ftcj_basis* basis, const int kmes
                 break;
             }
             if (mult == 1) npb_fill = P->npb;
-            p.rho_blocks = P->npb;
+            if (ch == 0) default_chunk = P->chunk_max;
             size_t bytes = sizeof(double) * 2 * (size_t)P->nk * P->nao * P->nao;
             double *Dk = nullptr, *Jk = nullptr, *EJ = nullptr;
             cudaError_t e = cudaMalloc(&Dk, bytes);

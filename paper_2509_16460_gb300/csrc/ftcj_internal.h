@@ -21,6 +21,11 @@ constexpr int kBatch = 32;                 // points per rho reduction batch
 constexpr int kChunkMax = 4096;            // G points per walk chunk
 constexpr int kRedPoints = 4;  // G points per block of the rho row reduction
 constexpr int kSortTile = 1024;            // candidates per sort tile
+// The split walks form n^i and n2^j n3^k (i, j + k <= degree) as exact FP32
+// integers: |n| <= 63 keeps degree 4 below 2^24, |n| <= 27 degree 5 (the
+// gradient's sums).
+constexpr int kSplitNmax = 63;
+constexpr int kSplitGradNmax = 27;
 
 __host__ __device__ constexpr int nterms(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
 __host__ __device__ constexpr int nmono(int lam) { return (lam + 1) * (lam + 2) / 2; }
@@ -145,6 +150,7 @@ struct ftcj_plan {
     int chunk_max;        // G points per walk chunk (a plan parameter)
     int max_chunk_pts;
     int n1_min, n1_max;
+    int n_abs_max;  // largest |n_i| of the sphere's G = sum_i n_i b_i
     // pairs
     int64_t npairs, npairs_ordered;
     int64_t class_start[ftcj::kNclass + 1];
@@ -268,6 +274,8 @@ int apply_pair_cutoffs(ftcj_plan* P);    // sort records by cutoff within each c
 int rho_walk_split_blocks_per_sm(ftcj_plan* P, int part, int* out);  // part: 0 all, 1 classes 0-2, 2 classes 3-4
 int launch_rho_walk_split(ftcj_plan* P, int ndens, cudaStream_t s);
 int launch_j_walk_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s);
+int launch_j_walk_grad_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s);
+bool split_grad_walk_exact(const ftcj_plan* P);
 
 // --- measurement (profile.cu) ---
 void release_profiling(ftcj_plan* P);

@@ -450,6 +450,11 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     int rc = build_walk(P);
     if (rc) return rc;
     if (prm->chunk_points <= 0 && P->precision == FTCJ_PREC_SPLIT && (rc = default_split_chunk(P))) return rc;
+    P->n_abs_max = 0;
+    for (int v : P->gvec) P->n_abs_max = std::max(P->n_abs_max, std::abs(v));
+    if (P->precision == FTCJ_PREC_SPLIT && P->n_abs_max > kSplitNmax)
+        return fail(FTCJ_EUNSUPPORTED, "a G index |n_i| above 63: the split form's walks need n^4 exact in FP32 "
+                                       "(use FTCJ_PREC_FP64 for this cell and cutoff)");
 
     FTCJ_CUDA(cudaFree(0));
     int dev = 0;
@@ -601,6 +606,8 @@ int ftcj_plan_info(const ftcj_plan* P, ftcj_info* o) {
     o->n1_table = P->precision == FTCJ_PREC_SPLIT ? split_xtab_entries(P) : 0;
     o->pair_g_units_screened = P->d_rec_gcut ? P->units_screened : o->pair_g_units;
     o->pair_g_units_walked = P->d_rec_gcut ? P->units_walked : o->pair_g_units;
+    o->n_abs_max = P->n_abs_max;
+    o->grad_split = P->precision == FTCJ_PREC_SPLIT && split_grad_walk_exact(P) ? 1 : 0;
     return FTCJ_OK;
 }
 

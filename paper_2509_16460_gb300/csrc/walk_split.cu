@@ -521,7 +521,9 @@ __global__ void __launch_bounds__(kTile, PART == 1 ? 4 : 3) k_rho_walk_split(
 
 // ---- J -------------------------------------------------------------------
 
-template <int L, bool ORTHO, bool CUT>
+// L: degree of the sums (the record's class, or one more for the nuclear
+// gradient's sums); C: the record's class, which places its terms in `lay`.
+template <int L, bool ORTHO, bool CUT, int C = L>
 __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __restrict__ cst,
                              const SState* __restrict__ init_c, const WLine* __restrict__ lines, const WChunk ch,
                              const float4* __restrict__ wsm,
@@ -530,8 +532,8 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
     const int tid = threadIdx.x;
     const bool valid = tid < tl.count;
     const long long pi = (long long)tl.first + tid;
-    const long long cnt = lay.start[L + 1] - lay.start[L];
-    const long long loc = pi - lay.start[L];
+    const long long cnt = lay.start[C + 1] - lay.start[C];
+    const long long loc = pi - lay.start[C];
     const SConst k = valid ? cst[pi] : idle_const();
     const SState* init_p = init_c + (valid ? pi : 0);
     // the record's J' accumulators live in a thread-private shared-memory slice
@@ -602,7 +604,7 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
                     float p = 1.f;
 #pragma unroll
                     for (int i = 1; i <= L; ++i) {
-                        p *= x;  // n1^i, exact (|n1|^4 < 2^24)
+                        p *= x;  // n1^i, exact (|n1|^L < 2^24)
                         A[i] = cdf{df_add_u(A[i].re, df_mulf_u(t.re, p)), df_add_u(A[i].im, df_mulf_u(t.im, p))};
                     }
                 }
@@ -645,7 +647,7 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
             const float2 jv = Jsm[t * kTile + tid];
-            Jp_dc[lay.base[L] + (long long)t * cnt + loc] = (double)jv.x + (double)jv.y;
+            Jp_dc[lay.base[C] + (long long)t * cnt + loc] = (double)jv.x + (double)jv.y;
         }
     }
 }
@@ -654,9 +656,12 @@ __device__ void j_tile_split(const Tile& tl, const Layout& lay, const SConst* __
 // 0-2 only (a 10-term J' slice, sized for four blocks per SM); PART 2: classes
 // 3-4.  Parts 1 and 2 run as two launches side by side where the shared
 // memory of the one-kernel walk (a long chunk's W beside a 35-term J' slice)
-// would hold it below three blocks per SM.
-template <bool ORTHO, bool CUT, int PART>
-__global__ void __launch_bounds__(kTile, PART == 1 ? 4 : 3) k_j_walk_split(
+// would hold it below three blocks per SM.  E = 1: the sums of degree L + 1
+// that the nuclear gradient contracts (one more power of G from d/dR_A), into
+// the gradient's term layout; the slices grow to 20 resp. 56 terms, and the
+// degree-5 part takes the registers of two blocks per SM.
+template <bool ORTHO, bool CUT, int PART, int E>
+__global__ void __launch_bounds__(kTile, PART == 1 ? 4 : (E ? 2 : 3)) k_j_walk_split(
     const Tile* __restrict__ tiles, int tile0, Layout lay, const SConst* __restrict__ cst,
     const SState* __restrict__ init, long long npairs, const WLine* __restrict__ lines,
     const WChunk* __restrict__ chunks, int nchunks, const double2* __restrict__ W, long long ng_half, int nx,
@@ -667,7 +672,7 @@ __global__ void __launch_bounds__(kTile, PART == 1 ? 4 : 3) k_j_walk_split(
     const int npts = ch.p1 - ch.p0;
     float4* wsm = ssm;
     float2* Jsm = reinterpret_cast<float2*>(ssm + max_chunk_pts);
-    float4* Xs = reinterpret_cast<float4*>(Jsm + nterms(PART == 1 ? 2 : 4) * kTile);
+    float4* Xs = reinterpret_cast<float4*>(Jsm + nterms((PART == 1 ? 2 : 4) + E) * kTile);
     const double2* Wd = W + (long long)d * ng_half + ch.p0;
     for (int i = threadIdx.x; i < npts; i += blockDim.x) {
         const double2 v = Wd[i];
@@ -678,24 +683,26 @@ __global__ void __launch_bounds__(kTile, PART == 1 ? 4 : 3) k_j_walk_split(
     const Tile tl = tiles[tix];
     double* Jp_dc = Jp + ((long long)d * nchunks + cidx) * lay.total;
     const SState* init_c = init + (long long)cidx * npairs;
+#define FTCJ_J_TILE(c) j_tile_split<(c) + E, ORTHO, CUT, (c)>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx)
     if (PART == 1) {
         switch (tl.cls) {
-            case 0: j_tile_split<0, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
-            case 1: j_tile_split<1, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
-            default: j_tile_split<2, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+            case 0: FTCJ_J_TILE(0); break;
+            case 1: FTCJ_J_TILE(1); break;
+            default: FTCJ_J_TILE(2); break;
         }
     } else if (PART == 2) {
-        if (tl.cls == 3) j_tile_split<3, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx);
-        else j_tile_split<4, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx);
+        if (tl.cls == 3) FTCJ_J_TILE(3);
+        else FTCJ_J_TILE(4);
     } else {
         switch (tl.cls) {
-            case 0: j_tile_split<0, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
-            case 1: j_tile_split<1, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
-            case 2: j_tile_split<2, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
-            case 3: j_tile_split<3, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
-            default: j_tile_split<4, ORTHO, CUT>(tl, lay, cst, init_c, lines, ch, wsm, Jp_dc, Jsm, Xs, nx); break;
+            case 0: FTCJ_J_TILE(0); break;
+            case 1: FTCJ_J_TILE(1); break;
+            case 2: FTCJ_J_TILE(2); break;
+            case 3: FTCJ_J_TILE(3); break;
+            default: FTCJ_J_TILE(4); break;
         }
     }
+#undef FTCJ_J_TILE
 }
 
 Layout make_layout(const ftcj_plan* P) {
@@ -703,6 +710,14 @@ Layout make_layout(const ftcj_plan* P) {
     for (int c = 0; c <= kNclass; ++c) l.start[c] = P->class_start[c];
     for (int c = 0; c < kNclass; ++c) l.base[c] = P->term_base[c];
     l.total = P->total_terms;
+    return l;
+}
+
+Layout make_grad_layout(const ftcj_plan* P) {
+    Layout l;
+    for (int c = 0; c <= kNclass; ++c) l.start[c] = P->class_start[c];
+    for (int c = 0; c < kNclass; ++c) l.base[c] = P->term_base_g[c];
+    l.total = P->total_terms_g;
     return l;
 }
 
@@ -721,15 +736,15 @@ size_t rho_smem(const ftcj_plan* P, int part = 0) {
            sizeof(float2) * (size_t)nterms(part == 1 ? 2 : 4) * kTile + xtab_bytes(P);
 }
 
-size_t j_smem(const ftcj_plan* P, int part) {
-    const int hi = part == 1 ? 2 : 4;
+size_t j_smem(const ftcj_plan* P, int part, int e = 0) {
+    const int hi = (part == 1 ? 2 : 4) + e;
     return sizeof(float4) * (size_t)std::max(P->max_chunk_pts, 1) + sizeof(float2) * (size_t)nterms(hi) * kTile +
            xtab_bytes(P);
 }
 
 // the walk kernels for the plan's shape: X(n1) table or recurrence, with or without per-pair cutoffs
 using RhoKernel = decltype(&k_rho_walk_split<true, true, 0>);
-using JKernel = decltype(&k_j_walk_split<true, true, 0>);
+using JKernel = decltype(&k_j_walk_split<true, true, 0, 0>);
 
 template <int PART>
 RhoKernel rho_kernel_part(const ftcj_plan* P) {
@@ -742,15 +757,21 @@ RhoKernel rho_kernel(const ftcj_plan* P, int part = 0) {
     return part == 1 ? rho_kernel_part<1>(P) : (part == 2 ? rho_kernel_part<2>(P) : rho_kernel_part<0>(P));
 }
 
-template <int PART>
+template <int PART, int E>
 JKernel j_kernel_part(const ftcj_plan* P) {
     const bool c = P->d_rec_gcut != nullptr;
-    if (use_xtab(P)) return c ? k_j_walk_split<true, true, PART> : k_j_walk_split<true, false, PART>;
-    return c ? k_j_walk_split<false, true, PART> : k_j_walk_split<false, false, PART>;
+    if (use_xtab(P)) return c ? k_j_walk_split<true, true, PART, E> : k_j_walk_split<true, false, PART, E>;
+    return c ? k_j_walk_split<false, true, PART, E> : k_j_walk_split<false, false, PART, E>;
 }
 
 JKernel j_kernel(const ftcj_plan* P, int part) {
-    return part == 1 ? j_kernel_part<1>(P) : (part == 2 ? j_kernel_part<2>(P) : j_kernel_part<0>(P));
+    return part == 1 ? j_kernel_part<1, 0>(P) : (part == 2 ? j_kernel_part<2, 0>(P) : j_kernel_part<0, 0>(P));
+}
+
+// the gradient's walk always runs as its two class parts (the 56-term slice of
+// classes 3-4 would hold a one-kernel walk to few blocks per SM)
+JKernel j_grad_kernel(const ftcj_plan* P, int part) {
+    return part == 1 ? j_kernel_part<1, 1>(P) : j_kernel_part<2, 1>(P);
 }
 
 }  // namespace
@@ -777,6 +798,9 @@ int setup_split(ftcj_plan* P) {
     for (int part = 0; part < 3 && !rc; ++part) rc = allow_dynamic_smem((const void*)rho_kernel(P, part), rho_smem(P, part));
     if (rc) return rc;
     for (int part = 0; part < 3 && !rc; ++part) rc = allow_dynamic_smem((const void*)j_kernel(P, part), j_smem(P, part));
+    if (rc) return rc;
+    for (int part = 1; part < 3 && !rc; ++part)
+        rc = allow_dynamic_smem((const void*)j_grad_kernel(P, part), j_smem(P, part, 1));
     if (rc) return rc;
     // split the walk by class only where shared memory holds the one-kernel walk below three blocks per SM
     int dev = 0, per_sm = 0;
@@ -859,6 +883,44 @@ int launch_j_walk_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s
         FTCJ_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));
     } else {
         go(0, 0, (int)P->tiles.size(), s);
+        FTCJ_CUDA(cudaGetLastError());
+    }
+    return FTCJ_OK;
+}
+
+bool split_grad_walk_exact(const ftcj_plan* P) { return P->n_abs_max <= kSplitGradNmax; }
+
+// The degree-(L+1) back-contraction of the nuclear gradient in double-float,
+// into d_Jg (FP64, the gradient's term layout).  Both class parts run side by
+// side (classes 3-4 on the plan's second stream), each over its own tiles.
+int launch_j_walk_grad_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s) {
+    const int nch = (int)P->chunks.size();
+    if (P->tiles.empty()) return FTCJ_OK;
+    if (P->ng_half == 0) {
+        FTCJ_CUDA(cudaMemsetAsync(P->d_Jg, 0, sizeof(double) * (size_t)ndens * std::max(nch, 1) * P->total_terms_g, s));
+        return FTCJ_OK;
+    }
+    const int nx = use_xtab(P) ? xtab_entries(P) : 0;
+    int nhi = 0;  // tiles are ordered by decreasing class: classes 3-4 lead
+    while (nhi < (int)P->tiles.size() && P->tiles[nhi].cls >= 3) ++nhi;
+    const int nlo = (int)P->tiles.size() - nhi;
+    auto go = [&](int part, int tile0, int ntiles, cudaStream_t st) {
+        j_grad_kernel(P, part)<<<dim3((unsigned)ntiles, nch, ndens), kTile, j_smem(P, part, 1), st>>>(
+            P->d_tiles, tile0, make_grad_layout(P), reinterpret_cast<const SConst*>(P->d_split_const),
+            reinterpret_cast<const SState*>(P->d_split_init), P->npairs, P->d_lines, P->d_chunks, nch,
+            reinterpret_cast<const double2*>(W), P->ng_half, nx, P->max_chunk_pts, P->d_Jg);
+    };
+    if (nhi > 0 && nlo > 0) {
+        FTCJ_CUDA(cudaEventRecord(P->ev_fork, s));
+        FTCJ_CUDA(cudaStreamWaitEvent(P->aux, P->ev_fork, 0));
+        go(2, 0, nhi, P->aux);
+        FTCJ_CUDA(cudaGetLastError());
+        go(1, nhi, nlo, s);
+        FTCJ_CUDA(cudaGetLastError());
+        FTCJ_CUDA(cudaEventRecord(P->ev_join, P->aux));
+        FTCJ_CUDA(cudaStreamWaitEvent(s, P->ev_join, 0));
+    } else {
+        go(nhi > 0 ? 2 : 1, 0, (int)P->tiles.size(), s);
         FTCJ_CUDA(cudaGetLastError());
     }
     return FTCJ_OK;

@@ -51,7 +51,7 @@ class Info(ctypes.Structure):
                 ("pairs_by_class", ctypes.c_int64 * 5), ("nlines", _c_int), ("nchunks", _c_int),
                 ("gcut", _c_double), ("volume", _c_double), ("device_bytes", ctypes.c_size_t),
                 ("rho_blocks", _c_int), ("n1_table", _c_int), ("pair_g_units_screened", ctypes.c_int64),
-                ("pair_g_units_walked", ctypes.c_int64)]
+                ("pair_g_units_walked", ctypes.c_int64), ("n_abs_max", _c_int), ("grad_split", _c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -191,7 +191,8 @@ def _params_of(w, precision=FTCJ_PREC_FP64, max_dens=None, chunk_points=0, rho_b
 
 
 def autotune(w, precision=FTCJ_PREC_FP64):
-    """ftcj_autotune for one workload: (chunk_points, rho_blocks, best_ms)."""
+    """ftcj_autotune for one workload: (chunk_points, rho_blocks, best_ms); a 0
+    stands for the plan's own default, so the pair passes straight back to Plan."""
     keep = []
     cell, basis = _describe(w.A, w.xyz, w.shells, keep)
     km = (ctypes.c_int * 3)(*[int(k) for k in w.kmesh])

@@ -121,7 +121,7 @@ def test_autotune_picks_a_valid_shape(orc, F):
     import torch
     w = sorted(W.cfg4(), key=lambda c: c.nao * c.nk)[10]
     chunk, rb, ms = F.autotune(w, precision=F.FTCJ_PREC_SPLIT)
-    assert chunk in (512, 1024, 2048, 4096) and rb >= 1 and ms > 0
+    assert chunk in (0, 512, 1024, 2048, 4096) and rb >= 0 and ms > 0  # 0: the plan's own default
     p = F.Plan.from_workload(w, precision=F.FTCJ_PREC_SPLIT, chunk_points=chunk, rho_blocks=rb)
     J, E = p.jbuild(dk(w))
     torch.cuda.synchronize()

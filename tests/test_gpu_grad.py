@@ -41,6 +41,7 @@ def test_gradient_matches_oracle(orc, F, name):
     ref = orc.grad(w)
     for prec in (F.FTCJ_PREC_FP64, F.FTCJ_PREC_SPLIT):
         p = F.Plan.from_workload(w, precision=prec)
+        assert p.info["grad_split"] == (1 if prec == F.FTCJ_PREC_SPLIT else 0)
         E, g = p.grad(dk(w))
         torch.cuda.synchronize()
         g = g.cpu().numpy()
@@ -48,6 +49,71 @@ def test_gradient_matches_oracle(orc, F, name):
         assert np.abs(g - ref).max() <= 1e-10 * scale, (name, prec, np.abs(g - ref).max())
         assert np.abs(g.sum(axis=1)).max() <= 1e-10 * scale  # translational invariance
         p.close()
+
+
+def test_split_gradient_beyond_the_exact_fp32_powers(orc, F):
+    """The split gradient's degree-(L+1) sums hold n^5 in FP32, exact only for
+    |n_i| <= 27: a 24-bohr cell with Gcut 8 (|n_i| up to ~34) runs them in FP64
+    and must still match the oracle; with Gcut 20 (|n_i| > 63) the split form
+    is refused, since its degree-4 powers would round."""
+    import torch
+    w = W.tiny(seed=63, A=np.diag([24.0, 21.6, 26.4]), centres=[[0.1, 0.2, 0.3], [1.5, 0.7, -0.5]])
+    w.gcut = 8.0
+    p = F.Plan.from_workload(w, precision=F.FTCJ_PREC_SPLIT)
+    assert 27 < p.info["n_abs_max"] <= 63 and p.info["grad_split"] == 0
+    E, g = p.grad(dk(w))
+    _, Eb = p.jbuild(dk(w))
+    torch.cuda.synchronize()
+    p.close()
+    g = g.cpu().numpy()
+    ref = orc.grad(w)
+    scale = max(1.0, np.abs(ref).max())
+    assert np.abs(g - ref).max() <= 1e-10 * scale, np.abs(g - ref).max()
+    assert abs(float(E[0] - Eb[0])) <= 1e-12 * max(1.0, abs(float(Eb[0])))
+    w.gcut = 20.0
+    with pytest.raises(F.FtcjError, match="63"):
+        F.Plan.from_workload(w, precision=F.FTCJ_PREC_SPLIT)
+
+
+def test_split_gradient_with_pair_cutoffs_is_that_of_the_screened_energy(F):
+    """Diamond-like cell, split form, per-pair cutoffs at 1e-12: the gradient
+    walks the points the build walks, so it matches central differences
+    (h = 1e-4 bohr) of the screened GPU energies and stays within the
+    screening error of the whole-sphere gradient."""
+    import torch
+    w = W.cfg2()
+    D = dk(w)
+    eps = 1e-12
+    full = F.Plan.from_workload(w, precision=F.FTCJ_PREC_SPLIT)
+    _, g_full = full.grad(D)
+    full.close()
+    p = F.Plan.from_workload(w, precision=F.FTCJ_PREC_SPLIT, pair_gcut_eps=eps)
+    assert p.info["pair_g_units_walked"] < 0.5 * p.info["pair_g_units"] and p.info["grad_split"] == 1
+    E, g = p.grad(D)
+    _, Eb = p.jbuild(D)
+    torch.cuda.synchronize()
+    p.close()
+    g = g.cpu().numpy()
+    g_full = g_full.cpu().numpy()
+    scale = max(1.0, np.abs(g_full).max())
+    assert abs(float(E[0] - Eb[0])) <= 1e-12 * abs(float(Eb[0]))
+    assert np.abs(g - g_full).max() <= 1e-8 * scale, np.abs(g - g_full).max()
+    assert np.abs(g.sum(axis=1)).max() <= 1e-9 * scale
+    h = 1e-4
+    x0 = w.xyz.copy()
+    for c, d in ((0, 0), (5, 2)):
+        e = []
+        for sgn in (1, -1):
+            w.xyz = x0.copy()
+            w.xyz[c, d] += sgn * h
+            q = F.Plan.from_workload(w, precision=F.FTCJ_PREC_SPLIT, pair_gcut_eps=eps)
+            _, Eq = q.jbuild(D)
+            torch.cuda.synchronize()
+            e.append(float(Eq[0]))
+            q.close()
+        fd = (e[0] - e[1]) / (2 * h)
+        assert abs(fd - g[0, c, d]) <= 1e-6 * scale, (c, d, fd, g[0, c, d])
+    w.xyz = x0
 
 
 def test_gradient_central_differences_of_gpu_energy(F):
