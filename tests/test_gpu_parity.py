@@ -215,6 +215,35 @@ def test_host_buffer_paths_agree(F, torch_cuda):
         plan.close()
 
 
+def test_host_buffers_full_size_batched(F, torch_cuda):
+    """Diamond-like cell (240 AOs, k 4x4x4), split form, with and without
+    per-pair cutoffs: three densities in batches of two through the host-buffer
+    entry point, page-locked (read and written over the host link by the
+    k-mesh transforms) and pageable (staging copies), on repeated calls, give
+    the device-buffer build's J^k and E_J (up to the order of the J -> AO
+    atomic additions); E_J scales as the square of the density."""
+    torch = torch_cuda
+    w = W.cfg2()
+    D1 = np.ascontiguousarray(w.Dk)
+    D = np.concatenate([D1, 0.5 * D1, -0.25 * D1], axis=0)
+    for eps in (0.0, 1e-12):
+        plan = F.Plan.from_workload(w, precision=F.FTCJ_PREC_SPLIT, max_dens=2, pair_gcut_eps=eps)
+        Jd, Ed = plan.jbuild(torch.from_numpy(D).cuda())
+        torch.cuda.synchronize()
+        Jd, Ed = Jd.cpu(), Ed.cpu()
+        scale = float(Jd.abs().max())
+        assert abs(float(Ed[1]) - 0.25 * float(Ed[0])) <= 1e-12 * abs(float(Ed[0]))
+        assert abs(float(Ed[2]) - 0.0625 * float(Ed[0])) <= 1e-12 * abs(float(Ed[0]))
+        Dh = torch.from_numpy(D).pin_memory()
+        for pin_out in (True, True, False):
+            Jh = torch.full(tuple(D.shape), float("nan"), dtype=torch.complex128, pin_memory=pin_out)
+            Eh = torch.empty(D.shape[0], dtype=torch.float64, pin_memory=pin_out)
+            plan.jbuild_host(Dh, Jh, Eh)
+            assert float((Jh - Jd).abs().max()) <= 1e-13 * scale, (eps, pin_out, float((Jh - Jd).abs().max()))
+            assert float((Eh - Ed).abs().max()) <= 1e-13 * float(Ed.abs().max()), (eps, pin_out)
+        plan.close()
+
+
 def test_check_density_flags_broken_input(F, torch_cuda):
     torch = torch_cuda
     w = W.tiny(seed=28, kmesh=(2, 1, 1))
