@@ -46,7 +46,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the batch and molecular-crystal legs")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batch, molecular-crystal and slab legs")
+    ap.add_argument("--leg", choices=["batch", "molecular_crystal", "slab"], default=None,
+                    help="run only this extra workload (one GPU, rank 0) and print its JSON; for profiling")
     return ap.parse_args()
 
 
@@ -368,6 +370,11 @@ def main():
     from paper_2509_16460_gb300 import workloads as W
 
     torch.cuda.set_device(local)
+    if args.leg:
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        legs = {"batch": batch_leg, "molecular_crystal": cfg3_leg, "slab": slab_leg}
+        print(json.dumps({"leg": args.leg, **legs[args.leg](ftcj, W, torch, flush, args.steps)}), flush=True)
+        return 0
     dist = None
     if world > 1:
         import torch.distributed as dist
