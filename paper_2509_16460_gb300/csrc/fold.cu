@@ -402,9 +402,10 @@ __device__ __forceinline__ void tri_index(long long t, int n, int& mu, int& nu) 
 // The fold of a Hermitian D^k (D^k_{nu mu} = conj D^k_{mu nu}): then
 // D^{0n}_{nu mu} = D^{0,-n}_{mu nu}, so only the upper triangle mu <= nu is read
 // and transformed, and each result is also written, transposed, at cell -n.
-// Same arithmetic and lane layout as k_fold_reg<0, N2, N3, G3>.
+// Same arithmetic and lane layout as k_fold_reg<0, N2, N3, G3>.  Six blocks
+// per SM (80 registers): a 240-AO cell's 904 blocks then run in one wave.
 template <int N2, int N3, bool G3>
-__global__ void __launch_bounds__(kRegBlock) k_fold_reg_herm(const double2* __restrict__ in, double* __restrict__ out,
+__global__ void __launch_bounds__(kRegBlock, G3 ? 1 : 6) k_fold_reg_herm(const double2* __restrict__ in, double* __restrict__ out,
                                                              int nao, long long T, int N1, df inv_nk) {
     constexpr int P = N2 * N3;
     const LaneGroup lg = lane_group(N1);
