@@ -80,6 +80,35 @@ def test_split_cfg2_diamond_full(orc, F):
     split_check(orc, F, W.cfg2(), steps=False)
 
 
+def test_split_class_parts_against_oracle(orc, F):
+    """s, p and d shells on two centres of a 12-bohr cell, about 2,650
+    half-sphere points in one 4096-point chunk: shared memory holds the
+    one-kernel walks below three blocks per SM, so both walks run by class
+    (classes 3-4 and 0-2 as separate launches, the J parts side by side).
+    Against the oracle, and against the one-kernel walks of the same cell
+    (512-point chunks and an explicit rho block count)."""
+    import torch
+    spec = [(0, 0, [0.3, 2.0]), (0, 1, [0.6]), (0, 2, [0.9]), (1, 0, [0.5]), (1, 1, [1.1]), (1, 2, [0.7])]
+    w = W.tiny(seed=35, A=np.diag([12.0, 11.5, 12.5]), shell_spec=spec, omega=0.5, kmesh=(2, 1, 1))
+    ref = orc.lrj(w)
+    Dk = torch.from_numpy(np.ascontiguousarray(w.Dk)).cuda()
+    parts = F.Plan.from_workload(w, precision=F.FTCJ_PREC_SPLIT, chunk_points=4096)
+    whole = F.Plan.from_workload(w, precision=F.FTCJ_PREC_SPLIT, chunk_points=512, rho_blocks=64)
+    assert parts.info["nchunks"] == 1 and whole.info["nchunks"] > 1
+    assert parts.launches_per_batch() == whole.launches_per_batch() + 2  # rho and J in two launches each
+    out = []
+    for plan in (parts, whole):
+        Jk, EJ = plan.jbuild(Dk)
+        torch.cuda.synchronize()
+        Jk, EJ = Jk.cpu().numpy(), EJ.cpu().numpy()
+        dJ = float(np.abs(Jk - ref["Jk"]).max())
+        dE = float(np.abs(EJ - ref["EJ"]).max())
+        assert dJ <= SPLIT_J_TOL and dE <= SPLIT_E_TOL, (dJ, dE)
+        out.append(Jk)
+        plan.close()
+    assert np.abs(out[0] - out[1]).max() <= 1e-12 * max(1.0, np.abs(ref["Jk"]).max())
+
+
 def test_split_cfg3_against_fp64_form(F):
     """Full molecular-crystal cell: the split form against the FP64 form (which is
     itself checked against the oracle at sampled G and by invariants)."""
