@@ -105,6 +105,14 @@ typedef struct {
                              screening estimate 8 pi eta G (4 pi/G^2) e^{-G^2/4w^2} |rho_ab(G)|
                              falls under this value (split form only; EUNSUPPORTED with FP64).
                              0: every pair over the whole sphere. */
+    int shard_count;    /* > 1: a record-sharded plan for one of shard_count GPUs: it keeps only
+                           share shard_index (0-based) of the screened pair records, a contiguous
+                           range of their class-sorted order balanced by the walks' per-record cost
+                           (ftcj_shard_bounds).  The shards' ftcj_rho and ftcj_jback outputs are
+                           partial sums, to be summed across the shards (an all-reduce) before
+                           ftcj_potential resp. ftcj_unfold_j; ftcj_jbuild, ftcj_jbuild_host and
+                           ftcj_grad refuse a shard plan (EINVAL).  <= 1: the whole pair list. */
+    int shard_index;
 } ftcj_params;
 
 typedef struct {
@@ -147,6 +155,14 @@ typedef struct ftcj_plan ftcj_plan;
  * longer than the walk chunk), ENOMEM, ECUDA. */
 int ftcj_plan_create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3],
                      const ftcj_params* params, ftcj_plan** out);
+
+/* The record shares of a sharded build (host only, no device needed): records
+ * sorted by class L (class_counts[L] of them, L = 0..4) are cut into
+ * shard_count contiguous ranges of nearly equal walk cost, per record 38 L +
+ * 100 FP32 operations per point in the split form, 4 L + 24 FP64 operations in
+ * the FP64 form.  bounds[0..shard_count] (written): share s is records
+ * [bounds[s], bounds[s+1]).  Errors: EINVAL. */
+int ftcj_shard_bounds(const int64_t* class_counts, int precision, int shard_count, int64_t* bounds);
 
 /* Sizes and counts of a plan (host struct, filled by the call). */
 int ftcj_plan_info(const ftcj_plan* plan, ftcj_info* out);

@@ -31,6 +31,15 @@ int j_walk(ftcj_plan* P, int nd, const double* W, cudaStream_t s) {
     return P->precision == FTCJ_PREC_SPLIT ? launch_j_walk_split(P, nd, W, s) : launch_j_walk(P, nd, W, s);
 }
 
+// the whole-build calls need every pair record: a shard plan's partial rho
+// and J^{0n} must be summed across the shards between the steps
+int whole_plan(const ftcj_plan* P) {
+    if (P->shard_count > 1)
+        return fail(FTCJ_EINVAL, "a shard plan (shard_count > 1) runs the step calls, with the partial rho and "
+                                 "J^{0n} summed across the shards between them");
+    return FTCJ_OK;
+}
+
 int check(const ftcj_plan* P, int ndens, bool batch_limit) {
     if (!P) return fail(FTCJ_EINVAL, "null plan");
     if (ndens < 1) return fail(FTCJ_EINVAL, "ndens must be >= 1");
@@ -123,6 +132,7 @@ int ftcj_unfold_j(ftcj_plan* P, int ndens, const double* J0n, double* Jk, void* 
 int ftcj_jbuild(ftcj_plan* P, int ndens, const double* Dk, double* Jk, double* EJ, void* stream) {
     int rc = check(P, ndens, false);
     if (rc) return rc;
+    if ((rc = whole_plan(P))) return rc;
     if (!Dk || !Jk || !EJ) return fail(FTCJ_EINVAL, "null buffer");
     cudaStream_t s = as_stream(stream);
     size_t per = (size_t)P->nk * P->nao * P->nao * 2;  // doubles per complex density
@@ -137,6 +147,7 @@ int ftcj_jbuild_host(ftcj_plan* P, int ndens, const double* Dk_host, double* Jk_
                      void* stream) {
     int rc = check(P, ndens, false);
     if (rc) return rc;
+    if ((rc = whole_plan(P))) return rc;
     if (!Dk_host || !Jk_host || !EJ_host) return fail(FTCJ_EINVAL, "null buffer");
     cudaStream_t s = as_stream(stream);
     size_t per = (size_t)P->nk * P->nao * P->nao * 2;
@@ -165,6 +176,7 @@ int ftcj_jbuild_host(ftcj_plan* P, int ndens, const double* Dk_host, double* Jk_
 int ftcj_grad(ftcj_plan* P, int ndens, const double* Dk, double* EJ, double* grad, void* stream) {
     int rc = check(P, ndens, false);
     if (rc) return rc;
+    if ((rc = whole_plan(P))) return rc;
     if (!Dk || !EJ || !grad) return fail(FTCJ_EINVAL, "null buffer");
     cudaStream_t s = as_stream(stream);
     size_t per = (size_t)P->nk * P->nao * P->nao * 2;

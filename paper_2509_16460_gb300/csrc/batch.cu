@@ -95,6 +95,8 @@ int ftcj_autotune(const ftcj_cell* cell, const ftcj_basis* basis, const int kmes
             ftcj_params p = *in;
             p.max_dens = 1;
             p.chunk_points = ch;
+            p.shard_count = 0;  // a share's walks take the shape of the whole plan's
+            p.shard_index = 0;
             // the plan's own count (it fills the GPU, and splits the walk by
             // class where shared memory calls for it), then twice the fill
             p.rho_blocks = mult == 1 ? 0 : 2 * npb_fill;
@@ -144,6 +146,8 @@ int ftcj_autotune(const ftcj_cell* cell, const ftcj_basis* basis, const int kmes
                 best_t = t;
                 best = p;
                 best.max_dens = in->max_dens;
+                best.shard_count = in->shard_count;
+                best.shard_index = in->shard_index;
             }
             if (2 * npb_fill > tiles) break;  // no more blocks than tiles
         }
@@ -167,6 +171,10 @@ int ftcj_batch_create(int ncell, const ftcj_cell* cells, const ftcj_basis* bases
     int rc = FTCJ_OK;
     for (int c = 0; c < ncell && rc == FTCJ_OK; ++c) {
         ftcj_params p = params[c];
+        if (p.shard_count > 1) {
+            rc = fail(FTCJ_EINVAL, "a batch takes whole plans (shard_count <= 1)");
+            break;
+        }
         if (flags & FTCJ_BATCH_AUTOTUNE) rc = ftcj_autotune(&cells[c], &bases[c], kmeshes + 3 * c, &params[c], &p,
                                                             nullptr);
         ftcj_plan* P = nullptr;

@@ -153,6 +153,7 @@ struct ftcj_plan {
     int n_abs_max;  // largest |n_i| of the sphere's G = sum_i n_i b_i
     // pairs
     int64_t npairs, npairs_ordered;
+    int shard_count = 1, shard_index = 0;  // record-sharded plan: share shard_index of shard_count
     int64_t class_start[ftcj::kNclass + 1];
     int64_t term_base[ftcj::kNclass];  // SoA offset of each class in a per-density term array
     int64_t total_terms;
@@ -270,7 +271,9 @@ int setup_split(ftcj_plan* P);
 int split_xtab_entries(const ftcj_plan* P);  // 0 when the split walks run the n1 recurrence
 size_t split_rho_smem(const ftcj_plan* P, int part);  // shared memory of one split structure-factor block (part: 0 all classes, 1 classes 0-2)
 int launch_pair_gcut(ftcj_plan* P);      // per-record cutoffs from the (double) maps, in build_maps
-int apply_pair_cutoffs(ftcj_plan* P);    // sort records by cutoff within each class, radius per tile
+int apply_pair_cutoffs(ftcj_plan* P);
+int keep_record_share(ftcj_plan* P);
+void shard_bounds(const int64_t* class_counts, int precision, int shard_count, int64_t* bounds);    // sort records by cutoff within each class, radius per tile
 int rho_walk_split_blocks_per_sm(ftcj_plan* P, int part, int* out);  // part: 0 all, 1 classes 0-2, 2 classes 3-4
 int launch_rho_walk_split(ftcj_plan* P, int ndens, cudaStream_t s);
 int launch_j_walk_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s);

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "ftcj_internal.h"
@@ -38,6 +39,80 @@ int permute(ftcj_plan* P, T** ptr, const int* d_perm, long long n) {
 }
 
 }  // namespace
+
+// Share s of a sharded build: the records sorted by class are cut where the
+// running walk cost (per record and point: 38 L + 100 FP32 operations in the
+// split form, 4 L + 24 FP64 operations in the FP64 form, the same constants as
+// the rho-walk schedule) first reaches s / S of the total, so that the shares
+// take nearly equal walk time on equal GPUs.
+void shard_bounds(const int64_t* class_counts, int precision, int shard_count, int64_t* bounds) {
+    auto cost = [&](int L) { return precision == FTCJ_PREC_SPLIT ? 38.0 * L + 100.0 : 4.0 * L + 24.0; };
+    double total = 0.0;
+    int64_t n = 0;
+    for (int c = 0; c < kNclass; ++c) {
+        total += cost(c) * (double)class_counts[c];
+        n += class_counts[c];
+    }
+    bounds[0] = 0;
+    for (int s = 1; s < shard_count; ++s) {
+        // the first record index whose running cost reaches s / S of the total
+        const double target = total * s / shard_count;
+        double acc = 0.0;
+        int64_t start = 0, b = n;
+        for (int c = 0; c < kNclass; ++c) {
+            const double w = cost(c), here = w * (double)class_counts[c];
+            if (acc + here >= target) {
+                b = start + (int64_t)std::ceil((target - acc) / w - 1e-9);
+                break;
+            }
+            acc += here;
+            start += class_counts[c];
+        }
+        bounds[s] = std::min(std::max(b, bounds[s - 1]), n);
+    }
+    bounds[shard_count] = n;
+}
+
+// Keeps only this plan's share of the class-sorted records (a contiguous
+// range): the per-record arrays are cut to it, the class boundaries and the
+// ordered-pair count follow.
+int keep_record_share(ftcj_plan* P) {
+    if (P->shard_count <= 1) return FTCJ_OK;
+    int64_t counts[kNclass];
+    for (int c = 0; c < kNclass; ++c) counts[c] = P->class_start[c + 1] - P->class_start[c];
+    std::vector<int64_t> b((size_t)P->shard_count + 1);
+    shard_bounds(counts, P->precision, P->shard_count, b.data());
+    const long long first = b[P->shard_index], count = b[P->shard_index + 1] - first;
+    std::vector<PairDev> pr((size_t)count);
+    if (count > 0)
+        FTCJ_CUDA(cudaMemcpy(pr.data(), P->d_pairs + first, sizeof(PairDev) * pr.size(), cudaMemcpyDeviceToHost));
+    auto cut = [&](auto** ptr, size_t elem) -> int {
+        void* fresh = nullptr;
+        FTCJ_CUDA(cudaMalloc(&fresh, elem * (size_t)std::max<long long>(count, 1)));
+        if (count > 0) {
+            cudaError_t e = cudaMemcpy(fresh, reinterpret_cast<char*>(*ptr) + elem * (size_t)first,
+                                       elem * (size_t)count, cudaMemcpyDeviceToDevice);
+            if (e != cudaSuccess) {
+                cudaFree(fresh);
+                return cuda_fail(e, "record share copy");
+            }
+        }
+        cudaFree(*ptr);
+        *ptr = static_cast<std::remove_reference_t<decltype(**ptr)>*>(fresh);
+        return FTCJ_OK;
+    };
+    int rc = cut(&P->d_pairs, sizeof(PairDev));
+    if (!rc) rc = cut(&P->d_walk, sizeof(PairWalk));
+    if (rc) return rc;
+    for (int c = 0; c <= kNclass; ++c)
+        P->class_start[c] = std::min<int64_t>(std::max<int64_t>(P->class_start[c] - first, 0), count);
+    P->npairs = count;
+    P->npairs_ordered = 0;
+    for (const PairDev& r : pr)
+        P->npairs_ordered += (int64_t)(P->groups[r.ga].mem1 - P->groups[r.ga].mem0) *
+                             (P->groups[r.gb].mem1 - P->groups[r.gb].mem0) * r.weight;
+    return FTCJ_OK;
+}
 
 int apply_pair_cutoffs(ftcj_plan* P) {
     const long long n = P->npairs;

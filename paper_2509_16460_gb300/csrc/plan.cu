@@ -359,6 +359,10 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     P->precision = prm->precision;
     if (!(prm->pair_gcut_eps >= 0.0) || !finite(prm->pair_gcut_eps))
         return fail(FTCJ_EINVAL, "pair_gcut_eps must be a finite number >= 0");
+    if (prm->shard_count > 1 && (prm->shard_index < 0 || prm->shard_index >= prm->shard_count))
+        return fail(FTCJ_EINVAL, "shard_index must be in [0, shard_count)");
+    P->shard_count = std::max(1, prm->shard_count);
+    P->shard_index = P->shard_count > 1 ? prm->shard_index : 0;
     if (prm->pair_gcut_eps > 0.0 && prm->precision != FTCJ_PREC_SPLIT)
         return fail(FTCJ_EUNSUPPORTED, "per-pair G cutoffs are implemented in the split form's walks");
     if (!(prm->pair_thresh > 0.0 && prm->pair_thresh < 1.0)) return fail(FTCJ_EINVAL, "pair_thresh in (0,1)");
@@ -470,6 +474,7 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     if ((rc = dalloc(P, &P->d_tw, (size_t)3 * 16 * 16 * 2))) return rc;
 
     if ((rc = screen_and_sort(P))) return rc;
+    if ((rc = keep_record_share(P))) return rc;
 
     // per-class SoA layout of the Hermite terms
     P->total_terms = 0;
@@ -560,6 +565,14 @@ const char* ftcj_strerror(int code) {
 }
 
 const char* ftcj_last_error(void) { return g_last_error.c_str(); }
+
+int ftcj_shard_bounds(const int64_t* class_counts, int precision, int shard_count, int64_t* bounds) {
+    if (!class_counts || !bounds || shard_count < 1) return fail(FTCJ_EINVAL, "bad argument");
+    for (int c = 0; c < kNclass; ++c)
+        if (class_counts[c] < 0) return fail(FTCJ_EINVAL, "negative class count");
+    shard_bounds(class_counts, precision, shard_count, bounds);
+    return FTCJ_OK;
+}
 
 int ftcj_plan_create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], const ftcj_params* params,
                      ftcj_plan** out) {

@@ -41,7 +41,7 @@ class BasisDesc(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("omega", _c_double), ("gcut", _c_double), ("eps_g", _c_double), ("pair_thresh", _c_double),
                 ("precision", _c_int), ("max_dens", _c_int), ("chunk_points", _c_int), ("rho_blocks", _c_int),
-                ("pair_gcut_eps", _c_double)]
+                ("pair_gcut_eps", _c_double), ("shard_count", _c_int), ("shard_index", _c_int)]
 
 
 class Info(ctypes.Structure):
@@ -65,7 +65,7 @@ EXPORTED = [
     "ftcj_get_gvectors", "ftcj_get_pairs", "ftcj_get_groups", "ftcj_strerror", "ftcj_last_error",
     "ftcj_profile_enable", "ftcj_profile_read", "ftcj_launches_per_batch", "ftcj_probe_fma_peak",
     "ftcj_potential_noalloc", "ftcj_batch_create", "ftcj_batch_info", "ftcj_batch_jbuild", "ftcj_batch_capture",
-    "ftcj_batch_replay", "ftcj_batch_destroy", "ftcj_autotune", "ftcj_grad",
+    "ftcj_batch_replay", "ftcj_batch_destroy", "ftcj_autotune", "ftcj_grad", "ftcj_shard_bounds",
 ]
 
 FTCJ_BATCH_AUTOTUNE = 1
@@ -129,6 +129,7 @@ def _declare(L):
     L.ftcj_autotune.argtypes = [ctypes.POINTER(Cell), ctypes.POINTER(BasisDesc), _ip, ctypes.POINTER(Params),
                                 ctypes.POINTER(Params), _dp]
     L.ftcj_grad.argtypes = [P, _c_int, P, P, P, P]
+    L.ftcj_shard_bounds.argtypes = [ctypes.POINTER(ctypes.c_int64), _c_int, _c_int, ctypes.POINTER(ctypes.c_int64)]
     L.ftcj_strerror.argtypes = [_c_int]
     L.ftcj_strerror.restype = ctypes.c_char_p
     L.ftcj_last_error.argtypes = []
@@ -187,7 +188,16 @@ def _describe(A, xyz, shells, keep):
 
 def _params_of(w, precision=FTCJ_PREC_FP64, max_dens=None, chunk_points=0, rho_blocks=0, pair_gcut_eps=0.0):
     return Params(float(w.omega), float(w.gcut), float(w.eps_g), float(w.pair_thresh), int(precision),
-                  int(max_dens or w.ndens), int(chunk_points), int(rho_blocks), float(pair_gcut_eps))
+                  int(max_dens or w.ndens), int(chunk_points), int(rho_blocks), float(pair_gcut_eps), 0, 0)
+
+
+def shard_bounds(class_counts, precision, shard_count):
+    """ftcj_shard_bounds: the record ranges [b[s], b[s+1]) of a sharded build
+    (host only)."""
+    cc = (ctypes.c_int64 * 5)(*[int(c) for c in class_counts])
+    out = (ctypes.c_int64 * (int(shard_count) + 1))()
+    _check(lib().ftcj_shard_bounds(cc, int(precision), int(shard_count), out), "ftcj_shard_bounds")
+    return [int(v) for v in out]
 
 
 def autotune(w, precision=FTCJ_PREC_FP64):
@@ -289,13 +299,16 @@ class Plan:
     """A plan for one cell, basis and k-mesh (ftcj_plan_create)."""
 
     def __init__(self, A, xyz, shells, kmesh, omega, eps_g=1e-14, gcut=0.0, pair_thresh=1e-12,
-                 precision=FTCJ_PREC_FP64, max_dens=1, chunk_points=0, rho_blocks=0, pair_gcut_eps=0.0):
+                 precision=FTCJ_PREC_FP64, max_dens=1, chunk_points=0, rho_blocks=0, pair_gcut_eps=0.0,
+                 shard_count=0, shard_index=0):
         L = lib()
         self._keep = []
         cell, basis = _describe(A, xyz, shells, self._keep)
         km = (ctypes.c_int * 3)(*[int(k) for k in kmesh])
         prm = Params(float(omega), float(gcut), float(eps_g), float(pair_thresh), int(precision), int(max_dens),
-                     int(chunk_points), int(rho_blocks), float(pair_gcut_eps))
+                     int(chunk_points), int(rho_blocks), float(pair_gcut_eps), int(shard_count), int(shard_index))
+        self.shard_count = max(1, int(shard_count))
+        self.shard_index = int(shard_index)
         h = _c_void_p()
         _check(L.ftcj_plan_create(ctypes.byref(cell), ctypes.byref(basis), km, ctypes.byref(prm), ctypes.byref(h)),
                "ftcj_plan_create")
@@ -312,11 +325,11 @@ class Plan:
 
     @classmethod
     def from_workload(cls, w, max_dens=None, precision=FTCJ_PREC_FP64, chunk_points=0, rho_blocks=0,
-                      pair_gcut_eps=0.0):
+                      pair_gcut_eps=0.0, shard_count=0, shard_index=0):
         return cls(w.A, w.xyz, w.shells, w.kmesh, w.omega, eps_g=w.eps_g, gcut=w.gcut, pair_thresh=w.pair_thresh,
                    precision=precision, max_dens=max_dens or w.ndens, chunk_points=chunk_points,
-                   pair_gcut_eps=pair_gcut_eps,
-                   rho_blocks=rho_blocks)
+                   pair_gcut_eps=pair_gcut_eps, rho_blocks=rho_blocks, shard_count=shard_count,
+                   shard_index=shard_index)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -549,6 +562,35 @@ def _autograd_function():
 
 
 _LRC = None
+
+
+def sharded_jbuild(plan, Dk, group=None, all_reduce=None):
+    """The build of a record-sharded plan (shard_count > 1; one plan, GPU and
+    rank per share): J^k and E_J of the whole pair list on every rank.  The
+    partial rho(G) and J^{0n} of the shards are summed across the ranks of
+    `group` between the steps (torch.distributed all-reduce: NCCL on GPUs,
+    gloo in host tests; `all_reduce(tensor)` may replace it), and the potential
+    and the unfold run on the sums.  Every step is the library's."""
+    import torch
+    if all_reduce is None:
+        import torch.distributed as dist
+
+        def all_reduce(t):
+            dist.all_reduce(t, group=group)
+    nd = Dk.shape[0]
+    Jk = torch.empty(Dk.shape, dtype=torch.complex128, device=Dk.device)
+    EJ = torch.empty(nd, dtype=torch.float64, device=Dk.device)
+    for b0 in range(0, nd, plan.max_dens):
+        b1 = min(nd, b0 + plan.max_dens)
+        D0n = plan.fold_density(Dk[b0:b1].contiguous())
+        rho = plan.rho(D0n)
+        all_reduce(torch.view_as_real(rho))
+        W, E = plan.potential(rho)
+        J0n = plan.jback(W)
+        all_reduce(J0n)
+        Jk[b0:b1] = plan.unfold_j(J0n)
+        EJ[b0:b1] = E
+    return Jk, EJ
 
 
 def long_range_energy(Dk, xyz, plan):
