@@ -226,7 +226,12 @@ int ftcj_potential(ftcj_plan* plan, int ndens, const double* rho, double* W, dou
  * it keeps the last call's contents; calls that overlap on the GPU share it
  * and race, so serialise them.  The first call on a device looks up the
  * array's device address with that device current; make that first call
- * before any stream capture.  Errors: EINVAL when ndens * ceil(ng/256) >
+ * before any stream capture.  The address is cached per device ordinal for
+ * the life of the process, which assumes the device's primary context lives
+ * that long: after cudaDeviceReset (or any re-creation of the primary
+ * context) the cached address is stale, so do not call this entry point
+ * again in that process.  All pointers must be on the current device, and
+ * `stream` must belong to it.  Errors: EINVAL when ndens * ceil(ng/256) >
  * FTCJ_NOALLOC_MAX_PARTIALS (split the densities over several calls), for a
  * singular lattice, or omega <= 0.  The paper has no counterpart to this
  * entry point. */

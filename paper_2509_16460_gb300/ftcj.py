@@ -510,16 +510,24 @@ def potential_noalloc(A, omega, gvec, rho, W=None, EJ=None, stream=None):
     [ndens, ng]; W and E_J are allocated here by torch when not given."""
     import torch
     nd, ng = int(rho.shape[0]), int(rho.shape[1])
+    dev = rho.device
     if W is None:
-        W = torch.empty((nd, ng), dtype=torch.complex128, device=rho.device)
+        W = torch.empty((nd, ng), dtype=torch.complex128, device=dev)
     if EJ is None:
-        EJ = torch.empty(nd, dtype=torch.float64, device=rho.device)
+        EJ = torch.empty(nd, dtype=torch.float64, device=dev)
+    # the library takes the scratch array's address and the default stream of
+    # the CURRENT device: every tensor must live there, and that device is made
+    # current for the call
+    for name, t in (("gvec", gvec), ("W", W), ("EJ", EJ)):
+        if t.device != dev:
+            raise FtcjError(f"{name} is on {t.device}, rho on {dev}: all four must share one device")
     Ah = (ctypes.c_double * 9)(*[float(x) for x in np.asarray(A, dtype=np.float64).ravel()])
-    _check(lib().ftcj_potential_noalloc(Ah, float(omega), nd, ng, _dev_ptr(gvec, torch.int32, (ng, 3), "gvec"),
-                                        _dev_ptr(rho, torch.complex128, (nd, ng), "rho"),
-                                        _dev_ptr(W, torch.complex128, (nd, ng), "W"),
-                                        _dev_ptr(EJ, torch.float64, (nd,), "EJ"), _stream_ptr(stream)),
-           "ftcj_potential_noalloc")
+    with torch.cuda.device(dev):
+        _check(lib().ftcj_potential_noalloc(Ah, float(omega), nd, ng, _dev_ptr(gvec, torch.int32, (ng, 3), "gvec"),
+                                            _dev_ptr(rho, torch.complex128, (nd, ng), "rho"),
+                                            _dev_ptr(W, torch.complex128, (nd, ng), "W"),
+                                            _dev_ptr(EJ, torch.float64, (nd,), "EJ"), _stream_ptr(stream)),
+               "ftcj_potential_noalloc")
     return W, EJ
 
 

@@ -155,6 +155,17 @@ def rotation(rng: np.random.Generator) -> np.ndarray:
     ])
 
 
+def min_image_distance(A: np.ndarray, f1: np.ndarray, f2: np.ndarray, reach: int = 2) -> float:
+    """Shortest distance between two sites given in fractional coordinates,
+    over the lattice translations with |T_i| <= reach (enough for the cells
+    drawn here, whose angles stay within 60-120 degrees)."""
+    d = np.asarray(f1, float) - np.asarray(f2, float)
+    d -= np.round(d)
+    r = np.arange(-reach, reach + 1)
+    T = np.stack(np.meshgrid(r, r, r, indexing="ij"), axis=-1).reshape(-1, 3)
+    return float(np.min(np.linalg.norm((d[None, :] + T) @ A, axis=1)))
+
+
 # ----------------------------------------------------------------------------
 # element templates (synthetic, geometric exponent sequences)
 # ----------------------------------------------------------------------------
@@ -312,17 +323,22 @@ def cfg5(seed: int = 5, kmesh=(3, 3, 1)) -> Workload:
     xyz: List[np.ndarray] = []
     kinds: List[str] = []
     for layer in range(4):
+        fr: List[np.ndarray] = []
         for i in range(4):
             for j in range(-2, 2):
                 p = i * u + j * v
                 f = np.linalg.solve(A.T, p)
-                f -= np.floor(f)
-                pos = f @ A + np.array([0, 0, layer * d])
-                if any(np.linalg.norm(pos - q) < 1e-6 for q in xyz):
+                # wrap into [0, 1) with a tolerance, so that a site on the cell
+                # boundary (f = 1 - eps) lands on 0 and is seen as an image
+                f = np.mod(np.round(f, 10), 1.0)
+                if any(min_image_distance(A, f, g) < 1e-6 for g in fr):
                     continue
-                xyz.append(pos)
+                fr.append(f)
+                xyz.append(f @ A + np.array([0, 0, layer * d]))
                 kinds.append("Mg" if (i + j + layer) % 2 == 0 else "O")
-    # keep 8 per layer: the square cell of side 2*sqrt(2)*d holds 8 lattice sites
+        # the square cell of side 2 sqrt(2) d holds 8 sites of a rock-salt (001) layer
+        if len(fr) != 8:
+            raise AssertionError(f"slab layer {layer}: {len(fr)} sites, expected 8")
     top = max(p[2] for p in xyz)
     mg_top = [p for p, k in zip(xyz, kinds) if k == "Mg" and abs(p[2] - top) < 1e-6][0]
     xyz.append(mg_top + np.array([0, 0, 4.3]))

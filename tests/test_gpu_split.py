@@ -1,6 +1,9 @@
 """GPU parity of the split-precision form (double-float walks) against the FP64
 CPU oracle.  Bar: max|dJ| <= 1e-8 Eh and |dE_J| <= 1e-8 Eh (the bound stated
-for the split form); the measured errors are printed."""
+for the split form), and max|dJ| <= 1e-11 Eh, a bar 100x above the measured
+level (~1e-13), so that a regression of the double-float path by orders of
+magnitude fails here although it would still meet the bound; the measured
+errors are printed."""
 import dataclasses
 
 import numpy as np
@@ -13,6 +16,7 @@ pytestmark = pytest.mark.gpu
 
 SPLIT_J_TOL = 1e-8
 SPLIT_E_TOL = 1e-8
+SPLIT_J_MEASURED_BAR = 1e-11
 
 
 @pytest.fixture(scope="module")
@@ -40,6 +44,7 @@ def split_check(orc, F, w, steps=True):
     print(f"{w.name}: split max|dJ|={dJ:.3e} |dE|={dE:.3e} max|J|={np.abs(ref['Jk']).max():.3e}")
     assert dJ <= SPLIT_J_TOL, (w.name, dJ)
     assert dE <= SPLIT_E_TOL, (w.name, dE)
+    assert dJ <= SPLIT_J_MEASURED_BAR, (w.name, dJ)
     if steps:
         compare_pairs(orc, plan, w)
         nd = min(w.ndens, plan.max_dens)
