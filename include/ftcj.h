@@ -143,6 +143,9 @@ typedef struct {
                                  needs <= 63) */
     int grad_split;           /* 1: ftcj_grad's back-contraction runs in double-float (split
                                  form with n_abs_max <= 27), 0: in FP64 */
+    int rho_walk_launches;    /* kernel launches of one structure-factor walk pass: 2 where the
+                                 split form runs it as two class parts, else 1 (0: nothing to walk) */
+    int j_walk_launches;      /* the same for the back-contraction walk */
 } ftcj_info;
 
 typedef struct ftcj_plan ftcj_plan;

@@ -621,6 +621,9 @@ int ftcj_plan_info(const ftcj_plan* P, ftcj_info* o) {
     o->pair_g_units_walked = P->d_rec_gcut ? P->units_walked : o->pair_g_units;
     o->n_abs_max = P->n_abs_max;
     o->grad_split = P->precision == FTCJ_PREC_SPLIT && split_grad_walk_exact(P) ? 1 : 0;
+    const bool walks = P->ng_half > 0 && !P->tiles.empty();
+    o->rho_walk_launches = walks ? (P->rho_hi_tiles > 0 ? 2 : 1) : 0;
+    o->j_walk_launches = walks ? (P->precision == FTCJ_PREC_SPLIT ? split_j_launches(P) : 1) : 0;
     return FTCJ_OK;
 }
 

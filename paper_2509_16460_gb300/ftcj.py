@@ -51,7 +51,8 @@ class Info(ctypes.Structure):
                 ("pairs_by_class", ctypes.c_int64 * 5), ("nlines", _c_int), ("nchunks", _c_int),
                 ("gcut", _c_double), ("volume", _c_double), ("device_bytes", ctypes.c_size_t),
                 ("rho_blocks", _c_int), ("n1_table", _c_int), ("pair_g_units_screened", ctypes.c_int64),
-                ("pair_g_units_walked", ctypes.c_int64), ("n_abs_max", _c_int), ("grad_split", _c_int)]
+                ("pair_g_units_walked", ctypes.c_int64), ("n_abs_max", _c_int), ("grad_split", _c_int),
+                ("rho_walk_launches", _c_int), ("j_walk_launches", _c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
