@@ -69,12 +69,16 @@ def errors(Jk, EJ, ref):
 def test_class_split_multichunk_two_densities_against_oracle(F, case):
     w, ref = case
     parts, Jp, Ep = build(F, w, precision=F.FTCJ_PREC_SPLIT, chunk_points=4096)
-    whole, Jw, Ew = build(F, w, precision=F.FTCJ_PREC_SPLIT, chunk_points=1024, rho_blocks=2 * 152)
+    # 512-point chunks keep three one-kernel J blocks per SM; an explicit block
+    # count runs the one-kernel structure-factor walk
+    whole, Jw, Ew = build(F, w, precision=F.FTCJ_PREC_SPLIT, chunk_points=512, rho_blocks=2 * 152)
     try:
         assert parts.info["ng_half"] == 4977
         assert parts.info["nchunks"] == 2 and whole.info["nchunks"] > 2
         assert w.ndens == 2 and parts.max_dens == 2
         # rho walk and J walk each in two class launches against one
+        assert (parts.info["rho_walk_launches"], parts.info["j_walk_launches"]) == (2, 2)
+        assert (whole.info["rho_walk_launches"], whole.info["j_walk_launches"]) == (1, 1)
         assert parts.launches_per_batch() == whole.launches_per_batch() + 2
         assert all(n > 0 for n in parts.info["pairs_by_class"])
         scale = np.abs(ref["Jk"]).max()
