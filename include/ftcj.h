@@ -113,7 +113,15 @@ typedef struct {
                            ftcj_potential resp. ftcj_unfold_j; ftcj_jbuild, ftcj_jbuild_host and
                            ftcj_grad refuse a shard plan (EINVAL).  <= 1: the whole pair list. */
     int shard_index;
+    int contraction;    /* FTCJ_CONTRACT_WALK (0): the G walks for the structure-factor pass;
+                           FTCJ_CONTRACT_TC (1): the tensor-core separable contraction (Sec. 2.4,
+                           orthorhombic fully separable case): rho(n) as a sliced bf16 tcgen05 matrix
+                           product over (pair record, i, j), split form and orthorhombic cells only
+                           (EUNSUPPORTED otherwise), whole sphere (pair_gcut_eps = 0) */
 } ftcj_params;
+
+#define FTCJ_CONTRACT_WALK 0
+#define FTCJ_CONTRACT_TC 1
 
 typedef struct {
     int nao;                  /* AOs per cell */
@@ -268,6 +276,12 @@ int ftcj_unfold_j(ftcj_plan* plan, int ndens, const double* J0n, double* Jk, voi
  * (the FP64 one walks the whole sphere).
  * Asynchronous on `stream`. */
 int ftcj_grad(ftcj_plan* plan, int ndens, const double* Dk, double* EJ, double* grad, void* stream);
+
+/* Device error word of the plan's kernels that wait on one another inside a
+ * block (the tensor-core contraction): bit 0 set when a bounded wait gave up
+ * (the results of that build are invalid).  Synchronises `stream`, returns
+ * the word in *flags and clears it.  A plan without such kernels reports 0. */
+int ftcj_plan_status(ftcj_plan* plan, int* flags, void* stream);
 
 /* Largest |Im D^{0n}| and largest |D^{0n}_{mu nu} - D^{0,-n}_{nu mu}| of
  * the input (host doubles out), i.e. how far D^k is from the precondition.

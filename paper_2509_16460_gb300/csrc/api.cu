@@ -24,6 +24,7 @@ void* device_alias(const void* host) {
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 int rho_walk(ftcj_plan* P, int nd, cudaStream_t s) {
+    if (P->tc) return launch_tc_rho(P, nd, s);
     return P->precision == FTCJ_PREC_SPLIT ? launch_rho_walk_split(P, nd, s) : launch_rho_walk(P, nd, s);
 }
 
@@ -192,6 +193,18 @@ int ftcj_grad(ftcj_plan* P, int ndens, const double* Dk, double* EJ, double* gra
             return rc;
         if ((rc = launch_grad_assemble(P, nd, P->d_D0n, grad + (size_t)b0 * P->ncentre * 3, s))) return rc;
     }
+    return FTCJ_OK;
+}
+
+int ftcj_plan_status(ftcj_plan* P, int* flags, void* stream) {
+    if (!P || !flags) return fail(FTCJ_EINVAL, "null argument");
+    cudaStream_t s = as_stream(stream);
+    *flags = 0;
+    if (P->d_tc_err) {
+        FTCJ_CUDA(cudaMemcpyAsync(flags, P->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FTCJ_CUDA(cudaMemsetAsync(P->d_tc_err, 0, sizeof(int), s));
+    }
+    FTCJ_CUDA(cudaStreamSynchronize(s));
     return FTCJ_OK;
 }
 

@@ -207,6 +207,24 @@ struct ftcj_plan {
     double* d_check = nullptr;       // [2]
     void* d_split_init = nullptr;    // split form: walk state at each chunk start, [nchunks][npairs]
     void* d_split_const = nullptr;   // split form: recurrence multipliers, [npairs]
+    // tensor-core separable contraction of the structure-factor pass (tc.cu)
+    bool tc = false;
+    int tc_axis[3] = {0, 1, 2};  // row axes a, b and the column axis c
+    int tc_ncols = 0, tc_nd = 0, tc_npad = 0;  // n_c = 0..ncols-1; densities per launch; MMA N
+    int tc_colw = 0, tc_G = 0;                 // real columns per (i, j) block; blocks per window
+    int tc_rows = 0, tc_mtiles = 0, tc_nna = 0, tc_nnb = 0, tc_tabw = 0;
+    int64_t tc_nkappa = 0;
+    int tc_nwin = 0, tc_wpg = 0, tc_ngroups = 0;  // K windows, windows per group, groups (partial rows)
+    int tc_tslots = 0;                            // stage-table slots in shared memory
+    void* d_tc_rows = nullptr;   // int2 [rows]
+    int* d_tc_map = nullptr;     // [rows][ncols]
+    int* d_tc_kappa = nullptr;   // [nwin * 512] record ids of each window
+    int* d_tc_wpairs = nullptr;  // (i | j << 3) of the windows' blocks
+    void* d_tc_winfo = nullptr;  // int4 [nwin]: class, blocks, first block
+    void* d_tc_tab = nullptr;    // float4 [npairs][tabw]
+    float* d_tc_cl = nullptr;    // [npairs]
+    int* d_tc_err = nullptr;     // device error word of the bounded waits
+    int rho_rows = 0;            // partial rows the rho reduction sums (walk blocks or tensor-core groups)
     int precision = FTCJ_PREC_FP64;
     bool ortho = false;  // reciprocal metric diagonal (orthorhombic cell)
     ftcj::CellConst cc;
@@ -279,6 +297,11 @@ int launch_rho_walk_split(ftcj_plan* P, int ndens, cudaStream_t s);
 int launch_j_walk_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s);
 int launch_j_walk_grad_split(ftcj_plan* P, int ndens, const double* W, cudaStream_t s);
 bool split_grad_walk_exact(const ftcj_plan* P);
+
+// --- tensor-core separable contraction (tc.cu) ---
+int setup_tc(ftcj_plan* P);
+int launch_tc_rho(ftcj_plan* P, int ndens, cudaStream_t s);
+int tc_rho_launches(const ftcj_plan* P, int nd);
 
 // --- measurement (profile.cu) ---
 void release_profiling(ftcj_plan* P);

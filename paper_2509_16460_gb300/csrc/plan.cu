@@ -301,7 +301,8 @@ void free_device(ftcj_plan* P) {
                     P->d_gvec, P->d_vg, P->d_tw, P->d_Tmat, P->d_D0n, P->d_J0n, P->d_cbuf0, P->d_cbuf1,
                     P->d_Dp, P->d_Jp, P->d_rho_part, P->d_rho, P->d_W, P->d_Epart, P->d_Dk_stage,
                     P->d_Jk_stage, P->d_EJ_stage, P->d_check, P->d_split_init, P->d_split_const, P->d_Jg,
-                    P->d_maps, P->d_map_off, P->d_sched, P->d_rec_gcut};
+                    P->d_maps, P->d_map_off, P->d_sched, P->d_rec_gcut, P->d_tc_rows, P->d_tc_map,
+                    P->d_tc_kappa, P->d_tc_tab, P->d_tc_cl, P->d_tc_err, P->d_tc_wpairs, P->d_tc_winfo};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (P->ev_fork) cudaEventDestroy(P->ev_fork);
@@ -365,6 +366,13 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     P->shard_index = P->shard_count > 1 ? prm->shard_index : 0;
     if (prm->pair_gcut_eps > 0.0 && prm->precision != FTCJ_PREC_SPLIT)
         return fail(FTCJ_EUNSUPPORTED, "per-pair G cutoffs are implemented in the split form's walks");
+    if (prm->contraction != FTCJ_CONTRACT_WALK && prm->contraction != FTCJ_CONTRACT_TC)
+        return fail(FTCJ_EINVAL, "contraction must be FTCJ_CONTRACT_WALK or FTCJ_CONTRACT_TC");
+    P->tc = prm->contraction == FTCJ_CONTRACT_TC;
+    if (P->tc && prm->precision != FTCJ_PREC_SPLIT)
+        return fail(FTCJ_EUNSUPPORTED, "the tensor-core contraction is part of the split-precision form");
+    if (P->tc && prm->pair_gcut_eps > 0.0)
+        return fail(FTCJ_EUNSUPPORTED, "the tensor-core contraction covers the whole sphere (pair_gcut_eps = 0)");
     if (!(prm->pair_thresh > 0.0 && prm->pair_thresh < 1.0)) return fail(FTCJ_EINVAL, "pair_thresh in (0,1)");
     P->omega = prm->omega;
     P->cc.vpar[0] = 4.0 * M_PI / P->vol;
@@ -519,6 +527,9 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
         P->npb = P->npb_hi + std::max(1, std::min(nlo, P->num_sms * bps_lo / nch));
     }
     if ((rc = build_rho_schedule(P))) return rc;
+    if (P->tc && !P->ortho) return fail(FTCJ_EUNSUPPORTED, "the tensor-core contraction needs an orthorhombic cell");
+    if (P->tc && (rc = setup_tc(P))) return rc;
+    P->rho_rows = P->tc ? P->tc_ngroups : P->npb;
 
     size_t nn = (size_t)P->nao * P->nao;
     size_t md = (size_t)P->max_dens;
@@ -529,7 +540,8 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     if ((rc = dalloc(P, &P->d_Dp, md * (size_t)P->total_terms))) return rc;
     if ((rc = dalloc(P, &P->d_Jp, md * (size_t)nch * (size_t)P->total_terms))) return rc;
     if ((rc = dalloc(P, &P->d_Jg, md * (size_t)nch * (size_t)P->total_terms_g))) return rc;
-    if ((rc = dalloc(P, &P->d_rho_part, 2 * md * (size_t)P->npb * (size_t)P->ng_half))) return rc;
+    if ((rc = dalloc(P, &P->d_rho_part, 2 * md * (size_t)std::max(P->npb, P->rho_rows) * (size_t)P->ng_half)))
+        return rc;
     if ((rc = dalloc(P, &P->d_rho, 2 * md * (size_t)P->ng_half))) return rc;
     if ((rc = dalloc(P, &P->d_W, 2 * md * (size_t)P->ng_half))) return rc;
     P->nEblocks = (int)std::max<int64_t>(1, (P->ng_half + kRedPoints - 1) / kRedPoints);
@@ -615,14 +627,14 @@ int ftcj_plan_info(const ftcj_plan* P, ftcj_info* o) {
     o->gcut = P->gcut;
     o->volume = P->vol;
     o->device_bytes = P->device_bytes;
-    o->rho_blocks = P->npb;
+    o->rho_blocks = P->rho_rows;
     o->n1_table = P->precision == FTCJ_PREC_SPLIT ? split_xtab_entries(P) : 0;
     o->pair_g_units_screened = P->d_rec_gcut ? P->units_screened : o->pair_g_units;
     o->pair_g_units_walked = P->d_rec_gcut ? P->units_walked : o->pair_g_units;
     o->n_abs_max = P->n_abs_max;
     o->grad_split = P->precision == FTCJ_PREC_SPLIT && split_grad_walk_exact(P) ? 1 : 0;
     const bool walks = P->ng_half > 0 && !P->tiles.empty();
-    o->rho_walk_launches = walks ? (P->rho_hi_tiles > 0 ? 2 : 1) : 0;
+    o->rho_walk_launches = walks ? (P->tc ? tc_rho_launches(P, P->max_dens) : (P->rho_hi_tiles > 0 ? 2 : 1)) : 0;
     o->j_walk_launches = walks ? (P->precision == FTCJ_PREC_SPLIT ? split_j_launches(P) : 1) : 0;
     return FTCJ_OK;
 }

@@ -22,7 +22,9 @@ int64_t launches_per_batch(const ftcj_plan* P) {
     int64_t n = 0;
     n += fold;                                         // a2
     n += P->npairs > 0 ? 1 : 0;                        // a3
-    n += (P->ng_half > 0 && !P->tiles.empty()) ? (P->rho_hi_tiles > 0 ? 2 : 1) : 0;  // a4
+    n += (P->ng_half > 0 && !P->tiles.empty())
+             ? (P->tc ? tc_rho_launches(P, P->max_dens) : (P->rho_hi_tiles > 0 ? 2 : 1))
+             : 0;  // a4
     n += P->ng_half > 0 ? 2 : 0;                       // a5: reduce + energy
     n += (P->ng_half > 0 && !P->tiles.empty()) ? (P->precision == FTCJ_PREC_SPLIT ? split_j_launches(P) : 1) : 0;  // a6
     n += P->npairs > 0 ? 1 : 0;                        // a7

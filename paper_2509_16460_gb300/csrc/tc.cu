@@ -1,0 +1,1064 @@
+// Tensor-core form of the structure-factor pass (Alg. 1) for orthorhombic
+// cells.
+//
+// In an orthorhombic cell the pair prefactor factorises over the three axes
+// (Sec. 2.4, the orthorhombic fully separable case; App. D):
+//   exp(-|G|^2/4p) exp(-i G.P) = X(n_a) Y(n_b) Z(n_c),
+//   X(n) = exp(-c M_aa n^2) exp(-2 pi i f_a n),   c = 1/(4p),
+// f_a the fractional coordinate of the pair centre.  With a pair record's
+// Hermite densities D'_{ijk} (the walks' convention: the record adds
+// X Y Z sum_ijk D'_ijk (-i n_a)^i (-i n_b)^j (-i n_c)^k to rho(n)),
+//   rho(n_a, n_b, n_c) = sum_{(i,j)} P_ij(n_a, n_b) sum_r A[(n_a, n_b), r] B_ij[r, n_c]
+//   A = X_r(n_a) Y_r(n_b)                              (geometry only)
+//   B_ij = Z_r(n_c) sum_k D'_{r,ijk} (-i n_c)^k         (per density)
+//   P_ij = (-i n_a)^i (-i n_b)^j                        (exact small integers)
+// For the records of one class L, all (i, j) with i + j <= L share A, so the
+// column blocks B_ij (up to G of them side by side) form one complex matrix
+// product over K = records: rows are the (n_a, n_b) of the sphere's
+// projection, columns (i, j) x n_c >= 0 x densities (the stored half sphere
+// maps to n_c >= 0, through -n and a conjugate where n_c < 0).  The powers
+// P_ij are applied to each block's sums when tensor memory is drained, so
+// that A carries only the Gaussian and the phase: a row's entries over a
+// window of records sorted by their width differ little in size, which is
+// what keeps the slicing below at full relative precision.
+//
+// Precision.  bf16 products summed in FP32 carry 8 bits; the target is FP64-
+// class.  The operands are therefore split after Ozaki, Ogita, Oishi and Rump
+// ("Error-free transformations of matrix multiplication by using fast
+// routines of matrix multiplication", Numer. Algorithms 59, 2012): every row
+// of A and every column of B, over a window of 512 records, gets a
+// power-of-two scale 2^e bounding its entries, and each entry is cut into six
+// slices m_s 2^{e-6-7s} with integers |m_s| <= 64.  Slice s of A times slice t
+// of B is a tcgen05.mma of kind::f16 (bf16 operands, FP32 accumulator in
+// tensor memory); products with s + t <= 5 are formed (21 per k-step), the
+// others fall below 2^-40 of the window's scale.  Products of the same level
+// s + t land in one accumulator: levels 0, 1, 2 are exact integer sums
+// (|m| <= 64, at most 3 products per level and 1024 real K terms per window
+// keep every partial sum below 2^24), levels 3..5 share a fourth, rounded
+// accumulator.  At each window's end the accumulators are scaled by
+// 2^{eA+eB}, multiplied by P_ij and added in double-float (FP32 pairs,
+// df.cuh) to sums kept in tensor memory, which are written as FP64 partial
+// rows and summed across window groups in fixed order by the row reduction.
+//
+// Kernel shape (one CTA per SM: 512 tensor-memory columns and ~200 KB of
+// shared memory), thirteen warps: warps 0-10 form the operand slices of a
+// 16-record stage into one of two shared-memory buffers (plain 16-byte stores
+// in the no-swizzle K-major core-matrix layout the MMA descriptors name);
+// lane 0 of warp 11 issues the MMAs; warp 12 stages each stage's record
+// factor tables with bulk copies (cp.async.bulk, completion counted in bytes
+// on an mbarrier) and their Hermite terms into a ring of shared-memory slots
+// ahead of use.  Warps 0-11 also compute the window scales and drain tensor
+// memory.  Stages are handed over with mbarriers (arrivals; tcgen05.commit
+// for the MMA side).  Every wait is bounded: past ~2 s of clock a waiting
+// thread raises the CTA's abort flag and the plan's device error word, every
+// thread leaves its loops, the copies and MMAs in flight are waited for
+// (again bounded) and tensor memory is freed before the CTA exits.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <set>
+#include <vector>
+
+#include "df.cuh"
+#include "ftcj_internal.h"
+
+namespace ftcj {
+namespace {
+
+constexpr int kTcM = 128;                      // rows per tile (MMA M)
+constexpr int kTcStageK = 16;                  // records per stage: two MMA k-steps of 16 real (re, im)
+constexpr int kTcWin = 512;                    // records per exact-accumulation window (1024 real K)
+constexpr int kTcStagesPerWin = kTcWin / kTcStageK;
+constexpr int kTcNmma = 256;                   // MMA N at most
+constexpr int kTcS = 6;                        // slices per operand
+constexpr int kTcAcc = 4;                      // accumulators: levels 0, 1, 2 exact, levels 3..5 rounded
+constexpr int kTcTmemCols = 512;
+constexpr int kTcGmax = 15;                    // (i, j) blocks per window at most (class 4 has 15)
+constexpr int kTcEbMax = 128;                  // column scales per window at most
+constexpr int kTcNbuf = 2;                     // stage buffers
+constexpr int kTcTabSlotsMax = 4;              // stage tables in flight
+constexpr int kTcAsliceBytes = kTcM * 2 * kTcStageK * 2;  // 128 rows x 32 real K x bf16
+constexpr long long kTcSpinCycles = 1LL << 32;            // ~2 s of SM clock per wait
+
+struct TcArgs {
+    const int2* rows;    // (n_a, n_b) per row
+    const int* map;      // [rows][ncols]: half-sphere index, ~index where the stored point is -n, INT_MIN none
+    const int* wrec;     // [nwin][kTcWin]: record ids of each window, -1 for padding
+    const int4* winfo;   // [nwin]: class L, number of (i,j) blocks, first block index into wpairs
+    const int* wpairs;   // (i | j << 3) of each block
+    const float4* tab;   // per record [tabw]: X(0..), Y(0..), Z(0..) as complex double-float
+    const float* cl;     // per record c log2(e)
+    const float2* Dp;    // Hermite densities (double-float), [dens][dp_total]
+    long long dp_total;
+    long long cls_start[kNclass + 1];
+    long long term_base[kNclass];
+    double2* out;        // partial rows [dens][ngroups][ng_half]
+    long long ng_half;
+    int* err;            // device error word (bit 0: a bounded wait gave up)
+    float Maa, Mbb, Mcc;
+    int ax, bx, cx;      // lattice axes of the row indices (a, b) and of the column index (c)
+    int tabw, offY, offZ;
+    int ncols;           // complex columns per density and block: n_c = 0 .. ncols-1
+    int nd, d0;          // densities of this launch, first density
+    int colw;            // real columns per block: 2 nd ncols
+    int G;               // blocks per window at most
+    int npad;            // MMA N: G colw rounded up to 16
+    int accw;            // real columns of the double-float sums: colw rounded up to 8
+    int nwin, win_per_group, ngroups;
+    int nrows;
+};
+
+// ---- PTX wrappers -----------------------------------------------------------
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(saddr(b)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(saddr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for phase `parity` of b to complete; false when it gave up (after
+// ~2 s of clock, or because another thread of the CTA already did).
+__device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+    const long long t0 = clock64();
+    while (!mbar_test(b, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kTcSpinCycles) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+// A bounded barrier of the eight operand warps (an mbarrier counting one
+// arrival per warp): unlike bar.sync it cannot hang when a thread has left
+// after a failed wait.  The outcome is the same for every lane of a warp.
+__device__ bool prod_sync(uint64_t* b, uint32_t& ph, volatile int* abort_flag, int lane) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(b);
+    const bool ok = mbar_wait(b, ph, abort_flag);
+    ph ^= 1u;
+    return __all_sync(0xffffffffu, ok);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major, no swizzle, core matrices of 8
+// rows x 16 B; K-adjacent core matrices 128 B apart (leading byte offset),
+// 8-row groups 512 B apart (stride byte offset: 32 real K per stage row)
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(512u >> 4) << 32) |
+           (1ull << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* b) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(b))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_st8(uint32_t taddr, const float (&v)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// ---- operand slices ---------------------------------------------------------
+
+// 2^k for an exponent in the normal FP32 range (k clamped to it)
+__device__ __forceinline__ float pow2f(int k) {
+    k = max(-126, min(127, k));
+    return __int_as_float((k + 127) << 23);
+}
+
+// Slices of x = hi + lo (|x| < 2^e, sc = 2^(6-e)): o[s] = m_s 2^(-7s) with
+// integers |m_s| <= 64 (<= 72 for s = 3, which takes the low part's
+// rounding), so that x = 2^(e-6) sum_s o[s] up to 2^(e-41).  Each slice rounds
+// the remainder to a multiple of 2^(-7s) by adding and subtracting 1.5 x
+// 2^(23-7s) (round to nearest even, no fast-math reassociation); slices 0-2
+// peel the high part exactly, the low part joins at slice 3 with one rounding
+// below 2^(e-45).
+__device__ __forceinline__ void slice6(float hi, float lo, float sc, float (&o)[kTcS]) {
+    float h = hi * sc;
+    const float l = lo * sc;
+    o[0] = (h + 0x1.8p23f) - 0x1.8p23f;
+    h -= o[0];
+    o[1] = (h + 0x1.8p16f) - 0x1.8p16f;
+    h -= o[1];
+    o[2] = (h + 0x1.8p9f) - 0x1.8p9f;
+    h = (h - o[2]) + l;
+    o[3] = (h + 0x1.8p2f) - 0x1.8p2f;
+    h -= o[3];
+    o[4] = (h + 0x1.8p-5f) - 0x1.8p-5f;
+    h -= o[4];
+    o[5] = (h + 0x1.8p-12f) - 0x1.8p-12f;
+}
+
+__device__ __forceinline__ uint32_t pack_bf2(float a, float b) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);  // exact: every slice has <= 8 significant bits
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// element offset of (row, k) in a stage tile [rows][32 real K] of core matrices
+__device__ __forceinline__ int tile_off(int row, int k) {
+    return (((row >> 3) * 4 + (k >> 3)) << 6) + ((row & 7) << 3) + (k & 7);
+}
+
+// (-i)^p z
+__device__ __forceinline__ cdf rot_mi(cdf z, int p) {
+    switch (p & 3) {
+        case 0: return z;
+        case 1: return cdf{z.im, df_neg(z.re)};
+        case 2: return cdf{df_neg(z.re), df_neg(z.im)};
+        default: return cdf{df_neg(z.im), z.re};
+    }
+}
+
+__device__ __forceinline__ int exp_bound(float log2_bound) {
+    // smallest e with 2^e > the bound, from a log2 estimate good to ~1e-4
+    if (!(log2_bound > -100.f)) return -100;
+    return (int)floorf(log2_bound + 1e-3f) + 1;
+}
+
+struct TcRow {
+    int na, nb;
+    float Q;  // M_aa na^2 + M_bb nb^2
+};
+
+struct TcSmem {
+    int rec[kTcWin];
+    int pairs[kTcGmax];
+    int tidx[kTcGmax][5];  // index of D'_{ijk} for block (i, j) and k = 0..4 (-1 past the class's degree)
+    int eA[kTcM];
+    int eB[kTcEbMax];
+    TcRow rowi[kTcM];
+    int winL, wnpair, clmin_bits;
+    uint64_t full[kTcNbuf], empty[kTcNbuf], accf, acce, done, psync;
+    uint64_t tfull[kTcTabSlotsMax], tempty[kTcTabSlotsMax];
+    uint32_t tmem;
+    int abort_flag;
+};
+
+// One table slot of a stage: the 16 records' factor tables (copied whole by
+// the bulk-copy engine, tabw float4 each), then the Hermite terms D'_{ijk},
+// k = 0..4, of each (record, block, density) (zero past the record's degree).
+__host__ __device__ inline size_t tab_slot_bytes(int tabw, int G, int nd) {
+    const size_t b = (size_t)kTcStageK * tabw * 16 + (size_t)kTcStageK * G * nd * 5 * 8;
+    return (b + 127) / 128 * 128;
+}
+
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(saddr(dst)), "l"(src), "r"(bytes), "r"(saddr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* b, uint32_t tx) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(saddr(b)),
+                 "r"(tx)
+                 : "memory");
+}
+
+// index of D'_{p1 p2 p3} (powers of n_1, n_2, n_3) for powers (i, j, k) of (n_a, n_b, n_c)
+__device__ __forceinline__ int term_of(const TcArgs& g, int i, int j, int k) {
+    const int p1 = g.ax == 0 ? i : (g.bx == 0 ? j : k);
+    const int p2 = g.ax == 1 ? i : (g.bx == 1 ? j : k);
+    const int lam = i + j + k;
+    return lam_offset(lam) + mono_index(lam, p1, p2);
+}
+
+// A: the four records of group gg (stage-local 4 gg .. 4 gg + 3) for one row,
+// X_r(n_a) Y_r(n_b) sliced, as six 16-byte stores (one core-matrix row per slice)
+__device__ __forceinline__ void form_a(const TcArgs& g, const TcSmem& sm, const float4* tabs, int q, int row,
+                                       int gg, float scA, unsigned char* as) {
+    const TcRow ri = sm.rowi[row];
+    const bool rvalid = ri.na != INT_MIN;
+    const float sa = ri.na < 0 ? -1.f : 1.f, sb = ri.nb < 0 ? -1.f : 1.f;  // X(-n) = conj X(n)
+    const int ia = abs(ri.na), ib = g.offY + abs(ri.nb);
+    float sl[kTcS][8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int kq = gg * 4 + u;
+        cdf a{{0.f, 0.f}, {0.f, 0.f}};
+        if (rvalid && sm.rec[q * kTcStageK + kq] >= 0) {
+            const float4 xv = tabs[kq * g.tabw + ia], yv = tabs[kq * g.tabw + ib];
+            a = cdf_mul(cdf{{xv.x, xv.y}, {sa * xv.z, sa * xv.w}}, cdf{{yv.x, yv.y}, {sb * yv.z, sb * yv.w}});
+        }
+        float sr[kTcS], si[kTcS];
+        slice6(a.re.hi, a.re.lo, scA, sr);
+        slice6(a.im.hi, a.im.lo, scA, si);
+#pragma unroll
+        for (int s = 0; s < kTcS; ++s) {
+            sl[s][2 * u] = sr[s];
+            sl[s][2 * u + 1] = si[s];
+        }
+    }
+    const int off = tile_off(row, gg * 8);
+#pragma unroll
+    for (int s = 0; s < kTcS; ++s) {
+        uint4 v;
+        v.x = pack_bf2(sl[s][0], sl[s][1]);
+        v.y = pack_bf2(sl[s][2], sl[s][3]);
+        v.z = pack_bf2(sl[s][4], sl[s][5]);
+        v.w = pack_bf2(sl[s][6], sl[s][7]);
+        *reinterpret_cast<uint4*>(as + (size_t)s * kTcAsliceBytes + (size_t)off * 2) = v;
+    }
+}
+
+// B: four records (stage-local 4 kg .. 4 kg + 3) of one (block gb, output pair
+// p = n_c nd + d), sliced, in the real form rows (record, re) -> [Re B | Im B],
+// (record, im) -> [-Im B | Re B]: columns gb colw + 2p and + 1, one 16-byte
+// core-matrix row per slice and column.  Blocks past the window's count are zero.
+__device__ __forceinline__ void form_b(const TcArgs& g, const TcSmem& sm, const float4* tabs, const float2* dps,
+                                       int q, int kg, int gb, int p, unsigned char* bs, int bslice) {
+    const int nc = p / g.nd, d = p - nc * g.nd;
+    float s0[kTcS][8], s1[kTcS][8];  // column 2p: (Re, -Im) per record; column 2p + 1: (Im, Re)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int kq = kg * 4 + u;
+        cdf bv{{0.f, 0.f}, {0.f, 0.f}};
+        if (gb < sm.wnpair && sm.rec[q * kTcStageK + kq] >= 0) {
+            const float4 zv = tabs[kq * g.tabw + g.offZ + nc];
+            const float2* dv = dps + ((kq * g.G + gb) * g.nd + d) * 5;
+            df re{0.f, 0.f}, im{0.f, 0.f};
+            float pw = 1.f;
+#pragma unroll
+            for (int kk = 0; kk < 5; ++kk) {
+                const float2 v = dv[kk];
+                const df term = df_mulf(df{v.x, v.y}, pw);  // D'_k n_c^k, exact power
+                switch (kk & 3) {                           // (-i)^k
+                    case 0: re = df_add(re, term); break;
+                    case 1: im = df_sub(im, term); break;
+                    case 2: re = df_sub(re, term); break;
+                    default: im = df_add(im, term); break;
+                }
+                pw *= (float)nc;
+            }
+            bv = cdf_mul(cdf{{zv.x, zv.y}, {zv.z, zv.w}}, cdf{re, im});
+        }
+        const float scB = pow2f(6 - sm.eB[gb * g.ncols * g.nd + p]);
+        float sr[kTcS], si[kTcS];
+        slice6(bv.re.hi, bv.re.lo, scB, sr);
+        slice6(bv.im.hi, bv.im.lo, scB, si);
+#pragma unroll
+        for (int s = 0; s < kTcS; ++s) {
+            s0[s][2 * u] = sr[s];
+            s0[s][2 * u + 1] = -si[s];
+            s1[s][2 * u] = si[s];
+            s1[s][2 * u + 1] = sr[s];
+        }
+    }
+    const int c0 = gb * g.colw + 2 * p;
+    const int o0 = tile_off(c0, kg * 8), o1 = tile_off(c0 + 1, kg * 8);
+#pragma unroll
+    for (int s = 0; s < kTcS; ++s) {
+        uint4 v;
+        v.x = pack_bf2(s0[s][0], s0[s][1]);
+        v.y = pack_bf2(s0[s][2], s0[s][3]);
+        v.z = pack_bf2(s0[s][4], s0[s][5]);
+        v.w = pack_bf2(s0[s][6], s0[s][7]);
+        *reinterpret_cast<uint4*>(bs + (size_t)s * bslice + (size_t)o0 * 2) = v;
+        v.x = pack_bf2(s1[s][0], s1[s][1]);
+        v.y = pack_bf2(s1[s][2], s1[s][3]);
+        v.z = pack_bf2(s1[s][4], s1[s][5]);
+        v.w = pack_bf2(s1[s][6], s1[s][7]);
+        *reinterpret_cast<uint4*>(bs + (size_t)s * bslice + (size_t)o1 * 2) = v;
+    }
+}
+
+constexpr int kTcProdWarps = 11;
+constexpr int kTcProdThreads = kTcProdWarps * 32;
+constexpr int kTcMmaWarp = 11;
+constexpr int kTcLoadWarp = 12;
+constexpr int kTcWarps = 13;
+constexpr int kTcEpiWarps = 12;
+constexpr int kTcEpiThreads = kTcEpiWarps * 32;
+constexpr int kTcThreadsAll = kTcWarps * 32;
+
+__global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslots) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    unsigned char* abuf = tsm;                                                    // [nbuf][S][8192]
+    unsigned char* bbuf = abuf + (size_t)kTcNbuf * kTcS * kTcAsliceBytes;          // [nbuf][S][npad*64]
+    const int bslice = g.npad * 64;
+    unsigned char* tring = bbuf + (size_t)kTcNbuf * kTcS * bslice;                 // [ntslots][slot]
+    const size_t tslot = tab_slot_bytes(g.tabw, g.G, g.nd);
+    TcSmem& sm = *reinterpret_cast<TcSmem*>(tring + (size_t)ntslots * tslot);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int kg = blockIdx.x, mt = blockIdx.y;
+    const int w0 = kg * g.win_per_group, w1 = min(g.nwin, w0 + g.win_per_group);
+    volatile int* abort_flag = &sm.abort_flag;
+    const bool mma_warp = warp == kTcMmaWarp, load_warp = warp == kTcLoadWarp;
+
+    if (tid == 0) {
+        for (int b = 0; b < kTcNbuf; ++b) {
+            mbar_init(&sm.full[b], kTcProdWarps);
+            mbar_init(&sm.empty[b], 1);
+        }
+        for (int b = 0; b < ntslots; ++b) {
+            mbar_init(&sm.tfull[b], 1);
+            mbar_init(&sm.tempty[b], kTcProdWarps);
+        }
+        mbar_init(&sm.accf, 1);
+        mbar_init(&sm.acce, kTcEpiWarps);
+        mbar_init(&sm.done, 1);
+        mbar_init(&sm.psync, kTcWarps);
+        sm.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < kTcM) {
+        const int m = mt * kTcM + tid;
+        const int2 rw = m < g.nrows ? __ldg(g.rows + m) : make_int2(INT_MIN, 0);
+        TcRow ri;
+        ri.na = rw.x;
+        ri.nb = rw.y;
+        ri.Q = rw.x != INT_MIN ? g.Maa * (float)rw.x * (float)rw.x + g.Mbb * (float)rw.y * (float)rw.y : 0.f;
+        sm.rowi[tid] = ri;
+    }
+    // zero both stage buffers once: padding columns of B are never written
+    for (int i = tid; i < kTcNbuf * kTcS * bslice / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(bbuf)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (mma_warp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&sm.tmem)),
+                     "r"(kTcTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem;
+
+    // epilogue roles (warps 0-11): TMEM lanes 32 (w & 3) .. + 31, 8-column chunks c8 = w / 4 (mod 3)
+    const int equad = warp & 3, ewarp3 = warp >> 2, erow = 32 * equad + lane;
+    const uint32_t tlane = (uint32_t)(32 * equad) << 16;
+    const int npo = g.nd * g.ncols;  // complex outputs per block
+    const int nchunk = g.colw / 8;   // 8-column chunks of a block (4 complex outputs each)
+    const uint32_t acc_hi = (uint32_t)(4 * g.npad), acc_lo = acc_hi + (uint32_t)g.colw;
+    if (!load_warp) {
+        for (int c8 = ewarp3; c8 < nchunk; c8 += 3) {
+            const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            tc_st8(tmem + tlane + acc_hi + (uint32_t)(8 * c8), z);
+            tc_st8(tmem + tlane + acc_lo + (uint32_t)(8 * c8), z);
+        }
+        tc_wait_st();
+    }
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(g.npad >> 3) << 17) |
+                           ((uint32_t)(kTcM >> 4) << 24);
+    long long gs = 0;  // stages so far (every role counts the same)
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int w = w0; w < w1 && ok; ++w) {
+        // ---- window records, blocks and scales ----
+        for (int i = tid; i < kTcWin; i += kTcThreadsAll) sm.rec[i] = __ldg(g.wrec + (size_t)w * kTcWin + i);
+        for (int i = tid; i < kTcEbMax; i += kTcThreadsAll) sm.eB[i] = -100;
+        if (tid == 0) {
+            const int4 wi = __ldg(g.winfo + w);
+            sm.winL = wi.x;
+            sm.wnpair = wi.y;
+            for (int b = 0; b < wi.y; ++b) {
+                const int pr = __ldg(g.wpairs + wi.z + b), i = pr & 7, j = pr >> 3;
+                sm.pairs[b] = pr;
+                for (int kk = 0; kk < 5; ++kk) sm.tidx[b][kk] = kk <= wi.x - i - j ? term_of(g, i, j, kk) : -1;
+            }
+            sm.clmin_bits = __float_as_int(INFINITY);
+        }
+        if (!(ok = prod_sync(&sm.psync, ph, abort_flag, lane))) break;
+        const int L = sm.winL, npair = sm.wnpair;
+        if (!load_warp) {
+            // A: |X Y| = exp(-c Q) <= exp(-c_min Q): the window's smallest width gives every row's scale
+            float cmin = INFINITY;
+            for (int k = tid; k < kTcWin; k += kTcEpiThreads) {
+                const int r = sm.rec[k];
+                if (r >= 0) cmin = fminf(cmin, __ldg(g.cl + r));
+            }
+            cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, 16));
+            cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, 8));
+            cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, 4));
+            cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, 2));
+            cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, 1));
+            if (lane == 0 && cmin < INFINITY) atomicMin(&sm.clmin_bits, __float_as_int(cmin));
+            // B: |B_ij| <= exp(-c Mcc n^2) sum_k |D'_ijk| n^k, per (block, n_c, density) over the window
+            // (warp-uniform trip counts: 512 = 384 + 128)
+            const long long cnt = g.cls_start[L + 1] - g.cls_start[L];
+            const float2* dpL = g.Dp + g.term_base[L];
+            for (int k = tid; k < kTcWin; k += kTcEpiThreads) {
+                const int r = sm.rec[k];
+                const float cr = r >= 0 ? __ldg(g.cl + r) : 0.f;
+                const long long loc = r - g.cls_start[L];
+                for (int gb = 0; gb < npair; ++gb) {
+                    for (int d = 0; d < g.nd; ++d) {
+                        float cm[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+                        if (r >= 0) {
+                            const float2* dp = dpL + (long long)(g.d0 + d) * g.dp_total + loc;
+#pragma unroll
+                            for (int kk = 0; kk < 5; ++kk) {
+                                const int t = sm.tidx[gb][kk];
+                                if (t >= 0) cm[kk] = fabsf(__ldg(dp + (long long)t * cnt).x) * 1.0001f;
+                            }
+                        }
+                        for (int nc = 0; nc < g.ncols; ++nc) {
+                            const float x = (float)nc;
+                            const float sv = cm[0] + x * (cm[1] + x * (cm[2] + x * (cm[3] + x * cm[4])));
+                            int eb = r >= 0 && sv > 0.f ? exp_bound(log2f(sv) - cr * g.Mcc * x * x) : -100;
+                            eb = __reduce_max_sync(0xffffffffu, eb);  // warp maximum, one shared atomic per warp
+                            if (lane == 0) atomicMax(&sm.eB[gb * npo + nc * g.nd + d], eb);
+                        }
+                    }
+                }
+            }
+        }
+        if (!(ok = prod_sync(&sm.psync, ph, abort_flag, lane))) break;
+        const float clmin = __int_as_float(sm.clmin_bits);
+        // ---- stages ----
+        if (load_warp) {
+            const long long cnt = g.cls_start[L + 1] - g.cls_start[L];
+            const float2* dpL = g.Dp + g.term_base[L];
+            for (int q = 0; q < kTcStagesPerWin; ++q, ++gs) {
+                const int ts = (int)(gs % ntslots);
+                const long long use = gs / ntslots;
+                if (use > 0) {
+                    ok = __all_sync(0xffffffffu, mbar_wait(&sm.tempty[ts], (uint32_t)((use - 1) & 1), abort_flag));
+                    if (!ok) break;
+                }
+                unsigned char* slotp = tring + (size_t)ts * tslot;
+                float2* dps = reinterpret_cast<float2*>(slotp + (size_t)kTcStageK * g.tabw * 16);
+                const int ntri = kTcStageK * g.G * g.nd;
+                for (int tri = lane; tri < ntri; tri += 32) {
+                    const int d = tri % g.nd, t2 = tri / g.nd, gb = t2 % g.G, u = t2 / g.G;
+                    const int r = sm.rec[q * kTcStageK + u];
+                    const bool live = r >= 0 && gb < npair;
+                    const float2* dp = dpL + (long long)(g.d0 + d) * g.dp_total + (live ? r - g.cls_start[L] : 0);
+                    float2 v[5];
+#pragma unroll
+                    for (int kk = 0; kk < 5; ++kk) {
+                        const int t = live ? sm.tidx[gb][kk] : -1;
+                        v[kk] = t >= 0 ? __ldg(dp + (long long)t * cnt) : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int kk = 0; kk < 5; ++kk) dps[tri * 5 + kk] = v[kk];
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    uint32_t nv = 0;
+                    for (int u = 0; u < kTcStageK; ++u) nv += sm.rec[q * kTcStageK + u] >= 0 ? 1u : 0u;
+                    mbar_arrive_tx(&sm.tfull[ts], nv * (uint32_t)g.tabw * 16u);
+                    for (int u = 0; u < kTcStageK; ++u) {
+                        const int r = sm.rec[q * kTcStageK + u];
+                        if (r >= 0)
+                            bulk_copy(slotp + (size_t)u * g.tabw * 16, g.tab + (size_t)r * g.tabw,
+                                      (uint32_t)g.tabw * 16u, &sm.tfull[ts]);
+                    }
+                }
+                __syncwarp();
+            }
+        } else if (!mma_warp) {
+            const int nbt = (kTcStageK / 4) * g.G * npo;  // B tasks per stage (four records each)
+            for (int q = 0; q < kTcStagesPerWin; ++q, ++gs) {
+                const int slot = (int)(gs & 1), ts = (int)(gs % ntslots);
+                ok = __all_sync(0xffffffffu, mbar_wait(&sm.tfull[ts], (uint32_t)((gs / ntslots) & 1), abort_flag));
+                if (!ok) break;
+                if (gs >= kTcNbuf) {
+                    ok = __all_sync(0xffffffffu, mbar_wait(&sm.empty[slot], (uint32_t)(((gs >> 1) - 1) & 1), abort_flag));
+                    if (!ok) break;
+                }
+                const unsigned char* slotp = tring + (size_t)ts * tslot;
+                const float4* tabs = reinterpret_cast<const float4*>(slotp);
+                const float2* dps = reinterpret_cast<const float2*>(slotp + (size_t)kTcStageK * g.tabw * 16);
+                unsigned char* as = abuf + (size_t)slot * kTcS * kTcAsliceBytes;
+                unsigned char* bs = bbuf + (size_t)slot * kTcS * bslice;
+                for (int task = tid; task < kTcM * 4; task += kTcProdThreads) {
+                    const int row = task & (kTcM - 1), gg = task >> 7;
+                    const int eAr = exp_bound(-clmin * sm.rowi[row].Q);
+                    form_a(g, sm, tabs, q, row, gg, pow2f(6 - eAr), as);
+                }
+                for (int task = tid; task < nbt; task += kTcProdThreads) {
+                    const int p = task % npo, t2 = task / npo, gb = t2 % g.G, kg = t2 / g.G;
+                    form_b(g, sm, tabs, dps, q, kg, gb, p, bs, bslice);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&sm.full[slot]);
+                    mbar_arrive(&sm.tempty[ts]);
+                }
+            }
+        } else {
+            if (lane == 0) {
+                const uint32_t a0 = saddr(abuf), b0 = saddr(bbuf);
+                bool first[kTcAcc] = {true, true, true, true};
+                bool mok = true;
+                for (int q = 0; q < kTcStagesPerWin; ++q, ++gs) {
+                    const int slot = (int)(gs & 1);
+                    if (!(mok = mbar_wait(&sm.full[slot], (uint32_t)((gs >> 1) & 1), abort_flag))) break;
+                    tc_fence_after();
+                    const uint32_t as = a0 + slot * kTcS * kTcAsliceBytes, bs = b0 + slot * kTcS * bslice;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+#pragma unroll
+                        for (int s = 0; s < kTcS; ++s)
+#pragma unroll
+                            for (int t = 0; s + t < kTcS; ++t) {
+                                const int lv = min(s + t, kTcAcc - 1);
+                                tc_mma(tmem + (uint32_t)(lv * g.npad), sdesc(as + s * kTcAsliceBytes + h * 256),
+                                       sdesc(bs + t * bslice + h * 256), idesc, first[lv] ? 0u : 1u);
+                                first[lv] = false;
+                            }
+                    tc_commit(&sm.empty[slot]);
+                }
+                if (mok) tc_commit(&sm.accf);
+                ok = mok;
+            }
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            gs = __shfl_sync(0xffffffffu, gs, 0);
+        }
+        if (!ok) break;
+        // ---- drain: each block's level sums, scaled and times P_ij, into the double-float sums (warps 0-11) ----
+        if (!load_warp) {
+            ok = __all_sync(0xffffffffu, mbar_wait(&sm.accf, (uint32_t)((w - w0) & 1), abort_flag));
+            if (!ok) break;
+            tc_fence_after();
+            const TcRow ri = sm.rowi[erow];
+            const int eAe = exp_bound(-clmin * ri.Q);
+            for (int c8 = ewarp3; c8 < nchunk; c8 += 3) {
+                float H[8], Lo[8];
+                tc_ld8(tmem + tlane + acc_hi + (uint32_t)(8 * c8), H);
+                tc_ld8(tmem + tlane + acc_lo + (uint32_t)(8 * c8), Lo);
+                for (int gb = 0; gb < npair; ++gb) {
+                    const int i = sm.pairs[gb] & 7, j = sm.pairs[gb] >> 3;
+                    float pij = 1.f;  // n_a^i n_b^j, exact
+                    for (int k = 0; k < i; ++k) pij *= (float)ri.na;
+                    for (int k = 0; k < j; ++k) pij *= (float)ri.nb;
+                    float T[kTcAcc][8];
+#pragma unroll
+                    for (int lv = 0; lv < kTcAcc; ++lv)
+                        tc_ld8(tmem + tlane + (uint32_t)(lv * g.npad + gb * g.colw + 8 * c8), T[lv]);
+#pragma unroll
+                    for (int u = 0; u < 8; u += 2) {
+                        const int p = 4 * c8 + u / 2;
+                        if (p < npo) {
+                            cdf v;
+                            v.re = df_add(df_add(two_sum(T[0][u], T[1][u]), df{T[2][u], 0.f}), df{T[3][u], 0.f});
+                            v.im = df_add(df_add(two_sum(T[0][u + 1], T[1][u + 1]), df{T[2][u + 1], 0.f}),
+                                          df{T[3][u + 1], 0.f});
+                            const float sc = pow2f(eAe + sm.eB[gb * npo + p] - 12);  // exact power of two
+                            v = cdf{df_mulf(df{v.re.hi * sc, v.re.lo * sc}, pij),
+                                    df_mulf(df{v.im.hi * sc, v.im.lo * sc}, pij)};
+                            v = rot_mi(v, i + j);
+                            const df re = df_add(df{H[u], Lo[u]}, v.re), im = df_add(df{H[u + 1], Lo[u + 1]}, v.im);
+                            H[u] = re.hi;
+                            Lo[u] = re.lo;
+                            H[u + 1] = im.hi;
+                            Lo[u + 1] = im.lo;
+                        }
+                    }
+                }
+                tc_st8(tmem + tlane + acc_hi + (uint32_t)(8 * c8), H);
+                tc_st8(tmem + tlane + acc_lo + (uint32_t)(8 * c8), Lo);
+            }
+            tc_wait_st();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.acce);
+            // the MMAs of the next window wait for every warp's drain
+            if (mma_warp && w + 1 < w1) {
+                ok = __all_sync(0xffffffffu, mbar_wait(&sm.acce, (uint32_t)((w - w0) & 1), abort_flag));
+                tc_fence_after();
+            }
+        }
+        if (!(ok = prod_sync(&sm.psync, ph, abort_flag, lane) && ok)) break;  // window tables reused next window
+    }
+    // ---- partial rows ----
+    if (ok && !*abort_flag && !load_warp) {
+        tc_fence_after();
+        const int mo = mt * kTcM + erow;
+        for (int c8 = ewarp3; c8 < nchunk; c8 += 3) {
+            float H[8], Lo[8];
+            tc_ld8(tmem + tlane + acc_hi + (uint32_t)(8 * c8), H);
+            tc_ld8(tmem + tlane + acc_lo + (uint32_t)(8 * c8), Lo);
+            if (mo < g.nrows) {
+#pragma unroll
+                for (int u = 0; u < 8; u += 2) {
+                    const int p = 4 * c8 + u / 2;
+                    if (p < npo) {
+                        const int nc = p / g.nd, d = p - nc * g.nd;
+                        int idx = __ldg(g.map + (size_t)mo * g.ncols + nc);
+                        if (idx != INT_MIN) {
+                            const bool cj = idx < 0;
+                            if (cj) idx = ~idx;
+                            const double re = (double)H[u] + (double)Lo[u];
+                            const double im = (double)H[u + 1] + (double)Lo[u + 1];
+                            g.out[((long long)(g.d0 + d) * g.ngroups + kg) * g.ng_half + idx] =
+                                make_double2(re, cj ? -im : im);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (load_warp && lane == 0) {
+        // bulk copies still in flight (after a failed wait) land before the CTA exits
+        for (int b = 0; b < ntslots && b < gs; ++b) {
+            const long long last = gs - 1 - ((gs - 1 - b) % ntslots);  // last stage that used slot b
+            const long long t0 = clock64();
+            while (!mbar_test(&sm.tfull[b], (uint32_t)((last / ntslots) & 1)) && clock64() - t0 < kTcSpinCycles) {
+            }
+        }
+    }
+    if (mma_warp) {
+        // everything issued completes before tensor memory is freed
+        if (lane == 0) {
+            tc_commit(&sm.done);
+            const long long t0 = clock64();
+            while (!mbar_test(&sm.done, 0u) && clock64() - t0 < kTcSpinCycles) {
+            }
+        }
+        __syncwarp();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*abort_flag && tid == 0) atomicOr(g.err, 1);
+    if (mma_warp) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+    }
+}
+
+// per-record factor tables X(0..na), Y(0..nb), Z(0..nc) in FP64, kept as double-float
+__global__ void k_tc_tables(const PairWalk* __restrict__ walk, long long npairs, int ax, int bx, int cx, int nna,
+                            int nnb, int nnc, double Maa, double Mbb, double Mcc, float4* __restrict__ tab,
+                            float* __restrict__ cl) {
+    const int tabw = nna + nnb + nnc;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npairs * tabw) return;
+    const long long r = t / tabw;
+    const int e = (int)(t - r * tabw);
+    const PairWalk w = walk[r];
+    const double f[3] = {w.f1, w.f2, w.f3};
+    double M, fr;
+    int n;
+    if (e < nna) {
+        n = e;
+        M = Maa;
+        fr = f[ax];
+    } else if (e < nna + nnb) {
+        n = e - nna;
+        M = Mbb;
+        fr = f[bx];
+    } else {
+        n = e - nna - nnb;
+        M = Mcc;
+        fr = f[cx];
+    }
+    const double gval = exp(-w.c * M * (double)n * (double)n);
+    double th = fr * (double)n;
+    th -= rint(th);
+    double s, c;
+    sincospi(2.0 * th, &s, &c);
+    const df re = df_from_double(gval * c), im = df_from_double(-gval * s);
+    tab[t] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    if (e == 0) cl[r] = (float)(w.c * 1.4426950408889634);
+}
+
+// shared memory of one CTA with `nts` table slots (at least 120 KB, so that a
+// second CTA never shares an SM: each one takes all 512 tensor-memory
+// columns, and a second would wait in tcgen05.alloc)
+size_t tc_smem_bytes(int npad, int tabw, int G, int nd, int nts) {
+    const size_t need = (size_t)kTcNbuf * kTcS * kTcAsliceBytes + (size_t)kTcNbuf * kTcS * npad * 64 +
+                        (size_t)nts * tab_slot_bytes(tabw, G, nd) + sizeof(TcSmem) + 64;
+    return std::max<size_t>(need, 120 * 1024);
+}
+
+template <class T>
+int tc_upload(ftcj_plan* P, T** ptr, const std::vector<T>& v) {
+    const size_t n = std::max<size_t>(v.size(), 1);
+    cudaError_t e = cudaMalloc((void**)ptr, sizeof(T) * n);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        return fail(FTCJ_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    P->device_bytes += sizeof(T) * n;
+    if (!v.empty()) FTCJ_CUDA(cudaMemcpy(*ptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    return FTCJ_OK;
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// column layout for nd densities and ncols values of n_c: real columns per
+// block (a multiple of 8) and the largest block count G whose level
+// accumulators (4 x G x colw, rounded to 16) and double-float sums (2 colw)
+// fit the 512 tensor-memory columns; G = 0 when not even one block fits
+void tc_columns(int nd, int ncols, int* colw, int* G, int* npad) {
+    *colw = round_up(2 * nd * ncols, 8);
+    *G = 0;
+    *npad = 0;
+    for (int gg = kTcGmax; gg >= 1; --gg) {
+        const int np = round_up(gg * *colw, 16);
+        if (np <= kTcNmma && 4 * np + 2 * *colw <= kTcTmemCols && gg * nd * ncols <= kTcEbMax) {
+            *G = gg;
+            *npad = np;
+            return;
+        }
+    }
+}
+
+}  // namespace
+
+int tc_supported(const ftcj_plan* P) { return P->ortho ? 1 : 0; }
+
+// Plan-time set-up of the tensor-core form: the column axis, the rows and
+// their half-sphere map, the factor tables, the windows (class, block group,
+// 512 records sorted by width) and the partial-row count.
+int setup_tc(ftcj_plan* P) {
+    if (!P->ortho) return fail(FTCJ_EUNSUPPORTED, "the tensor-core contraction needs an orthorhombic cell");
+    if (P->precision != FTCJ_PREC_SPLIT)
+        return fail(FTCJ_EUNSUPPORTED, "the tensor-core contraction is part of the split-precision form");
+    if (P->d_rec_gcut) return fail(FTCJ_EUNSUPPORTED, "the tensor-core contraction walks the whole sphere");
+    if (P->npairs >= (1 << 24)) return fail(FTCJ_EUNSUPPORTED, "more than 2^24 pair records");
+    const int64_t ngh = P->ng_half;
+    int64_t recs_by_class[kNclass];
+    for (int L = 0; L < kNclass; ++L) recs_by_class[L] = P->class_start[L + 1] - P->class_start[L];
+    // the column axis: operand work ~ row tiles x (record passes x 128 rows + B entries), per density group
+    struct AxisPlan {
+        std::vector<std::pair<int, int>> rows;
+        int ncols = 0, nd = 0, colw = 0, G = 0, npad = 0;
+    } best;
+    int best_c = -1;
+    double best_cost = 1e300;
+    for (int c = 0; c < 3; ++c) {
+        const int a = (c + 1) % 3, b = (c + 2) % 3;
+        AxisPlan ap;
+        std::set<std::pair<int, int>> rs;
+        int ncmax = 0;
+        for (int64_t q = 0; q < ngh; ++q) {
+            int n[3] = {P->gvec[3 * q], P->gvec[3 * q + 1], P->gvec[3 * q + 2]};
+            if (n[c] < 0)
+                for (int x = 0; x < 3; ++x) n[x] = -n[x];
+            rs.insert({n[a], n[b]});
+            ncmax = std::max(ncmax, n[c]);
+        }
+        ap.ncols = ncmax + 1;
+        for (ap.nd = P->max_dens; ap.nd >= 1; --ap.nd) {
+            tc_columns(ap.nd, ap.ncols, &ap.colw, &ap.G, &ap.npad);
+            if (ap.G > 0) break;
+        }
+        if (ap.nd < 1 || ap.G < 1) continue;
+        ap.rows.assign(rs.begin(), rs.end());
+        const double mt = (double)((ap.rows.size() + kTcM - 1) / kTcM);
+        const double launches = (double)((P->max_dens + ap.nd - 1) / ap.nd);
+        double work = 0.0;
+        for (int L = 0; L < kNclass; ++L) {
+            const int nb = (L + 1) * (L + 2) / 2;
+            const double passes = (double)((nb + ap.G - 1) / ap.G);
+            work += (double)recs_by_class[L] * (passes * kTcM + 1.5 * nb * ap.nd * ap.ncols);
+        }
+        const double cost = launches * mt * work;
+        if (cost < best_cost) {
+            best_cost = cost;
+            best_c = c;
+            best = ap;
+        }
+    }
+    if (best_c < 0) return fail(FTCJ_EUNSUPPORTED, "the sphere is too long on every axis for the tensor-core tile");
+    const int c = best_c, a = (c + 1) % 3, b = (c + 2) % 3;
+    P->tc_axis[0] = a;
+    P->tc_axis[1] = b;
+    P->tc_axis[2] = c;
+    P->tc_ncols = best.ncols;
+    P->tc_nd = best.nd;
+    P->tc_colw = best.colw;
+    P->tc_G = best.G;
+    P->tc_npad = best.npad;
+    P->tc_rows = (int)best.rows.size();
+    P->tc_mtiles = (P->tc_rows + kTcM - 1) / kTcM;
+    // half-sphere map: row (n_a, n_b), column n_c >= 0
+    std::vector<int> map((size_t)P->tc_rows * P->tc_ncols, INT_MIN);
+    {
+        std::vector<std::pair<int, int>>& rows = best.rows;
+        for (int64_t q = 0; q < ngh; ++q) {
+            int n[3] = {P->gvec[3 * q], P->gvec[3 * q + 1], P->gvec[3 * q + 2]};
+            bool cj = false;
+            if (n[c] < 0) {
+                for (int x = 0; x < 3; ++x) n[x] = -n[x];
+                cj = true;
+            }
+            const auto it = std::lower_bound(rows.begin(), rows.end(), std::make_pair(n[a], n[b]));
+            const size_t rix = (size_t)(it - rows.begin());
+            map[rix * P->tc_ncols + n[c]] = cj ? ~(int)q : (int)q;
+        }
+    }
+    std::vector<int2> rowv(best.rows.size());
+    int nam = 0, nbm = 0;
+    for (size_t i = 0; i < best.rows.size(); ++i) {
+        rowv[i] = make_int2(best.rows[i].first, best.rows[i].second);
+        nam = std::max(nam, std::abs(best.rows[i].first));
+        nbm = std::max(nbm, std::abs(best.rows[i].second));
+    }
+    P->tc_nna = nam + 1;
+    P->tc_nnb = nbm + 1;
+    // factor tables first: the windows below sort records by their width
+    const int tabw = P->tc_nna + P->tc_nnb + P->tc_ncols;
+    P->tc_tabw = tabw;
+    const size_t ntab = (size_t)std::max<int64_t>(P->npairs, 1) * tabw;
+    FTCJ_CUDA(cudaMalloc(&P->d_tc_tab, sizeof(float4) * ntab));
+    P->device_bytes += sizeof(float4) * ntab;
+    FTCJ_CUDA(cudaMalloc(&P->d_tc_cl, sizeof(float) * std::max<int64_t>(P->npairs, 1)));
+    P->device_bytes += sizeof(float) * std::max<int64_t>(P->npairs, 1);
+    FTCJ_CUDA(cudaMalloc(&P->d_tc_err, sizeof(int)));
+    FTCJ_CUDA(cudaMemset(P->d_tc_err, 0, sizeof(int)));
+    std::vector<float> clh((size_t)std::max<int64_t>(P->npairs, 1), 0.f);
+    if (P->npairs > 0) {
+        const long long n = P->npairs * (long long)tabw;
+        k_tc_tables<<<(unsigned)((n + 255) / 256), 256>>>(P->d_walk, P->npairs, a, b, c, P->tc_nna, P->tc_nnb,
+                                                        P->tc_ncols, P->M[4 * a], P->M[4 * b], P->M[4 * c],
+                                                        reinterpret_cast<float4*>(P->d_tc_tab), P->d_tc_cl);
+        FTCJ_CUDA(cudaGetLastError());
+        FTCJ_CUDA(cudaMemcpy(clh.data(), P->d_tc_cl, sizeof(float) * P->npairs, cudaMemcpyDeviceToHost));
+    }
+    // windows: for each class L, its (i, j) blocks in groups of G, and the
+    // class's records sorted by width c = 1/4p in blocks of 512 (the K order of
+    // the matrix product; records of similar width have entries of similar size)
+    std::vector<int> wrec, wpairs;
+    std::vector<int4> winfo;
+    for (int L = 0; L < kNclass; ++L) {
+        std::vector<int> recs;
+        for (int64_t r = P->class_start[L]; r < P->class_start[L + 1]; ++r) recs.push_back((int)r);
+        if (recs.empty()) continue;
+        std::stable_sort(recs.begin(), recs.end(), [&](int x, int y) { return clh[x] < clh[y]; });
+        std::vector<int> blocks;
+        for (int i = 0; i <= L; ++i)
+            for (int j = 0; i + j <= L; ++j) blocks.push_back(i | (j << 3));
+        for (size_t g0 = 0; g0 < blocks.size(); g0 += P->tc_G) {
+            const int nb = (int)std::min<size_t>(P->tc_G, blocks.size() - g0);
+            const int first = (int)wpairs.size();
+            wpairs.insert(wpairs.end(), blocks.begin() + g0, blocks.begin() + g0 + nb);
+            for (size_t r0 = 0; r0 < recs.size(); r0 += kTcWin) {
+                winfo.push_back(make_int4(L, nb, first, 0));
+                for (int k = 0; k < kTcWin; ++k) wrec.push_back(r0 + k < recs.size() ? recs[r0 + k] : -1);
+            }
+        }
+    }
+    if (winfo.empty()) {  // no records: one empty window keeps the launch shape valid
+        winfo.push_back(make_int4(0, 0, 0, 0));
+        wrec.assign(kTcWin, -1);
+    }
+    P->tc_nwin = (int)winfo.size();
+    // window groups: one CTA per SM over all (group, row tile) pairs, so the
+    // grid is a single wave of equal CTAs (a partial second wave would double the pass)
+    const int want = std::max(1, std::min(P->tc_nwin, P->num_sms / std::max(1, P->tc_mtiles)));
+    P->tc_wpg = std::max(1, (P->tc_nwin + want - 1) / want);
+    P->tc_ngroups = (P->tc_nwin + P->tc_wpg - 1) / P->tc_wpg;
+    // table slots in flight: as many as shared memory holds, 2 to 4
+    int dev = 0, optin = 0;
+    FTCJ_CUDA(cudaGetDevice(&dev));
+    FTCJ_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    P->tc_tslots = 0;
+    for (int nts = kTcTabSlotsMax; nts >= 2 && !P->tc_tslots; --nts)
+        if (tc_smem_bytes(P->tc_npad, tabw, P->tc_G, P->tc_nd, nts) <= (size_t)optin) P->tc_tslots = nts;
+    if (!P->tc_tslots)
+        return fail(FTCJ_EUNSUPPORTED, "the G sphere is too long for the tensor-core kernel's shared-memory tables");
+    int rc;
+    int2* rows_dev = nullptr;
+    if ((rc = tc_upload(P, &rows_dev, rowv))) return rc;
+    P->d_tc_rows = rows_dev;
+    if ((rc = tc_upload(P, &P->d_tc_map, map))) return rc;
+    if ((rc = tc_upload(P, &P->d_tc_kappa, wrec))) return rc;
+    if ((rc = tc_upload(P, &P->d_tc_wpairs, wpairs))) return rc;
+    int4* winfo_dev = nullptr;
+    if ((rc = tc_upload(P, &winfo_dev, winfo))) return rc;
+    P->d_tc_winfo = winfo_dev;
+    return allow_dynamic_smem((const void*)k_tc_rho, tc_smem_bytes(P->tc_npad, tabw, P->tc_G, P->tc_nd, P->tc_tslots));
+}
+
+int launch_tc_rho(ftcj_plan* P, int ndens, cudaStream_t s) {
+    if (P->ng_half == 0 || P->npairs == 0) {
+        FTCJ_CUDA(cudaMemsetAsync(P->d_rho_part, 0, sizeof(double2) * (size_t)ndens * P->tc_ngroups * P->ng_half, s));
+        return FTCJ_OK;
+    }
+    TcArgs g;
+    g.rows = reinterpret_cast<const int2*>(P->d_tc_rows);
+    g.map = P->d_tc_map;
+    g.wrec = P->d_tc_kappa;
+    g.winfo = reinterpret_cast<const int4*>(P->d_tc_winfo);
+    g.wpairs = P->d_tc_wpairs;
+    g.tab = reinterpret_cast<const float4*>(P->d_tc_tab);
+    g.cl = P->d_tc_cl;
+    g.Dp = reinterpret_cast<const float2*>(P->d_Dp);
+    g.dp_total = P->total_terms;
+    for (int cc = 0; cc <= kNclass; ++cc) g.cls_start[cc] = P->class_start[cc];
+    for (int cc = 0; cc < kNclass; ++cc) g.term_base[cc] = P->term_base[cc];
+    g.out = reinterpret_cast<double2*>(P->d_rho_part);
+    g.ng_half = P->ng_half;
+    g.err = P->d_tc_err;
+    g.Maa = (float)P->M[4 * P->tc_axis[0]];
+    g.Mbb = (float)P->M[4 * P->tc_axis[1]];
+    g.Mcc = (float)P->M[4 * P->tc_axis[2]];
+    g.ax = P->tc_axis[0];
+    g.bx = P->tc_axis[1];
+    g.cx = P->tc_axis[2];
+    g.tabw = P->tc_tabw;
+    g.offY = P->tc_nna;
+    g.offZ = P->tc_nna + P->tc_nnb;
+    g.ncols = P->tc_ncols;
+    g.G = P->tc_G;
+    g.nwin = P->tc_nwin;
+    g.win_per_group = P->tc_wpg;
+    g.ngroups = P->tc_ngroups;
+    g.nrows = P->tc_rows;
+    const size_t smem = tc_smem_bytes(P->tc_npad, P->tc_tabw, P->tc_G, P->tc_nd, P->tc_tslots);
+    for (int d0 = 0; d0 < ndens; d0 += P->tc_nd) {
+        g.d0 = d0;
+        g.nd = std::min(P->tc_nd, ndens - d0);
+        int colw, Gx, npad;
+        tc_columns(g.nd, g.ncols, &colw, &Gx, &npad);
+        // the plan's block count G is kept; a smaller last density group only narrows each block
+        g.colw = colw;
+        g.npad = round_up(P->tc_G * colw, 16);
+        k_tc_rho<<<dim3((unsigned)P->tc_ngroups, (unsigned)P->tc_mtiles), kTcThreadsAll, smem, s>>>(g, P->tc_tslots);
+        FTCJ_CUDA(cudaGetLastError());
+    }
+    return FTCJ_OK;
+}
+
+int tc_rho_launches(const ftcj_plan* P, int nd) { return (nd + P->tc_nd - 1) / P->tc_nd; }
+
+}  // namespace ftcj

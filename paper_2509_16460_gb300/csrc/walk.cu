@@ -613,7 +613,7 @@ int launch_rho_reduce(ftcj_plan* P, int ndens, double* rho_out, double* W_out, d
                       cudaStream_t s) {
     const double2* part = rho_in ? reinterpret_cast<const double2*>(rho_in)
                                  : reinterpret_cast<const double2*>(P->d_rho_part);
-    int nparts = rho_in ? 1 : P->npb;
+    int nparts = rho_in ? 1 : P->rho_rows;
     if (P->ng_half > 0) {
         dim3 g(P->nEblocks, ndens);
         k_rho_reduce<<<g, 256, 0, s>>>(part, nparts, P->ng_half, P->d_vg, reinterpret_cast<double2*>(rho_out),

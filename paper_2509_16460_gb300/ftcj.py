@@ -41,7 +41,8 @@ class BasisDesc(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("omega", _c_double), ("gcut", _c_double), ("eps_g", _c_double), ("pair_thresh", _c_double),
                 ("precision", _c_int), ("max_dens", _c_int), ("chunk_points", _c_int), ("rho_blocks", _c_int),
-                ("pair_gcut_eps", _c_double), ("shard_count", _c_int), ("shard_index", _c_int)]
+                ("pair_gcut_eps", _c_double), ("shard_count", _c_int), ("shard_index", _c_int),
+                ("contraction", _c_int)]
 
 
 class Info(ctypes.Structure):
@@ -67,7 +68,11 @@ EXPORTED = [
     "ftcj_profile_enable", "ftcj_profile_read", "ftcj_launches_per_batch", "ftcj_probe_fma_peak",
     "ftcj_potential_noalloc", "ftcj_batch_create", "ftcj_batch_info", "ftcj_batch_jbuild", "ftcj_batch_capture",
     "ftcj_batch_replay", "ftcj_batch_destroy", "ftcj_autotune", "ftcj_grad", "ftcj_shard_bounds",
+    "ftcj_plan_status",
 ]
+
+FTCJ_CONTRACT_WALK = 0
+FTCJ_CONTRACT_TC = 1
 
 FTCJ_BATCH_AUTOTUNE = 1
 
@@ -110,6 +115,7 @@ def _declare(L):
         getattr(L, name).argtypes = [P, _c_int, P, P, P]
     L.ftcj_potential.argtypes = [P, _c_int, P, P, P, P]
     L.ftcj_check_density.argtypes = [P, _c_int, P, _dp, _dp, P]
+    L.ftcj_plan_status.argtypes = [P, _ip, P]
     L.ftcj_get_gvectors.argtypes = [P, _ip]
     L.ftcj_get_pairs.argtypes = [P, _ip]
     L.ftcj_get_groups.argtypes = [P, _ip, _dp, _ip, _ip]
@@ -187,9 +193,11 @@ def _describe(A, xyz, shells, keep):
     return cell, basis
 
 
-def _params_of(w, precision=FTCJ_PREC_FP64, max_dens=None, chunk_points=0, rho_blocks=0, pair_gcut_eps=0.0):
+def _params_of(w, precision=FTCJ_PREC_FP64, max_dens=None, chunk_points=0, rho_blocks=0, pair_gcut_eps=0.0,
+               contraction=0):
     return Params(float(w.omega), float(w.gcut), float(w.eps_g), float(w.pair_thresh), int(precision),
-                  int(max_dens or w.ndens), int(chunk_points), int(rho_blocks), float(pair_gcut_eps), 0, 0)
+                  int(max_dens or w.ndens), int(chunk_points), int(rho_blocks), float(pair_gcut_eps), 0, 0,
+                  int(contraction))
 
 
 def shard_bounds(class_counts, precision, shard_count):
@@ -301,13 +309,14 @@ class Plan:
 
     def __init__(self, A, xyz, shells, kmesh, omega, eps_g=1e-14, gcut=0.0, pair_thresh=1e-12,
                  precision=FTCJ_PREC_FP64, max_dens=1, chunk_points=0, rho_blocks=0, pair_gcut_eps=0.0,
-                 shard_count=0, shard_index=0):
+                 shard_count=0, shard_index=0, contraction=FTCJ_CONTRACT_WALK):
         L = lib()
         self._keep = []
         cell, basis = _describe(A, xyz, shells, self._keep)
         km = (ctypes.c_int * 3)(*[int(k) for k in kmesh])
         prm = Params(float(omega), float(gcut), float(eps_g), float(pair_thresh), int(precision), int(max_dens),
-                     int(chunk_points), int(rho_blocks), float(pair_gcut_eps), int(shard_count), int(shard_index))
+                     int(chunk_points), int(rho_blocks), float(pair_gcut_eps), int(shard_count), int(shard_index),
+                     int(contraction))
         self.shard_count = max(1, int(shard_count))
         self.shard_index = int(shard_index)
         h = _c_void_p()
@@ -326,11 +335,11 @@ class Plan:
 
     @classmethod
     def from_workload(cls, w, max_dens=None, precision=FTCJ_PREC_FP64, chunk_points=0, rho_blocks=0,
-                      pair_gcut_eps=0.0, shard_count=0, shard_index=0):
+                      pair_gcut_eps=0.0, shard_count=0, shard_index=0, contraction=FTCJ_CONTRACT_WALK):
         return cls(w.A, w.xyz, w.shells, w.kmesh, w.omega, eps_g=w.eps_g, gcut=w.gcut, pair_thresh=w.pair_thresh,
                    precision=precision, max_dens=max_dens or w.ndens, chunk_points=chunk_points,
                    pair_gcut_eps=pair_gcut_eps, rho_blocks=rho_blocks, shard_count=shard_count,
-                   shard_index=shard_index)
+                   shard_index=shard_index, contraction=contraction)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -467,6 +476,13 @@ class Plan:
         nl = ctypes.c_int64()
         _check(lib().ftcj_profile_read(self._h, ms, ctypes.byref(nb), ctypes.byref(nl)), "ftcj_profile_read")
         return dict(zip(PHASES, list(ms))), nb.value, nl.value
+
+    def status(self, stream=None) -> int:
+        """ftcj_plan_status: the device error word of the last builds (0: every
+        bounded wait completed); clears it."""
+        f = ctypes.c_int()
+        _check(lib().ftcj_plan_status(self._h, ctypes.byref(f), _stream_ptr(stream)), "ftcj_plan_status")
+        return f.value
 
     def launches_per_batch(self, nd: int = 1) -> int:
         n = ctypes.c_int64()

@@ -1,0 +1,114 @@
+"""The tensor-core separable contraction (Sec. 2.4, orthorhombic fully
+separable case) against the FP64 oracle.  rho(G) is a sliced bf16 tcgen05
+matrix product over (pair record, i, j) with exact level accumulators and
+double-float window sums; the bar is the split form's: max|dJ| <= 1e-8 Eh
+and |dE_J| <= 1e-8 Eh, plus rho element by element at 1e-10 of max|rho|.
+Every build must also leave the device error word of the bounded waits at
+zero."""
+import numpy as np
+import pytest
+
+from paper_2509_16460_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+J_TOL = 1e-8
+RHO_REL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def F():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2509_16460_gb300 import build
+    build.build()
+    from paper_2509_16460_gb300 import ftcj
+    return ftcj
+
+
+def tc_plan(F, w, **kw):
+    return F.Plan.from_workload(w, precision=F.FTCJ_PREC_SPLIT, contraction=F.FTCJ_CONTRACT_TC, **kw)
+
+
+def check_against_oracle(orc, F, w, **kw):
+    import torch
+    ref = orc.lrj(w, want_j0n=False)
+    plan = tc_plan(F, w, **kw)
+    try:
+        Dk = torch.from_numpy(np.ascontiguousarray(w.Dk)).cuda()
+        Jk, EJ = plan.jbuild(Dk)
+        nd = min(w.ndens, plan.max_dens)
+        rho = plan.rho(plan.fold_density(Dk[:nd].contiguous())).cpu().numpy()
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        Jk, EJ = Jk.cpu().numpy(), EJ.cpu().numpy()
+        dJ = float(np.abs(Jk - ref["Jk"]).max())
+        dE = float(np.abs(EJ - ref["EJ"]).max())
+        Gh = plan.gvectors()
+        idx = {tuple(g): i for i, g in enumerate(ref["G"].tolist())}
+        sel = np.array([idx[tuple(g)] for g in Gh.tolist()])
+        rref = ref["rho"][:nd, sel]
+        drho = float(np.abs(rho - rref).max())
+        scale = float(np.abs(rref).max())
+        print(f"{w.name}: tc max|dJ|={dJ:.3e} |dE|={dE:.3e} max|drho|={drho:.3e} (max|rho|={scale:.3e}, "
+              f"max|J|={np.abs(ref['Jk']).max():.3e}) launches/pass={plan.info['rho_walk_launches']}")
+        assert drho <= RHO_REL * max(1.0, scale), (w.name, drho)
+        assert dJ <= J_TOL and dE <= J_TOL * max(1.0, float(np.abs(ref["EJ"]).max())), (w.name, dJ, dE)
+        return plan.info
+    finally:
+        plan.close()
+
+
+def test_tc_cfg1_gamma(orc, F):
+    check_against_oracle(orc, F, W.cfg1())
+
+
+def test_tc_orthorhombic_kmesh_two_densities(orc, F):
+    spec = [(0, 0, [0.3, 1.1, 4.0]), (0, 1, [0.5, 1.3]), (0, 2, [0.7]),
+            (1, 0, [0.25, 2.0]), (1, 1, [0.8]), (1, 2, [0.45])]
+    w = W.tiny(seed=41, A=np.diag([4.6, 5.3, 6.1]), kmesh=(2, 1, 2), shell_spec=spec, omega=0.45, ndens=2)
+    check_against_oracle(orc, F, w)
+
+
+def test_tc_reduced_crystal_many_windows(orc, F):
+    """The molecular-crystal lattice and G sphere (4,977 half-sphere points,
+    5 row tiles or fewer), a reduced basis with two densities: several K
+    windows per group, several groups."""
+    from tests.test_gpu_launch_shapes import reduced_crystal
+    info = check_against_oracle(orc, F, reduced_crystal())
+    assert info["ng_half"] == 4977
+
+
+def test_tc_cfg3_against_split_walk(F):
+    """Full molecular crystal: the tensor-core form against the split form's
+    walks (both double-float class; the walk is checked against the oracle
+    at sampled G and by invariants)."""
+    import torch
+    w = W.cfg3()
+    Dk = torch.from_numpy(np.ascontiguousarray(w.Dk)).cuda()
+    walk = F.Plan.from_workload(w, precision=F.FTCJ_PREC_SPLIT)
+    Jw, Ew = walk.jbuild(Dk)
+    rw = walk.rho(walk.fold_density(Dk)).cpu().numpy()
+    walk.close()
+    tc = tc_plan(F, w)
+    Jt, Et = tc.jbuild(Dk)
+    rt = tc.rho(tc.fold_density(Dk)).cpu().numpy()
+    torch.cuda.synchronize()
+    assert tc.status() == 0
+    tc.close()
+    dJ = float((Jt - Jw).abs().max())
+    dE = float((Et - Ew).abs().max())
+    drho = float(np.abs(rt - rw).max())
+    print(f"cfg3 tc vs walk: max|dJ|={dJ:.3e} |dE|={dE:.3e} max|drho|={drho:.3e} max|rho|={np.abs(rw).max():.3e}")
+    assert drho <= RHO_REL * np.abs(rw).max()
+    assert dJ <= J_TOL and dE <= J_TOL * max(1.0, float(Ew.abs().max()))
+
+
+def test_tc_refusals(F):
+    with pytest.raises(F.FtcjError, match="orthorhombic"):
+        tc_plan(F, W.tiny(seed=42, A=np.array([[5.0, 0.0, 0.0], [1.2, 5.1, 0.0], [0.0, 0.0, 5.5]])))
+    with pytest.raises(F.FtcjError, match="split"):
+        F.Plan.from_workload(W.cfg1(), precision=F.FTCJ_PREC_FP64, contraction=F.FTCJ_CONTRACT_TC)
+    with pytest.raises(F.FtcjError, match="whole sphere"):
+        tc_plan(F, W.cfg1(), pair_gcut_eps=1e-12)
