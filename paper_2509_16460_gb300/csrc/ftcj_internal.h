@@ -116,6 +116,19 @@ struct RecBlocks {
     int stage[kNclass];
 };
 
+// Where the split form's Hermite-term map writes D'_t: with pos == nullptr the
+// per-class SoA layout in record order (MapLayout); else the tensor-core
+// layout [dens][class c][term t][position], the position of a record within
+// its class given by pos (the contraction's K order), the class's stride
+// rounded up to 16 entries so that every 16 consecutive positions of a term
+// are one aligned 128-byte row.
+struct TermDest {
+    const int* pos;
+    long long base[kNclass];
+    long long stride[kNclass];
+    long long total;
+};
+
 // Per-cell constants, passed to kernels by value (so plans of different cells
 // can be alive and used together).
 struct CellConst {
@@ -224,6 +237,8 @@ struct ftcj_plan {
     void* d_tc_tab = nullptr;    // float4 [npairs][tabw]
     float* d_tc_cl = nullptr;    // [npairs]
     int* d_tc_err = nullptr;     // device error word of the bounded waits
+    int* d_tc_pos = nullptr;     // [npairs]: position of each record in its class's K order
+    long long tc_dp_base[ftcj::kNclass] = {}, tc_dp_stride[ftcj::kNclass] = {}, tc_dp_total = 0;
     int rho_rows = 0;            // partial rows the rho reduction sums (walk blocks or tensor-core groups)
     int precision = FTCJ_PREC_FP64;
     bool ortho = false;  // reciprocal metric diagonal (orthorhombic cell)

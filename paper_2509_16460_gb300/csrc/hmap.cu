@@ -279,7 +279,8 @@ __global__ void __launch_bounds__(256) k_hermite_map_df(const PairDev* __restric
                                                         const long long* __restrict__ moff,
                                                         const float2* __restrict__ maps,
                                                         const double* __restrict__ D0n, int nao, int nk,
-                                                        MapLayout lay, RecBlocks rb, float2* __restrict__ Dp) {
+                                                        MapLayout lay, RecBlocks rb, TermDest dst,
+                                                        float2* __restrict__ Dp) {
     extern __shared__ float2 stage[];
     const int d = blockIdx.y;
     const int c = block_class(rb);
@@ -316,8 +317,9 @@ __global__ void __launch_bounds__(256) k_hermite_map_df(const PairDev* __restric
         const float2 x = v[e];
         acc = df_add(acc, df_mul_u(df{m.x, m.y}, df{x.x, x.y}));
     }
-    const long long off = (long long)d * lay.total + lay.base[c] + (i - lay.start[c]) +
-                          (long long)t * (lay.start[c + 1] - lay.start[c]);
+    const long long off = dst.pos ? (long long)d * dst.total + dst.base[c] + (long long)t * dst.stride[c] + dst.pos[i]
+                                  : (long long)d * lay.total + lay.base[c] + (i - lay.start[c]) +
+                                        (long long)t * (lay.start[c + 1] - lay.start[c]);
     Dp[off] = make_float2(acc.hi, acc.lo);
 }
 
@@ -463,6 +465,18 @@ size_t rec_blocks_smem(const RecBlocks& rb) {
     return m;
 }
 
+// the tensor-core plans take the Hermite terms in their own K order
+TermDest term_dest(const ftcj_plan* P) {
+    TermDest t;
+    t.pos = P->tc ? P->d_tc_pos : nullptr;
+    for (int c = 0; c < kNclass; ++c) {
+        t.base[c] = P->tc_dp_base[c];
+        t.stride[c] = P->tc_dp_stride[c];
+    }
+    t.total = P->tc_dp_total;
+    return t;
+}
+
 MapLayout make_map_layout(const ftcj_plan* P) {
     MapLayout l;
     for (int c = 0; c <= kNclass; ++c) l.start[c] = P->class_start[c];
@@ -585,7 +599,7 @@ int launch_hermite_map(ftcj_plan* P, int ndens, const double* D0n, cudaStream_t 
         dim3 g((unsigned)P->rb_terms.bstart[kNclass], ndens);
         k_hermite_map_df<<<g, 256, P->rb_terms_smem, s>>>(P->d_pairs, P->d_groups, P->d_members, P->d_map_off,
                                                           reinterpret_cast<const float2*>(P->d_maps), D0n, P->nao,
-                                                          P->nk, make_map_layout(P), P->rb_terms,
+                                                          P->nk, make_map_layout(P), P->rb_terms, term_dest(P),
                                                           reinterpret_cast<float2*>(P->d_Dp));
         FTCJ_CUDA(cudaGetLastError());
         return FTCJ_OK;

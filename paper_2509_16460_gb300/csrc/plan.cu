@@ -302,7 +302,8 @@ void free_device(ftcj_plan* P) {
                     P->d_Dp, P->d_Jp, P->d_rho_part, P->d_rho, P->d_W, P->d_Epart, P->d_Dk_stage,
                     P->d_Jk_stage, P->d_EJ_stage, P->d_check, P->d_split_init, P->d_split_const, P->d_Jg,
                     P->d_maps, P->d_map_off, P->d_sched, P->d_rec_gcut, P->d_tc_rows, P->d_tc_map,
-                    P->d_tc_kappa, P->d_tc_tab, P->d_tc_cl, P->d_tc_err, P->d_tc_wpairs, P->d_tc_winfo};
+                    P->d_tc_kappa, P->d_tc_tab, P->d_tc_cl, P->d_tc_err, P->d_tc_wpairs, P->d_tc_winfo,
+                    P->d_tc_pos};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (P->ev_fork) cudaEventDestroy(P->ev_fork);
@@ -537,7 +538,8 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     if ((rc = dalloc(P, &P->d_J0n, md * P->nk * nn))) return rc;
     if ((rc = dalloc(P, &P->d_cbuf0, 2 * md * P->nk * nn))) return rc;
     if ((rc = dalloc(P, &P->d_cbuf1, 2 * md * P->nk * nn))) return rc;
-    if ((rc = dalloc(P, &P->d_Dp, md * (size_t)P->total_terms))) return rc;
+    // the tensor-core layout pads each class to 16 positions (and the last bulk copy may read 16 past a class)
+    if ((rc = dalloc(P, &P->d_Dp, md * (size_t)std::max<long long>(P->total_terms, P->tc_dp_total) + 64))) return rc;
     if ((rc = dalloc(P, &P->d_Jp, md * (size_t)nch * (size_t)P->total_terms))) return rc;
     if ((rc = dalloc(P, &P->d_Jg, md * (size_t)nch * (size_t)P->total_terms_g))) return rc;
     if ((rc = dalloc(P, &P->d_rho_part, 2 * md * (size_t)std::max(P->npb, P->rho_rows) * (size_t)P->ng_half)))

@@ -86,14 +86,15 @@ struct TcArgs {
     const int2* rows;    // (n_a, n_b) per row
     const int* map;      // [rows][ncols]: half-sphere index, ~index where the stored point is -n, INT_MIN none
     const int* wrec;     // [nwin][kTcWin]: record ids of each window, -1 for padding
-    const int4* winfo;   // [nwin]: class L, number of (i,j) blocks, first block index into wpairs
+    const int4* winfo;   // [nwin]: class L, number of (i,j) blocks, first block index into wpairs,
+                         // position of the window's first record in its class's K order
     const int* wpairs;   // (i | j << 3) of each block
     const float4* tab;   // per record [tabw]: X(0..), Y(0..), Z(0..) as complex double-float
     const float* cl;     // per record c log2(e)
-    const float2* Dp;    // Hermite densities (double-float), [dens][dp_total]
+    const float2* Dp;    // Hermite densities (double-float) in the K order: [dens][class][term][position]
     long long dp_total;
-    long long cls_start[kNclass + 1];
-    long long term_base[kNclass];
+    long long dp_base[kNclass];
+    long long dp_stride[kNclass];
     double2* out;        // partial rows [dens][ngroups][ng_half]
     long long ng_half;
     int* err;            // device error word (bit 0: a bounded wait gave up)
@@ -270,7 +271,7 @@ struct TcSmem {
     int eA[kTcM];
     int eB[kTcEbMax];
     TcRow rowi[kTcM];
-    int winL, wnpair, clmin_bits;
+    int winL, wnpair, wpos, clmin_bits;
     uint64_t full[kTcNbuf], empty[kTcNbuf], accf, acce, done, psync;
     uint64_t tfull[kTcTabSlotsMax], tempty[kTcTabSlotsMax];
     uint32_t tmem;
@@ -278,10 +279,11 @@ struct TcSmem {
 };
 
 // One table slot of a stage: the 16 records' factor tables (copied whole by
-// the bulk-copy engine, tabw float4 each), then the Hermite terms D'_{ijk},
-// k = 0..4, of each (record, block, density) (zero past the record's degree).
+// the bulk-copy engine, tabw float4 each), then the Hermite terms D'_{ijk} of
+// the 16 records as rows [block][density][k = 0..4][record] (one 128-byte
+// bulk copy per row; rows past the block's degree are not written or read).
 __host__ __device__ inline size_t tab_slot_bytes(int tabw, int G, int nd) {
-    const size_t b = (size_t)kTcStageK * tabw * 16 + (size_t)kTcStageK * G * nd * 5 * 8;
+    const size_t b = (size_t)kTcStageK * tabw * 16 + (size_t)G * nd * 5 * kTcStageK * 8;
     return (b + 127) / 128 * 128;
 }
 
@@ -357,12 +359,14 @@ __device__ __forceinline__ void form_b(const TcArgs& g, const TcSmem& sm, const 
         cdf bv{{0.f, 0.f}, {0.f, 0.f}};
         if (gb < sm.wnpair && sm.rec[q * kTcStageK + kq] >= 0) {
             const float4 zv = tabs[kq * g.tabw + g.offZ + nc];
-            const float2* dv = dps + ((kq * g.G + gb) * g.nd + d) * 5;
+            const float2* dv = dps + (gb * g.nd + d) * 5 * kTcStageK + kq;
+            const int pr = sm.pairs[gb], nk = sm.winL - (pr & 7) - (pr >> 3);  // k = 0 .. L - i - j
             df re{0.f, 0.f}, im{0.f, 0.f};
             float pw = 1.f;
 #pragma unroll
             for (int kk = 0; kk < 5; ++kk) {
-                const float2 v = dv[kk];
+                if (kk > nk) break;
+                const float2 v = dv[kk * kTcStageK];
                 const df term = df_mulf(df{v.x, v.y}, pw);  // D'_k n_c^k, exact power
                 switch (kk & 3) {                           // (-i)^k
                     case 0: re = df_add(re, term); break;
@@ -404,14 +408,16 @@ __device__ __forceinline__ void form_b(const TcArgs& g, const TcSmem& sm, const 
     }
 }
 
-constexpr int kTcProdWarps = 11;
+constexpr int kTcProdWarps = 14;
 constexpr int kTcProdThreads = kTcProdWarps * 32;
-constexpr int kTcMmaWarp = 11;
-constexpr int kTcLoadWarp = 12;
-constexpr int kTcWarps = 13;
+constexpr int kTcMmaWarp = 14;
+constexpr int kTcLoadWarp = 15;
+constexpr int kTcWarps = 16;
 constexpr int kTcEpiWarps = 12;
 constexpr int kTcEpiThreads = kTcEpiWarps * 32;
 constexpr int kTcThreadsAll = kTcWarps * 32;
+constexpr int kTcTasksMax = 3;        // operand tasks per thread and stage: (512 + 4 G npo) / 448 <= 3
+constexpr int kTcTaskA = 1 << 20;     // task flag: an A task (row | group << 7), else a B task
 
 __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslots) {
     extern __shared__ __align__(1024) unsigned char tsm[];
@@ -426,6 +432,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslo
     const int w0 = kg * g.win_per_group, w1 = min(g.nwin, w0 + g.win_per_group);
     volatile int* abort_flag = &sm.abort_flag;
     const bool mma_warp = warp == kTcMmaWarp, load_warp = warp == kTcLoadWarp;
+    const bool epi = warp < kTcEpiWarps;  // drains tensor memory: four lane quadrants x three column thirds
 
     if (tid == 0) {
         for (int b = 0; b < kTcNbuf; ++b) {
@@ -473,13 +480,35 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslo
     const int npo = g.nd * g.ncols;  // complex outputs per block
     const int nchunk = g.colw / 8;   // 8-column chunks of a block (4 complex outputs each)
     const uint32_t acc_hi = (uint32_t)(4 * g.npad), acc_lo = acc_hi + (uint32_t)g.colw;
-    if (!load_warp) {
+    if (epi) {
         for (int c8 = ewarp3; c8 < nchunk; c8 += 3) {
             const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             tc_st8(tmem + tlane + acc_hi + (uint32_t)(8 * c8), z);
             tc_st8(tmem + tlane + acc_lo + (uint32_t)(8 * c8), z);
         }
         tc_wait_st();
+    }
+    // The operand tasks of a stage, the same for every stage: B tasks (four
+    // records of one (block, output pair)) then A tasks (four records of one
+    // row), dealt to the operand threads in snake order (0..P-1, P-1..0, ...),
+    // so that the heavier B tasks and the A tasks spread evenly.
+    int tk[kTcTasksMax], ntask = 0;
+    {
+        const int nbt = (kTcStageK / 4) * g.G * npo, ntot = nbt + kTcM * 4;
+#pragma unroll
+        for (int e = 0; e < kTcTasksMax; ++e) {
+            const int k = e * kTcProdThreads + ((e & 1) ? kTcProdThreads - 1 - tid : tid);
+            tk[e] = 0;
+            if (!mma_warp && !load_warp && k < ntot) {
+                if (k < nbt) {
+                    const int p = k % npo, t2 = k / npo, gb = t2 % g.G, kgq = t2 / g.G;
+                    tk[e] = kgq | (gb << 2) | (p << 6);
+                } else {
+                    tk[e] = (k - nbt) | kTcTaskA;
+                }
+                ntask = e + 1;
+            }
+        }
     }
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(g.npad >> 3) << 17) |
                            ((uint32_t)(kTcM >> 4) << 24);
@@ -494,6 +523,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslo
             const int4 wi = __ldg(g.winfo + w);
             sm.winL = wi.x;
             sm.wnpair = wi.y;
+            sm.wpos = wi.w;
             for (int b = 0; b < wi.y; ++b) {
                 const int pr = __ldg(g.wpairs + wi.z + b), i = pr & 7, j = pr >> 3;
                 sm.pairs[b] = pr;
@@ -518,12 +548,12 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslo
             if (lane == 0 && cmin < INFINITY) atomicMin(&sm.clmin_bits, __float_as_int(cmin));
             // B: |B_ij| <= exp(-c Mcc n^2) sum_k |D'_ijk| n^k, per (block, n_c, density) over the window
             // (warp-uniform trip counts: 512 = 384 + 128)
-            const long long cnt = g.cls_start[L + 1] - g.cls_start[L];
-            const float2* dpL = g.Dp + g.term_base[L];
+            const long long cnt = g.dp_stride[L];
+            const float2* dpL = g.Dp + g.dp_base[L];
             for (int k = tid; k < kTcWin; k += kTcEpiThreads) {
                 const int r = sm.rec[k];
                 const float cr = r >= 0 ? __ldg(g.cl + r) : 0.f;
-                const long long loc = r - g.cls_start[L];
+                const long long loc = sm.wpos + k;
                 for (int gb = 0; gb < npair; ++gb) {
                     for (int d = 0; d < g.nd; ++d) {
                         float cm[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -550,8 +580,10 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslo
         const float clmin = __int_as_float(sm.clmin_bits);
         // ---- stages ----
         if (load_warp) {
-            const long long cnt = g.cls_start[L + 1] - g.cls_start[L];
-            const float2* dpL = g.Dp + g.term_base[L];
+            // rows of D' a stage needs: (block, density, k <= L - i - j)
+            int nrow = 0;
+            for (int gb = 0; gb < npair; ++gb) nrow += g.nd * (L - (sm.pairs[gb] & 7) - (sm.pairs[gb] >> 3) + 1);
+            const float2* dpL = g.Dp + g.dp_base[L];
             for (int q = 0; q < kTcStagesPerWin; ++q, ++gs) {
                 const int ts = (int)(gs % ntslots);
                 const long long use = gs / ntslots;
@@ -561,37 +593,42 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslo
                 }
                 unsigned char* slotp = tring + (size_t)ts * tslot;
                 float2* dps = reinterpret_cast<float2*>(slotp + (size_t)kTcStageK * g.tabw * 16);
-                const int ntri = kTcStageK * g.G * g.nd;
-                for (int tri = lane; tri < ntri; tri += 32) {
-                    const int d = tri % g.nd, t2 = tri / g.nd, gb = t2 % g.G, u = t2 / g.G;
-                    const int r = sm.rec[q * kTcStageK + u];
-                    const bool live = r >= 0 && gb < npair;
-                    const float2* dp = dpL + (long long)(g.d0 + d) * g.dp_total + (live ? r - g.cls_start[L] : 0);
-                    float2 v[5];
-#pragma unroll
-                    for (int kk = 0; kk < 5; ++kk) {
-                        const int t = live ? sm.tidx[gb][kk] : -1;
-                        v[kk] = t >= 0 ? __ldg(dp + (long long)t * cnt) : make_float2(0.f, 0.f);
-                    }
-#pragma unroll
-                    for (int kk = 0; kk < 5; ++kk) dps[tri * 5 + kk] = v[kk];
-                }
-                __syncwarp();
+                // A stage holds records from its first entry on, or none (the padding at a
+                // window's end): its D' rows are copied only when it holds some, and then
+                // stay inside the class's 16-padded stride.
+                const int srow = sm.rec[q * kTcStageK] >= 0 ? nrow : 0;
                 if (lane == 0) {
                     uint32_t nv = 0;
                     for (int u = 0; u < kTcStageK; ++u) nv += sm.rec[q * kTcStageK + u] >= 0 ? 1u : 0u;
-                    mbar_arrive_tx(&sm.tfull[ts], nv * (uint32_t)g.tabw * 16u);
-                    for (int u = 0; u < kTcStageK; ++u) {
-                        const int r = sm.rec[q * kTcStageK + u];
+                    mbar_arrive_tx(&sm.tfull[ts], nv * (uint32_t)g.tabw * 16u + (uint32_t)srow * kTcStageK * 8u);
+                }
+                __syncwarp();
+                // lanes 0-15: the records' factor tables; the rest: 128-byte rows of D'
+                for (int idx = lane; idx < kTcStageK + srow; idx += 32) {
+                    if (idx < kTcStageK) {
+                        const int r = sm.rec[q * kTcStageK + idx];
                         if (r >= 0)
-                            bulk_copy(slotp + (size_t)u * g.tabw * 16, g.tab + (size_t)r * g.tabw,
+                            bulk_copy(slotp + (size_t)idx * g.tabw * 16, g.tab + (size_t)r * g.tabw,
                                       (uint32_t)g.tabw * 16u, &sm.tfull[ts]);
+                    } else {
+                        int row = idx - kTcStageK, gb = 0;
+                        for (;;) {  // row -> (block, density, k)
+                            const int nkb = L - (sm.pairs[gb] & 7) - (sm.pairs[gb] >> 3) + 1;
+                            if (row < g.nd * nkb) break;
+                            row -= g.nd * nkb;
+                            ++gb;
+                        }
+                        const int pr = sm.pairs[gb], nkb = L - (pr & 7) - (pr >> 3) + 1;
+                        const int d = row / nkb, kk = row - d * nkb;
+                        const long long src = (long long)(g.d0 + d) * g.dp_total +
+                                              (long long)sm.tidx[gb][kk] * g.dp_stride[L] + sm.wpos + q * kTcStageK;
+                        bulk_copy(dps + ((gb * g.nd + d) * 5 + kk) * kTcStageK, dpL + src, kTcStageK * 8u,
+                                  &sm.tfull[ts]);
                     }
                 }
                 __syncwarp();
             }
         } else if (!mma_warp) {
-            const int nbt = (kTcStageK / 4) * g.G * npo;  // B tasks per stage (four records each)
             for (int q = 0; q < kTcStagesPerWin; ++q, ++gs) {
                 const int slot = (int)(gs & 1), ts = (int)(gs % ntslots);
                 ok = __all_sync(0xffffffffu, mbar_wait(&sm.tfull[ts], (uint32_t)((gs / ntslots) & 1), abort_flag));
@@ -605,14 +642,17 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslo
                 const float2* dps = reinterpret_cast<const float2*>(slotp + (size_t)kTcStageK * g.tabw * 16);
                 unsigned char* as = abuf + (size_t)slot * kTcS * kTcAsliceBytes;
                 unsigned char* bs = bbuf + (size_t)slot * kTcS * bslice;
-                for (int task = tid; task < kTcM * 4; task += kTcProdThreads) {
-                    const int row = task & (kTcM - 1), gg = task >> 7;
-                    const int eAr = exp_bound(-clmin * sm.rowi[row].Q);
-                    form_a(g, sm, tabs, q, row, gg, pow2f(6 - eAr), as);
-                }
-                for (int task = tid; task < nbt; task += kTcProdThreads) {
-                    const int p = task % npo, t2 = task / npo, gb = t2 % g.G, kg = t2 / g.G;
-                    form_b(g, sm, tabs, dps, q, kg, gb, p, bs, bslice);
+#pragma unroll
+                for (int e = 0; e < kTcTasksMax; ++e) {
+                    if (e < ntask) {
+                        const int k = tk[e];
+                        if (k & kTcTaskA) {
+                            const int row = k & (kTcM - 1), gg = (k >> 7) & 3;
+                            form_a(g, sm, tabs, q, row, gg, pow2f(6 - exp_bound(-clmin * sm.rowi[row].Q)), as);
+                        } else {
+                            form_b(g, sm, tabs, dps, q, k & 3, (k >> 2) & 15, k >> 6, bs, bslice);
+                        }
+                    }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
@@ -652,7 +692,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslo
         }
         if (!ok) break;
         // ---- drain: each block's level sums, scaled and times P_ij, into the double-float sums (warps 0-11) ----
-        if (!load_warp) {
+        if (epi) {
             ok = __all_sync(0xffffffffu, mbar_wait(&sm.accf, (uint32_t)((w - w0) & 1), abort_flag));
             if (!ok) break;
             tc_fence_after();
@@ -698,16 +738,16 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslo
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.acce);
-            // the MMAs of the next window wait for every warp's drain
-            if (mma_warp && w + 1 < w1) {
-                ok = __all_sync(0xffffffffu, mbar_wait(&sm.acce, (uint32_t)((w - w0) & 1), abort_flag));
-                tc_fence_after();
-            }
+        }
+        // the MMAs of the next window wait for every draining warp
+        if (mma_warp && w + 1 < w1) {
+            ok = __all_sync(0xffffffffu, mbar_wait(&sm.acce, (uint32_t)((w - w0) & 1), abort_flag));
+            tc_fence_after();
         }
         if (!(ok = prod_sync(&sm.psync, ph, abort_flag, lane) && ok)) break;  // window tables reused next window
     }
     // ---- partial rows ----
-    if (ok && !*abort_flag && !load_warp) {
+    if (ok && !*abort_flag && epi) {
         tc_fence_after();
         const int mo = mt * kTcM + erow;
         for (int c8 = ewarp3; c8 < nchunk; c8 += 3) {
@@ -959,11 +999,20 @@ int setup_tc(ftcj_plan* P) {
     // the matrix product; records of similar width have entries of similar size)
     std::vector<int> wrec, wpairs;
     std::vector<int4> winfo;
+    std::vector<int> pos((size_t)std::max<int64_t>(P->npairs, 1), 0);
+    // Hermite terms in the K order: [dens][class][term][position], each class's stride a multiple of 16
+    P->tc_dp_total = 0;
+    for (int L = 0; L < kNclass; ++L) {
+        P->tc_dp_base[L] = P->tc_dp_total;
+        P->tc_dp_stride[L] = (recs_by_class[L] + kTcStageK - 1) / kTcStageK * kTcStageK;
+        P->tc_dp_total += (long long)nterms(L) * P->tc_dp_stride[L];
+    }
     for (int L = 0; L < kNclass; ++L) {
         std::vector<int> recs;
         for (int64_t r = P->class_start[L]; r < P->class_start[L + 1]; ++r) recs.push_back((int)r);
         if (recs.empty()) continue;
         std::stable_sort(recs.begin(), recs.end(), [&](int x, int y) { return clh[x] < clh[y]; });
+        for (size_t k = 0; k < recs.size(); ++k) pos[recs[k]] = (int)k;
         std::vector<int> blocks;
         for (int i = 0; i <= L; ++i)
             for (int j = 0; i + j <= L; ++j) blocks.push_back(i | (j << 3));
@@ -972,7 +1021,7 @@ int setup_tc(ftcj_plan* P) {
             const int first = (int)wpairs.size();
             wpairs.insert(wpairs.end(), blocks.begin() + g0, blocks.begin() + g0 + nb);
             for (size_t r0 = 0; r0 < recs.size(); r0 += kTcWin) {
-                winfo.push_back(make_int4(L, nb, first, 0));
+                winfo.push_back(make_int4(L, nb, first, (int)r0));
                 for (int k = 0; k < kTcWin; ++k) wrec.push_back(r0 + k < recs.size() ? recs[r0 + k] : -1);
             }
         }
@@ -1003,6 +1052,7 @@ int setup_tc(ftcj_plan* P) {
     if ((rc = tc_upload(P, &P->d_tc_map, map))) return rc;
     if ((rc = tc_upload(P, &P->d_tc_kappa, wrec))) return rc;
     if ((rc = tc_upload(P, &P->d_tc_wpairs, wpairs))) return rc;
+    if ((rc = tc_upload(P, &P->d_tc_pos, pos))) return rc;
     int4* winfo_dev = nullptr;
     if ((rc = tc_upload(P, &winfo_dev, winfo))) return rc;
     P->d_tc_winfo = winfo_dev;
@@ -1023,9 +1073,11 @@ int launch_tc_rho(ftcj_plan* P, int ndens, cudaStream_t s) {
     g.tab = reinterpret_cast<const float4*>(P->d_tc_tab);
     g.cl = P->d_tc_cl;
     g.Dp = reinterpret_cast<const float2*>(P->d_Dp);
-    g.dp_total = P->total_terms;
-    for (int cc = 0; cc <= kNclass; ++cc) g.cls_start[cc] = P->class_start[cc];
-    for (int cc = 0; cc < kNclass; ++cc) g.term_base[cc] = P->term_base[cc];
+    g.dp_total = P->tc_dp_total;
+    for (int cc = 0; cc < kNclass; ++cc) {
+        g.dp_base[cc] = P->tc_dp_base[cc];
+        g.dp_stride[cc] = P->tc_dp_stride[cc];
+    }
     g.out = reinterpret_cast<double2*>(P->d_rho_part);
     g.ng_half = P->ng_half;
     g.err = P->d_tc_err;
