@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary diamond line and the batch and slab legs")
-    ap.add_argument("--forms", default="split,fp64,split_pair_gcut",
+    ap.add_argument("--forms", default="split_tc,split,fp64,split_pair_gcut",
                     help="comma list of the headline forms to time (split is always timed)")
     ap.add_argument("--leg", choices=["batch", "molecular_crystal", "slab", "diamond"], default=None,
                     help="run only this extra workload (one GPU, rank 0) and print its JSON; for profiling")
@@ -221,7 +221,20 @@ def make_workload(W, name):
     return {"molecular_crystal": W.cfg3, "diamond": W.cfg2}[name]()
 
 
-FORMS = {"split": ("split", 0.0), "fp64": ("fp64", 0.0), "split_pair_gcut": ("split", PAIR_GCUT_EPS)}
+# form -> (pipe, per-pair cutoff eps, contraction): "split_tc" is the split form with the
+# tensor-core separable contraction of the structure-factor pass (orthorhombic cells)
+FORMS = {"split_tc": ("split", 0.0, 1), "split": ("split", 0.0, 0), "fp64": ("fp64", 0.0, 0),
+         "split_pair_gcut": ("split", PAIR_GCUT_EPS, 0)}
+
+
+def measured_bf16_peak():
+    """Sustained dense bf16 rate of this machine's GB300 (measured file if
+    present, else the recipe's fallback), for a kernel timed inside a long step."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["bf16_tflops_sustained"]) * 1e12, "MEASURED_PEAKS.json bf16_tflops_sustained, of measured"
+    except (OSError, KeyError, ValueError):
+        return 1.7e15, "fallback 1.7 PFLOP/s bf16 sustained, of fallback"
 
 
 def measure_form(ctx, w, wname, form):
@@ -233,10 +246,10 @@ def measure_form(ctx, w, wname, form):
     ftcj, torch, args, dist = ctx["ftcj"], ctx["torch"], ctx["args"], ctx["dist"]
     world, rank, local = ctx["world"], ctx["rank"], ctx["local"]
     flush, stream, barrier = ctx["flush"], ctx["stream"], ctx["barrier"]
-    pipe, eps = FORMS[form]
+    pipe, eps, contraction = FORMS[form]
     prec = ftcj.FTCJ_PREC_SPLIT if pipe == "split" else ftcj.FTCJ_PREC_FP64
     sharded = world > 1
-    plan = ftcj.Plan.from_workload(w, precision=prec, pair_gcut_eps=eps,
+    plan = ftcj.Plan.from_workload(w, precision=prec, pair_gcut_eps=eps, contraction=contraction,
                                    shard_count=world if sharded else 0, shard_index=rank if sharded else 0)
     info = plan.info
     Dk = ctx["Dk"]
@@ -302,9 +315,11 @@ def measure_form(ctx, w, wname, form):
     if not sharded:
         phase_ms, batches, launches = plan.profile_read()
         plan.profile_enable(0)
-        walks = {"k_rho_walk" + suffix: phase_ms["rho_walk"], "k_j_walk" + suffix: phase_ms["j_walk"]}
+        rho_name = "k_tc_rho" if contraction else "k_rho_walk" + suffix
+        walks = {rho_name: phase_ms["rho_walk"], "k_j_walk" + suffix: phase_ms["j_walk"]}
         kname = max(walks, key=walks.get)
         pass_ms = walks[kname] * max(1, -(-nd // plan.max_dens)) / max(batches, 1)
+        rho_pass_ms = phase_ms["rho_walk"] * max(1, -(-nd // plan.max_dens)) / max(batches, 1)
         phases = {k: v / max(batches, 1) for k, v in phase_ms.items()}
         timed_what = "the library's phase events around the whole walk pass (all class-part launches)"
     else:
@@ -327,6 +342,18 @@ def measure_form(ctx, w, wname, form):
                               "x densities" + (" x walked fraction of the units" if eps > 0 else ""),
                 "flops_per_pass": flops, "pass_ms": pass_ms, "timed": timed_what,
                 "nominal_peak": 152 * 2 * 2.07e9 * (2 if pipe == "fp64" else 128) / 1e12}
+    if contraction and not sharded:
+        # the tensor-core structure-factor pass: bf16 MMA flops (slice products included) against the
+        # sustained dense bf16 rate, and its algorithmic (4L+14) rate
+        bf16_peak, bf16_src = measured_bf16_peak()
+        mma = float(info["tc_mma_flops"]) * max(1, -(-nd // plan.max_dens))
+        roofline["tc_rho"] = {"bound": "tensor", "kernel": "k_tc_rho", "pass_ms": rho_pass_ms,
+                              "achieved": mma / (rho_pass_ms * 1e-3) / 1e12, "peak": bf16_peak / 1e12,
+                              "unit": "TFLOP/s", "frac": mma / (rho_pass_ms * 1e-3) / bf16_peak,
+                              "mma_flops_per_pass": mma, "peak_source": bf16_src,
+                              "algorithmic_tflops": walk_flops(info, nd) / (rho_pass_ms * 1e-3) / 1e12,
+                              "note": "21 bf16 slice products per exact-to-2^-41 product (6 slices a side), "
+                                      "real form of the complex product (4 real per complex multiply-add)"}
     if pipe == "split":
         roofline["fp32_pipe_ops_per_pass"] = emu
         roofline["fp32_pipe_ops_frac"] = emu / (pass_ms * 1e-3) / peak
@@ -597,7 +624,9 @@ def main():
     w = W.cfg3()
     ctx["Dk"] = torch.from_numpy(np.ascontiguousarray(w.Dk)).cuda()
     ctx["Dk_host"] = torch.from_numpy(np.ascontiguousarray(w.Dk)).pin_memory()
-    want = ["split"] + [f for f in args.forms.split(",") if f and f != "split"]
+    ortho = bool(np.allclose(w.A - np.diag(np.diag(w.A)), 0.0))
+    head_form = "split_tc" if ortho else "split"
+    want = [head_form] + [f for f in args.forms.split(",") if f and f != head_form]
     forms, results, infos = {}, {}, {}
     for f in want:
         if f not in FORMS:
@@ -606,13 +635,17 @@ def main():
         results[f] = r.pop("result")
         infos[f] = r.pop("info")
         forms[f] = r
-    head = forms["split"]
-    info = infos["split"]
+    head = forms[head_form]
+    info = infos[head_form]
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "strong",
-        "vs_baseline": None, "dtype": "f32x2 walks (double-float), f64 setup/sums/E_J", "data": "synthetic",
-        "config": {"workload": WORKLOADS[HEADLINE], "form": "split", "ndens": w.ndens,
+        "vs_baseline": None,
+        "dtype": ("bf16x6-sliced tcgen05 structure-factor contraction with exact FP32 level sums, f32x2 "
+                  "(double-float) operands, back-contraction walk and window sums, f64 setup/sums/E_J"
+                  if head_form == "split_tc" else "f32x2 walks (double-float), f64 setup/sums/E_J"),
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[HEADLINE], "form": head_form, "ndens": w.ndens,
                    "pair_g_units_per_step": head["pair_g_units_per_step"],
                    "npairs_ordered": info["npairs_ordered"] if world == 1 else None,
                    "pair_records": info["npairs"] if world == 1 else None,
@@ -631,10 +664,12 @@ def main():
     }
     if "fp64" in forms:
         line["split_speedup_vs_fp64"] = forms["fp64"]["ms_per_step"] / head["ms_per_step"]
-        dJ = float(np.abs(results["split"][0] - results["fp64"][0]).max())
-        dE = float(np.abs(results["split"][1] - results["fp64"][1]).max())
-        line["split_vs_fp64_max_abs_dJ"] = dJ
-        line["split_vs_fp64_abs_dEJ"] = dE
+        for f in forms:
+            if f != "fp64":
+                forms[f]["max_abs_dJ_vs_fp64"] = float(np.abs(results[f][0] - results["fp64"][0]).max())
+                forms[f]["abs_dEJ_vs_fp64"] = float(np.abs(results[f][1] - results["fp64"][1]).max())
+        line["split_vs_fp64_max_abs_dJ"] = forms[head_form]["max_abs_dJ_vs_fp64"]
+        line["split_vs_fp64_abs_dEJ"] = forms[head_form]["abs_dEJ_vs_fp64"]
     if rank == 0 and world == 1 and not args.no_extra:
         extra_steps = max(3, min(args.steps, 10))
         line["diamond"] = diamond_leg(ctx)

@@ -154,6 +154,10 @@ typedef struct {
     int rho_walk_launches;    /* kernel launches of one structure-factor walk pass: 2 where the
                                  split form runs it as two class parts, else 1 (0: nothing to walk) */
     int j_walk_launches;      /* the same for the back-contraction walk */
+    int contraction;          /* FTCJ_CONTRACT_WALK or FTCJ_CONTRACT_TC (the plan's structure-factor pass) */
+    int64_t tc_mma_flops;     /* tensor-core contraction: bf16 MMA flops (2 per multiply-add, every slice
+                                 product and padding column included) of one structure-factor pass over
+                                 max_dens densities; 0 for the walks */
 } ftcj_info;
 
 typedef struct ftcj_plan ftcj_plan;

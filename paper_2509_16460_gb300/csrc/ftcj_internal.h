@@ -229,6 +229,7 @@ struct ftcj_plan {
     int64_t tc_nkappa = 0;
     int tc_nwin = 0, tc_wpg = 0, tc_ngroups = 0;  // K windows, windows per group, groups (partial rows)
     int tc_tslots = 0;                            // stage-table slots in shared memory
+    int64_t tc_mma_flops = 0;                     // bf16 MMA flops of one pass over max_dens densities
     void* d_tc_rows = nullptr;   // int2 [rows]
     int* d_tc_map = nullptr;     // [rows][ncols]
     int* d_tc_kappa = nullptr;   // [nwin * 512] record ids of each window

@@ -638,6 +638,8 @@ int ftcj_plan_info(const ftcj_plan* P, ftcj_info* o) {
     const bool walks = P->ng_half > 0 && !P->tiles.empty();
     o->rho_walk_launches = walks ? (P->tc ? tc_rho_launches(P, P->max_dens) : (P->rho_hi_tiles > 0 ? 2 : 1)) : 0;
     o->j_walk_launches = walks ? (P->precision == FTCJ_PREC_SPLIT ? split_j_launches(P) : 1) : 0;
+    o->contraction = P->tc ? FTCJ_CONTRACT_TC : FTCJ_CONTRACT_WALK;
+    o->tc_mma_flops = P->tc ? P->tc_mma_flops : 0;
     return FTCJ_OK;
 }
 

@@ -1031,6 +1031,17 @@ int setup_tc(ftcj_plan* P) {
         wrec.assign(kTcWin, -1);
     }
     P->tc_nwin = (int)winfo.size();
+    // MMA work of one pass: per window and row tile, 32 stages x 2 k-steps x 21 slice products of
+    // M = 128 rows, N = the window's columns, K = 16, for every density group
+    P->tc_mma_flops = 0;
+    for (int d0 = 0; d0 < P->max_dens; d0 += P->tc_nd) {
+        const int ndg = std::min(P->tc_nd, P->max_dens - d0);
+        const int colw = round_up(2 * ndg * P->tc_ncols, 8), np = round_up(P->tc_G * colw, 16);
+        for (const int4& wi : winfo) {
+            const long long nw = std::min(np, round_up(std::max(1, wi.y) * colw, 16));
+            P->tc_mma_flops += (long long)P->tc_mtiles * kTcStagesPerWin * 2 * 21 * 2LL * kTcM * nw * 16;
+        }
+    }
     // window groups: one CTA per SM over all (group, row tile) pairs, so the
     // grid is a single wave of equal CTAs (a partial second wave would double the pass)
     const int want = std::max(1, std::min(P->tc_nwin, P->num_sms / std::max(1, P->tc_mtiles)));

@@ -53,7 +53,8 @@ class Info(ctypes.Structure):
                 ("gcut", _c_double), ("volume", _c_double), ("device_bytes", ctypes.c_size_t),
                 ("rho_blocks", _c_int), ("n1_table", _c_int), ("pair_g_units_screened", ctypes.c_int64),
                 ("pair_g_units_walked", ctypes.c_int64), ("n_abs_max", _c_int), ("grad_split", _c_int),
-                ("rho_walk_launches", _c_int), ("j_walk_launches", _c_int)]
+                ("rho_walk_launches", _c_int), ("j_walk_launches", _c_int), ("contraction", _c_int),
+                ("tc_mma_flops", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
