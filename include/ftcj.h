@@ -117,7 +117,10 @@ typedef struct {
                            FTCJ_CONTRACT_TC (1): the tensor-core separable contraction (Sec. 2.4,
                            orthorhombic fully separable case): rho(n) as a sliced bf16 tcgen05 matrix
                            product over (pair record, i, j), split form and orthorhombic cells only
-                           (EUNSUPPORTED otherwise), whole sphere (pair_gcut_eps = 0) */
+                           (EUNSUPPORTED otherwise), whole sphere (pair_gcut_eps = 0); the
+                           back-contraction (Alg. S1) takes the same form where the sphere's
+                           (n_a, n_b) rows fit one exact accumulation, else the split walk
+                           (ftcj_info.j_contraction says which) */
 } ftcj_params;
 
 #define FTCJ_CONTRACT_WALK 0
@@ -158,6 +161,10 @@ typedef struct {
     int64_t tc_mma_flops;     /* tensor-core contraction: bf16 MMA flops (2 per multiply-add, every slice
                                  product and padding column included) of one structure-factor pass over
                                  max_dens densities; 0 for the walks */
+    int j_contraction;        /* the back-contraction's form: FTCJ_CONTRACT_TC where a tensor-core plan's
+                                 rows fit one exact accumulation (<= 672 rows of (n_a, n_b)), else
+                                 FTCJ_CONTRACT_WALK */
+    int64_t tc_j_mma_flops;   /* the same count for one tensor-core back-contraction; 0 for the walk */
 } ftcj_info;
 
 typedef struct ftcj_plan ftcj_plan;

@@ -29,6 +29,7 @@ int rho_walk(ftcj_plan* P, int nd, cudaStream_t s) {
 }
 
 int j_walk(ftcj_plan* P, int nd, const double* W, cudaStream_t s) {
+    if (P->tc_j) return launch_tc_j(P, nd, W, s);
     return P->precision == FTCJ_PREC_SPLIT ? launch_j_walk_split(P, nd, W, s) : launch_j_walk(P, nd, W, s);
 }
 

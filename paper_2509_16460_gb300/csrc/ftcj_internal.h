@@ -240,6 +240,16 @@ struct ftcj_plan {
     int* d_tc_err = nullptr;     // device error word of the bounded waits
     int* d_tc_pos = nullptr;     // [npairs]: position of each record in its class's K order
     long long tc_dp_base[ftcj::kNclass] = {}, tc_dp_stride[ftcj::kNclass] = {}, tc_dp_total = 0;
+    // tensor-core form of the back-contraction (tc.cu); false: the split walk runs it
+    bool tc_j = false;
+    int tc_jnd = 0, tc_jgw = 0, tc_jG = 0, tc_jnpad = 0;  // densities per launch, columns per density, blocks per item, MMA N
+    int tc_jnstage = 0, tc_jnitems = 0;                     // 8-row stages, work items
+    int tc_jparts = 0, tc_jspp = 0;                         // row parts (one exact accumulation each), stages per part
+    int64_t tc_j_mma_flops = 0;                             // bf16 MMA flops of one pass over max_dens densities
+    void* d_tc_jitems = nullptr;  // int4 [items]: class, blocks, first block, first record
+    int* d_tc_jpairs = nullptr;   // (i | j << 3) of the items' blocks
+    void* d_tc_vs = nullptr;      // bf16 sliced V_ij stage tiles
+    int* d_tc_ev = nullptr;       // their column scales
     int rho_rows = 0;            // partial rows the rho reduction sums (walk blocks or tensor-core groups)
     int precision = FTCJ_PREC_FP64;
     bool ortho = false;  // reciprocal metric diagonal (orthorhombic cell)
@@ -318,6 +328,10 @@ bool split_grad_walk_exact(const ftcj_plan* P);
 int setup_tc(ftcj_plan* P);
 int launch_tc_rho(ftcj_plan* P, int ndens, cudaStream_t s);
 int tc_rho_launches(const ftcj_plan* P, int nd);
+int launch_tc_j(ftcj_plan* P, int ndens, const double* W, cudaStream_t s);
+int tc_j_launches(const ftcj_plan* P, int nd);
+// partial back-contraction sums the J -> AO map adds: one per walk chunk, or per row part of the tensor-core form
+inline int jp_chunks(const ftcj_plan* P) { return P->tc_j ? P->tc_jparts : (int)P->chunks.size(); }
 
 // --- measurement (profile.cu) ---
 void release_profiling(ftcj_plan* P);

@@ -624,7 +624,7 @@ int launch_jtransform_map(ftcj_plan* P, int ndens, double* J0n, cudaStream_t s) 
         dim3 g((unsigned)P->rb_outs.bstart[kNclass], ndens);
         k_jtransform_map_df<<<g, 256, P->rb_outs_smem, s>>>(P->d_pairs, P->d_groups, P->d_members, P->d_map_off,
                                                             reinterpret_cast<const float2*>(P->d_maps), P->d_Jp,
-                                                            (int)P->chunks.size(), P->nao, P->nk,
+                                                            jp_chunks(P), P->nao, P->nk,
                                                             make_map_layout(P), P->rb_outs, J0n);
         FTCJ_CUDA(cudaGetLastError());
         return FTCJ_OK;
@@ -632,7 +632,7 @@ int launch_jtransform_map(ftcj_plan* P, int ndens, double* J0n, cudaStream_t s) 
     const long long n = P->mt_outs.tstart[kNclass];
     dim3 g((unsigned)((n + 255) / 256), ndens);
     k_jtransform_map<<<g, 256, 0, s>>>(P->d_pairs, P->d_groups, P->d_members, P->d_map_off, P->d_maps, P->d_Jp,
-                                       (int)P->chunks.size(), P->nao, P->nk, make_map_layout(P), P->mt_outs, J0n);
+                                       jp_chunks(P), P->nao, P->nk, make_map_layout(P), P->mt_outs, J0n);
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }

@@ -303,7 +303,7 @@ void free_device(ftcj_plan* P) {
                     P->d_Jk_stage, P->d_EJ_stage, P->d_check, P->d_split_init, P->d_split_const, P->d_Jg,
                     P->d_maps, P->d_map_off, P->d_sched, P->d_rec_gcut, P->d_tc_rows, P->d_tc_map,
                     P->d_tc_kappa, P->d_tc_tab, P->d_tc_cl, P->d_tc_err, P->d_tc_wpairs, P->d_tc_winfo,
-                    P->d_tc_pos};
+                    P->d_tc_pos, P->d_tc_jitems, P->d_tc_jpairs, P->d_tc_vs, P->d_tc_ev};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (P->ev_fork) cudaEventDestroy(P->ev_fork);
@@ -540,7 +540,7 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     if ((rc = dalloc(P, &P->d_cbuf1, 2 * md * P->nk * nn))) return rc;
     // the tensor-core layout pads each class to 16 positions (and the last bulk copy may read 16 past a class)
     if ((rc = dalloc(P, &P->d_Dp, md * (size_t)std::max<long long>(P->total_terms, P->tc_dp_total) + 64))) return rc;
-    if ((rc = dalloc(P, &P->d_Jp, md * (size_t)nch * (size_t)P->total_terms))) return rc;
+    if ((rc = dalloc(P, &P->d_Jp, md * (size_t)std::max(nch, jp_chunks(P)) * (size_t)P->total_terms))) return rc;
     if ((rc = dalloc(P, &P->d_Jg, md * (size_t)nch * (size_t)P->total_terms_g))) return rc;
     if ((rc = dalloc(P, &P->d_rho_part, 2 * md * (size_t)std::max(P->npb, P->rho_rows) * (size_t)P->ng_half)))
         return rc;
@@ -637,9 +637,13 @@ int ftcj_plan_info(const ftcj_plan* P, ftcj_info* o) {
     o->grad_split = P->precision == FTCJ_PREC_SPLIT && split_grad_walk_exact(P) ? 1 : 0;
     const bool walks = P->ng_half > 0 && !P->tiles.empty();
     o->rho_walk_launches = walks ? (P->tc ? tc_rho_launches(P, P->max_dens) : (P->rho_hi_tiles > 0 ? 2 : 1)) : 0;
-    o->j_walk_launches = walks ? (P->precision == FTCJ_PREC_SPLIT ? split_j_launches(P) : 1) : 0;
+    o->j_walk_launches =
+        walks ? (P->tc_j ? tc_j_launches(P, P->max_dens) : (P->precision == FTCJ_PREC_SPLIT ? split_j_launches(P) : 1))
+              : 0;
     o->contraction = P->tc ? FTCJ_CONTRACT_TC : FTCJ_CONTRACT_WALK;
     o->tc_mma_flops = P->tc ? P->tc_mma_flops : 0;
+    o->j_contraction = P->tc_j ? FTCJ_CONTRACT_TC : FTCJ_CONTRACT_WALK;
+    o->tc_j_mma_flops = P->tc_j ? P->tc_j_mma_flops : 0;
     return FTCJ_OK;
 }
 

@@ -26,7 +26,9 @@ int64_t launches_per_batch(const ftcj_plan* P) {
              ? (P->tc ? tc_rho_launches(P, P->max_dens) : (P->rho_hi_tiles > 0 ? 2 : 1))
              : 0;  // a4
     n += P->ng_half > 0 ? 2 : 0;                       // a5: reduce + energy
-    n += (P->ng_half > 0 && !P->tiles.empty()) ? (P->precision == FTCJ_PREC_SPLIT ? split_j_launches(P) : 1) : 0;  // a6
+    n += (P->ng_half > 0 && !P->tiles.empty())
+             ? (P->tc_j ? tc_j_launches(P, P->max_dens) : (P->precision == FTCJ_PREC_SPLIT ? split_j_launches(P) : 1))
+             : 0;  // a6
     n += P->npairs > 0 ? 1 : 0;                        // a7
     n += fold;                                         // a8
     return n;

@@ -881,9 +881,500 @@ void tc_columns(int nd, int ncols, int* colw, int* G, int* npad) {
     }
 }
 
+
+// ---- the back-contraction (Alg. S1) in the same separable form -------------
+//
+// The walks' back-contraction sums, over the stored half sphere,
+//   J'_{r,ijk} = Re sum_n (-i)^{i+j+k} n_a^i n_b^j n_c^k X_r(n_a) Y_r(n_b) Z_r(n_c) W(n).
+// On the grid of rows m = (n_a, n_b) and columns n_c >= 0 (a stored point -n
+// enters as conj W, since the conjugate of the summand at -n is the summand
+// at n with conj W) this is
+//   J'_{r,ijk} = Re (-i)^k sum_{n_c} n_c^k Z_r(n_c) U_ij[r, n_c],
+//   U_ij[r, n_c] = sum_m A^T[r, m] V_ij[m, n_c],
+//   A^T[r, m] = X_r(n_a) Y_r(n_b),  V_ij = (-i)^{i+j} n_a^i n_b^j W(m, n_c),
+// a complex matrix product with M = 128 records of one class, K = the rows
+// (real and imaginary parts), N = (i, j) blocks x densities x n_c.  V_ij does
+// not depend on the record: it is sliced once per build (k_tc_vbound,
+// k_tc_vslice) into stage tiles in global memory that bulk copies bring into
+// shared memory, and only A^T is formed in the kernel, from the 128 records'
+// factor tables staged once per work item.  Every entry of A^T has modulus
+// <= 1 (scale 2^1 for all of them); each column of V_ij gets its own scale
+// over all rows, so that entries far out in the sphere (where W has decayed)
+// sit many bits below their column's scale.  Seven slices (products with
+// s + t <= 6, 28 per k-step) keep the truncation below 2^-45 of the scales.
+// The rows are cut into parts of at most 512 (1024 real K terms), each a
+// work item of its own: within a part, levels 0-3 are exact (the level-3 sums
+// stay below 1024 x 14720 < 2^24 in units of 2^-21: |A| <= 1 bounds the
+// leading slice of A by 32) and only levels 4-6 share the rounded fifth
+// accumulator.  The tensor core's FP32 accumulation does not round to
+// nearest, so the rounded accumulator's error grows with the number of MMAs
+// that add into it and with its size; keeping level 3 out of it keeps that
+// error ~2^-7 of the four-accumulator scheme's.  The level sums go straight
+// to the epilogue, which forms the part's J' for k <= L - i - j in
+// double-float and writes it as one of the partial FP64 sums the J -> AO map
+// adds.
+
+constexpr int kTcJStageM = 8;        // rows per stage: one MMA k-step of 16 real K
+constexpr int kTcJS = 7;             // slices per operand
+constexpr int kTcJProducts = kTcJS * (kTcJS + 1) / 2;  // slice products formed: s + t <= 6
+constexpr int kTcJPartStages = 64;   // stages per row part at most: 512 rows, one exact accumulation
+constexpr int kTcJPartRows = kTcJPartStages * kTcJStageM;
+constexpr int kTcJAcc = 5;           // accumulators: levels 0-3 exact, levels 4-6 rounded
+constexpr int kTcJNmax = 96;         // MMA N at most: five level accumulators in the 512 columns
+constexpr int kTcJAsliceBytes = kTcM * 2 * kTcJStageM * 2;  // 128 records x 16 real K x bf16
+constexpr int kTcJTasks = kTcM * kTcJStageM;                  // (record, row) entries of a stage
+constexpr int kTcPairsAll = 15;      // (i, j) with i + j <= 4
+
+__host__ __device__ constexpr int pair_index(int i, int j) { return i * 5 - i * (i - 1) / 2 + j; }
+
+__device__ __forceinline__ void pair_of_index(int pr, int& i, int& j) {
+    i = 0;
+    while (pr > 4 - i) {
+        pr -= 5 - i;
+        ++i;
+    }
+    j = pr;
+}
+
+// Seven slices of x = hi + lo (|x| < 2^e, sc = 2^(6-e)): o[s] = m_s 2^(-7s),
+// integers |m_s| <= 64, x = 2^(e-6) sum_s o[s] up to 2^(e-51).  As in the
+// six-slice split, but the low part joins at slice 3 through an error-free
+// sum, so that none of its bits above 2^-45 (in units of o[0]) is lost.
+__device__ __forceinline__ void slice7(float hi, float lo, float sc, float (&o)[kTcJS]) {
+    float h = hi * sc;
+    const float l = lo * sc;
+    o[0] = (h + 0x1.8p23f) - 0x1.8p23f;
+    h -= o[0];
+    o[1] = (h + 0x1.8p16f) - 0x1.8p16f;
+    h -= o[1];
+    o[2] = (h + 0x1.8p9f) - 0x1.8p9f;
+    h -= o[2];
+    const df j = two_sum(h, l);  // h + l = j.hi + j.lo exactly
+    o[3] = (j.hi + 0x1.8p2f) - 0x1.8p2f;
+    h = (j.hi - o[3]) + j.lo;
+    o[4] = (h + 0x1.8p-5f) - 0x1.8p-5f;
+    h -= o[4];
+    o[5] = (h + 0x1.8p-12f) - 0x1.8p-12f;
+    h -= o[5];
+    o[6] = (h + 0x1.8p-19f) - 0x1.8p-19f;
+}
+
+// element offset of (row, k) in a stage tile [rows][16 real K] of core matrices
+__device__ __forceinline__ int tile_off16(int row, int k) {
+    return (((row >> 3) * 2 + (k >> 3)) << 6) + ((row & 7) << 3) + (k & 7);
+}
+
+// K-major, no swizzle: K-adjacent core matrices 128 B apart, 8-row groups 256 B apart
+__device__ __forceinline__ uint64_t sdesc16(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(256u >> 4) << 32) |
+           (1ull << 46);
+}
+
+struct TcJArgs {
+    const int2* rows;       // (n_a, n_b) per row (the structure-factor pass's rows)
+    const int* map;         // [rows][ncols]: half-sphere index, ~index where the stored point is -n, INT_MIN none
+    const double2* W;       // potential W(G) on the half sphere, [dens][ng_half]
+    const int4* items;      // work items: class L | row part << 8, blocks, first block index into ipairs, first record
+    const int* ipairs;      // (i | j << 3) of each block
+    const float4* tab;      // per record [tabw]: X(0..), Y(0..), Z(0..) as complex double-float
+    __nv_bfloat16* vs;      // sliced V_ij: [15 (i, j)][stage][slice][colw x 16 real K] stage tiles
+    int* ev;                // column scales of V_ij: [15][nd][ncols]
+    double* Jp;             // partial back-contraction sums [dens][part][term] in the split form's class layout
+    long long ng_half;
+    long long jp_total;     // doubles per density of Jp
+    long long cls_start[kNclass + 1];
+    long long term_base[kNclass];
+    int* err;               // device error word (bit 0: a bounded wait gave up)
+    int ax, bx, cx;
+    int tabw, offY, offZ;
+    int ncols, nd, d0;
+    int gw;                 // real columns per density: 2 ncols rounded up to 8
+    int colw;               // real columns per block: nd gw
+    int npad;               // MMA N of a full item: blocks x colw rounded up to 16 (<= 128)
+    int nrows, nstage, nitems;
+    int nparts, spp;        // row parts, stages per part
+};
+
+// column scales: the exponent bound of max over the rows of |n_a^i n_b^j W(m, n_c)|
+__global__ void __launch_bounds__(256) k_tc_vbound(TcJArgs g) {
+    const int col = blockIdx.x;  // ((i, j) nd + d) ncols + n_c
+    const int nc = col % g.ncols, d = (col / g.ncols) % g.nd, pr = col / (g.ncols * g.nd);
+    int i, j;
+    pair_of_index(pr, i, j);
+    float mx = 0.f;
+    for (int m = threadIdx.x; m < g.nrows; m += blockDim.x) {
+        const int2 rw = __ldg(g.rows + m);
+        const int idx = __ldg(g.map + (size_t)m * g.ncols + nc);
+        if (idx == INT_MIN) continue;
+        const double2 w = __ldg(g.W + (long long)(g.d0 + d) * g.ng_half + (idx < 0 ? ~idx : idx));
+        float p = 1.f;
+        for (int k = 0; k < i; ++k) p *= (float)abs(rw.x);
+        for (int k = 0; k < j; ++k) p *= (float)abs(rw.y);
+        mx = fmaxf(mx, p * (float)fmax(fabs(w.x), fabs(w.y)));
+    }
+    __shared__ float red[256];
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + st]);
+        __syncthreads();
+    }
+    // |Re V|, |Im V| <= mx up to the FP32 rounding of the bound
+    if (threadIdx.x == 0) g.ev[col] = red[0] > 0.f ? exp_bound(log2f(red[0] * 1.0001f)) : -100;
+}
+
+// V_ij sliced into stage tiles: tile (i, j), stage q, slice s holds column
+// d gw + 2 n_c + part and K = (row, re/im) in the real form rows
+// (m, re) -> [Re V | Im V], (m, im) -> [-Im V | Re V]; columns past 2 ncols
+// stay zero from the allocation.
+__global__ void __launch_bounds__(256) k_tc_vslice(TcJArgs g) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long per_pair = (long long)g.nstage * kTcJStageM * g.nd * g.ncols;
+    if (t >= kTcPairsAll * per_pair) return;
+    const int pr = (int)(t / per_pair);
+    long long rem = t - pr * per_pair;
+    const int nc = (int)(rem % g.ncols);
+    rem /= g.ncols;
+    const int d = (int)(rem % g.nd);
+    rem /= g.nd;
+    const int ml = (int)(rem % kTcJStageM), q = (int)(rem / kTcJStageM);
+    const int m = q * kTcJStageM + ml;
+    int i, j;
+    pair_of_index(pr, i, j);
+    cdf v{{0.f, 0.f}, {0.f, 0.f}};
+    if (m < g.nrows) {
+        const int2 rw = __ldg(g.rows + m);
+        const int idx = __ldg(g.map + (size_t)m * g.ncols + nc);
+        if (idx != INT_MIN) {
+            const double2 w = __ldg(g.W + (long long)(g.d0 + d) * g.ng_half + (idx < 0 ? ~idx : idx));
+            float p = 1.f;  // n_a^i n_b^j, exact
+            for (int k = 0; k < i; ++k) p *= (float)rw.x;
+            for (int k = 0; k < j; ++k) p *= (float)rw.y;
+            const cdf wv{split_double(w.x), split_double(idx < 0 ? -w.y : w.y)};
+            v = rot_mi(cdf{df_mulf(wv.re, p), df_mulf(wv.im, p)}, i + j);
+        }
+    }
+    const float sc = pow2f(6 - g.ev[(pr * g.nd + d) * g.ncols + nc]);
+    float sr[kTcJS], si[kTcJS];
+    slice7(v.re.hi, v.re.lo, sc, sr);
+    slice7(v.im.hi, v.im.lo, sc, si);
+    const int c0 = d * g.gw + 2 * nc;
+    __nv_bfloat16* base = g.vs + ((size_t)pr * g.nstage + q) * kTcJS * (size_t)g.colw * 16;
+    const int o0 = tile_off16(c0, 2 * ml), o1 = tile_off16(c0 + 1, 2 * ml);
+#pragma unroll
+    for (int s = 0; s < kTcJS; ++s) {
+        __nv_bfloat16* bs = base + (size_t)s * g.colw * 16;
+        *reinterpret_cast<uint32_t*>(bs + o0) = pack_bf2(sr[s], -si[s]);
+        *reinterpret_cast<uint32_t*>(bs + o1) = pack_bf2(si[s], sr[s]);
+    }
+}
+
+struct TcJSmem {
+    int rec[kTcM];
+    int pairs[kTcGmax];
+    int tidx[kTcGmax][5];  // index of J'_{ijk} for block (i, j) and k = 0..4 (-1 past the class's degree)
+    int2 rowi[kTcJPartRows];  // the part's rows
+    int iL, inb, ipart;
+    uint64_t full[kTcNbuf], empty[kTcNbuf], bfull[kTcNbuf], tfull, accf, acce, done, psync;
+    uint32_t tmem;
+    int abort_flag;
+};
+
+// index of J'_{p1 p2 p3} (powers of n_1, n_2, n_3) for powers (i, j, k) of (n_a, n_b, n_c)
+__device__ __forceinline__ int term_of_j(const TcJArgs& g, int i, int j, int k) {
+    const int p1 = g.ax == 0 ? i : (g.bx == 0 ? j : k);
+    const int p2 = g.ax == 1 ? i : (g.bx == 1 ? j : k);
+    const int lam = i + j + k;
+    return lam_offset(lam) + mono_index(lam, p1, p2);
+}
+
+// A^T entry (record r, stage row ml): X_r(n_a) Y_r(n_b) sliced, one 4-byte
+// store (re, im) per slice; a warp's 32 entries (8 records x 4 rows) fill
+// eight core-matrix rows, 128 contiguous bytes
+__device__ __forceinline__ void form_aj(const TcJArgs& g, const TcJSmem& sm, const float4* tabs, int q, int k,
+                                        unsigned char* as) {
+    const int ml = (k & 3) | (((k >> 5) & 1) << 2);
+    const int r = ((k >> 2) & 7) | ((k >> 6) << 3);
+    const int m = q * kTcJStageM + ml;  // q: stage of the part
+    cdf a{{0.f, 0.f}, {0.f, 0.f}};
+    if (sm.rowi[m].x != INT_MIN && sm.rec[r] >= 0) {
+        const int2 rw = sm.rowi[m];
+        const float4 xv = tabs[r * g.tabw + abs(rw.x)], yv = tabs[r * g.tabw + g.offY + abs(rw.y)];
+        const float sa = rw.x < 0 ? -1.f : 1.f, sb = rw.y < 0 ? -1.f : 1.f;  // X(-n) = conj X(n)
+        a = cdf_mul(cdf{{xv.x, xv.y}, {sa * xv.z, sa * xv.w}}, cdf{{yv.x, yv.y}, {sb * yv.z, sb * yv.w}});
+    }
+    float sr[kTcJS], si[kTcJS];
+    slice7(a.re.hi, a.re.lo, 0x1p5f, sr);  // |A| <= 1 < 2^1
+    slice7(a.im.hi, a.im.lo, 0x1p5f, si);
+    const int off = tile_off16(r, 2 * ml);
+#pragma unroll
+    for (int s = 0; s < kTcJS; ++s)
+        *reinterpret_cast<uint32_t*>(as + (size_t)s * kTcJAsliceBytes + (size_t)off * 2) = pack_bf2(sr[s], si[s]);
+}
+
+// Persistent over the work items (class, group of (i, j) blocks, 128
+// records, row part), with the structure-factor kernel's roles: warps 0-13
+// form the A^T slices of each 8-row stage, lane 0 of warp 14 issues the MMAs, warp 15
+// brings the item's factor tables (once per item) and the V_ij stage tiles
+// in with bulk copies; warps 0-11 then form J' from tensor memory (lane
+// quadrant w & 3, (block, density) groups w / 4 mod 3).  Waits are bounded
+// as in the structure-factor kernel.
+__global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_j(TcJArgs g) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    const int bslice = g.npad * 32;
+    unsigned char* abuf = tsm;                                                     // [nbuf][S][4096]
+    unsigned char* bbuf = abuf + (size_t)kTcNbuf * kTcJS * kTcJAsliceBytes;          // [nbuf][S][npad x 32]
+    float4* tabs = reinterpret_cast<float4*>(bbuf + (size_t)kTcNbuf * kTcJS * bslice);  // [128][tabw]
+    TcJSmem& sm = *reinterpret_cast<TcJSmem*>(tabs + (size_t)kTcM * g.tabw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    volatile int* abort_flag = &sm.abort_flag;
+    const bool mma_warp = warp == kTcMmaWarp, load_warp = warp == kTcLoadWarp, epi = warp < kTcEpiWarps;
+    if (tid == 0) {
+        for (int b = 0; b < kTcNbuf; ++b) {
+            mbar_init(&sm.full[b], kTcProdWarps);
+            mbar_init(&sm.empty[b], 1);
+            mbar_init(&sm.bfull[b], 1);
+        }
+        mbar_init(&sm.tfull, 1);
+        mbar_init(&sm.accf, 1);
+        mbar_init(&sm.acce, kTcEpiWarps);
+        mbar_init(&sm.done, 1);
+        mbar_init(&sm.psync, kTcWarps);
+        sm.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // columns of B past an item's blocks are never read into an output: clear them once
+    for (int i = tid; i < kTcNbuf * kTcJS * bslice / 16; i += kTcThreadsAll)
+        reinterpret_cast<uint4*>(bbuf)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (mma_warp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&sm.tmem)),
+                     "r"(kTcTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem;
+    const int equad = warp & 3, ethird = warp >> 2, erow = 32 * equad + lane;
+    const uint32_t tlane = (uint32_t)(32 * equad) << 16;
+    long long gs = 0;  // stages so far (every role counts the same)
+    int nit = 0;       // items finished
+    int ntab = 0;      // table loads issued (load warp)
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int it = blockIdx.x; it < g.nitems; it += gridDim.x) {
+        // ---- the item: class, blocks, records ----
+        const int4 in = __ldg(g.items + it);
+        const int iL = in.x & 255, part = in.x >> 8;
+        if (tid == 0) {
+            sm.iL = iL;
+            sm.inb = in.y;
+            sm.ipart = part;
+            for (int b = 0; b < in.y; ++b) {
+                const int pr = __ldg(g.ipairs + in.z + b), i = pr & 7, j = pr >> 3;
+                sm.pairs[b] = pr;
+                for (int kk = 0; kk < 5; ++kk) sm.tidx[b][kk] = kk <= iL - i - j ? term_of_j(g, i, j, kk) : -1;
+            }
+        }
+        if (tid < kTcM) sm.rec[tid] = (long long)in.w + tid < g.cls_start[iL + 1] ? in.w + tid : -1;
+        for (int m = tid; m < kTcJPartRows; m += kTcThreadsAll) {
+            const int mg = part * g.spp * kTcJStageM + m;
+            sm.rowi[m] = m < g.spp * kTcJStageM && mg < g.nrows ? __ldg(g.rows + mg) : make_int2(INT_MIN, 0);
+        }
+        if (!(ok = prod_sync(&sm.psync, ph, abort_flag, lane))) break;
+        const int L = sm.iL, nb = sm.inb, q0 = sm.ipart * g.spp, nst = min(g.spp, g.nstage - q0);
+        if (load_warp) {
+            // the records' factor tables, then every stage's V_ij tiles
+            if (lane == 0) {
+                uint32_t nv = 0;
+                for (int r = 0; r < kTcM; ++r) nv += sm.rec[r] >= 0 ? 1u : 0u;
+                mbar_arrive_tx(&sm.tfull, nv * (uint32_t)g.tabw * 16u);
+            }
+            __syncwarp();
+            for (int r = lane; r < kTcM; r += 32)
+                if (sm.rec[r] >= 0)
+                    bulk_copy(tabs + (size_t)r * g.tabw, g.tab + (size_t)sm.rec[r] * g.tabw, (uint32_t)g.tabw * 16u,
+                              &sm.tfull);
+            ++ntab;
+            const uint32_t blk = (uint32_t)g.colw * 32u;  // bytes of one block's slice of a stage
+            for (int q = 0; q < nst; ++q, ++gs) {
+                const int slot = (int)(gs & 1);
+                if (gs >= kTcNbuf) {
+                    ok = __all_sync(0xffffffffu, mbar_wait(&sm.empty[slot], (uint32_t)(((gs >> 1) - 1) & 1), abort_flag));
+                    if (!ok) break;
+                }
+                unsigned char* bs = bbuf + (size_t)slot * kTcJS * bslice;
+                if (lane == 0) mbar_arrive_tx(&sm.bfull[slot], (uint32_t)(nb * kTcJS) * blk);
+                __syncwarp();
+                for (int c = lane; c < nb * kTcJS; c += 32) {
+                    const int gb = c / kTcJS, s = c - gb * kTcJS;
+                    const int pr = sm.pairs[gb];
+                    const size_t src =
+                        (((size_t)pair_index(pr & 7, pr >> 3) * g.nstage + q0 + q) * kTcJS + s) * g.colw * 16;
+                    bulk_copy(bs + (size_t)s * bslice + (size_t)gb * blk, g.vs + src, blk, &sm.bfull[slot]);
+                }
+                __syncwarp();
+            }
+        } else if (!mma_warp) {
+            ok = __all_sync(0xffffffffu, mbar_wait(&sm.tfull, (uint32_t)(nit & 1), abort_flag));
+            if (ok) {
+                for (int q = 0; q < nst; ++q, ++gs) {
+                    const int slot = (int)(gs & 1);
+                    if (gs >= kTcNbuf) {
+                        ok = __all_sync(0xffffffffu,
+                                        mbar_wait(&sm.empty[slot], (uint32_t)(((gs >> 1) - 1) & 1), abort_flag));
+                        if (!ok) break;
+                    }
+                    unsigned char* as = abuf + (size_t)slot * kTcJS * kTcJAsliceBytes;
+                    for (int k = tid; k < kTcJTasks; k += kTcProdThreads) form_aj(g, sm, tabs, q, k, as);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sm.full[slot]);
+                }
+            }
+        } else {
+            if (lane == 0) {
+                const uint32_t a0 = saddr(abuf), b0 = saddr(bbuf);
+                const int nw = min(g.npad, (nb * g.colw + 15) / 16 * 16);
+                const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nw >> 3) << 17) |
+                                       ((uint32_t)(kTcM >> 4) << 24);
+                bool first[kTcJAcc] = {true, true, true, true, true};
+                bool mok = true;
+                if (nit > 0) mok = mbar_wait(&sm.acce, (uint32_t)((nit - 1) & 1), abort_flag);  // tensor memory drained
+                tc_fence_after();
+                for (int q = 0; q < nst && mok; ++q, ++gs) {
+                    const int slot = (int)(gs & 1);
+                    if (!(mok = mbar_wait(&sm.full[slot], (uint32_t)((gs >> 1) & 1), abort_flag))) break;
+                    if (!(mok = mbar_wait(&sm.bfull[slot], (uint32_t)((gs >> 1) & 1), abort_flag))) break;
+                    tc_fence_after();
+                    const uint32_t as = a0 + slot * kTcJS * kTcJAsliceBytes, bs = b0 + slot * kTcJS * bslice;
+#pragma unroll
+                    for (int s = 0; s < kTcJS; ++s)
+#pragma unroll
+                        for (int t = 0; s + t < kTcJS; ++t) {
+                            const int lv = min(s + t, kTcJAcc - 1);
+                            tc_mma(tmem + (uint32_t)(lv * g.npad), sdesc16(as + s * kTcJAsliceBytes),
+                                   sdesc16(bs + t * bslice), idesc, first[lv] ? 0u : 1u);
+                            first[lv] = false;
+                        }
+                    tc_commit(&sm.empty[slot]);
+                }
+                if (mok) tc_commit(&sm.accf);
+                ok = mok;
+            }
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            gs = __shfl_sync(0xffffffffu, gs, 0);
+        }
+        if (!ok) break;
+        // ---- J'_{r,ijk} = Re (-i)^k sum_{n_c} n_c^k Z_r(n_c) U_ij[r, n_c] (warps 0-11) ----
+        if (epi) {
+            ok = __all_sync(0xffffffffu, mbar_wait(&sm.accf, (uint32_t)(nit & 1), abort_flag));
+            if (!ok) break;
+            tc_fence_after();
+            const int r = sm.rec[erow];
+            const long long cnt = g.cls_start[L + 1] - g.cls_start[L];
+            for (int grp = ethird; grp < nb * g.nd; grp += 3) {
+                const int gb = grp / g.nd, d = grp - gb * g.nd;
+                const int pr = sm.pairs[gb], i = pr & 7, j = pr >> 3, nk = L - i - j;
+                const int* evp = g.ev + (pair_index(i, j) * g.nd + d) * g.ncols;
+                cdf J[5];
+#pragma unroll
+                for (int kk = 0; kk < 5; ++kk) J[kk] = cdf{{0.f, 0.f}, {0.f, 0.f}};
+                for (int c8 = 0; c8 < g.gw / 8; ++c8) {
+                    float T[kTcJAcc][8];
+#pragma unroll
+                    for (int lv = 0; lv < kTcJAcc; ++lv)
+                        tc_ld8(tmem + tlane + (uint32_t)(lv * g.npad + gb * g.colw + d * g.gw + 8 * c8), T[lv]);
+                    if (r < 0) continue;
+#pragma unroll
+                    for (int u = 0; u < 8; u += 2) {
+                        const int nc = 4 * c8 + u / 2;
+                        if (nc < g.ncols) {
+                            cdf v;
+                            v.re = df_add(df_add(df_add(two_sum(T[0][u], T[1][u]), df{T[2][u], 0.f}), df{T[3][u], 0.f}),
+                                          df{T[4][u], 0.f});
+                            v.im = df_add(df_add(df_add(two_sum(T[0][u + 1], T[1][u + 1]), df{T[2][u + 1], 0.f}),
+                                                 df{T[3][u + 1], 0.f}),
+                                          df{T[4][u + 1], 0.f});
+                            const float sc = pow2f(1 + __ldg(evp + nc) - 12);  // exact power of two
+                            v = cdf{df{v.re.hi * sc, v.re.lo * sc}, df{v.im.hi * sc, v.im.lo * sc}};
+                            const float4 zv = tabs[erow * g.tabw + g.offZ + nc];
+                            const cdf zu = cdf_mul(cdf{{zv.x, zv.y}, {zv.z, zv.w}}, v);
+                            float pw = 1.f;  // n_c^k, exact
+#pragma unroll
+                            for (int kk = 0; kk < 5; ++kk) {
+                                if (kk <= nk) J[kk] = cdf{df_add(J[kk].re, df_mulf(zu.re, pw)), df_add(J[kk].im, df_mulf(zu.im, pw))};
+                                pw *= (float)nc;
+                            }
+                        }
+                    }
+                }
+                if (r >= 0) {
+                    double* jp = g.Jp + ((long long)(g.d0 + d) * g.nparts + sm.ipart) * g.jp_total + g.term_base[L] +
+                                 (r - g.cls_start[L]);
+#pragma unroll
+                    for (int kk = 0; kk < 5; ++kk)
+                        if (kk <= nk) {
+                            const df re = rot_mi(J[kk], kk).re;
+                            jp[(long long)sm.tidx[gb][kk] * cnt] = (double)re.hi + (double)re.lo;
+                        }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.acce);
+        }
+        ++nit;
+        // the tables, records and blocks are rewritten by the next item
+        if (!(ok = prod_sync(&sm.psync, ph, abort_flag, lane) && ok)) break;
+    }
+    if (load_warp && lane == 0) {
+        // bulk copies still in flight (after a failed wait) land before the CTA exits
+        for (int b = 0; b < kTcNbuf && b < gs; ++b) {
+            const long long last = gs - 1 - ((gs - 1 - b) % kTcNbuf);
+            const long long t0 = clock64();
+            while (!mbar_test(&sm.bfull[b], (uint32_t)((last >> 1) & 1)) && clock64() - t0 < kTcSpinCycles) {
+            }
+        }
+        if (ntab > 0) {
+            const long long t0 = clock64();
+            while (!mbar_test(&sm.tfull, (uint32_t)((ntab - 1) & 1)) && clock64() - t0 < kTcSpinCycles) {
+            }
+        }
+    }
+    if (mma_warp) {
+        // everything issued completes before tensor memory is freed
+        if (lane == 0) {
+            tc_commit(&sm.done);
+            const long long t0 = clock64();
+            while (!mbar_test(&sm.done, 0u) && clock64() - t0 < kTcSpinCycles) {
+            }
+        }
+        __syncwarp();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*abort_flag && tid == 0) atomicOr(g.err, 1);
+    if (mma_warp) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+    }
+}
+
+size_t tc_j_smem_bytes(int npad, int tabw) {
+    const size_t need = (size_t)kTcNbuf * kTcJS * kTcJAsliceBytes + (size_t)kTcNbuf * kTcJS * npad * 32 +
+                        (size_t)kTcM * tabw * 16 + sizeof(TcJSmem) + 64;
+    return std::max<size_t>(need, 120 * 1024);
+}
+
 }  // namespace
 
 int tc_supported(const ftcj_plan* P) { return P->ortho ? 1 : 0; }
+
+int setup_tc_j(ftcj_plan* P);
 
 // Plan-time set-up of the tensor-core form: the column axis, the rows and
 // their half-sphere map, the factor tables, the windows (class, block group,
@@ -1067,7 +1558,9 @@ int setup_tc(ftcj_plan* P) {
     int4* winfo_dev = nullptr;
     if ((rc = tc_upload(P, &winfo_dev, winfo))) return rc;
     P->d_tc_winfo = winfo_dev;
-    return allow_dynamic_smem((const void*)k_tc_rho, tc_smem_bytes(P->tc_npad, tabw, P->tc_G, P->tc_nd, P->tc_tslots));
+    if ((rc = allow_dynamic_smem((const void*)k_tc_rho, tc_smem_bytes(P->tc_npad, tabw, P->tc_G, P->tc_nd, P->tc_tslots))))
+        return rc;
+    return setup_tc_j(P);
 }
 
 int launch_tc_rho(ftcj_plan* P, int ndens, cudaStream_t s) {
@@ -1123,5 +1616,152 @@ int launch_tc_rho(ftcj_plan* P, int ndens, cudaStream_t s) {
 }
 
 int tc_rho_launches(const ftcj_plan* P, int nd) { return (nd + P->tc_nd - 1) / P->tc_nd; }
+
+// Plan-time set-up of the tensor-core back-contraction: densities per
+// launch, (i, j) blocks per work item, the items and the V_ij tile buffer.
+// tc_j stays false, and the split walk runs the back-contraction, where the
+// rows exceed one exact accumulation, one density's columns exceed the MMA
+// width, or the factor tables exceed shared memory.
+int setup_tc_j(ftcj_plan* P) {
+    P->tc_j = false;
+    const int gw = round_up(2 * P->tc_ncols, 8);
+    int64_t tiles[kNclass];
+    for (int L = 0; L < kNclass; ++L) tiles[L] = (P->class_start[L + 1] - P->class_start[L] + kTcM - 1) / kTcM;
+    // densities per launch: the fewest A^T formations (items x launches)
+    int nd_best = 0, G_best = 0;
+    double cost_best = 1e300;
+    for (int nd = 1; nd <= P->max_dens; ++nd) {
+        const int colw = nd * gw;
+        if (colw > kTcJNmax) break;
+        const int G = std::min(kTcGmax, kTcJNmax / colw);
+        double items = 0.0;
+        for (int L = 0; L < kNclass; ++L) {
+            const int nb = (L + 1) * (L + 2) / 2;
+            items += (double)tiles[L] * ((nb + G - 1) / G);
+        }
+        const double cost = (double)((P->max_dens + nd - 1) / nd) * items;
+        if (cost <= cost_best) {
+            cost_best = cost;
+            nd_best = nd;
+            G_best = G;
+        }
+    }
+    if (!nd_best) return FTCJ_OK;
+    const int npad = round_up(G_best * nd_best * gw, 16);
+    int dev = 0, optin = 0;
+    FTCJ_CUDA(cudaGetDevice(&dev));
+    FTCJ_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (tc_j_smem_bytes(npad, P->tc_tabw) > (size_t)optin) return FTCJ_OK;
+    // row parts of at most 64 stages, as even as the stage count allows
+    const int nstage = (P->tc_rows + kTcJStageM - 1) / kTcJStageM;
+    const int spp = (nstage + (nstage + kTcJPartStages - 1) / kTcJPartStages - 1) /
+                    ((nstage + kTcJPartStages - 1) / kTcJPartStages);
+    const int nparts = (nstage + spp - 1) / spp;  // every part holds at least one stage
+    // work items, the costliest classes first: (class, block group, 128 records, row part)
+    std::vector<int4> items;
+    std::vector<int> ipairs;
+    for (int L = kNclass - 1; L >= 0; --L) {
+        if (!tiles[L]) continue;
+        std::vector<int> blocks;
+        for (int i = 0; i <= L; ++i)
+            for (int j = 0; i + j <= L; ++j) blocks.push_back(i | (j << 3));
+        for (size_t g0 = 0; g0 < blocks.size(); g0 += G_best) {
+            const int nb = (int)std::min<size_t>(G_best, blocks.size() - g0);
+            const int first = (int)ipairs.size();
+            ipairs.insert(ipairs.end(), blocks.begin() + g0, blocks.begin() + g0 + nb);
+            for (int64_t t = 0; t < tiles[L]; ++t)
+                for (int h = 0; h < nparts; ++h)
+                    items.push_back(make_int4(L | (h << 8), nb, first, (int)(P->class_start[L] + t * kTcM)));
+        }
+    }
+    P->tc_jnd = nd_best;
+    P->tc_jgw = gw;
+    P->tc_jG = G_best;
+    P->tc_jnpad = npad;
+    P->tc_jnstage = nstage;
+    P->tc_jparts = nparts;
+    P->tc_jspp = spp;
+    P->tc_jnitems = (int)items.size();
+    // MMA work of one back-contraction over max_dens densities: per item and stage 21 slice
+    // products of M = 128 records, N = the item's columns, K = 16
+    P->tc_j_mma_flops = 0;
+    for (int d0 = 0; d0 < P->max_dens; d0 += nd_best) {
+        const int colw = std::min(nd_best, P->max_dens - d0) * gw, np = round_up(G_best * colw, 16);
+        for (const int4& it : items) {
+            const int part = it.x >> 8, nst = std::min(spp, nstage - part * spp);
+            P->tc_j_mma_flops +=
+                (long long)nst * kTcJProducts * 2LL * kTcM * std::min(np, round_up(it.y * colw, 16)) * 16;
+        }
+    }
+    int rc;
+    int4* items_dev = nullptr;
+    if ((rc = tc_upload(P, &items_dev, items))) return rc;
+    P->d_tc_jitems = items_dev;
+    if ((rc = tc_upload(P, &P->d_tc_jpairs, ipairs))) return rc;
+    const size_t nvs = (size_t)kTcPairsAll * P->tc_jnstage * kTcJS * (size_t)nd_best * gw * 16;
+    FTCJ_CUDA(cudaMalloc(&P->d_tc_vs, sizeof(__nv_bfloat16) * nvs));
+    P->device_bytes += sizeof(__nv_bfloat16) * nvs;
+    FTCJ_CUDA(cudaMemset(P->d_tc_vs, 0, sizeof(__nv_bfloat16) * nvs));
+    const size_t nev = (size_t)kTcPairsAll * nd_best * P->tc_ncols;
+    FTCJ_CUDA(cudaMalloc(&P->d_tc_ev, sizeof(int) * nev));
+    P->device_bytes += sizeof(int) * nev;
+    if ((rc = allow_dynamic_smem((const void*)k_tc_j, tc_j_smem_bytes(npad, P->tc_tabw)))) return rc;
+    P->tc_j = true;
+    return FTCJ_OK;
+}
+
+int launch_tc_j(ftcj_plan* P, int ndens, const double* W, cudaStream_t s) {
+    if (P->ng_half == 0 || P->npairs == 0) {
+        FTCJ_CUDA(cudaMemsetAsync(P->d_Jp, 0, sizeof(double) * (size_t)ndens * P->tc_jparts * P->total_terms, s));
+        return FTCJ_OK;
+    }
+    TcJArgs g;
+    g.rows = reinterpret_cast<const int2*>(P->d_tc_rows);
+    g.map = P->d_tc_map;
+    g.W = reinterpret_cast<const double2*>(W);
+    g.items = reinterpret_cast<const int4*>(P->d_tc_jitems);
+    g.ipairs = P->d_tc_jpairs;
+    g.tab = reinterpret_cast<const float4*>(P->d_tc_tab);
+    g.vs = reinterpret_cast<__nv_bfloat16*>(P->d_tc_vs);
+    g.ev = P->d_tc_ev;
+    g.Jp = P->d_Jp;
+    g.ng_half = P->ng_half;
+    g.jp_total = P->total_terms;
+    for (int c = 0; c <= kNclass; ++c) g.cls_start[c] = P->class_start[c];
+    for (int c = 0; c < kNclass; ++c) g.term_base[c] = P->term_base[c];
+    g.err = P->d_tc_err;
+    g.ax = P->tc_axis[0];
+    g.bx = P->tc_axis[1];
+    g.cx = P->tc_axis[2];
+    g.tabw = P->tc_tabw;
+    g.offY = P->tc_nna;
+    g.offZ = P->tc_nna + P->tc_nnb;
+    g.ncols = P->tc_ncols;
+    g.gw = P->tc_jgw;
+    g.nrows = P->tc_rows;
+    g.nstage = P->tc_jnstage;
+    g.nitems = P->tc_jnitems;
+    g.nparts = P->tc_jparts;
+    g.spp = P->tc_jspp;
+    const size_t smem = tc_j_smem_bytes(P->tc_jnpad, P->tc_tabw);
+    const int grid = std::max(1, std::min(P->num_sms, P->tc_jnitems));
+    for (int d0 = 0; d0 < ndens; d0 += P->tc_jnd) {
+        g.d0 = d0;
+        g.nd = std::min(P->tc_jnd, ndens - d0);
+        // the plan's block count is kept; a smaller last density group only narrows each block
+        g.colw = g.nd * g.gw;
+        g.npad = round_up(P->tc_jG * g.colw, 16);
+        k_tc_vbound<<<(unsigned)(kTcPairsAll * g.nd * g.ncols), 256, 0, s>>>(g);
+        FTCJ_CUDA(cudaGetLastError());
+        const long long nv = (long long)kTcPairsAll * g.nstage * kTcJStageM * g.nd * g.ncols;
+        k_tc_vslice<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(g);
+        FTCJ_CUDA(cudaGetLastError());
+        k_tc_j<<<(unsigned)grid, kTcThreadsAll, smem, s>>>(g);
+        FTCJ_CUDA(cudaGetLastError());
+    }
+    return FTCJ_OK;
+}
+
+int tc_j_launches(const ftcj_plan* P, int nd) { return 3 * ((nd + P->tc_jnd - 1) / P->tc_jnd); }
 
 }  // namespace ftcj

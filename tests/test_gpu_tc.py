@@ -1,10 +1,11 @@
 """The tensor-core separable contraction (Sec. 2.4, orthorhombic fully
 separable case) against the FP64 oracle.  rho(G) is a sliced bf16 tcgen05
 matrix product over (pair record, i, j) with exact level accumulators and
-double-float window sums; the bar is the split form's: max|dJ| <= 1e-8 Eh
-and |dE_J| <= 1e-8 Eh, plus rho element by element at 1e-10 of max|rho|.
-Every build must also leave the device error word of the bounded waits at
-zero."""
+double-float window sums; the back-contraction J'_ijk (Alg. S1) is one over
+the sphere's (n_a, n_b) rows with records as the M side.  The bar is the
+split form's: max|dJ| <= 1e-8 Eh and |dE_J| <= 1e-8 Eh, plus rho element by
+element at 1e-10 of max|rho|.  Every build must also leave the device error
+word of the bounded waits at zero."""
 import numpy as np
 import pytest
 
@@ -52,7 +53,9 @@ def check_against_oracle(orc, F, w, **kw):
         drho = float(np.abs(rho - rref).max())
         scale = float(np.abs(rref).max())
         print(f"{w.name}: tc max|dJ|={dJ:.3e} |dE|={dE:.3e} max|drho|={drho:.3e} (max|rho|={scale:.3e}, "
-              f"max|J|={np.abs(ref['Jk']).max():.3e}) launches/pass={plan.info['rho_walk_launches']}")
+              f"max|J|={np.abs(ref['Jk']).max():.3e}) launches/pass={plan.info['rho_walk_launches']} "
+              f"j form={plan.info['j_contraction']} launches={plan.info['j_walk_launches']}")
+        assert plan.info["j_contraction"] == F.FTCJ_CONTRACT_TC
         assert drho <= RHO_REL * max(1.0, scale), (w.name, drho)
         assert dJ <= J_TOL and dE <= J_TOL * max(1.0, float(np.abs(ref["EJ"]).max())), (w.name, dJ, dE)
         return plan.info
@@ -92,6 +95,7 @@ def test_tc_cfg3_against_split_walk(F):
     rw = walk.rho(walk.fold_density(Dk)).cpu().numpy()
     walk.close()
     tc = tc_plan(F, w)
+    info = tc.info
     Jt, Et = tc.jbuild(Dk)
     rt = tc.rho(tc.fold_density(Dk)).cpu().numpy()
     torch.cuda.synchronize()
@@ -100,9 +104,42 @@ def test_tc_cfg3_against_split_walk(F):
     dJ = float((Jt - Jw).abs().max())
     dE = float((Et - Ew).abs().max())
     drho = float(np.abs(rt - rw).max())
-    print(f"cfg3 tc vs walk: max|dJ|={dJ:.3e} |dE|={dE:.3e} max|drho|={drho:.3e} max|rho|={np.abs(rw).max():.3e}")
+    print(f"cfg3 tc vs walk: max|dJ|={dJ:.3e} |dE|={dE:.3e} max|drho|={drho:.3e} max|rho|={np.abs(rw).max():.3e} "
+          f"|E_J|={float(Ew.abs().max()):.6e} j form={info['j_contraction']} parts={info['j_walk_launches']}")
     assert drho <= RHO_REL * np.abs(rw).max()
     assert dJ <= J_TOL and dE <= J_TOL * max(1.0, float(Ew.abs().max()))
+
+
+def jback_pair(F, w):
+    """J^{0n} from the same potential W through the split walk's and the
+    tensor-core back-contraction: the difference is the J pass's alone."""
+    import torch
+    Dk = torch.from_numpy(np.ascontiguousarray(w.Dk)).cuda()
+    walk = F.Plan.from_workload(w, precision=F.FTCJ_PREC_SPLIT)
+    tc = tc_plan(F, w)
+    try:
+        assert tc.info["j_contraction"] == F.FTCJ_CONTRACT_TC
+        assert walk.info["j_contraction"] == F.FTCJ_CONTRACT_WALK
+        nd = min(w.ndens, walk.max_dens)
+        rho = walk.rho(walk.fold_density(Dk[:nd].contiguous()))
+        W, _ = walk.potential(rho)
+        Jw = walk.jback(W).cpu().numpy()
+        Jt = tc.jback(W).cpu().numpy()
+        torch.cuda.synchronize()
+        assert tc.status() == 0
+        return Jw, Jt, tc.info
+    finally:
+        walk.close()
+        tc.close()
+
+
+def test_tc_jback_reduced_crystal_same_potential(F):
+    from tests.test_gpu_launch_shapes import reduced_crystal
+    Jw, Jt, info = jback_pair(F, reduced_crystal())
+    d = float(np.abs(Jt - Jw).max())
+    print(f"reduced crystal jback: max|dJ0n|={d:.3e} max|J0n|={np.abs(Jw).max():.3e} "
+          f"items={info['j_walk_launches']} mma={info['tc_j_mma_flops']:.3e}")
+    assert d <= 1e-9
 
 
 def test_tc_refusals(F):
