@@ -172,7 +172,7 @@ def traffic_from_profile(kernel: str, workload: str):
     source hash must match)."""
     tag = {"diamond": "diamond240_k444", "molecular_crystal": "molecular_crystal"}[workload]
     path = os.path.join(ROOT, "profiles", f"{kernel}_{tag}.md")
-    src_name = "walk_split.cu" if kernel.endswith("_split") else "walk.cu"
+    src_name = "tc.cu" if kernel.startswith("k_tc_") else ("walk_split.cu" if kernel.endswith("_split") else "walk.cu")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -316,10 +316,12 @@ def measure_form(ctx, w, wname, form):
         phase_ms, batches, launches = plan.profile_read()
         plan.profile_enable(0)
         rho_name = "k_tc_rho" if contraction else "k_rho_walk" + suffix
-        walks = {rho_name: phase_ms["rho_walk"], "k_j_walk" + suffix: phase_ms["j_walk"]}
+        j_name = "k_tc_j" if info["j_contraction"] else "k_j_walk" + suffix
+        walks = {rho_name: phase_ms["rho_walk"], j_name: phase_ms["j_walk"]}
         kname = max(walks, key=walks.get)
         pass_ms = walks[kname] * max(1, -(-nd // plan.max_dens)) / max(batches, 1)
         rho_pass_ms = phase_ms["rho_walk"] * max(1, -(-nd // plan.max_dens)) / max(batches, 1)
+        j_pass_ms = phase_ms["j_walk"] * max(1, -(-nd // plan.max_dens)) / max(batches, 1)
         phases = {k: v / max(batches, 1) for k, v in phase_ms.items()}
         timed_what = "the library's phase events around the whole walk pass (all class-part launches)"
     else:
@@ -330,7 +332,7 @@ def measure_form(ctx, w, wname, form):
         timed_what = "CUDA events around the rho step (Hermite map + structure-factor walk) of this rank's share"
     achieved = flops / (pass_ms * 1e-3)
     peak = ctx["peaks"][pipe]
-    parts = info["rho_walk_launches"] if kname.startswith("k_rho") else info["j_walk_launches"]
+    parts = info["rho_walk_launches"] if "rho" in kname else info["j_walk_launches"]
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": traffic_from_profile(kname, wname) if (eps == 0 and not sharded) else None,
@@ -343,17 +345,39 @@ def measure_form(ctx, w, wname, form):
                 "flops_per_pass": flops, "pass_ms": pass_ms, "timed": timed_what,
                 "nominal_peak": 152 * 2 * 2.07e9 * (2 if pipe == "fp64" else 128) / 1e12}
     if contraction and not sharded:
-        # the tensor-core structure-factor pass: bf16 MMA flops (slice products included) against the
-        # sustained dense bf16 rate, and its algorithmic (4L+14) rate
+        # the tensor-core passes: bf16 MMA flops (slice products included) against the sustained dense
+        # bf16 rate, and their algorithmic (4L+14) rate; the dominant one heads the roofline
         bf16_peak, bf16_src = measured_bf16_peak()
-        mma = float(info["tc_mma_flops"]) * max(1, -(-nd // plan.max_dens))
-        roofline["tc_rho"] = {"bound": "tensor", "kernel": "k_tc_rho", "pass_ms": rho_pass_ms,
-                              "achieved": mma / (rho_pass_ms * 1e-3) / 1e12, "peak": bf16_peak / 1e12,
-                              "unit": "TFLOP/s", "frac": mma / (rho_pass_ms * 1e-3) / bf16_peak,
-                              "mma_flops_per_pass": mma, "peak_source": bf16_src,
-                              "algorithmic_tflops": walk_flops(info, nd) / (rho_pass_ms * 1e-3) / 1e12,
-                              "note": "21 bf16 slice products per exact-to-2^-41 product (6 slices a side), "
-                                      "real form of the complex product (4 real per complex multiply-add)"}
+        reps = max(1, -(-nd // plan.max_dens))
+        tc = {}
+        for key, kern, mma, t_ms, note in (
+                ("tc_rho", "k_tc_rho", float(info["tc_mma_flops"]) * reps, rho_pass_ms,
+                 "21 bf16 slice products per product exact to 2^-41 (6 slices a side), real form of the "
+                 "complex product (4 real per complex multiply-add)"),
+                ("tc_j", "k_tc_j", float(info["tc_j_mma_flops"]) * reps, j_pass_ms,
+                 "28 bf16 slice products per product exact to 2^-45 (7 slices a side), real form of the "
+                 "complex product")):
+            if mma <= 0:
+                continue
+            tc[kern] = {"bound": "tensor", "kernel": kern, "pass_ms": t_ms,
+                        "achieved": mma / (t_ms * 1e-3) / 1e12, "peak": bf16_peak / 1e12, "unit": "TFLOP/s",
+                        "frac": mma / (t_ms * 1e-3) / bf16_peak, "mma_flops_per_pass": mma,
+                        "peak_source": bf16_src,
+                        "algorithmic_tflops": walk_flops(info, nd) / (t_ms * 1e-3) / 1e12,
+                        "algorithmic_frac_of_fp32": walk_flops(info, nd) / (t_ms * 1e-3) / peak,
+                        "traffic": traffic_from_profile(kern, wname), "note": note}
+            roofline[key] = tc[kern]
+        if kname in tc:
+            head = dict(tc[kname])
+            head["launches_per_pass"] = parts
+            head["timed"] = timed_what
+            head["flops_rule"] = ("per pass: the bf16 MMA flops the kernel issues (every slice product and "
+                                  "padding column, 2 per multiply-add), x density groups")
+            for k2 in ("tc_rho", "tc_j"):
+                if k2 in roofline:
+                    head[k2] = roofline[k2]
+            head["alu_view"] = {k2: roofline[k2] for k2 in ("achieved", "peak", "frac", "pipe") if k2 in roofline}
+            roofline = head
     if pipe == "split":
         roofline["fp32_pipe_ops_per_pass"] = emu
         roofline["fp32_pipe_ops_frac"] = emu / (pass_ms * 1e-3) / peak
@@ -641,8 +665,9 @@ def main():
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None,
-        "dtype": ("bf16x6-sliced tcgen05 structure-factor contraction with exact FP32 level sums, f32x2 "
-                  "(double-float) operands, back-contraction walk and window sums, f64 setup/sums/E_J"
+        "dtype": ("bf16-sliced tcgen05 contractions (structure factor: 6 slices a side; back-contraction: "
+                  "7 slices a side where the plan takes it, else the f32x2 walk) with exact FP32 level sums, "
+                  "f32x2 (double-float) operands and window sums, f64 setup/sums/E_J"
                   if head_form == "split_tc" else "f32x2 walks (double-float), f64 setup/sums/E_J"),
         "data": "synthetic",
         "config": {"workload": WORKLOADS[HEADLINE], "form": head_form, "ndens": w.ndens,
