@@ -121,6 +121,10 @@ typedef struct {
                            back-contraction (Alg. S1) takes the same form where the sphere's
                            (n_a, n_b) rows fit one exact accumulation, else the split walk
                            (ftcj_info.j_contraction says which) */
+    int tc_wait_log2;   /* tensor-core kernels: each wait between their roles gives up after
+                           2^tc_wait_log2 clock cycles (0: 2^32, about 2 s), raises the plan's device
+                           error word (ftcj_plan_status) and lets the kernel drain and return; 1..40,
+                           small values are for tests of that path */
 } ftcj_params;
 
 #define FTCJ_CONTRACT_WALK 0

@@ -109,6 +109,7 @@ struct TcArgs {
     int accw;            // real columns of the double-float sums: colw rounded up to 8
     int nwin, win_per_group, ngroups;
     int nrows;
+    long long spin;      // clock cycles a wait between roles may take before it gives up
 };
 
 // ---- PTX wrappers -----------------------------------------------------------
@@ -135,11 +136,11 @@ __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
 
 // Waits for phase `parity` of b to complete; false when it gave up (after
 // ~2 s of clock, or because another thread of the CTA already did).
-__device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+__device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, long long spin) {
     const long long t0 = clock64();
     while (!mbar_test(b, parity)) {
         if (*abort_flag) return false;
-        if (clock64() - t0 > kTcSpinCycles) {
+        if (clock64() - t0 > spin) {
             *abort_flag = 1;
             return false;
         }
@@ -150,10 +151,10 @@ __device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag
 // A bounded barrier of the eight operand warps (an mbarrier counting one
 // arrival per warp): unlike bar.sync it cannot hang when a thread has left
 // after a failed wait.  The outcome is the same for every lane of a warp.
-__device__ bool prod_sync(uint64_t* b, uint32_t& ph, volatile int* abort_flag, int lane) {
+__device__ bool prod_sync(uint64_t* b, uint32_t& ph, volatile int* abort_flag, int lane, long long spin) {
     __syncwarp();
     if (lane == 0) mbar_arrive(b);
-    const bool ok = mbar_wait(b, ph, abort_flag);
+    const bool ok = mbar_wait(b, ph, abort_flag, spin);
     ph ^= 1u;
     return __all_sync(0xffffffffu, ok);
 }
@@ -531,7 +532,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslo
             }
             sm.clmin_bits = __float_as_int(INFINITY);
         }
-        if (!(ok = prod_sync(&sm.psync, ph, abort_flag, lane))) break;
+        if (!(ok = prod_sync(&sm.psync, ph, abort_flag, lane, g.spin))) break;
         const int L = sm.winL, npair = sm.wnpair;
         if (!load_warp) {
             // A: |X Y| = exp(-c Q) <= exp(-c_min Q): the window's smallest width gives every row's scale
@@ -576,7 +577,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslo
                 }
             }
         }
-        if (!(ok = prod_sync(&sm.psync, ph, abort_flag, lane))) break;
+        if (!(ok = prod_sync(&sm.psync, ph, abort_flag, lane, g.spin))) break;
         const float clmin = __int_as_float(sm.clmin_bits);
         // ---- stages ----
         if (load_warp) {
@@ -588,7 +589,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslo
                 const int ts = (int)(gs % ntslots);
                 const long long use = gs / ntslots;
                 if (use > 0) {
-                    ok = __all_sync(0xffffffffu, mbar_wait(&sm.tempty[ts], (uint32_t)((use - 1) & 1), abort_flag));
+                    ok = __all_sync(0xffffffffu, mbar_wait(&sm.tempty[ts], (uint32_t)((use - 1) & 1), abort_flag, g.spin));
                     if (!ok) break;
                 }
                 unsigned char* slotp = tring + (size_t)ts * tslot;
@@ -631,10 +632,10 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslo
         } else if (!mma_warp) {
             for (int q = 0; q < kTcStagesPerWin; ++q, ++gs) {
                 const int slot = (int)(gs & 1), ts = (int)(gs % ntslots);
-                ok = __all_sync(0xffffffffu, mbar_wait(&sm.tfull[ts], (uint32_t)((gs / ntslots) & 1), abort_flag));
+                ok = __all_sync(0xffffffffu, mbar_wait(&sm.tfull[ts], (uint32_t)((gs / ntslots) & 1), abort_flag, g.spin));
                 if (!ok) break;
                 if (gs >= kTcNbuf) {
-                    ok = __all_sync(0xffffffffu, mbar_wait(&sm.empty[slot], (uint32_t)(((gs >> 1) - 1) & 1), abort_flag));
+                    ok = __all_sync(0xffffffffu, mbar_wait(&sm.empty[slot], (uint32_t)(((gs >> 1) - 1) & 1), abort_flag, g.spin));
                     if (!ok) break;
                 }
                 const unsigned char* slotp = tring + (size_t)ts * tslot;
@@ -668,7 +669,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslo
                 bool mok = true;
                 for (int q = 0; q < kTcStagesPerWin; ++q, ++gs) {
                     const int slot = (int)(gs & 1);
-                    if (!(mok = mbar_wait(&sm.full[slot], (uint32_t)((gs >> 1) & 1), abort_flag))) break;
+                    if (!(mok = mbar_wait(&sm.full[slot], (uint32_t)((gs >> 1) & 1), abort_flag, g.spin))) break;
                     tc_fence_after();
                     const uint32_t as = a0 + slot * kTcS * kTcAsliceBytes, bs = b0 + slot * kTcS * bslice;
 #pragma unroll
@@ -693,7 +694,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslo
         if (!ok) break;
         // ---- drain: each block's level sums, scaled and times P_ij, into the double-float sums (warps 0-11) ----
         if (epi) {
-            ok = __all_sync(0xffffffffu, mbar_wait(&sm.accf, (uint32_t)((w - w0) & 1), abort_flag));
+            ok = __all_sync(0xffffffffu, mbar_wait(&sm.accf, (uint32_t)((w - w0) & 1), abort_flag, g.spin));
             if (!ok) break;
             tc_fence_after();
             const TcRow ri = sm.rowi[erow];
@@ -741,10 +742,10 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslo
         }
         // the MMAs of the next window wait for every draining warp
         if (mma_warp && w + 1 < w1) {
-            ok = __all_sync(0xffffffffu, mbar_wait(&sm.acce, (uint32_t)((w - w0) & 1), abort_flag));
+            ok = __all_sync(0xffffffffu, mbar_wait(&sm.acce, (uint32_t)((w - w0) & 1), abort_flag, g.spin));
             tc_fence_after();
         }
-        if (!(ok = prod_sync(&sm.psync, ph, abort_flag, lane) && ok)) break;  // window tables reused next window
+        if (!(ok = prod_sync(&sm.psync, ph, abort_flag, lane, g.spin) && ok)) break;  // window tables reused next window
     }
     // ---- partial rows ----
     if (ok && !*abort_flag && epi) {
@@ -993,6 +994,7 @@ struct TcJArgs {
     int npad;               // MMA N of a full item: blocks x colw rounded up to 16 (<= 128)
     int nrows, nstage, nitems;
     int nparts, spp;        // row parts, stages per part
+    long long spin;         // clock cycles a wait between roles may take before it gives up
 };
 
 // column scales: the exponent bound of max over the rows of |n_a^i n_b^j W(m, n_c)|
@@ -1183,7 +1185,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_j(TcJArgs g) {
             const int mg = part * g.spp * kTcJStageM + m;
             sm.rowi[m] = m < g.spp * kTcJStageM && mg < g.nrows ? __ldg(g.rows + mg) : make_int2(INT_MIN, 0);
         }
-        if (!(ok = prod_sync(&sm.psync, ph, abort_flag, lane))) break;
+        if (!(ok = prod_sync(&sm.psync, ph, abort_flag, lane, g.spin))) break;
         const int L = sm.iL, nb = sm.inb, q0 = sm.ipart * g.spp, nst = min(g.spp, g.nstage - q0);
         if (load_warp) {
             // the records' factor tables, then every stage's V_ij tiles
@@ -1202,7 +1204,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_j(TcJArgs g) {
             for (int q = 0; q < nst; ++q, ++gs) {
                 const int slot = (int)(gs & 1);
                 if (gs >= kTcNbuf) {
-                    ok = __all_sync(0xffffffffu, mbar_wait(&sm.empty[slot], (uint32_t)(((gs >> 1) - 1) & 1), abort_flag));
+                    ok = __all_sync(0xffffffffu, mbar_wait(&sm.empty[slot], (uint32_t)(((gs >> 1) - 1) & 1), abort_flag, g.spin));
                     if (!ok) break;
                 }
                 unsigned char* bs = bbuf + (size_t)slot * kTcJS * bslice;
@@ -1218,13 +1220,13 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_j(TcJArgs g) {
                 __syncwarp();
             }
         } else if (!mma_warp) {
-            ok = __all_sync(0xffffffffu, mbar_wait(&sm.tfull, (uint32_t)(nit & 1), abort_flag));
+            ok = __all_sync(0xffffffffu, mbar_wait(&sm.tfull, (uint32_t)(nit & 1), abort_flag, g.spin));
             if (ok) {
                 for (int q = 0; q < nst; ++q, ++gs) {
                     const int slot = (int)(gs & 1);
                     if (gs >= kTcNbuf) {
                         ok = __all_sync(0xffffffffu,
-                                        mbar_wait(&sm.empty[slot], (uint32_t)(((gs >> 1) - 1) & 1), abort_flag));
+                                        mbar_wait(&sm.empty[slot], (uint32_t)(((gs >> 1) - 1) & 1), abort_flag, g.spin));
                         if (!ok) break;
                     }
                     unsigned char* as = abuf + (size_t)slot * kTcJS * kTcJAsliceBytes;
@@ -1242,12 +1244,12 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_j(TcJArgs g) {
                                        ((uint32_t)(kTcM >> 4) << 24);
                 bool first[kTcJAcc] = {true, true, true, true, true};
                 bool mok = true;
-                if (nit > 0) mok = mbar_wait(&sm.acce, (uint32_t)((nit - 1) & 1), abort_flag);  // tensor memory drained
+                if (nit > 0) mok = mbar_wait(&sm.acce, (uint32_t)((nit - 1) & 1), abort_flag, g.spin);  // tensor memory drained
                 tc_fence_after();
                 for (int q = 0; q < nst && mok; ++q, ++gs) {
                     const int slot = (int)(gs & 1);
-                    if (!(mok = mbar_wait(&sm.full[slot], (uint32_t)((gs >> 1) & 1), abort_flag))) break;
-                    if (!(mok = mbar_wait(&sm.bfull[slot], (uint32_t)((gs >> 1) & 1), abort_flag))) break;
+                    if (!(mok = mbar_wait(&sm.full[slot], (uint32_t)((gs >> 1) & 1), abort_flag, g.spin))) break;
+                    if (!(mok = mbar_wait(&sm.bfull[slot], (uint32_t)((gs >> 1) & 1), abort_flag, g.spin))) break;
                     tc_fence_after();
                     const uint32_t as = a0 + slot * kTcJS * kTcJAsliceBytes, bs = b0 + slot * kTcJS * bslice;
 #pragma unroll
@@ -1270,7 +1272,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_j(TcJArgs g) {
         if (!ok) break;
         // ---- J'_{r,ijk} = Re (-i)^k sum_{n_c} n_c^k Z_r(n_c) U_ij[r, n_c] (warps 0-11) ----
         if (epi) {
-            ok = __all_sync(0xffffffffu, mbar_wait(&sm.accf, (uint32_t)(nit & 1), abort_flag));
+            ok = __all_sync(0xffffffffu, mbar_wait(&sm.accf, (uint32_t)(nit & 1), abort_flag, g.spin));
             if (!ok) break;
             tc_fence_after();
             const int r = sm.rec[erow];
@@ -1328,7 +1330,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_j(TcJArgs g) {
         }
         ++nit;
         // the tables, records and blocks are rewritten by the next item
-        if (!(ok = prod_sync(&sm.psync, ph, abort_flag, lane) && ok)) break;
+        if (!(ok = prod_sync(&sm.psync, ph, abort_flag, lane, g.spin) && ok)) break;
     }
     if (load_warp && lane == 0) {
         // bulk copies still in flight (after a failed wait) land before the CTA exits
@@ -1373,6 +1375,11 @@ size_t tc_j_smem_bytes(int npad, int tabw) {
 }  // namespace
 
 int tc_supported(const ftcj_plan* P) { return P->ortho ? 1 : 0; }
+
+// clock-cycle budget of one wait between the kernels' roles
+long long tc_spin(const ftcj_plan* P) {
+    return P->params.tc_wait_log2 > 0 ? (1LL << P->params.tc_wait_log2) : kTcSpinCycles;
+}
 
 int setup_tc_j(ftcj_plan* P);
 
@@ -1600,6 +1607,7 @@ int launch_tc_rho(ftcj_plan* P, int ndens, cudaStream_t s) {
     g.win_per_group = P->tc_wpg;
     g.ngroups = P->tc_ngroups;
     g.nrows = P->tc_rows;
+    g.spin = tc_spin(P);
     const size_t smem = tc_smem_bytes(P->tc_npad, P->tc_tabw, P->tc_G, P->tc_nd, P->tc_tslots);
     for (int d0 = 0; d0 < ndens; d0 += P->tc_nd) {
         g.d0 = d0;
@@ -1742,6 +1750,7 @@ int launch_tc_j(ftcj_plan* P, int ndens, const double* W, cudaStream_t s) {
     g.nstage = P->tc_jnstage;
     g.nitems = P->tc_jnitems;
     g.nparts = P->tc_jparts;
+    g.spin = tc_spin(P);
     g.spp = P->tc_jspp;
     const size_t smem = tc_j_smem_bytes(P->tc_jnpad, P->tc_tabw);
     const int grid = std::max(1, std::min(P->num_sms, P->tc_jnitems));

@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
     _fields_ = [("omega", _c_double), ("gcut", _c_double), ("eps_g", _c_double), ("pair_thresh", _c_double),
                 ("precision", _c_int), ("max_dens", _c_int), ("chunk_points", _c_int), ("rho_blocks", _c_int),
                 ("pair_gcut_eps", _c_double), ("shard_count", _c_int), ("shard_index", _c_int),
-                ("contraction", _c_int)]
+                ("contraction", _c_int), ("tc_wait_log2", _c_int)]
 
 
 class Info(ctypes.Structure):
@@ -198,7 +198,7 @@ def _params_of(w, precision=FTCJ_PREC_FP64, max_dens=None, chunk_points=0, rho_b
                contraction=0):
     return Params(float(w.omega), float(w.gcut), float(w.eps_g), float(w.pair_thresh), int(precision),
                   int(max_dens or w.ndens), int(chunk_points), int(rho_blocks), float(pair_gcut_eps), 0, 0,
-                  int(contraction))
+                  int(contraction), 0)
 
 
 def shard_bounds(class_counts, precision, shard_count):
@@ -310,14 +310,14 @@ class Plan:
 
     def __init__(self, A, xyz, shells, kmesh, omega, eps_g=1e-14, gcut=0.0, pair_thresh=1e-12,
                  precision=FTCJ_PREC_FP64, max_dens=1, chunk_points=0, rho_blocks=0, pair_gcut_eps=0.0,
-                 shard_count=0, shard_index=0, contraction=FTCJ_CONTRACT_WALK):
+                 shard_count=0, shard_index=0, contraction=FTCJ_CONTRACT_WALK, tc_wait_log2=0):
         L = lib()
         self._keep = []
         cell, basis = _describe(A, xyz, shells, self._keep)
         km = (ctypes.c_int * 3)(*[int(k) for k in kmesh])
         prm = Params(float(omega), float(gcut), float(eps_g), float(pair_thresh), int(precision), int(max_dens),
                      int(chunk_points), int(rho_blocks), float(pair_gcut_eps), int(shard_count), int(shard_index),
-                     int(contraction))
+                     int(contraction), int(tc_wait_log2))
         self.shard_count = max(1, int(shard_count))
         self.shard_index = int(shard_index)
         h = _c_void_p()
@@ -336,11 +336,12 @@ class Plan:
 
     @classmethod
     def from_workload(cls, w, max_dens=None, precision=FTCJ_PREC_FP64, chunk_points=0, rho_blocks=0,
-                      pair_gcut_eps=0.0, shard_count=0, shard_index=0, contraction=FTCJ_CONTRACT_WALK):
+                      pair_gcut_eps=0.0, shard_count=0, shard_index=0, contraction=FTCJ_CONTRACT_WALK,
+                      tc_wait_log2=0):
         return cls(w.A, w.xyz, w.shells, w.kmesh, w.omega, eps_g=w.eps_g, gcut=w.gcut, pair_thresh=w.pair_thresh,
                    precision=precision, max_dens=max_dens or w.ndens, chunk_points=chunk_points,
                    pair_gcut_eps=pair_gcut_eps, rho_blocks=rho_blocks, shard_count=shard_count,
-                   shard_index=shard_index, contraction=contraction)
+                   shard_index=shard_index, contraction=contraction, tc_wait_log2=tc_wait_log2)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

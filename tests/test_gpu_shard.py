@@ -57,3 +57,39 @@ def test_shards_sum_to_the_whole_build(orc, F, precision, S, eps):
         shards[0].jbuild(Dk)
     for p in shards + [whole]:
         p.close()
+
+
+def test_tensor_core_shards_sum_to_the_whole_build(orc, F):
+    """The tensor-core form on record shards (what `bench.py --gpus N` runs):
+    each share's windows and items hold different records, so the shares'
+    slice scales differ from the whole plan's and the sums agree to the
+    form's rounding, not bit for bit."""
+    import torch
+    w = ragged()
+    ref = orc.lrj(w)
+    kw = dict(precision=F.FTCJ_PREC_SPLIT, contraction=F.FTCJ_CONTRACT_TC)
+    whole = F.Plan.from_workload(w, **kw)
+    shards = [F.Plan.from_workload(w, shard_count=2, shard_index=s, **kw) for s in range(2)]
+    try:
+        assert all(p.info["contraction"] == F.FTCJ_CONTRACT_TC for p in shards + [whole])
+        assert sum(p.info["npairs"] for p in shards) == whole.info["npairs"]
+        Dk = torch.from_numpy(np.ascontiguousarray(w.Dk)).cuda()
+        D0n = shards[0].fold_density(Dk)
+        rho = sum(p.rho(D0n) for p in shards)
+        Wg, E = shards[0].potential(rho)
+        J0n = sum(p.jback(Wg) for p in shards)
+        Jk = shards[0].unfold_j(J0n)
+        Jw, Ew = whole.jbuild(Dk)
+        torch.cuda.synchronize()
+        assert all(p.status() == 0 for p in shards + [whole])
+        scale = float(Jw.abs().max())
+        d_whole = float((Jk - Jw).abs().max())
+        d_ref = float(np.abs(Jk.cpu().numpy() - ref["Jk"]).max())
+        print(f"tc shards: max|dJ| vs whole {d_whole:.3e} (max|J| {scale:.3e}), vs oracle {d_ref:.3e}")
+        assert d_whole <= 1e-10 * scale
+        assert float((E - Ew).abs().max()) <= 1e-10 * float(Ew.abs().max())
+        assert d_ref <= 1e-8
+        assert np.abs(E.cpu().numpy() - ref["EJ"]).max() <= 1e-8 * max(1.0, float(np.abs(ref["EJ"]).max()))
+    finally:
+        for p in shards + [whole]:
+            p.close()

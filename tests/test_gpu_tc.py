@@ -149,3 +149,23 @@ def test_tc_refusals(F):
         F.Plan.from_workload(W.cfg1(), precision=F.FTCJ_PREC_FP64, contraction=F.FTCJ_CONTRACT_TC)
     with pytest.raises(F.FtcjError, match="whole sphere"):
         tc_plan(F, W.cfg1(), pair_gcut_eps=1e-12)
+
+
+def test_tc_waits_give_up_and_report(orc, F):
+    """With a wait budget of 2 clock cycles the tensor-core kernels' waits
+    between their roles give up at once: the kernels raise the plan's error
+    word, drain what they have in flight and return; the call completes, the
+    status reports bit 0 (and is cleared by reading it), and the context stays
+    usable: a plan with the default budget then matches the oracle."""
+    import torch
+    w = W.cfg1()
+    Dk = torch.from_numpy(np.ascontiguousarray(w.Dk)).cuda()
+    short = tc_plan(F, w, tc_wait_log2=1)
+    try:
+        short.jbuild(Dk)
+        torch.cuda.synchronize()
+        assert short.status() & 1
+        assert short.status() == 0
+    finally:
+        short.close()
+    check_against_oracle(orc, F, w)
