@@ -493,7 +493,7 @@ def autotune_leg(ftcj, W, torch, flush, steps):
             "rho_blocks": rb, "shape_note": "0 = the plan's own default", "autotune_s": tune_s}
 
 
-def diamond_leg(ctx, forms=("split", "fp64")):
+def diamond_leg(ctx, forms=("split_tc", "split", "fp64")):
     """Secondary line: the diamond-like 240-AO cell, k 4x4x4, every form timed
     as the headline is, and (unless disabled) checked whole against the oracle."""
     import numpy as np
@@ -532,8 +532,10 @@ def slab_leg(ftcj, W, torch, flush, steps):
                        f"{len(w.xyz)} centres, {w.nao} spherical AOs, k 3x3x1, omega 0.4", "ndens": w.ndens}
     stream = torch.cuda.current_stream()
     res = {}
-    for form, prec in (("split", ftcj.FTCJ_PREC_SPLIT), ("fp64", ftcj.FTCJ_PREC_FP64)):
-        p = ftcj.Plan.from_workload(w, precision=prec)
+    for form, prec, con in (("split_tc", ftcj.FTCJ_PREC_SPLIT, ftcj.FTCJ_CONTRACT_TC),
+                            ("split", ftcj.FTCJ_PREC_SPLIT, ftcj.FTCJ_CONTRACT_WALK),
+                            ("fp64", ftcj.FTCJ_PREC_FP64, ftcj.FTCJ_CONTRACT_WALK)):
+        p = ftcj.Plan.from_workload(w, precision=prec, contraction=con)
         units = float(p.info["pair_g_units"]) * w.ndens
         out["pair_g_units_per_step"] = units
         J, E = p.jbuild(Dk)
@@ -541,6 +543,9 @@ def slab_leg(ftcj, W, torch, flush, steps):
             p.jbuild(Dk, J, E)
         ms = time_events(lambda: p.jbuild(Dk, J, E), steps, flush, stream)
         out[form] = {"ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT}
+        if con == ftcj.FTCJ_CONTRACT_TC:
+            out[form]["status"] = p.status()
+            out[form]["j_contraction"] = int(p.info["j_contraction"])
         res[form] = (J.clone(), E.clone())
         if form == "split":
             EJ, G = p.grad(Dk)
@@ -560,6 +565,8 @@ def slab_leg(ftcj, W, torch, flush, steps):
     out["split_vs_fp64_max_abs_dJ"] = float((res["split"][0] - res["fp64"][0]).abs().max())
     out["split_vs_fp64_abs_dEJ"] = float((res["split"][1] - res["fp64"][1]).abs().max())
     out["split_speedup_vs_fp64"] = out["fp64"]["ms_per_step"] / out["split"]["ms_per_step"]
+    out["split_tc_vs_fp64_max_abs_dJ"] = float((res["split_tc"][0] - res["fp64"][0]).abs().max())
+    out["split_tc_vs_fp64_abs_dEJ"] = float((res["split_tc"][1] - res["fp64"][1]).abs().max())
     return out
 
 
@@ -634,7 +641,7 @@ def main():
         steps = max(3, min(args.steps, 10))
         if args.leg == "diamond":
             out = diamond_leg(ctx)
-            for f in ("split", "fp64"):
+            for f in ("split_tc", "split", "fp64"):
                 out[f].pop("clocks", None)
         elif args.leg == "batch":
             out = batch_leg(ftcj, W, torch, flush, steps)

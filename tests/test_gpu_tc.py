@@ -110,6 +110,35 @@ def test_tc_cfg3_against_split_walk(F):
     assert dJ <= J_TOL and dE <= J_TOL * max(1.0, float(Ew.abs().max()))
 
 
+def test_tc_diamond_against_oracle(orc, F):
+    """The diamond-like cubic cell (240 AOs, k 4x4x4, 64 densities folded
+    into one real D^{0n}), whole, against the oracle's whole build."""
+    check_against_oracle(orc, F, W.cfg2())
+
+
+def test_tc_slab_against_split_walk(F):
+    """The slab (orthorhombic, 940 AOs, k 3x3x1, 30 bohr along c with
+    vacuum): tensor-core form against the double-float walks."""
+    import torch
+    w = W.cfg5()
+    Dk = torch.from_numpy(np.ascontiguousarray(w.Dk)).cuda()
+    walk = F.Plan.from_workload(w, precision=F.FTCJ_PREC_SPLIT)
+    Jw, Ew = walk.jbuild(Dk)
+    torch.cuda.synchronize()
+    walk.close()
+    tc = tc_plan(F, w)
+    info = tc.info
+    Jt, Et = tc.jbuild(Dk)
+    torch.cuda.synchronize()
+    assert tc.status() == 0
+    tc.close()
+    dJ = float((Jt - Jw).abs().max())
+    dE = float((Et - Ew).abs().max())
+    print(f"slab tc vs walk: max|dJ|={dJ:.3e} |dE|={dE:.3e} |E_J|={float(Ew.abs().max()):.6e} "
+          f"j form={info['j_contraction']}")
+    assert dJ <= J_TOL and dE <= J_TOL * max(1.0, float(Ew.abs().max()))
+
+
 def jback_pair(F, w):
     """J^{0n} from the same potential W through the split walk's and the
     tensor-core back-contraction: the difference is the J pass's alone."""
