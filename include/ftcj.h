@@ -314,6 +314,21 @@ int ftcj_check_density(ftcj_plan* plan, int ndens, const double* Dk, double* max
  * With FTCJ_BATCH_AUTOTUNE each cell's walk shape (chunk size, rho-walk
  * blocks) is chosen by ftcj_autotune before its plan is made. */
 #define FTCJ_BATCH_AUTOTUNE 1
+/* With FTCJ_BATCH_PERSISTENT the structure-factor walks, the potentials and
+ * energies, and the back-contraction walks of every cell run as ONE
+ * persistent launch over a shared work queue (Alg. 1 and Alg. S1 over many
+ * cells): structure-factor items (cell, block of the cell's schedule, walk
+ * chunk, density) first, largest first, then back-contraction items (cell,
+ * tile, chunk, density) in the order the cells become ready.  The CTA that
+ * finishes a cell's last structure-factor item sums its FP64 rows in fixed
+ * order into rho, W and E_J; a back-contraction item waits (bounded, see
+ * ftcj_batch_set_wait) for its cell's potential.  The k-mesh transforms and
+ * Hermite maps run per cell on the streams before and after.  Every cell must
+ * be split precision without per-pair cutoffs and with the walk contraction
+ * (EUNSUPPORTED otherwise), all with or all without the orthorhombic X(n1)
+ * table, and each call builds exactly params[c].max_dens densities of cell c
+ * (EINVAL otherwise). */
+#define FTCJ_BATCH_PERSISTENT 2
 typedef struct ftcj_batch ftcj_batch;
 
 /* cells/bases/params are arrays of ncell; kmeshes is [ncell][3]. */
@@ -339,6 +354,16 @@ int ftcj_batch_capture(ftcj_batch* batch, const int* ndens, const double* const*
 /* Launches the captured graph on `stream` (the buffers of the capture are
  * read and written again).  Errors: EINVAL if nothing was captured. */
 int ftcj_batch_replay(ftcj_batch* batch, void* stream);
+
+/* Persistent batches: a back-contraction item gives up waiting for its
+ * cell's potential after 2^wait_log2 clock cycles (0: 2^32, about 2 s),
+ * raises the batch's error word and skips its work.  0..40, else EINVAL. */
+int ftcj_batch_set_wait(ftcj_batch* batch, int wait_log2);
+
+/* The error word of the last persistent launch (bit 0: a wait gave up),
+ * read on `stream` (synchronises it).  Returns FTCJ_ETIMEOUT when bit 0 is
+ * set, FTCJ_OK otherwise (and for batches that are not persistent). */
+int ftcj_batch_status(ftcj_batch* batch, int* flags, void* stream);
 
 void ftcj_batch_destroy(ftcj_batch* batch);
 

@@ -6,6 +6,12 @@
 // the currently least-loaded stream, and joins every stream back into the
 // caller's stream.  Because the fork and join are event edges, the whole
 // batch can be captured into one CUDA graph and replayed.
+//
+// A persistent batch (FTCJ_BATCH_PERSISTENT) runs the per-cell k-mesh
+// transforms and Hermite maps on the streams, then the structure-factor
+// walks, the potentials and the back-contraction walks of every cell as one
+// persistent launch over a shared work queue (walk_split.cu), then the
+// per-cell J -> AO maps and transforms on the streams again.
 #include <algorithm>
 #include <numeric>
 #include <vector>
@@ -20,6 +26,8 @@ constexpr int kBatchStreams = 8;
 
 struct ftcj_batch {
     std::vector<ftcj_plan*> plans;
+    ftcj::BatchWalks* walks = nullptr;  // the persistent launch's work queue (persistent batches)
+    long long spin = 1LL << 32;         // clock cycles a back-contraction item waits for its cell's potential
     std::vector<double> cost;  // estimated work per density
     cudaStream_t streams[kBatchStreams] = {};
     cudaEvent_t fork = nullptr;
@@ -33,6 +41,8 @@ using namespace ftcj;
 namespace {
 
 void release(ftcj_batch* B) {
+    if (B->walks) batch_walks_destroy(B->walks);
+    B->walks = nullptr;
     if (B->exec) cudaGraphExecDestroy(B->exec);
     if (B->graph) cudaGraphDestroy(B->graph);
     for (int i = 0; i < kBatchStreams; ++i) {
@@ -44,11 +54,71 @@ void release(ftcj_batch* B) {
     B->plans.clear();
 }
 
+// the cells in order of decreasing work, each on the currently least-loaded stream
+std::vector<int> assign(const ftcj_batch* B, const int* ndens, int ns) {
+    const int n = (int)B->plans.size();
+    std::vector<int> order(n), stream_of(n, 0);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return B->cost[a] * ndens[a] > B->cost[b] * ndens[b]; });
+    std::vector<double> load(ns, 0.0);
+    for (int c : order) {
+        const int i = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[i] += B->cost[c] * ndens[c];
+        stream_of[c] = i;
+    }
+    return stream_of;
+}
+
+int fork(ftcj_batch* B, int ns, cudaStream_t s) {
+    FTCJ_CUDA(cudaEventRecord(B->fork, s));
+    for (int i = 0; i < ns; ++i) FTCJ_CUDA(cudaStreamWaitEvent(B->streams[i], B->fork, 0));
+    return FTCJ_OK;
+}
+
+int join(ftcj_batch* B, int ns, cudaStream_t s) {
+    for (int i = 0; i < ns; ++i) {
+        FTCJ_CUDA(cudaEventRecord(B->join[i], B->streams[i]));
+        FTCJ_CUDA(cudaStreamWaitEvent(s, B->join[i], 0));
+    }
+    return FTCJ_OK;
+}
+
+// the persistent form: transforms and maps per cell on the streams, the walks of all cells in one launch
+int enqueue_persistent(ftcj_batch* B, const int* ndens, const double* const* Dk, double* const* Jk,
+                       double* const* EJ, cudaStream_t s) {
+    const int n = (int)B->plans.size();
+    for (int c = 0; c < n; ++c)
+        if (ndens[c] != B->plans[c]->max_dens)
+            return fail(FTCJ_EINVAL, "a persistent batch builds max_dens densities of every cell per call");
+    const int ns = std::min(kBatchStreams, std::max(n, 1));
+    const std::vector<int> st = assign(B, ndens, ns);
+    int rc;
+    if ((rc = fork(B, ns, s))) return rc;
+    for (int c = 0; c < n; ++c) {
+        ftcj_plan* P = B->plans[c];
+        if ((rc = launch_fold_build(P, ndens[c], Dk[c], P->d_D0n, B->streams[st[c]]))) return rc;
+        if ((rc = launch_hermite_map(P, ndens[c], P->d_D0n, B->streams[st[c]]))) return rc;
+    }
+    if ((rc = join(B, ns, s))) return rc;
+    if ((rc = batch_walks_launch(B->walks, B->plans, B->spin, s))) return rc;
+    if ((rc = fork(B, ns, s))) return rc;
+    for (int c = 0; c < n; ++c) {
+        ftcj_plan* P = B->plans[c];
+        cudaStream_t t = B->streams[st[c]];
+        if ((rc = launch_jtransform_map(P, ndens[c], P->d_J0n, t))) return rc;
+        if ((rc = launch_unfold(P, ndens[c], P->d_J0n, Jk[c], t))) return rc;
+        FTCJ_CUDA(cudaMemcpyAsync(EJ[c], P->d_EJ_stage, sizeof(double) * ndens[c], cudaMemcpyDeviceToDevice, t));
+    }
+    return join(B, ns, s);
+}
+
 int enqueue(ftcj_batch* B, const int* ndens, const double* const* Dk, double* const* Jk, double* const* EJ,
             cudaStream_t s) {
     const int n = (int)B->plans.size();
     for (int c = 0; c < n; ++c)
         if (ndens[c] < 1 || !Dk[c] || !Jk[c] || !EJ[c]) return fail(FTCJ_EINVAL, "bad per-cell argument");
+    if (B->walks) return enqueue_persistent(B, ndens, Dk, Jk, EJ, s);
     std::vector<int> order(n);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(),
@@ -178,7 +248,17 @@ int ftcj_batch_create(int ncell, const ftcj_cell* cells, const ftcj_basis* bases
         if (flags & FTCJ_BATCH_AUTOTUNE) rc = ftcj_autotune(&cells[c], &bases[c], kmeshes + 3 * c, &params[c], &p,
                                                             nullptr);
         ftcj_plan* P = nullptr;
-        if (rc == FTCJ_OK) rc = ftcj_plan_create(&cells[c], &bases[c], kmeshes + 3 * c, &p, &P);
+        if (rc == FTCJ_OK && (flags & FTCJ_BATCH_PERSISTENT) && p.chunk_points <= 0) {
+            // one kernel runs every cell's walks: its shared memory (and so its CTAs per SM) follows the
+            // longest chunk of the batch, so each cell takes the shortest chunk that holds its G lines
+            for (int ch = 512; ch <= 4096; ch *= 2) {
+                p.chunk_points = ch;
+                rc = ftcj_plan_create(&cells[c], &bases[c], kmeshes + 3 * c, &p, &P);
+                if (rc != FTCJ_EUNSUPPORTED) break;
+            }
+        } else if (rc == FTCJ_OK) {
+            rc = ftcj_plan_create(&cells[c], &bases[c], kmeshes + 3 * c, &p, &P);
+        }
         if (rc == FTCJ_OK) {
             B->plans.push_back(P);
             B->cost.push_back((double)P->npairs_ordered * (double)(2 * P->ng_half) +
@@ -193,6 +273,7 @@ int ftcj_batch_create(int ncell, const ftcj_cell* cells, const ftcj_basis* bases
         }
         if (e != cudaSuccess) rc = cuda_fail(e, "batch streams");
     }
+    if (rc == FTCJ_OK && (flags & FTCJ_BATCH_PERSISTENT)) rc = batch_walks_create(B->plans, &B->walks);
     if (rc) {
         release(B);
         delete B;
@@ -246,6 +327,24 @@ int ftcj_batch_replay(ftcj_batch* B, void* stream) {
     if (!B) return fail(FTCJ_EINVAL, "null batch");
     if (!B->exec) return fail(FTCJ_EINVAL, "nothing captured");
     FTCJ_CUDA(cudaGraphLaunch(B->exec, reinterpret_cast<cudaStream_t>(stream)));
+    return FTCJ_OK;
+}
+
+int ftcj_batch_set_wait(ftcj_batch* B, int wait_log2) {
+    if (!B || wait_log2 < 0 || wait_log2 > 40) return fail(FTCJ_EINVAL, "wait_log2 must be 0..40");
+    B->spin = 1LL << (wait_log2 ? wait_log2 : 32);
+    return FTCJ_OK;
+}
+
+int ftcj_batch_status(ftcj_batch* B, int* flags, void* stream) {
+    if (!B || !flags) return fail(FTCJ_EINVAL, "null argument");
+    *flags = 0;
+    if (!B->walks) return FTCJ_OK;
+    int rc = batch_walks_error(B->walks, flags, reinterpret_cast<cudaStream_t>(stream));
+    if (rc) return rc;
+    if (*flags & 1)
+        return fail(FTCJ_ETIMEOUT, "a back-contraction item of the persistent batch gave up waiting for its "
+                                   "cell's potential");
     return FTCJ_OK;
 }
 

@@ -329,6 +329,13 @@ int setup_tc(ftcj_plan* P);
 int launch_tc_rho(ftcj_plan* P, int ndens, cudaStream_t s);
 int tc_rho_launches(const ftcj_plan* P, int nd);
 int launch_tc_j(ftcj_plan* P, int ndens, const double* W, cudaStream_t s);
+// one persistent launch of the walks of a batch of cells (walk_split.cu)
+struct BatchWalks;
+int batch_walks_create(const std::vector<ftcj_plan*>& plans, BatchWalks** out);
+int batch_walks_launch(BatchWalks* bw, const std::vector<ftcj_plan*>& plans, long long spin, cudaStream_t s);
+int batch_walks_error(BatchWalks* bw, int* word, cudaStream_t s);
+int batch_walks_launches(const BatchWalks* bw);
+void batch_walks_destroy(BatchWalks* bw);
 int tc_j_launches(const ftcj_plan* P, int nd);
 // partial back-contraction sums the J -> AO map adds: one per walk chunk, or per row part of the tensor-core form
 inline int jp_chunks(const ftcj_plan* P) { return P->tc_j ? P->tc_jparts : (int)P->chunks.size(); }

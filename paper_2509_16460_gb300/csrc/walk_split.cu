@@ -774,6 +774,211 @@ JKernel j_grad_kernel(const ftcj_plan* P, int part) {
     return part == 1 ? j_kernel_part<1, 1>(P) : j_kernel_part<2, 1>(P);
 }
 
+
+// ---- one persistent launch over a batch of cells (form 2) -------------------
+//
+// Work items of every cell of a batch share one queue (a global counter):
+// structure-factor items (cell, persistent block b of the cell's LPT
+// schedule, chunk, density), the same work one block of the cell's own walk
+// launch does, writing that block's rho row, and back-contraction items
+// (cell, tile, chunk, density), all structure-factor items first.  The phase
+// change is per cell: the CTA that finishes a cell's last structure-factor
+// item sums its rows in fixed order, forms W = 2 v conj rho and E_J, and
+// raises the cell's ready flag; a CTA holding a back-contraction item of that
+// cell waits for the flag (every structure-factor item was taken before any
+// back-contraction item, by CTAs that wait on nothing, so the wait ends).  The wait is bounded: past the
+// budget the CTA raises the batch's error word and skips the item.  Data
+// written inside the launch (rows, W) is read through L2 (ld.global.cg),
+// never through the read-only path.
+
+struct BatchCell {
+    const Tile* tiles;
+    const int* sched;
+    int npb, nchunks, nx, ndens;
+    Layout lay;
+    const float2* Dp;
+    const SConst* cst;
+    const SState* init;
+    long long npairs;
+    const WLine* lines;
+    const WChunk* chunks;
+    double2* rho_part;   // [dens][npb][ng_half]
+    const double* vg;
+    double2* W;          // [dens][ng_half]
+    double* EJ;          // [dens]
+    double* Jp;          // [dens][nchunks][total]
+    long long ng_half;
+};
+
+// one tile of one class, out of line: each class's walk gets its own register allocation
+template <int Lc, bool ORTHO>
+__device__ __noinline__ void batch_rho_tile(const Tile tl, const BatchCell* C, const float2* __restrict__ Dp_d,
+                                            const SState* __restrict__ init_c, const WChunk ch, float4* buf,
+                                            float4* red, float4* row, float2* Dsm, float4* Xs, int* spt) {
+    rho_tile_split<Lc, ORTHO, false>(tl, C->lay, Dp_d, C->cst, init_c, C->lines, ch, buf, red, row, Dsm, Xs, C->nx,
+                                     spt);
+}
+
+template <int Lc, bool ORTHO>
+__device__ __noinline__ void batch_j_tile(const Tile tl, const BatchCell* C, const SState* __restrict__ init_c,
+                                          const WChunk ch, const float4* wsm, double* Jp_dc, float2* Jsm,
+                                          float4* Xs) {
+    j_tile_split<Lc, ORTHO, false, Lc>(tl, C->lay, C->cst, init_c, C->lines, ch, wsm, Jp_dc, Jsm, Xs, C->nx);
+}
+
+template <bool ORTHO>
+__device__ __forceinline__ void batch_rho_item(const BatchCell& C, int b, int cidx, int d, float4* ssm, int* spt) {
+    const WChunk ch = C.chunks[cidx];
+    const int npts = ch.p1 - ch.p0;
+    float4* buf = ssm;
+    float4* red = buf + kSBatch * (kTile + 1);
+    float2* Dsm = reinterpret_cast<float2*>(red + kTile);
+    float4* Xs = reinterpret_cast<float4*>(Dsm + nterms(4) * kTile);
+    float4* row = Xs + (ORTHO ? C.nx * kTile : 0);
+    for (int i = threadIdx.x; i < npts; i += blockDim.x) row[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    const float2* Dp_d = C.Dp + (long long)d * C.lay.total;
+    const SState* init_c = C.init + (long long)cidx * C.npairs;
+    for (int j = C.sched[b]; j < C.sched[b + 1]; ++j) {
+        const Tile tl = C.tiles[C.sched[C.npb + 1 + j]];
+#define FTCJ_BRHO(Lc) batch_rho_tile<Lc, ORTHO>(tl, &C, Dp_d, init_c, ch, buf, red, row, Dsm, Xs, spt)
+        switch (tl.cls) {
+            case 0: FTCJ_BRHO(0); break;
+            case 1: FTCJ_BRHO(1); break;
+            case 2: FTCJ_BRHO(2); break;
+            case 3: FTCJ_BRHO(3); break;
+            default: FTCJ_BRHO(4); break;
+        }
+#undef FTCJ_BRHO
+    }
+    __syncthreads();
+    double2* out = C.rho_part + ((long long)d * C.npb + b) * C.ng_half + ch.p0;
+    for (int i = threadIdx.x; i < npts; i += blockDim.x) {
+        const float4 v = row[i];
+        out[i] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    }
+    __syncthreads();
+}
+
+template <bool ORTHO>
+__device__ __forceinline__ void batch_j_item(const BatchCell& C, int tix, int cidx, int d, float4* ssm) {
+    const WChunk ch = C.chunks[cidx];
+    const int npts = ch.p1 - ch.p0;
+    float4* wsm = ssm;
+    float2* Jsm = reinterpret_cast<float2*>(ssm + npts);
+    float4* Xs = reinterpret_cast<float4*>(Jsm + nterms(4) * kTile);
+    const double2* Wd = C.W + (long long)d * C.ng_half + ch.p0;
+    for (int i = threadIdx.x; i < npts; i += blockDim.x) {
+        const double2 v = __ldcg(Wd + i);  // written in this launch: through L2
+        const df re = df_from_double(v.x), im = df_from_double(v.y);
+        wsm[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+    __syncthreads();
+    const Tile tl = C.tiles[tix];
+    double* Jp_dc = C.Jp + ((long long)d * C.nchunks + cidx) * C.lay.total;
+    const SState* init_c = C.init + (long long)cidx * C.npairs;
+#define FTCJ_BJ(c) batch_j_tile<(c), ORTHO>(tl, &C, init_c, ch, wsm, Jp_dc, Jsm, Xs)
+    switch (tl.cls) {
+        case 0: FTCJ_BJ(0); break;
+        case 1: FTCJ_BJ(1); break;
+        case 2: FTCJ_BJ(2); break;
+        case 3: FTCJ_BJ(3); break;
+        default: FTCJ_BJ(4); break;
+    }
+#undef FTCJ_BJ
+    __syncthreads();
+}
+
+// rho = the cell's rows summed in fixed order, W = 2 v conj rho, E_J = sum v |rho|^2 (one CTA)
+__device__ __noinline__ void batch_reduce_cell(const BatchCell& C, double* se) {
+    for (int d = 0; d < C.ndens; ++d) {
+        double e = 0.0;
+        for (long long p = threadIdx.x; p < C.ng_half; p += blockDim.x) {
+            const double2* src = C.rho_part + (long long)d * C.npb * C.ng_half + p;
+            double rr = 0.0, ri = 0.0;
+            for (int q = 0; q < C.npb; ++q) {
+                const double2 u = __ldcg(src + (long long)q * C.ng_half);
+                rr += u.x;
+                ri += u.y;
+            }
+            const double v = C.vg[p];
+            C.W[(long long)d * C.ng_half + p] = make_double2(2.0 * v * rr, -2.0 * v * ri);
+            e += v * (rr * rr + ri * ri);
+        }
+        se[threadIdx.x] = e;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) se[threadIdx.x] += se[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) C.EJ[d] = se[0];
+        __syncthreads();
+    }
+}
+
+// CTAs per SM the batch kernel is compiled for (registers: 3 -> 168, 2 -> 255)
+#ifndef FTCJ_BATCH_MINB
+#define FTCJ_BATCH_MINB 3
+#endif
+
+template <bool ORTHO>
+__global__ void __launch_bounds__(kTile, FTCJ_BATCH_MINB) k_batch_walks(const BatchCell* __restrict__ cells,
+                                                           const int4* __restrict__ items, int nitems,
+                                                           int* counter, int* remaining, int* ready, int* err,
+                                                           long long spin) {
+    extern __shared__ float4 ssm[];
+    __shared__ int spt[2 * kSBatch];
+    __shared__ double se[kTile];
+    __shared__ int s_item, s_go;
+    __shared__ BatchCell sc;  // the item's cell, read from shared memory rather than held in registers
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const int4 in = items[it];
+        if (threadIdx.x < (int)(sizeof(BatchCell) / 8))
+            reinterpret_cast<long long*>(&sc)[threadIdx.x] = reinterpret_cast<const long long*>(cells + in.x)[threadIdx.x];
+        __syncthreads();
+        const BatchCell& C = sc;
+        const int d = in.w & 0xffff;
+        if ((in.w >> 16) == 0) {
+            batch_rho_item<ORTHO>(C, in.y, in.z, d, ssm, spt);
+            // the last structure-factor item of the cell does its reduction
+            __threadfence();
+            if (threadIdx.x == 0) s_go = atomicSub(remaining + in.x, 1) == 1;
+            __syncthreads();
+            if (s_go) {
+                __threadfence();
+                batch_reduce_cell(C, se);
+                __threadfence();
+                if (threadIdx.x == 0) atomicExch(ready + in.x, 1);
+            }
+            __syncthreads();
+        } else {
+            if (threadIdx.x == 0) {
+                const long long t0 = clock64();
+                int ok = 1;
+                while (atomicAdd(ready + in.x, 0) == 0) {
+                    if (*(volatile int*)err || clock64() - t0 > spin) {
+                        atomicOr(err, 1);
+                        ok = 0;
+                        break;
+                    }
+                }
+                __threadfence();
+                s_go = ok;
+            }
+            __syncthreads();
+            if (s_go) batch_j_item<ORTHO>(C, in.y, in.z, d, ssm);
+            __syncthreads();
+        }
+    }
+}
+
+// shared memory of the batch kernel for one cell: the larger of its two walks' (one-kernel shapes)
+size_t batch_cell_smem(const ftcj_plan* P) { return std::max(rho_smem(P, 0), j_smem(P, 0)); }
+
 }  // namespace
 
 int split_xtab_entries(const ftcj_plan* P) { return use_xtab(P) ? xtab_entries(P) : 0; }
@@ -925,5 +1130,161 @@ int launch_j_walk_grad_split(ftcj_plan* P, int ndens, const double* W, cudaStrea
     }
     return FTCJ_OK;
 }
+
+
+// ---- the batch kernel's host side -----------------------------------------
+
+struct BatchWalks {
+    BatchCell* d_cells = nullptr;
+    int4* d_items = nullptr;
+    int* d_remaining0 = nullptr;  // structure-factor items per cell
+    int* d_state = nullptr;       // queue counter, error word, [ncell] remaining, [ncell] ready
+    int ncell = 0, nrho = 0, nitems = 0, grid = 0;
+    bool ortho = false;
+    size_t smem = 0;
+};
+
+void batch_walks_destroy(BatchWalks* bw) {
+    if (!bw) return;
+    void* ptrs[] = {bw->d_cells, bw->d_items, bw->d_remaining0, bw->d_state};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete bw;
+}
+
+int batch_walks_create(const std::vector<ftcj_plan*>& plans, BatchWalks** out) {
+    *out = nullptr;
+    const int n = (int)plans.size();
+    std::vector<BatchCell> cells(n);
+    struct It {
+        int4 v;
+        double cost, key;
+    };
+    std::vector<It> rho, jit;
+    std::vector<int> rem(n, 0);
+    size_t smem = 0;
+    const bool ortho = n > 0 && use_xtab(plans[0]);
+    for (int c = 0; c < n; ++c) {
+        const ftcj_plan* P = plans[c];
+        if (use_xtab(P) != ortho)
+            return fail(FTCJ_EUNSUPPORTED, "a persistent batch takes cells that all walk with the X(n1) table "
+                                           "(orthorhombic) or all without it");
+        if (P->precision != FTCJ_PREC_SPLIT || P->d_rec_gcut || P->tc)
+            return fail(FTCJ_EUNSUPPORTED, "the persistent batch runs the double-float walks over whole spheres "
+                                           "(split precision, no per-pair cutoffs, walk contraction)");
+        BatchCell& C = cells[c];
+        C.tiles = P->d_tiles;
+        C.sched = P->d_sched;
+        C.npb = P->npb;
+        C.nchunks = (int)P->chunks.size();
+        C.nx = use_xtab(P) ? xtab_entries(P) : 0;
+        C.ndens = P->max_dens;
+        C.lay = make_layout(P);
+        C.Dp = reinterpret_cast<const float2*>(P->d_Dp);
+        C.cst = reinterpret_cast<const SConst*>(P->d_split_const);
+        C.init = reinterpret_cast<const SState*>(P->d_split_init);
+        C.npairs = P->npairs;
+        C.lines = P->d_lines;
+        C.chunks = P->d_chunks;
+        C.rho_part = reinterpret_cast<double2*>(P->d_rho_part);
+        C.vg = P->d_vg;
+        C.W = reinterpret_cast<double2*>(P->d_W);
+        C.EJ = P->d_EJ_stage;
+        C.Jp = P->d_Jp;
+        C.ng_half = P->ng_half;
+        smem = std::max(smem, batch_cell_smem(P));
+        if (P->ng_half == 0 || P->tiles.empty()) continue;  // no work: W and J' stay zero (below)
+        // per-tile cost, the walks' constants (38L + 100 per point)
+        auto tcost = [&](int t) { return (double)P->tiles[t].count * (38.0 * P->tiles[t].cls + 100.0); };
+        for (int b = 0; b < P->npb; ++b) {
+            double bc = 0.0;
+            for (int j = P->rho_sched[b]; j < P->rho_sched[b + 1]; ++j) bc += tcost(P->rho_sched[P->npb + 1 + j]);
+            for (int ch = 0; ch < C.nchunks; ++ch)
+                for (int d = 0; d < C.ndens; ++d) {
+                    rho.push_back({make_int4(c, b, ch, d), bc * (P->chunks[ch].p1 - P->chunks[ch].p0), 0.0});
+                    ++rem[c];
+                }
+        }
+        for (int t = 0; t < (int)P->tiles.size(); ++t)
+            for (int ch = 0; ch < C.nchunks; ++ch)
+                for (int d = 0; d < C.ndens; ++d)
+                    jit.push_back({make_int4(c, t, ch, d), tcost(t) * (P->chunks[ch].p1 - P->chunks[ch].p0), 0.0});
+    }
+    // The queue: every structure-factor item first, largest first (the grid stays busy to the end of
+    // that phase); then the back-contraction items, by the queue position of their cell's last
+    // structure-factor item (the order in which the cells become ready), largest first within a cell.
+    // Every structure-factor item precedes every back-contraction item, and items are taken in queue
+    // order by CTAs that wait on nothing else, so a waiting item's cell is being finished.
+    std::stable_sort(rho.begin(), rho.end(), [](const It& a, const It& b) { return a.cost > b.cost; });
+    std::vector<double> last(n, 0.0);
+    for (size_t i = 0; i < rho.size(); ++i) last[rho[i].v.x] = (double)i;
+    for (It& x : jit) x.key = last[x.v.x];
+    std::stable_sort(jit.begin(), jit.end(), [](const It& a, const It& b) {
+        return a.key != b.key ? a.key < b.key : a.cost > b.cost;
+    });
+    std::vector<int4> items;
+    for (const It& x : rho) items.push_back(x.v);
+    for (const It& x : jit) items.push_back(make_int4(x.v.x, x.v.y, x.v.z, x.v.w | (1 << 16)));
+    BatchWalks* bw = new (std::nothrow) BatchWalks();
+    if (!bw) return fail(FTCJ_ENOMEM, "host allocation failed");
+    bw->ncell = n;
+    bw->nrho = (int)rho.size();
+    bw->nitems = (int)items.size();
+    bw->smem = smem;
+    bw->ortho = ortho;
+    const void* kern = ortho ? (const void*)k_batch_walks<true> : (const void*)k_batch_walks<false>;
+    cudaError_t e = cudaMalloc(&bw->d_cells, sizeof(BatchCell) * std::max(n, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&bw->d_items, sizeof(int4) * std::max<size_t>(items.size(), 1));
+    if (e == cudaSuccess) e = cudaMalloc(&bw->d_remaining0, sizeof(int) * std::max(n, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&bw->d_state, sizeof(int) * (2 + 2 * (size_t)std::max(n, 1)));
+    if (e == cudaSuccess) e = cudaMemcpy(bw->d_cells, cells.data(), sizeof(BatchCell) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !items.empty())
+        e = cudaMemcpy(bw->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(bw->d_remaining0, rem.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
+    int rc = e == cudaSuccess ? FTCJ_OK : cuda_fail(e, "batch work queue");
+    if (!rc) rc = allow_dynamic_smem(kern, smem);
+    int per_sm = 0;
+    if (!rc) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTile, smem);
+        if (e != cudaSuccess) rc = cuda_fail(e, "batch kernel occupancy");
+        else if (per_sm < 1) rc = fail(FTCJ_EUNSUPPORTED, "the batch's walks do not fit one SM");
+    }
+    if (rc) {
+        batch_walks_destroy(bw);
+        return rc;
+    }
+    bw->grid = std::max(1, std::min(bw->nitems, per_sm * plans[0]->num_sms));
+    *out = bw;
+    return FTCJ_OK;
+}
+
+int batch_walks_launch(BatchWalks* bw, const std::vector<ftcj_plan*>& plans, long long spin, cudaStream_t s) {
+    const int n = bw->ncell;
+    FTCJ_CUDA(cudaMemsetAsync(bw->d_state, 0, sizeof(int) * (2 + 2 * (size_t)n), s));
+    FTCJ_CUDA(cudaMemcpyAsync(bw->d_state + 2, bw->d_remaining0, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+    // cells without work: their potential, energy and J' are zero
+    for (ftcj_plan* P : plans)
+        if (P->ng_half == 0 || P->tiles.empty()) {
+            FTCJ_CUDA(cudaMemsetAsync(P->d_EJ_stage, 0, sizeof(double) * P->max_dens, s));
+            FTCJ_CUDA(cudaMemsetAsync(P->d_Jp, 0,
+                                      sizeof(double) * (size_t)P->max_dens * std::max<size_t>(P->chunks.size(), 1) *
+                                          P->total_terms,
+                                      s));
+        }
+    if (bw->nitems == 0) return FTCJ_OK;
+    auto kern = bw->ortho ? k_batch_walks<true> : k_batch_walks<false>;
+    kern<<<(unsigned)bw->grid, kTile, bw->smem, s>>>(bw->d_cells, bw->d_items, bw->nitems, bw->d_state,
+                                                     bw->d_state + 2, bw->d_state + 2 + n, bw->d_state + 1, spin);
+    FTCJ_CUDA(cudaGetLastError());
+    return FTCJ_OK;
+}
+
+int batch_walks_error(BatchWalks* bw, int* word, cudaStream_t s) {
+    FTCJ_CUDA(cudaMemcpyAsync(word, bw->d_state + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FTCJ_CUDA(cudaStreamSynchronize(s));
+    return FTCJ_OK;
+}
+
+int batch_walks_launches(const BatchWalks* bw) { return bw->nitems ? 1 : 0; }
 
 }  // namespace ftcj

@@ -69,13 +69,14 @@ EXPORTED = [
     "ftcj_profile_enable", "ftcj_profile_read", "ftcj_launches_per_batch", "ftcj_probe_fma_peak",
     "ftcj_potential_noalloc", "ftcj_batch_create", "ftcj_batch_info", "ftcj_batch_jbuild", "ftcj_batch_capture",
     "ftcj_batch_replay", "ftcj_batch_destroy", "ftcj_autotune", "ftcj_grad", "ftcj_shard_bounds",
-    "ftcj_plan_status",
+    "ftcj_plan_status", "ftcj_batch_set_wait", "ftcj_batch_status",
 ]
 
 FTCJ_CONTRACT_WALK = 0
 FTCJ_CONTRACT_TC = 1
 
 FTCJ_BATCH_AUTOTUNE = 1
+FTCJ_BATCH_PERSISTENT = 2
 
 FTCJ_NOALLOC_MAX_PARTIALS = 16384
 
@@ -132,6 +133,8 @@ def _declare(L):
     L.ftcj_batch_jbuild.argtypes = [P, _ip, VPP, VPP, VPP, P]
     L.ftcj_batch_capture.argtypes = [P, _ip, VPP, VPP, VPP, P]
     L.ftcj_batch_replay.argtypes = [P, P]
+    L.ftcj_batch_set_wait.argtypes = [P, _c_int]
+    L.ftcj_batch_status.argtypes = [P, _ip, P]
     L.ftcj_batch_destroy.argtypes = [P]
     L.ftcj_batch_destroy.restype = None
     L.ftcj_autotune.argtypes = [ctypes.POINTER(Cell), ctypes.POINTER(BasisDesc), _ip, ctypes.POINTER(Params),
@@ -228,7 +231,7 @@ class Batch:
     """Independent cells built together (ftcj_batch_*), optionally autotuned,
     optionally captured into one CUDA graph and replayed."""
 
-    def __init__(self, workloads, precision=FTCJ_PREC_FP64, autotune=False):
+    def __init__(self, workloads, precision=FTCJ_PREC_FP64, autotune=False, persistent=False):
         L = lib()
         self._keep = []
         n = len(workloads)
@@ -245,8 +248,8 @@ class Batch:
                 km[3 * i + j] = int(w.kmesh[j])
         self._keep += [cells, bases, prms, km]
         h = _c_void_p()
-        _check(L.ftcj_batch_create(n, cells, bases, km, prms, FTCJ_BATCH_AUTOTUNE if autotune else 0,
-                                   ctypes.byref(h)), "ftcj_batch_create")
+        flags = (FTCJ_BATCH_AUTOTUNE if autotune else 0) | (FTCJ_BATCH_PERSISTENT if persistent else 0)
+        _check(L.ftcj_batch_create(n, cells, bases, km, prms, flags, ctypes.byref(h)), "ftcj_batch_create")
         self._h = h
         self.n = n
         self.infos = []
@@ -292,6 +295,16 @@ class Batch:
 
     def replay(self, stream=None):
         _check(lib().ftcj_batch_replay(self._h, _stream_ptr(stream)), "ftcj_batch_replay")
+
+    def set_wait(self, wait_log2: int):
+        """Wait budget of the persistent launch's back-contraction items (ftcj_batch_set_wait)."""
+        _check(lib().ftcj_batch_set_wait(self._h, int(wait_log2)), "ftcj_batch_set_wait")
+
+    def status(self, stream=None) -> int:
+        """Error word of the last persistent launch; raises FtcjError (FTCJ_ETIMEOUT) when a wait gave up."""
+        w = _c_int(0)
+        _check(lib().ftcj_batch_status(self._h, ctypes.byref(w), _stream_ptr(stream)), "ftcj_batch_status")
+        return int(w.value)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

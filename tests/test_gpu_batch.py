@@ -133,3 +133,84 @@ def test_autotune_picks_a_valid_shape(orc, F):
     torch.cuda.synchronize()
     assert np.abs(J2[0].cpu().numpy() - ref["Jk"]).max() <= SPLIT_TOL
     B.close()
+
+
+def test_persistent_batch_against_oracle_and_graph_replay(orc, F):
+    """The persistent batch: the walks, potentials and energies of all cells in
+    one launch over a shared work queue, against the oracle per cell, against
+    the stream-per-cell batch, and captured into a graph and replayed."""
+    import torch
+    cells = batch_cells()
+    P = F.Batch(cells, precision=F.FTCJ_PREC_SPLIT, persistent=True)
+    S = F.Batch(cells, precision=F.FTCJ_PREC_SPLIT)
+    try:
+        Dks = [dk(w) for w in cells]
+        Jks, EJs = P.jbuild(Dks)
+        Jss, Ess = S.jbuild(Dks)
+        torch.cuda.synchronize()
+        assert P.status() == 0
+        refs = [orc.lrj(w, want_j0n=False) for w in cells]
+        worst = 0.0
+        for w, J, E, Js, Es, r in zip(cells, Jks, EJs, Jss, Ess, refs):
+            d = float(np.abs(J.cpu().numpy() - r["Jk"]).max())
+            worst = max(worst, d)
+            assert d <= SPLIT_TOL, w.name
+            assert d <= 1e-11, (w.name, d)
+            assert np.abs(E.cpu().numpy() - r["EJ"]).max() <= SPLIT_TOL * max(1.0, abs(r["EJ"][0])), w.name
+            # the same walks: only the order of the rho-row and energy sums differs
+            assert float((J - Js).abs().max()) <= 1e-12 * max(1.0, float(Js.abs().max())), w.name
+            assert float((E - Es).abs().max()) <= 1e-12 * max(1.0, float(Es.abs().max())), w.name
+        print(f"persistent batch: max|dJ| vs oracle over {len(cells)} cells {worst:.3e}")
+        s = torch.cuda.Stream()
+        Jg, Eg = P.outputs_like(Dks)
+        torch.cuda.synchronize()
+        P.capture(Dks, Jg, Eg, stream=s)
+        for _ in range(2):
+            for J in Jg:
+                J.zero_()
+            torch.cuda.synchronize()
+            P.replay(stream=s)
+            s.synchronize()
+            assert P.status(stream=s) == 0
+            # the energies are fixed-order sums; J^{0n} is scattered with FP64 atomics by the J -> AO map
+            for J, E, J0, E0 in zip(Jg, Eg, Jks, EJs):
+                assert float((J - J0).abs().max()) <= 1e-12 * max(1.0, float(J0.abs().max()))
+                assert float((E - E0).abs().max()) == 0.0
+        # only max_dens densities per cell, only split walks without cutoffs
+        with pytest.raises(F.FtcjError, match="max_dens"):
+            P.jbuild([D[:0] if D.shape[0] > 1 else torch.cat([D, D]) for D in Dks])
+        with pytest.raises(F.FtcjError, match="persistent batch"):
+            F.Batch(cells[:2], precision=F.FTCJ_PREC_FP64, persistent=True)
+    finally:
+        P.close()
+        S.close()
+
+
+def test_persistent_batch_wait_gives_up_and_reports(orc, F):
+    """A back-contraction item whose cell's potential is not ready within the
+    budget (here 2 clock cycles) raises the batch's error word and skips its
+    work: the launch ends, the status call returns FTCJ_ETIMEOUT, and the next
+    launch with the default budget matches the oracle.  Two small orthorhombic
+    cells give fewer structure-factor items than the grid has CTAs, so
+    back-contraction items are taken while those items still run and their
+    waits run out."""
+    import torch
+    cells = [W.tiny(seed=61), W.tiny(seed=62, kmesh=(2, 1, 1), ndens=2)]
+    B = F.Batch(cells, precision=F.FTCJ_PREC_SPLIT, persistent=True)
+    try:
+        Dks = [dk(w) for w in cells]
+        B.set_wait(1)
+        B.jbuild(Dks)
+        torch.cuda.synchronize()
+        with pytest.raises(F.FtcjError, match="timed out|gave up"):
+            B.status()
+        B.set_wait(0)
+        Jks, EJs = B.jbuild(Dks)
+        torch.cuda.synchronize()
+        assert B.status() == 0
+        for w, J, E in zip(cells, Jks, EJs):
+            r = orc.lrj(w, want_j0n=False)
+            assert np.abs(J.cpu().numpy() - r["Jk"]).max() <= SPLIT_TOL, w.name
+            assert np.abs(E.cpu().numpy() - r["EJ"]).max() <= SPLIT_TOL, w.name
+    finally:
+        B.close()
