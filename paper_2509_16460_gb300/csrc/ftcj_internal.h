@@ -239,6 +239,8 @@ struct ftcj_plan {
     float* d_tc_cl = nullptr;    // [npairs]
     int* d_tc_err = nullptr;     // device error word of the bounded waits
     int* d_tc_pos = nullptr;     // [npairs]: position of each record in its class's K order
+    int* d_tc_ebw = nullptr;     // [nwin][128]: the windows' column scales, per build
+    float* d_tc_clw = nullptr;   // [nwin]: the windows' smallest widths
     long long tc_dp_base[ftcj::kNclass] = {}, tc_dp_stride[ftcj::kNclass] = {}, tc_dp_total = 0;
     // tensor-core form of the back-contraction (tc.cu); false: the split walk runs it
     bool tc_j = false;

@@ -303,7 +303,8 @@ void free_device(ftcj_plan* P) {
                     P->d_Jk_stage, P->d_EJ_stage, P->d_check, P->d_split_init, P->d_split_const, P->d_Jg,
                     P->d_maps, P->d_map_off, P->d_sched, P->d_rec_gcut, P->d_tc_rows, P->d_tc_map,
                     P->d_tc_kappa, P->d_tc_tab, P->d_tc_cl, P->d_tc_err, P->d_tc_wpairs, P->d_tc_winfo,
-                    P->d_tc_pos, P->d_tc_jitems, P->d_tc_jpairs, P->d_tc_vs, P->d_tc_ev};
+                    P->d_tc_pos, P->d_tc_jitems, P->d_tc_jpairs, P->d_tc_vs, P->d_tc_ev,
+                    P->d_tc_ebw, P->d_tc_clw};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (P->ev_fork) cudaEventDestroy(P->ev_fork);

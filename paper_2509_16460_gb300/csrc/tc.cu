@@ -110,6 +110,8 @@ struct TcArgs {
     int nwin, win_per_group, ngroups;
     int nrows;
     long long spin;      // clock cycles a wait between roles may take before it gives up
+    int* ebw;            // [nwin][kTcEbMax]: column scales of each window (k_tc_rho_bounds)
+    float* clw;          // [nwin]: smallest c log2(e) of each window's records
 };
 
 // ---- PTX wrappers -----------------------------------------------------------
@@ -420,6 +422,62 @@ constexpr int kTcThreadsAll = kTcWarps * 32;
 constexpr int kTcTasksMax = 3;        // operand tasks per thread and stage: (512 + 4 G npo) / 448 <= 3
 constexpr int kTcTaskA = 1 << 20;     // task flag: an A task (row | group << 7), else a B task
 
+// Per window (one block each), once per build and density group: the
+// window's smallest width c (every row of A gets the scale exp(-c_min Q))
+// and the column scales of B, |B_ij| <= exp(-c Mcc n^2) sum_k |D'_ijk| n^k,
+// maximised over the window's records, per (block, n_c, density).
+__global__ void __launch_bounds__(256) k_tc_rho_bounds(TcArgs g) {
+    __shared__ int eB[kTcEbMax];
+    __shared__ int tidx[kTcGmax][5];
+    __shared__ int clmin_bits;
+    const int w = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+    const int4 wi = __ldg(g.winfo + w);
+    const int L = wi.x, npair = wi.y, npo = g.nd * g.ncols;
+    for (int i = tid; i < kTcEbMax; i += blockDim.x) eB[i] = -100;
+    if (tid == 0) {
+        for (int b = 0; b < npair; ++b) {
+            const int pr = __ldg(g.wpairs + wi.z + b), i = pr & 7, j = pr >> 3;
+            for (int kk = 0; kk < 5; ++kk) tidx[b][kk] = kk <= L - i - j ? term_of(g, i, j, kk) : -1;
+        }
+        clmin_bits = __float_as_int(INFINITY);
+    }
+    __syncthreads();
+    const long long cnt = g.dp_stride[L];
+    const float2* dpL = g.Dp + g.dp_base[L];
+    float cmin = INFINITY;
+    for (int k = tid; k < kTcWin; k += blockDim.x) {  // warp-uniform trip count (512 / 256)
+        const int r = __ldg(g.wrec + (size_t)w * kTcWin + k);
+        const float cr = r >= 0 ? __ldg(g.cl + r) : 0.f;
+        if (r >= 0) cmin = fminf(cmin, cr);
+        const long long loc = wi.w + k;
+        for (int gb = 0; gb < npair; ++gb) {
+            for (int d = 0; d < g.nd; ++d) {
+                float cm[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+                if (r >= 0) {
+                    const float2* dp = dpL + (long long)(g.d0 + d) * g.dp_total + loc;
+#pragma unroll
+                    for (int kk = 0; kk < 5; ++kk) {
+                        const int t = tidx[gb][kk];
+                        if (t >= 0) cm[kk] = fabsf(__ldg(dp + (long long)t * cnt).x) * 1.0001f;
+                    }
+                }
+                for (int nc = 0; nc < g.ncols; ++nc) {
+                    const float x = (float)nc;
+                    const float sv = cm[0] + x * (cm[1] + x * (cm[2] + x * (cm[3] + x * cm[4])));
+                    int eb = r >= 0 && sv > 0.f ? exp_bound(log2f(sv) - cr * g.Mcc * x * x) : -100;
+                    eb = __reduce_max_sync(0xffffffffu, eb);  // warp maximum, one shared atomic per warp
+                    if (lane == 0) atomicMax(&eB[gb * npo + nc * g.nd + d], eb);
+                }
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
+    if (lane == 0 && cmin < INFINITY) atomicMin(&clmin_bits, __float_as_int(cmin));
+    __syncthreads();
+    for (int i = tid; i < kTcEbMax; i += blockDim.x) g.ebw[(size_t)w * kTcEbMax + i] = eB[i];
+    if (tid == 0) g.clw[w] = __int_as_float(clmin_bits);
+}
+
 __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslots) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     unsigned char* abuf = tsm;                                                    // [nbuf][S][8192]
@@ -519,7 +577,7 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslo
     for (int w = w0; w < w1 && ok; ++w) {
         // ---- window records, blocks and scales ----
         for (int i = tid; i < kTcWin; i += kTcThreadsAll) sm.rec[i] = __ldg(g.wrec + (size_t)w * kTcWin + i);
-        for (int i = tid; i < kTcEbMax; i += kTcThreadsAll) sm.eB[i] = -100;
+        for (int i = tid; i < kTcEbMax; i += kTcThreadsAll) sm.eB[i] = __ldg(g.ebw + (size_t)w * kTcEbMax + i);
         if (tid == 0) {
             const int4 wi = __ldg(g.winfo + w);
             sm.winL = wi.x;
@@ -530,54 +588,10 @@ __global__ void __launch_bounds__(kTcThreadsAll, 1) k_tc_rho(TcArgs g, int ntslo
                 sm.pairs[b] = pr;
                 for (int kk = 0; kk < 5; ++kk) sm.tidx[b][kk] = kk <= wi.x - i - j ? term_of(g, i, j, kk) : -1;
             }
-            sm.clmin_bits = __float_as_int(INFINITY);
+            sm.clmin_bits = __float_as_int(__ldg(g.clw + w));
         }
         if (!(ok = prod_sync(&sm.psync, ph, abort_flag, lane, g.spin))) break;
         const int L = sm.winL, npair = sm.wnpair;
-        if (!load_warp) {
-            // A: |X Y| = exp(-c Q) <= exp(-c_min Q): the window's smallest width gives every row's scale
-            float cmin = INFINITY;
-            for (int k = tid; k < kTcWin; k += kTcEpiThreads) {
-                const int r = sm.rec[k];
-                if (r >= 0) cmin = fminf(cmin, __ldg(g.cl + r));
-            }
-            cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, 16));
-            cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, 8));
-            cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, 4));
-            cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, 2));
-            cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, 1));
-            if (lane == 0 && cmin < INFINITY) atomicMin(&sm.clmin_bits, __float_as_int(cmin));
-            // B: |B_ij| <= exp(-c Mcc n^2) sum_k |D'_ijk| n^k, per (block, n_c, density) over the window
-            // (warp-uniform trip counts: 512 = 384 + 128)
-            const long long cnt = g.dp_stride[L];
-            const float2* dpL = g.Dp + g.dp_base[L];
-            for (int k = tid; k < kTcWin; k += kTcEpiThreads) {
-                const int r = sm.rec[k];
-                const float cr = r >= 0 ? __ldg(g.cl + r) : 0.f;
-                const long long loc = sm.wpos + k;
-                for (int gb = 0; gb < npair; ++gb) {
-                    for (int d = 0; d < g.nd; ++d) {
-                        float cm[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-                        if (r >= 0) {
-                            const float2* dp = dpL + (long long)(g.d0 + d) * g.dp_total + loc;
-#pragma unroll
-                            for (int kk = 0; kk < 5; ++kk) {
-                                const int t = sm.tidx[gb][kk];
-                                if (t >= 0) cm[kk] = fabsf(__ldg(dp + (long long)t * cnt).x) * 1.0001f;
-                            }
-                        }
-                        for (int nc = 0; nc < g.ncols; ++nc) {
-                            const float x = (float)nc;
-                            const float sv = cm[0] + x * (cm[1] + x * (cm[2] + x * (cm[3] + x * cm[4])));
-                            int eb = r >= 0 && sv > 0.f ? exp_bound(log2f(sv) - cr * g.Mcc * x * x) : -100;
-                            eb = __reduce_max_sync(0xffffffffu, eb);  // warp maximum, one shared atomic per warp
-                            if (lane == 0) atomicMax(&sm.eB[gb * npo + nc * g.nd + d], eb);
-                        }
-                    }
-                }
-            }
-        }
-        if (!(ok = prod_sync(&sm.psync, ph, abort_flag, lane, g.spin))) break;
         const float clmin = __int_as_float(sm.clmin_bits);
         // ---- stages ----
         if (load_warp) {
@@ -1565,6 +1579,8 @@ int setup_tc(ftcj_plan* P) {
     int4* winfo_dev = nullptr;
     if ((rc = tc_upload(P, &winfo_dev, winfo))) return rc;
     P->d_tc_winfo = winfo_dev;
+    if ((rc = tc_upload(P, &P->d_tc_ebw, std::vector<int>((size_t)P->tc_nwin * kTcEbMax, -100)))) return rc;
+    if ((rc = tc_upload(P, &P->d_tc_clw, std::vector<float>((size_t)P->tc_nwin, 0.f)))) return rc;
     if ((rc = allow_dynamic_smem((const void*)k_tc_rho, tc_smem_bytes(P->tc_npad, tabw, P->tc_G, P->tc_nd, P->tc_tslots))))
         return rc;
     return setup_tc_j(P);
@@ -1608,6 +1624,8 @@ int launch_tc_rho(ftcj_plan* P, int ndens, cudaStream_t s) {
     g.ngroups = P->tc_ngroups;
     g.nrows = P->tc_rows;
     g.spin = tc_spin(P);
+    g.ebw = P->d_tc_ebw;
+    g.clw = P->d_tc_clw;
     const size_t smem = tc_smem_bytes(P->tc_npad, P->tc_tabw, P->tc_G, P->tc_nd, P->tc_tslots);
     for (int d0 = 0; d0 < ndens; d0 += P->tc_nd) {
         g.d0 = d0;
@@ -1617,13 +1635,15 @@ int launch_tc_rho(ftcj_plan* P, int ndens, cudaStream_t s) {
         // the plan's block count G is kept; a smaller last density group only narrows each block
         g.colw = colw;
         g.npad = round_up(P->tc_G * colw, 16);
+        k_tc_rho_bounds<<<(unsigned)P->tc_nwin, 256, 0, s>>>(g);
+        FTCJ_CUDA(cudaGetLastError());
         k_tc_rho<<<dim3((unsigned)P->tc_ngroups, (unsigned)P->tc_mtiles), kTcThreadsAll, smem, s>>>(g, P->tc_tslots);
         FTCJ_CUDA(cudaGetLastError());
     }
     return FTCJ_OK;
 }
 
-int tc_rho_launches(const ftcj_plan* P, int nd) { return (nd + P->tc_nd - 1) / P->tc_nd; }
+int tc_rho_launches(const ftcj_plan* P, int nd) { return 2 * ((nd + P->tc_nd - 1) / P->tc_nd); }
 
 // Plan-time set-up of the tensor-core back-contraction: densities per
 // launch, (i, j) blocks per work item, the items and the V_ij tile buffer.
