@@ -169,6 +169,11 @@ typedef struct {
                                  rows fit one exact accumulation (<= 672 rows of (n_a, n_b)), else
                                  FTCJ_CONTRACT_WALK */
     int64_t tc_j_mma_flops;   /* the same count for one tensor-core back-contraction; 0 for the walk */
+    int tc_column_axis;       /* tensor-core form: the lattice axis of the columns (n_c), 0..2 */
+    int tc_rows;              /* its rows (n_a, n_b) and row tiles of 128 */
+    int tc_row_tiles;
+    int tc_blocks_per_window; /* (i, j) blocks side by side in one structure-factor window */
+    int tc_dens_per_launch;   /* densities per structure-factor launch */
 } ftcj_info;
 
 typedef struct ftcj_plan ftcj_plan;

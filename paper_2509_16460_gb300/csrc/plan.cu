@@ -646,6 +646,13 @@ int ftcj_plan_info(const ftcj_plan* P, ftcj_info* o) {
     o->tc_mma_flops = P->tc ? P->tc_mma_flops : 0;
     o->j_contraction = P->tc_j ? FTCJ_CONTRACT_TC : FTCJ_CONTRACT_WALK;
     o->tc_j_mma_flops = P->tc_j ? P->tc_j_mma_flops : 0;
+    if (P->tc) {
+        o->tc_column_axis = P->tc_axis[2];
+        o->tc_rows = P->tc_rows;
+        o->tc_row_tiles = P->tc_mtiles;
+        o->tc_blocks_per_window = P->tc_G;
+        o->tc_dens_per_launch = P->tc_nd;
+    }
     return FTCJ_OK;
 }
 

@@ -54,7 +54,9 @@ class Info(ctypes.Structure):
                 ("rho_blocks", _c_int), ("n1_table", _c_int), ("pair_g_units_screened", ctypes.c_int64),
                 ("pair_g_units_walked", ctypes.c_int64), ("n_abs_max", _c_int), ("grad_split", _c_int),
                 ("rho_walk_launches", _c_int), ("j_walk_launches", _c_int), ("contraction", _c_int),
-                ("tc_mma_flops", ctypes.c_int64), ("j_contraction", _c_int), ("tc_j_mma_flops", ctypes.c_int64)]
+                ("tc_mma_flops", ctypes.c_int64), ("j_contraction", _c_int), ("tc_j_mma_flops", ctypes.c_int64),
+                ("tc_column_axis", _c_int), ("tc_rows", _c_int), ("tc_row_tiles", _c_int),
+                ("tc_blocks_per_window", _c_int), ("tc_dens_per_launch", _c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
