@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary diamond line and the batch and slab legs")
-    ap.add_argument("--forms", default="split_tc,split,fp64,split_pair_gcut",
+    ap.add_argument("--forms", default="split_tc,split,fp64,split_pair_gcut,fp64_pair_gcut",
                     help="comma list of the headline forms to time (split is always timed)")
     ap.add_argument("--leg", choices=["batch", "molecular_crystal", "slab", "diamond"], default=None,
                     help="run only this extra workload (one GPU, rank 0) and print its JSON; for profiling")
@@ -224,7 +224,7 @@ def make_workload(W, name):
 # form -> (pipe, per-pair cutoff eps, contraction): "split_tc" is the split form with the
 # tensor-core separable contraction of the structure-factor pass (orthorhombic cells)
 FORMS = {"split_tc": ("split", 0.0, 1), "split": ("split", 0.0, 0), "fp64": ("fp64", 0.0, 0),
-         "split_pair_gcut": ("split", PAIR_GCUT_EPS, 0)}
+         "split_pair_gcut": ("split", PAIR_GCUT_EPS, 0), "fp64_pair_gcut": ("fp64", PAIR_GCUT_EPS, 0)}
 
 
 def measured_bf16_peak():

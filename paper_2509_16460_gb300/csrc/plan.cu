@@ -366,8 +366,6 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
         return fail(FTCJ_EINVAL, "shard_index must be in [0, shard_count)");
     P->shard_count = std::max(1, prm->shard_count);
     P->shard_index = P->shard_count > 1 ? prm->shard_index : 0;
-    if (prm->pair_gcut_eps > 0.0 && prm->precision != FTCJ_PREC_SPLIT)
-        return fail(FTCJ_EUNSUPPORTED, "per-pair G cutoffs are implemented in the split form's walks");
     if (prm->tc_wait_log2 < 0 || prm->tc_wait_log2 > 40) return fail(FTCJ_EINVAL, "tc_wait_log2 must be 0..40");
     if (prm->contraction != FTCJ_CONTRACT_WALK && prm->contraction != FTCJ_CONTRACT_TC)
         return fail(FTCJ_EINVAL, "contraction must be FTCJ_CONTRACT_WALK or FTCJ_CONTRACT_TC");

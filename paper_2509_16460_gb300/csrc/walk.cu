@@ -155,7 +155,33 @@ __device__ __forceinline__ void powers23(int n2, int n3, double pq[L + 1][L + 1]
 
 // ---- rho -----------------------------------------------------------------
 
-__device__ __forceinline__ void rho_flush(double2* buf, double2* red, double2* row, int rbase, int nvalid) {
+// Per-pair cutoffs: the tile's part of a line under its G radius, the n1
+// with qa n1^2 + 2 qb n1 + qc < R2, intersected with [lo, hi] (the same FP32
+// test as the split form's walks).
+__device__ __forceinline__ void cut_range(const WLine& ln, float R2, int& lo, int& hi) {
+    const float disc = ln.qb * ln.qb - ln.qa * (ln.qc - R2);
+    if (!(disc >= 0.f)) {
+        lo = 1;
+        hi = 0;
+        return;
+    }
+    const float x0 = -ln.qb / ln.qa, h = sqrtf(disc) / ln.qa;
+    lo = max(lo, (int)ceilf(x0 - h));
+    hi = min(hi, (int)floorf(x0 + h));
+}
+
+// index within the chunk of the point n1 = m of line ln (stored order:
+// n1 = max(lo, 0) .. hi, then min(hi, -1) .. lo)
+__device__ __forceinline__ int point_index(const WLine& ln, int p0, int m) {
+    const int f = max(ln.lo, 0);
+    if (m >= 0) return ln.pt - p0 + (m - f);
+    const int n0 = ln.hi >= f ? ln.hi - f + 1 : 0;
+    return ln.pt - p0 + n0 + (min(ln.hi, -1) - m);
+}
+
+// idx: the batch's point indices in the row (per-pair cutoffs), else consecutive from rbase
+__device__ __forceinline__ void rho_flush(double2* buf, double2* red, double2* row, const int* idx, int rbase,
+                                          int nvalid) {
     __syncthreads();
     const int tid = threadIdx.x, j = tid & 31, wv = tid >> 5;
     if (j < nvalid) {
@@ -178,15 +204,16 @@ __device__ __forceinline__ void rho_flush(double2* buf, double2* red, double2* r
             sr += v.x;
             si += v.y;
         }
-        double2 o = row[rbase + tid];
-        row[rbase + tid] = make_double2(o.x + sr, o.y + si);
+        const int r = idx ? idx[tid] : rbase + tid;
+        const double2 o = row[r];
+        row[r] = make_double2(o.x + sr, o.y + si);
     }
 }
 
-template <int L>
+template <int L, bool CUT>
 __device__ void rho_tile(const double* M6, const Tile& tl, const Layout& lay, const double* __restrict__ Dp_d,
                          const PairWalk* __restrict__ walk, const WLine* __restrict__ lines, const WChunk ch,
-                         double2* buf, double2* red, double2* row) {
+                         double2* buf, double2* red, double2* row, int* spt) {
     constexpr int NT = nterms(L);
     const int tid = threadIdx.x;
     const bool valid = tid < tl.count;
@@ -198,12 +225,14 @@ __device__ void rho_tile(const double* M6, const Tile& tl, const Layout& lay, co
     for (int t = 0; t < NT; ++t) D[t] = valid ? Dp_d[lay.base[L] + (long long)t * cnt + loc] : 0.0;
     const PairWalk w = valid ? walk[pi] : idle_walk();
     WalkState s;
-    int slot = 0;
+    int slot = 0, par = 0;
     int rbase = 0;
     for (int li = ch.l0; li < ch.l1; ++li) {
         const WLine ln = lines[li];
         state_step(w, M6, ln.op, ln.n2, ln.n3, s);
-        if (ln.lo > ln.hi) continue;
+        int lo = ln.lo, hi = ln.hi;
+        if (CUT) cut_range(ln, tl.gcut2, lo, hi);
+        if (lo > hi) continue;
         // c_i = sum_{j,k} (-i)^{i+j+k} D'_ijk n2^j n3^k
         double cr[L + 1], ci[L + 1];
         {
@@ -233,10 +262,10 @@ __device__ void rho_tile(const double* M6, const Tile& tl, const Layout& lay, co
                     }
         }
         // forward half of the line: n1 = 0, 1, ..., hi
-        if (ln.hi >= 0) {
+        if (hi >= 0) {
             double g = s.gL, r = s.rF, pr = s.phLr, pim = s.phLi, x = 0.0;
-            for (int m = 0; m <= ln.hi; ++m) {
-                if (m >= ln.lo) {
+            for (int m = 0; m <= hi; ++m) {
+                if (m >= lo) {
                     double ar = cr[L], ai = ci[L];
 #pragma unroll
                     for (int i = L - 1; i >= 0; --i) {
@@ -245,10 +274,12 @@ __device__ void rho_tile(const double* M6, const Tile& tl, const Layout& lay, co
                     }
                     const double gr = g * pr, gi = g * pim;
                     buf[slot * (kTile + 1) + tid] = make_double2(gr * ar - gi * ai, gr * ai + gi * ar);
+                    if (CUT && tid == 0) spt[par * kBatch + slot] = point_index(ln, ch.p0, m);
                     if (++slot == kBatch) {
-                        rho_flush(buf, red, row, rbase, kBatch);
+                        rho_flush(buf, red, row, CUT ? spt + par * kBatch : nullptr, rbase, kBatch);
                         rbase += kBatch;
                         slot = 0;
+                        par ^= 1;
                     }
                 }
                 g *= r;
@@ -258,11 +289,11 @@ __device__ void rho_tile(const double* M6, const Tile& tl, const Layout& lay, co
             }
         }
         // backward half: n1 = -1, -2, ..., lo
-        if (ln.lo <= -1) {
+        if (lo <= -1) {
             double g = s.gL * s.rB, r = s.rB * w.q1, pr, pim, x = -1.0;
             cmul(s.phLr, s.phLi, w.e1r, -w.e1i, pr, pim);
-            for (int m = -1; m >= ln.lo; --m) {
-                if (m <= ln.hi) {
+            for (int m = -1; m >= lo; --m) {
+                if (m <= hi) {
                     double ar = cr[L], ai = ci[L];
 #pragma unroll
                     for (int i = L - 1; i >= 0; --i) {
@@ -271,10 +302,12 @@ __device__ void rho_tile(const double* M6, const Tile& tl, const Layout& lay, co
                     }
                     const double gr = g * pr, gi = g * pim;
                     buf[slot * (kTile + 1) + tid] = make_double2(gr * ar - gi * ai, gr * ai + gi * ar);
+                    if (CUT && tid == 0) spt[par * kBatch + slot] = point_index(ln, ch.p0, m);
                     if (++slot == kBatch) {
-                        rho_flush(buf, red, row, rbase, kBatch);
+                        rho_flush(buf, red, row, CUT ? spt + par * kBatch : nullptr, rbase, kBatch);
                         rbase += kBatch;
                         slot = 0;
+                        par ^= 1;
                     }
                 }
                 g *= r;
@@ -284,10 +317,11 @@ __device__ void rho_tile(const double* M6, const Tile& tl, const Layout& lay, co
             }
         }
     }
-    if (slot > 0) rho_flush(buf, red, row, rbase, slot);
+    if (slot > 0) rho_flush(buf, red, row, CUT ? spt + par * kBatch : nullptr, rbase, slot);
     __syncthreads();
 }
 
+template <bool CUT>
 __global__ void __launch_bounds__(kTile) k_rho_walk(const Tile* __restrict__ tiles, int ntiles, Layout lay,
                                                     const double* __restrict__ Dp, const PairWalk* __restrict__ walk,
                                                     const WLine* __restrict__ lines,
@@ -295,6 +329,7 @@ __global__ void __launch_bounds__(kTile) k_rho_walk(const Tile* __restrict__ til
                                                     double2* __restrict__ rho_part, long long ng_half, CellConst cc,
                                                     const int* __restrict__ sched) {
     extern __shared__ double2 smem[];
+    __shared__ int spt[2 * kBatch];  // point indices of the current and the previous batch (per-pair cutoffs)
     const int b = blockIdx.x, cidx = blockIdx.y, d = blockIdx.z;
     const WChunk ch = chunks[cidx];
     const int npts = ch.p1 - ch.p0;
@@ -308,11 +343,11 @@ __global__ void __launch_bounds__(kTile) k_rho_walk(const Tile* __restrict__ til
     for (int j = sched[b]; j < sched[b + 1]; ++j) {
         const Tile tl = tiles[sched[npb + 1 + j]];
         switch (tl.cls) {
-            case 0: rho_tile<0>(cc.M6, tl, lay, Dp_d, walk, lines, ch, buf, red, row); break;
-            case 1: rho_tile<1>(cc.M6, tl, lay, Dp_d, walk, lines, ch, buf, red, row); break;
-            case 2: rho_tile<2>(cc.M6, tl, lay, Dp_d, walk, lines, ch, buf, red, row); break;
-            case 3: rho_tile<3>(cc.M6, tl, lay, Dp_d, walk, lines, ch, buf, red, row); break;
-            default: rho_tile<4>(cc.M6, tl, lay, Dp_d, walk, lines, ch, buf, red, row); break;
+            case 0: rho_tile<0, CUT>(cc.M6, tl, lay, Dp_d, walk, lines, ch, buf, red, row, spt); break;
+            case 1: rho_tile<1, CUT>(cc.M6, tl, lay, Dp_d, walk, lines, ch, buf, red, row, spt); break;
+            case 2: rho_tile<2, CUT>(cc.M6, tl, lay, Dp_d, walk, lines, ch, buf, red, row, spt); break;
+            case 3: rho_tile<3, CUT>(cc.M6, tl, lay, Dp_d, walk, lines, ch, buf, red, row, spt); break;
+            default: rho_tile<4, CUT>(cc.M6, tl, lay, Dp_d, walk, lines, ch, buf, red, row, spt); break;
         }
     }
     __syncthreads();
@@ -403,7 +438,7 @@ __global__ void __launch_bounds__(256) k_energy_final(const double* __restrict__
 
 // L is the polynomial degree walked (the record's class, or class + 1 for the
 // gradient); the term layout is that of the record's class tl.cls.
-template <int L>
+template <int L, bool CUT>
 __device__ void j_tile(const double* M6, const Tile& tl, const Layout& lay, const PairWalk* __restrict__ walk,
                        const WLine* __restrict__ lines, const WChunk ch, const double2* __restrict__ wsm,
                        const double* __restrict__ pw, int n1min, double* __restrict__ Jp_dc) {
@@ -421,18 +456,20 @@ __device__ void j_tile(const double* M6, const Tile& tl, const Layout& lay, cons
     for (int li = ch.l0; li < ch.l1; ++li) {
         const WLine ln = lines[li];
         state_step(w, M6, ln.op, ln.n2, ln.n3, s);
-        if (ln.lo > ln.hi) continue;
+        int lo = ln.lo, hi = ln.hi;
+        if (CUT) cut_range(ln, tl.gcut2, lo, hi);
+        if (lo > hi) continue;
         double Ar[L + 1], Ai[L + 1];
 #pragma unroll
         for (int i = 0; i <= L; ++i) {
             Ar[i] = 0.0;
             Ai[i] = 0.0;
         }
-        int q = ln.pt - ch.p0;
-        if (ln.hi >= 0) {
+        int q = point_index(ln, ch.p0, max(lo, 0));
+        if (hi >= 0) {
             double g = s.gL, r = s.rF, pr = s.phLr, pim = s.phLi;
-            for (int m = 0; m <= ln.hi; ++m) {
-                if (m >= ln.lo) {
+            for (int m = 0; m <= hi; ++m) {
+                if (m >= lo) {
                     const double2 W = wsm[q++];
                     const double gr = g * pr, gi = g * pim;
                     const double tr = gr * W.x - gi * W.y, ti = gr * W.y + gi * W.x;
@@ -450,11 +487,12 @@ __device__ void j_tile(const double* M6, const Tile& tl, const Layout& lay, cons
                 cmul(pr, pim, w.e1r, w.e1i, pr, pim);
             }
         }
-        if (ln.lo <= -1) {
+        if (lo <= -1) {
+            q = point_index(ln, ch.p0, min(hi, -1));
             double g = s.gL * s.rB, r = s.rB * w.q1, pr, pim;
             cmul(s.phLr, s.phLi, w.e1r, -w.e1i, pr, pim);
-            for (int m = -1; m >= ln.lo; --m) {
-                if (m <= ln.hi) {
+            for (int m = -1; m >= lo; --m) {
+                if (m <= hi) {
                     const double2 W = wsm[q++];
                     const double gr = g * pr, gi = g * pim;
                     const double tr = gr * W.x - gi * W.y, ti = gr * W.y + gi * W.x;
@@ -502,7 +540,7 @@ __device__ void j_tile(const double* M6, const Tile& tl, const Layout& lay, cons
 
 // EXTRA = 0: the back-contraction of degree L; EXTRA = 1: degree L + 1, the
 // sums the nuclear gradient needs (one more power of G from d/dR).
-template <int EXTRA>
+template <int EXTRA, bool CUT>
 __global__ void __launch_bounds__(kTile) k_j_walk(const Tile* __restrict__ tiles, Layout lay,
                                                   const PairWalk* __restrict__ walk, const WLine* __restrict__ lines,
                                                   const WChunk* __restrict__ chunks, int nchunks,
@@ -526,13 +564,13 @@ __global__ void __launch_bounds__(kTile) k_j_walk(const Tile* __restrict__ tiles
     const Tile tl = tiles[tix];
     double* Jp_dc = Jp + ((long long)d * nchunks + cidx) * lay.total;
     switch (tl.cls + EXTRA) {
-        case 0: j_tile<0>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
-        case 1: j_tile<1>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
-        case 2: j_tile<2>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
-        case 3: j_tile<3>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
-        case 4: j_tile<4>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
+        case 0: j_tile<0, CUT>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
+        case 1: j_tile<1, CUT>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
+        case 2: j_tile<2, CUT>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
+        case 3: j_tile<3, CUT>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
+        case 4: j_tile<4, CUT>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc); break;
         default:
-            if (EXTRA) j_tile<5>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc);
+            if (EXTRA) j_tile<5, CUT>(cc.M6, tl, lay, walk, lines, ch, wsm, pw, n1min, Jp_dc);
             break;
     }
 }
@@ -574,16 +612,18 @@ size_t j_smem_bytes(const ftcj_plan* P) {
 }  // namespace
 
 int upload_walk_tables(ftcj_plan* P) {
-    int rc = allow_dynamic_smem((const void*)k_rho_walk, rho_smem_bytes(P));
-    if (rc) return rc;
-    rc = allow_dynamic_smem((const void*)k_j_walk<0>, j_smem_bytes(P));
-    if (rc) return rc;
-    return allow_dynamic_smem((const void*)k_j_walk<1>, j_smem_bytes(P));
+    int rc = allow_dynamic_smem((const void*)k_rho_walk<false>, rho_smem_bytes(P));
+    if (!rc) rc = allow_dynamic_smem((const void*)k_rho_walk<true>, rho_smem_bytes(P));
+    if (!rc) rc = allow_dynamic_smem((const void*)k_j_walk<0, false>, j_smem_bytes(P));
+    if (!rc) rc = allow_dynamic_smem((const void*)k_j_walk<0, true>, j_smem_bytes(P));
+    if (!rc) rc = allow_dynamic_smem((const void*)k_j_walk<1, false>, j_smem_bytes(P));
+    if (!rc) rc = allow_dynamic_smem((const void*)k_j_walk<1, true>, j_smem_bytes(P));
+    return rc;
 }
 
 int rho_walk_blocks_per_sm(ftcj_plan* P, int* out) {
     int n = 0;
-    FTCJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rho_walk, kTile, rho_smem_bytes(P)));
+    FTCJ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rho_walk<false>, kTile, rho_smem_bytes(P)));
     *out = n > 0 ? n : 1;
     return FTCJ_OK;
 }
@@ -601,7 +641,8 @@ int launch_rho_walk(ftcj_plan* P, int ndens, cudaStream_t s) {
         return FTCJ_OK;
     }
     dim3 g(P->npb, (unsigned)P->chunks.size(), ndens);
-    k_rho_walk<<<g, kTile, rho_smem_bytes(P), s>>>(P->d_tiles, (int)P->tiles.size(), make_layout(P), P->d_Dp,
+    auto kern = P->d_rec_gcut ? k_rho_walk<true> : k_rho_walk<false>;
+    kern<<<g, kTile, rho_smem_bytes(P), s>>>(P->d_tiles, (int)P->tiles.size(), make_layout(P), P->d_Dp,
                                                    P->d_walk, P->d_lines, P->d_chunks, P->npb,
                                                    reinterpret_cast<double2*>(P->d_rho_part), P->ng_half, P->cc,
                                                    P->d_sched);
@@ -641,7 +682,8 @@ int launch_j_walk(ftcj_plan* P, int ndens, const double* W, cudaStream_t s) {
     }
     dim3 g((unsigned)P->tiles.size(), nch, ndens);
     int n1cnt = P->n1_max - P->n1_min + 1;
-    k_j_walk<0><<<g, kTile, j_smem_bytes(P), s>>>(P->d_tiles, make_layout(P), P->d_walk, P->d_lines, P->d_chunks, nch,
+    auto kern = P->d_rec_gcut ? k_j_walk<0, true> : k_j_walk<0, false>;
+    kern<<<g, kTile, j_smem_bytes(P), s>>>(P->d_tiles, make_layout(P), P->d_walk, P->d_lines, P->d_chunks, nch,
                                                reinterpret_cast<const double2*>(W), P->ng_half, P->n1_min, n1cnt,
                                                P->max_chunk_pts, P->d_Jp, P->cc);
     FTCJ_CUDA(cudaGetLastError());
@@ -662,7 +704,8 @@ int launch_j_walk_grad(ftcj_plan* P, int ndens, const double* W, cudaStream_t s)
     }
     dim3 g((unsigned)P->tiles.size(), nch, ndens);
     int n1cnt = P->n1_max - P->n1_min + 1;
-    k_j_walk<1><<<g, kTile, j_smem_bytes(P), s>>>(P->d_tiles, make_grad_layout(P), P->d_walk, P->d_lines,
+    auto kern = P->d_rec_gcut ? k_j_walk<1, true> : k_j_walk<1, false>;
+    kern<<<g, kTile, j_smem_bytes(P), s>>>(P->d_tiles, make_grad_layout(P), P->d_walk, P->d_lines,
                                                   P->d_chunks, nch, reinterpret_cast<const double2*>(W), P->ng_half,
                                                   P->n1_min, n1cnt, P->max_chunk_pts, P->d_Jg, P->cc);
     FTCJ_CUDA(cudaGetLastError());

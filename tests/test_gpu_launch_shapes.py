@@ -125,3 +125,23 @@ def test_class_split_multichunk_with_pair_cutoffs_against_oracle(F, case):
         assert dJ <= SPLIT_J_TOL and dE <= SPLIT_J_TOL, (dJ, dE)
     finally:
         plan.close()
+
+
+def test_fp64_form_with_pair_cutoffs_against_oracle_and_split(F, case):
+    """Per-pair G cutoffs in the FP64 walks (Sec. 2.5 screening, eps 1e-12):
+    the same radius-sorted tiles and cut lines as the split form, so the two
+    forms agree to the split form's rounding, and both differ from the
+    whole-sphere oracle only by the screened-out terms."""
+    w, ref = case
+    f64, Jf, Ef = build(F, w, precision=F.FTCJ_PREC_FP64, chunk_points=4096, pair_gcut_eps=1e-12)
+    spl, Js, Es = build(F, w, precision=F.FTCJ_PREC_SPLIT, chunk_points=4096, pair_gcut_eps=1e-12)
+    try:
+        assert f64.info["pair_g_units_walked"] == spl.info["pair_g_units_walked"] < f64.info["pair_g_units"]
+        dJ, dE = errors(Jf, Ef, ref)
+        d_forms = float(np.abs(Jf - Js).max())
+        print(f"fp64 + pair cutoffs: max|dJ| vs oracle {dJ:.3e} |dE| {dE:.3e}; vs the split form {d_forms:.3e}")
+        assert dJ <= SPLIT_J_TOL and dE <= SPLIT_J_TOL
+        assert d_forms <= MEASURED_J_BAR
+    finally:
+        f64.close()
+        spl.close()

@@ -27,7 +27,7 @@ def ragged():
     return W.tiny(seed=41, A=np.diag([3.6, 3.9, 4.1]), kmesh=(2, 2, 1), shell_spec=spec, omega=0.45, ndens=2)
 
 
-@pytest.mark.parametrize("precision,S,eps", [(0, 2, 0.0), (1, 3, 0.0), (1, 2, 1e-12)])
+@pytest.mark.parametrize("precision,S,eps", [(0, 2, 0.0), (1, 3, 0.0), (1, 2, 1e-12), (0, 2, 1e-12)])
 def test_shards_sum_to_the_whole_build(orc, F, precision, S, eps):
     import torch
     w = ragged()

@@ -79,7 +79,6 @@ CASES = [
     ("shell centre", _centre, {}, "invalid argument", "centre out of range"),
     ("precision", None, {"precision": 7}, "unsupported input", "precision"),
     ("chunk 32", None, {"chunk_points": 32}, "invalid argument", "chunk_points"),
-    ("cutoffs in FP64", None, {"pair_gcut_eps": 1e-12}, "unsupported input", "split form"),
     ("negative cutoff eps", None, {"pair_gcut_eps": -1.0, "precision": 1}, "invalid argument", "pair_gcut_eps"),
     ("contraction 2", None, {"contraction": 2, "precision": 1}, "invalid argument", "contraction"),
     ("wait budget 41", None, {"tc_wait_log2": 41, "precision": 1, "contraction": 1}, "invalid argument",
