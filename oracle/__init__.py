@@ -60,6 +60,13 @@ def _declare(L):
     L.orc_lrj.argtypes = basis + [_ip, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                   _dp, _dp, _dp, _dp, ctypes.c_long, _ip, _dp, ctypes.c_int, ctypes.c_int, _dp]
     L.orc_lrj.restype = ctypes.c_int
+    L.orc_lrj_classified.argtypes = basis + [_ip, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, ctypes.c_long,
+                                             _ip, _dp, ctypes.c_int]
+    L.orc_lrj_classified.restype = ctypes.c_int
+    L.orc_gpw_density.argtypes = basis + [_ip, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _ip, _dp,
+                                          ctypes.c_int]
+    L.orc_gpw_density.restype = ctypes.c_int
     L.orc_rho_at.argtypes = basis + [_ip, ctypes.c_double, ctypes.c_int, _dp, ctypes.c_int, _ip, _dp,
                                      ctypes.c_int]
     L.orc_rho_at.restype = ctypes.c_int
@@ -169,6 +176,59 @@ def lrj(w, Dk=None, nthreads: int = 0, pair_stride: int = 1, want_rho: bool = Tr
         raise RuntimeError(f"orc_lrj failed: {rc}")
     return dict(Jk=Jk, EJ=EJ, rho=None if rho is None else rho[:, :nG], G=G[:nG], J0n=J0n,
                 npairs=int(stats[0]), nG=int(stats[1]), units=float(stats[2]), seconds=float(stats[3]))
+
+
+def alpha_cut_of(w, alpha_cut=None) -> float:
+    """Compact/diffuse exponent boundary: given, else w^2/2 (Sec. 2.6, Eq. "cd cutoff")."""
+    return 0.5 * w.omega ** 2 if alpha_cut is None else float(alpha_cut)
+
+
+def lrj_classified(w, alpha_cut=None, Dk=None, nthreads: int = 0, want_j0n: bool = False):
+    """The build with compact/diffuse pair classes (Sec. 2.6).  Returns a dict
+    with Jk, EJ, rhoC, rhoD (full sphere, oracle order), G and optionally J0n."""
+    b = _Basis(w.A, w.xyz, w.flat_basis())
+    Dk = np.ascontiguousarray(w.Dk if Dk is None else Dk, dtype=np.complex128)
+    ndens, nk, nao = Dk.shape[0], Dk.shape[1], Dk.shape[2]
+    gc = gcut_of(w)
+    nG = int(lib().orc_gsphere(_d(b.A), gc, 0, None))
+    Jk = np.zeros((ndens, nk, nao, nao), dtype=np.complex128)
+    EJ = np.zeros(ndens)
+    rc_ = np.zeros((ndens, max(nG, 1)), dtype=np.complex128)
+    rd_ = np.zeros((ndens, max(nG, 1)), dtype=np.complex128)
+    G = np.zeros((max(nG, 1), 3), dtype=np.int32)
+    J0n = np.zeros((ndens, nk, nao, nao), dtype=np.complex128) if want_j0n else None
+    km = np.ascontiguousarray(w.kmesh, dtype=np.int32)
+    rc = lib().orc_lrj_classified(*b.args(), _i(km), float(w.omega), gc, float(w.pair_thresh),
+                                  alpha_cut_of(w, alpha_cut), int(ndens), Dk.ctypes.data_as(_dp),
+                                  Jk.ctypes.data_as(_dp), _d(EJ), rc_.ctypes.data_as(_dp), rd_.ctypes.data_as(_dp),
+                                  nG, _i(G), J0n.ctypes.data_as(_dp) if J0n is not None else None, int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"orc_lrj_classified failed: {rc}")
+    return dict(Jk=Jk, EJ=EJ, rhoC=rc_[:, :nG], rhoD=rd_[:, :nG], G=G[:nG], J0n=J0n)
+
+
+def gpw_density(w, grid, alpha_cut=None, Dk=None, nthreads: int = 0):
+    """The DD density on the grid r_m = sum_i (m_i/N_i) a_i: [ndens][N1][N2][N3] (App. E)."""
+    b = _Basis(w.A, w.xyz, w.flat_basis())
+    Dk = np.ascontiguousarray(w.Dk if Dk is None else Dk, dtype=np.complex128)
+    gr = np.ascontiguousarray(grid, dtype=np.int32)
+    out = np.zeros((Dk.shape[0], int(gr[0]), int(gr[1]), int(gr[2])))
+    km = np.ascontiguousarray(w.kmesh, dtype=np.int32)
+    rc = lib().orc_gpw_density(*b.args(), _i(km), float(w.pair_thresh), alpha_cut_of(w, alpha_cut),
+                               int(Dk.shape[0]), Dk.ctypes.data_as(_dp), _i(gr), _d(out), int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"orc_gpw_density failed: {rc}")
+    return out
+
+
+def grid_transform(A, values, G):
+    """rho(G_n) = (Omega/N) sum_m rho(r_m) e^{-i G_n . r_m} for the listed n
+    triples, by the library FFT (e^{-2 pi i n.m/N} on the grid axes)."""
+    _, vol = reciprocal(A)
+    shape = values.shape[-3:]
+    F = np.fft.fftn(values, axes=(-3, -2, -1)) * (vol / float(np.prod(shape)))
+    n = np.asarray(G, dtype=np.int64)
+    return F[..., n[:, 0] % shape[0], n[:, 1] % shape[1], n[:, 2] % shape[2]]
 
 
 def rho_at(w, n_list, nthreads: int = 0):

@@ -30,6 +30,14 @@
  *      term; long-range steps 2-3), rho(-G) taken from its own explicit sum.
  *   6. J^k = sum_L exp(+i k.R_L) J^{0L} (Eq. "FT of J").
  *   7. E_J = 1/2 sum_G v(G) rho(G) rho(-G).
+ *   8. With the densities classified (Sec. 2.6): pair densities whose two
+ *      primitives both have exponents below alpha_cut are DD; an integral
+ *      between two compact pair densities keeps v(G), every other one takes
+ *      the full-range 4 pi / (Omega G^2) (orc_lrj_classified).
+ *   9. The DD density on a uniform real-space grid of the cell, summed over
+ *      lattice images from the basis functions themselves (App. E,
+ *      orc_gpw_density); its discrete Fourier transform is the GPW route to
+ *      rho_D(G).
  *
  * Normalisation: every primitive is scaled to unit self-overlap, computed
  * here from 1D Gaussian moments.  Spherical shells use real solid harmonics
@@ -632,18 +640,32 @@ int orc_fold_density(int ndens, const int* kmesh, int nao, const double* Dk, dou
     return 0;
 }
 
-/* The whole long-range build.  Outputs (any may be NULL except Jk/EJ):
- *   Jk     complex [ndens][Nk][nao][nao]
- *   EJ     [ndens]
- *   rho    complex [ndens][nG] in the order of G_out
- *   G_out  int [nG][3]
- *   J0n    complex [ndens][Ncell][nao][nao] (J^{0L} folded into the BvK cells)
- * pair_stride > 1 processes every pair_stride-th pair only (timing samples;
- * the results are then not the build).  stats[0..3] = npairs (ordered
- * primitive-shell pairs used), nG, pair*G units per pass, wall seconds. */
-int orc_lrj(ORC_BASIS_ARGS, const int* kmesh, double omega, double gcut, double pair_thresh, int ndens,
-            const double* Dk_in, double* Jk_out, double* EJ_out, double* rho_out, long g_cap, int* G_out,
-            double* J0n_out, int pair_stride, int nthreads, double* stats)
+/* A primitive is diffuse when its exponent lies below alpha_cut (Sec. 2.6,
+ * Eq. "cd cutoff": alpha_cut = w^2/2 by default); a primitive pair density is
+ * DD when both of its primitives are diffuse and compact (CC or CD) otherwise.
+ * alpha_cut <= 0 makes every pair compact. */
+static int pair_is_dd(const OShell* ha, int ka, const OShell* hb, int kb, double alpha_cut)
+{
+    return ha->ex[ka] < alpha_cut && hb->ex[kb] < alpha_cut;
+}
+
+/* The build with classified pair densities (Sec. 2.6).  An integral between
+ * two compact pair densities takes the long-range kernel of the Ewald split,
+ * v_LR(G) = 4 pi e^{-G^2/4w^2} / (Omega G^2); every integral with a DD
+ * density on either side is taken entirely in reciprocal space with the
+ * full-range kernel v_FR(G) = 4 pi / (Omega G^2), the G = 0 term removed.
+ * With rho_C and rho_D the sums over the compact and the DD pairs:
+ *   J^{0L}_{mu nu} (compact pair) = sum_G (mu0 nuL|G) [v_LR rho_C(-G) + v_FR rho_D(-G)]
+ *   J^{0L}_{mu nu} (DD pair)      = sum_G (mu0 nuL|G) v_FR [rho_C(-G) + rho_D(-G)]
+ *   E_J = 1/2 sum_G [v_LR rho_C rho_C(-G) + v_FR (rho_C rho_D(-G) + rho_D rho_C(-G) + rho_D rho_D(-G))]
+ * (a contracted shell whose primitives straddle alpha_cut is split into its
+ * compact and diffuse parts, which the per-primitive-pair sums do by
+ * themselves).  alpha_cut <= 0 is the plain long-range build.  rho_out gets
+ * rho_C, rhoD_out (may be NULL) rho_D. */
+static int lrj_core(ORC_BASIS_ARGS, const int* kmesh, double omega, double gcut, double pair_thresh,
+                    double alpha_cut, int ndens, const double* Dk_in, double* Jk_out, double* EJ_out,
+                    double* rho_out, double* rhoD_out, long g_cap, int* G_out, double* J0n_out, int pair_stride,
+                    int nthreads, double* stats)
 {
     struct timespec t0, t1;
     clock_gettime(CLOCK_MONOTONIC, &t0);
@@ -669,11 +691,13 @@ int orc_lrj(ORC_BASIS_ARGS, const int* kmesh, double omega, double gcut, double 
     if (G_out) memcpy(G_out, gl, sizeof(int) * 3 * (size_t)(nG < g_cap ? nG : g_cap));
     double* Gc = (double*)malloc(sizeof(double) * 3 * (size_t)(nG > 0 ? nG : 1));
     double* vG = (double*)malloc(sizeof(double) * (size_t)(nG > 0 ? nG : 1));
+    double* vF = (double*)malloc(sizeof(double) * (size_t)(nG > 0 ? nG : 1));
     long* neg = (long*)malloc(sizeof(long) * (size_t)(nG > 0 ? nG : 1));
     for (long g = 0; g < nG; ++g) {
         gvec(&S, gl + 3 * g, Gc + 3 * g);
         double g2 = gnorm2(&S, gl + 3 * g);
         vG[g] = 4.0 * M_PI * exp(-g2 / (4.0 * omega * omega)) / (S.vol * g2);
+        vF[g] = 4.0 * M_PI / (S.vol * g2);
         neg[g] = -1;
     }
     /* index of -G (searched plainly) */
@@ -692,22 +716,24 @@ int orc_lrj(ORC_BASIS_ARGS, const int* kmesh, double omega, double gcut, double 
 #ifdef _OPENMP
     nthr = omp_get_max_threads();
 #endif
-    cplx* rho_t = (cplx*)calloc((size_t)nthr * ndens * (size_t)(nG > 0 ? nG : 1), sizeof(cplx));
+    /* per thread: rho_C in the first ndens * nG entries, rho_D in the next */
+    cplx* rho_t = (cplx*)calloc((size_t)nthr * 2 * ndens * (size_t)(nG > 0 ? nG : 1), sizeof(cplx));
 
-    /* --- step 1: rho(G) ---------------------------------------------------- */
+    /* --- step 1: rho_C(G) and rho_D(G) ------------------------------------- */
 #pragma omp parallel
     {
         int tid = 0;
 #ifdef _OPENMP
         tid = omp_get_thread_num();
 #endif
-        cplx* my = rho_t + (size_t)tid * ndens * nG;
         cplx blk[(2 * ORC_LMAX + 1) * (2 * ORC_LMAX + 1) + ORC_MAXC * ORC_MAXC];
 #pragma omp for schedule(static)
         for (long ip = 0; ip < npr; ++ip) {
             const OPair* q = &P[ip * pair_stride];
             const OShell* ha = &S.sh[q->sa];
             const OShell* hb = &S.sh[q->sb];
+            const int dd = pair_is_dd(ha, q->ka, hb, q->kb, alpha_cut);
+            cplx* my = rho_t + ((size_t)tid * 2 + (size_t)dd) * ndens * nG;
             const double* Ac = xyz + 3 * ha->cen;
             double Bs[3];
             for (int x = 0; x < 3; ++x)
@@ -729,8 +755,12 @@ int orc_lrj(ORC_BASIS_ARGS, const int* kmesh, double omega, double gcut, double 
         }
     }
     cplx* rho = (cplx*)calloc((size_t)ndens * (size_t)(nG > 0 ? nG : 1), sizeof(cplx));
+    cplx* rhoD = (cplx*)calloc((size_t)ndens * (size_t)(nG > 0 ? nG : 1), sizeof(cplx));
     for (int t = 0; t < nthr; ++t)
-        for (size_t e = 0; e < (size_t)ndens * nG; ++e) rho[e] += rho_t[(size_t)t * ndens * nG + e];
+        for (size_t e = 0; e < (size_t)ndens * nG; ++e) {
+            rho[e] += rho_t[((size_t)t * 2) * ndens * nG + e];
+            rhoD[e] += rho_t[((size_t)t * 2 + 1) * ndens * nG + e];
+        }
     free(rho_t);
 
     /* --- step 2-3: J^{0L} per pair, then J^k and the folded J^{0n} ---------- */
@@ -750,11 +780,13 @@ int orc_lrj(ORC_BASIS_ARGS, const int* kmesh, double omega, double gcut, double 
             for (int x = 0; x < 3; ++x)
                 Bs[x] = xyz[3 * hb->cen + x] + q->L[0] * S.A[0][x] + q->L[1] * S.A[1][x] + q->L[2] * S.A[2][x];
             int nfab = ha->nf * hb->nf;
+            const int dd = pair_is_dd(ha, q->ka, hb, q->kb, alpha_cut);
             for (long g = 0; g < nG; ++g) {
                 memset(blk, 0, sizeof(cplx) * (size_t)nfab);
                 prim_pair_ft(ha, q->ka, Ac, hb, q->kb, Bs, Gc + 3 * g, blk);
                 for (int d = 0; d < ndens; ++d) {
-                    cplx w = vG[g] * rho[(size_t)d * nG + neg[g]];
+                    const cplx rc = rho[(size_t)d * nG + neg[g]], rd = rhoD[(size_t)d * nG + neg[g]];
+                    cplx w = dd ? vF[g] * (rc + rd) : vG[g] * rc + vF[g] * rd;
                     cplx* out = Jp + ((size_t)ip * ndens + d) * bsz;
                     for (int e = 0; e < nfab; ++e) out[e] += w * blk[e];
                 }
@@ -797,10 +829,15 @@ int orc_lrj(ORC_BASIS_ARGS, const int* kmesh, double omega, double gcut, double 
     /* --- energy ----------------------------------------------------------- */
     for (int d = 0; d < ndens; ++d) {
         cplx e = 0.0;
-        for (long g = 0; g < nG; ++g) e += vG[g] * rho[(size_t)d * nG + g] * rho[(size_t)d * nG + neg[g]];
+        for (long g = 0; g < nG; ++g) {
+            const cplx c = rho[(size_t)d * nG + g], cm = rho[(size_t)d * nG + neg[g]];
+            const cplx q = rhoD[(size_t)d * nG + g], qm = rhoD[(size_t)d * nG + neg[g]];
+            e += vG[g] * c * cm + vF[g] * (c * qm + q * cm + q * qm);
+        }
         EJ_out[d] = 0.5 * creal(e);
     }
     if (rho_out) memcpy(rho_out, rho, sizeof(cplx) * (size_t)ndens * nG);
+    if (rhoD_out) memcpy(rhoD_out, rhoD, sizeof(cplx) * (size_t)ndens * nG);
 
     clock_gettime(CLOCK_MONOTONIC, &t1);
     if (stats) {
@@ -810,14 +847,43 @@ int orc_lrj(ORC_BASIS_ARGS, const int* kmesh, double omega, double gcut, double 
         stats[3] = (double)(t1.tv_sec - t0.tv_sec) + 1e-9 * (double)(t1.tv_nsec - t0.tv_nsec);
     }
     free(rho);
+    free(rhoD);
     free(P);
     free(neg);
+    free(vF);
     free(vG);
     free(Gc);
     free(gl);
     free(D0n);
     free_system(&S);
     return 0;
+}
+
+/* The whole long-range build.  Outputs (any may be NULL except Jk/EJ):
+ *   Jk     complex [ndens][Nk][nao][nao]
+ *   EJ     [ndens]
+ *   rho    complex [ndens][nG] in the order of G_out
+ *   G_out  int [nG][3]
+ *   J0n    complex [ndens][Ncell][nao][nao] (J^{0L} folded into the BvK cells)
+ * pair_stride > 1 processes every pair_stride-th pair only (timing samples;
+ * the results are then not the build).  stats[0..3] = npairs (ordered
+ * primitive-shell pairs used), nG, pair*G units per pass, wall seconds. */
+int orc_lrj(ORC_BASIS_ARGS, const int* kmesh, double omega, double gcut, double pair_thresh, int ndens,
+            const double* Dk_in, double* Jk_out, double* EJ_out, double* rho_out, long g_cap, int* G_out,
+            double* J0n_out, int pair_stride, int nthreads, double* stats)
+{
+    return lrj_core(ORC_BASIS_PASS, kmesh, omega, gcut, pair_thresh, 0.0, ndens, Dk_in, Jk_out, EJ_out, rho_out,
+                    NULL, g_cap, G_out, J0n_out, pair_stride, nthreads, stats);
+}
+
+/* The classified build (see lrj_core): rhoC_out and rhoD_out complex
+ * [ndens][nG] in the order of G_out. */
+int orc_lrj_classified(ORC_BASIS_ARGS, const int* kmesh, double omega, double gcut, double pair_thresh,
+                       double alpha_cut, int ndens, const double* Dk_in, double* Jk_out, double* EJ_out,
+                       double* rhoC_out, double* rhoD_out, long g_cap, int* G_out, double* J0n_out, int nthreads)
+{
+    return lrj_core(ORC_BASIS_PASS, kmesh, omega, gcut, pair_thresh, alpha_cut, ndens, Dk_in, Jk_out, EJ_out,
+                    rhoC_out, rhoD_out, g_cap, G_out, J0n_out, 1, nthreads, NULL);
 }
 
 /* rho at listed reciprocal vectors (n triples), full pair loop; used to check
@@ -870,6 +936,121 @@ int orc_rho_at(ORC_BASIS_ARGS, const int* kmesh, double pair_thresh, int ndens, 
             }
         }
         for (int d = 0; d < nd; ++d) rho[(size_t)d * nGs + g] = accr[d] + I * acci[d];
+    }
+    free(P);
+    free(D0n);
+    free_system(&S);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* GPW: the DD density on a real-space grid (Sec. 2.6, App. E)               */
+/* ------------------------------------------------------------------------ */
+
+/* Functions of shell h built on its primitive k (contraction coefficient and
+ * unit-self-overlap scale included) at the displacement u = r - centre. */
+static void shell_values(const OShell* h, int k, const double u[3], double* out /* [nf] */)
+{
+    double e = exp(-h->ex[k] * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+    for (int f = 0; f < h->nf; ++f) {
+        double s = 0.0;
+        for (int c = 0; c < h->nc; ++c)
+            if (h->U[f][c] != 0.0)
+                s += h->U[f][c] * ipow(u[0], h->cx[c][0]) * ipow(u[1], h->cx[c][1]) * ipow(u[2], h->cx[c][2]);
+        out[f] = h->co[k] * h->nrm[k * h->nf + f] * s * e;
+    }
+}
+
+/* The density of the DD pairs on the grid r_m = sum_i (m_i / N_i) a_i,
+ * m_i = 0..N_i-1 (App. E, Eq. "rho_shellpair"):
+ *   rho_D(r) = sum_{DD pairs (a in mu, b in nu, L)} Re D^{0[L]}_{mu nu}
+ *              sum_T chi_a(r - A - T) chi_b(r - B - R_L - T),
+ * the ordered DD pairs of the screened list, T over the lattice translations
+ * whose product Gaussian e^{-p |r - P - T|^2} exceeds e^{-50}.  D^{0n} is real
+ * for time-reversal symmetric input; its imaginary part is not used.
+ * out: double [ndens][N1][N2][N3]. */
+int orc_gpw_density(ORC_BASIS_ARGS, const int* kmesh, double pair_thresh, double alpha_cut, int ndens,
+                    const double* Dk_in, const int* grid, double* out, int nthreads)
+{
+    OSys S;
+    int rc = build_system(&S, ORC_BASIS_PASS);
+    if (rc) return rc;
+    if (grid[0] < 1 || grid[1] < 1 || grid[2] < 1) {
+        free_system(&S);
+        return -4;
+    }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    const int nao = S.nao;
+    const int nk = kmesh[0] * kmesh[1] * kmesh[2];
+    const size_t nn = (size_t)nao * nao;
+    cplx* D0n = (cplx*)malloc(sizeof(cplx) * (size_t)ndens * nk * nn);
+    fold_density(ndens, kmesh, nao, (const cplx*)Dk_in, D0n);
+    OPair* P = NULL;
+    long np_all = enumerate_pairs(&S, pair_thresh, &P);
+    long ndd = 0;
+    for (long i = 0; i < np_all; ++i)
+        if (pair_is_dd(&S.sh[P[i].sa], P[i].ka, &S.sh[P[i].sb], P[i].kb, alpha_cut)) P[ndd++] = P[i];
+    const long npts = (long)grid[0] * grid[1] * grid[2];
+    memset(out, 0, sizeof(double) * (size_t)ndens * npts);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long m = 0; m < npts; ++m) {
+        const int m1 = (int)(m / ((long)grid[1] * grid[2])), m2 = (int)((m / grid[2]) % grid[1]),
+                  m3 = (int)(m % grid[2]);
+        double r[3];
+        for (int x = 0; x < 3; ++x)
+            r[x] = (double)m1 / grid[0] * S.A[0][x] + (double)m2 / grid[1] * S.A[1][x] +
+                   (double)m3 / grid[2] * S.A[2][x];
+        double va[2 * ORC_LMAX + 1], vb[2 * ORC_LMAX + 1];
+        for (long ip = 0; ip < ndd; ++ip) {
+            const OPair* q = &P[ip];
+            const OShell* ha = &S.sh[q->sa];
+            const OShell* hb = &S.sh[q->sb];
+            const double a = ha->ex[q->ka], b = hb->ex[q->kb], p = a + b;
+            const double* Ac = xyz + 3 * ha->cen;
+            double Bs[3], Pc[3];
+            for (int x = 0; x < 3; ++x) {
+                Bs[x] = xyz[3 * hb->cen + x] + q->L[0] * S.A[0][x] + q->L[1] * S.A[1][x] + q->L[2] * S.A[2][x];
+                Pc[x] = (a * Ac[x] + b * Bs[x]) / p;
+            }
+            const int cell = (wrap(q->L[0], kmesh[0]) * kmesh[1] + wrap(q->L[1], kmesh[1])) * kmesh[2] +
+                             wrap(q->L[2], kmesh[2]);
+            const double rs = sqrt(50.0 / p);
+            int tlo[3], thi[3];
+            for (int i = 0; i < 3; ++i) {
+                /* fractional coordinate of r - P along a_i, and the reach of the radius rs */
+                double phi = 0.0;
+                for (int x = 0; x < 3; ++x) phi += S.B[i][x] * (r[x] - Pc[x]);
+                phi /= 2.0 * M_PI;
+                double reach = rs * sqrt(S.M[i][i]) / (2.0 * M_PI);
+                tlo[i] = (int)ceil(phi - reach);
+                thi[i] = (int)floor(phi + reach);
+            }
+            for (int t1 = tlo[0]; t1 <= thi[0]; ++t1)
+                for (int t2 = tlo[1]; t2 <= thi[1]; ++t2)
+                    for (int t3 = tlo[2]; t3 <= thi[2]; ++t3) {
+                        double T[3], ua[3], ub[3], up2 = 0.0;
+                        for (int x = 0; x < 3; ++x) {
+                            T[x] = t1 * S.A[0][x] + t2 * S.A[1][x] + t3 * S.A[2][x];
+                            ua[x] = r[x] - Ac[x] - T[x];
+                            ub[x] = r[x] - Bs[x] - T[x];
+                            double up = r[x] - Pc[x] - T[x];
+                            up2 += up * up;
+                        }
+                        if (p * up2 > 50.0) continue;
+                        shell_values(ha, q->ka, ua, va);
+                        shell_values(hb, q->kb, ub, vb);
+                        for (int d = 0; d < ndens; ++d) {
+                            const cplx* Dc = D0n + ((size_t)d * nk + cell) * nn;
+                            double s = 0.0;
+                            for (int fa = 0; fa < ha->nf; ++fa)
+                                for (int fb = 0; fb < hb->nf; ++fb)
+                                    s += creal(Dc[(size_t)(ha->ao0 + fa) * nao + hb->ao0 + fb]) * va[fa] * vb[fb];
+                            out[(size_t)d * npts + m] += s;
+                        }
+                    }
+        }
     }
     free(P);
     free(D0n);

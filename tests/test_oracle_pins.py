@@ -363,3 +363,119 @@ def test_oracle_gradient_matches_central_differences(orc):
     w.xyz = x0
     # translational invariance: the gradients sum to zero
     assert np.abs(g.sum(axis=1)).max() < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# density classification and the GPW route (Sec. 2.6, App. E)
+# ---------------------------------------------------------------------------
+
+def dense_gpw_grid(w, pmax, margin=2):
+    """Grid points per axis that keep every alias of a DD transform (exponent
+    at most pmax) beyond e^{-46} on the sphere: N_i |b_i| >= Gcut + sqrt(4 pmax 46)."""
+    reach = orc_gcut(w) + math.sqrt(4.0 * pmax * 46.0)
+    return [int(math.ceil(reach * np.linalg.norm(w.A[i]) / (2 * math.pi))) + margin for i in range(3)]
+
+
+def orc_gcut(w):
+    from oracle import gcut_of
+    return gcut_of(w)
+
+
+def test_classified_build_without_diffuse_pairs_is_the_plain_build(orc):
+    w = W.tiny(seed=7, kmesh=(2, 1, 2), ndens=2)
+    r0 = orc.lrj(w)
+    r1 = orc.lrj_classified(w, alpha_cut=0.0)
+    assert np.array_equal(r0["Jk"], r1["Jk"])
+    assert np.array_equal(r0["EJ"], r1["EJ"])
+    assert np.abs(r1["rhoD"]).max() == 0.0
+
+
+@pytest.mark.parametrize("triclinic", [False, True])
+def test_gpw_grid_transform_is_the_pair_transform(orc, triclinic):
+    """rho_D(G) from the DD density sampled on a dense real-space grid (App. E)
+    and a library FFT equals the direct pair transforms summed over the DD pairs
+    (Eq. "AFT for pair density"): pins the collocation's images, normalisation
+    and sign conventions.  alpha_cut = 0.9 makes s, p and d primitives diffuse,
+    so DD pairs of classes 0..4 take part."""
+    A = np.array([[6.0, 0.0, 0.0], [1.1, 6.4, 0.0], [-0.7, 0.8, 6.9]]) if triclinic else None
+    w = W.tiny(seed=7, A=A, kmesh=(2, 1, 2), ndens=2)
+    acut = 0.9
+    r = orc.lrj_classified(w, alpha_cut=acut)
+    grid = dense_gpw_grid(w, pmax=1.6)
+    rho_r = orc.gpw_density(w, grid, alpha_cut=acut)
+    rg = orc.grid_transform(w.A, rho_r, r["G"])
+    scale = np.abs(r["rhoD"]).max()
+    assert scale > 0.1
+    assert np.abs(rg - r["rhoD"]).max() < 1e-13 * scale
+
+
+def test_classified_all_diffuse_is_the_full_range_limit(orc):
+    """With every primitive diffuse, the classified build is the long-range
+    build in the limit w -> infinity (v_LR -> 4 pi / (Omega G^2))."""
+    w = W.tiny(seed=5, kmesh=(1, 2, 1))
+    r = orc.lrj_classified(w, alpha_cut=1e9)
+    assert np.abs(r["rhoC"]).max() == 0.0
+    gc = orc_gcut(w)
+    w.gcut = gc
+    w.omega = 1e8
+    r_inf = orc.lrj(w)
+    assert abs(r["EJ"][0] - r_inf["EJ"][0]) < 1e-13 * abs(r_inf["EJ"][0])
+    assert np.abs(r["Jk"] - r_inf["Jk"]).max() < 1e-13 * np.abs(r_inf["Jk"]).max()
+
+
+def test_classified_parseval_hermitian_and_bilinear_symmetry(orc):
+    """E_J = (1/2Nk) sum_k Tr(D^k J^k) and Tr(D1 J[D2]) = Tr(D2 J[D1]) with
+    mixed classes: an integral class given the wrong kernel on one side only
+    breaks both."""
+    acut = 0.9
+    w = W.tiny(seed=7, kmesh=(2, 1, 2), ndens=2)
+    r = orc.lrj_classified(w, alpha_cut=acut)
+    Jk = r["Jk"]
+    assert np.abs(r["rhoC"]).max() > 0.1 and np.abs(r["rhoD"]).max() > 0.1
+    assert np.abs(Jk - np.conj(np.transpose(Jk, (0, 1, 3, 2)))).max() < 1e-13 * np.abs(Jk).max()
+    for d in range(2):
+        tr = sum(np.trace(w.Dk[d, k] @ Jk[d, k]) for k in range(w.nk)) / (2 * w.nk)
+        assert abs(tr.imag) < 1e-13
+        assert abs(tr.real - r["EJ"][d]) < 1e-12 * abs(r["EJ"][d])
+    D1, D2 = w.Dk[:1], w.Dk[1:]
+    J1 = orc.lrj_classified(w, alpha_cut=acut, Dk=D1)["Jk"]
+    J2 = orc.lrj_classified(w, alpha_cut=acut, Dk=D2)["Jk"]
+    t12 = sum(np.trace(D1[0, k] @ J2[0, k]) for k in range(w.nk))
+    t21 = sum(np.trace(D2[0, k] @ J1[0, k]) for k in range(w.nk))
+    assert abs(t12 - t21) < 1e-12 * abs(t12)
+
+
+def test_classified_energy_terms_match_erf_lattice_sums(orc):
+    """Neutral, dipole-free clouds of same-centre s Gaussians: compact charges
+    (exponents 2.5, 1.2) on one centre, diffuse ones (0.09, 0.15) on another.
+    Their compact-compact energy is the long-range erf(w r)/r lattice sum, the
+    diffuse-diffuse one and the cross term the full-range sums (Sec. 2.6: only
+    integrals between two compact densities keep the Ewald split).  The cell is
+    large enough that no diffuse function overlaps its own images."""
+    A = np.array([[26.0, 0.0, 0.0], [1.5, 27.0, 0.0], [-1.0, 1.2, 28.0]])
+    cen = [[0.3, 0.2, 0.1], [1.1, -0.4, 0.7]]
+    spec = [(0, 0, [2.5, 1.2]), (1, 0, [0.09, 0.15])]
+    w = W.tiny(seed=1, A=A, centres=cen, shell_spec=spec, omega=0.4, eps_g=1e-17, pair_thresh=1e-12)
+    for sa, _, sb, _, l1, l2, l3 in orc.pairs(w):
+        if sa == sb:
+            assert (l1, l2, l3) == (0, 0, 0)
+    acut = 0.5
+    q = np.array([1.0, -1.0, 0.7, -0.7])
+    qc = q * np.array([1, 1, 0, 0])
+    qd = q * np.array([0, 0, 1, 1])
+    E = {}
+    for name, qq in (("all", q), ("c", qc), ("d", qd)):
+        D = np.diag(qq).astype(np.complex128)[None, None]
+        E[name] = orc.lrj_classified(w, alpha_cut=acut, Dk=D)["EJ"][0]
+    charges = [(q[i], 2 * w.shells[i].exps[0], w.xyz[w.shells[i].centre]) for i in range(4)]
+    cc, dc = charges[:2], charges[2:]
+    e_cc = N.erf_lattice_energy(A, cc, 0.4, rmax=60.0)
+    e_dd = N.erf_lattice_energy(A, dc, math.inf, rmax=60.0)
+    e_x_full = N.erf_lattice_energy(A, charges, math.inf, rmax=60.0) - \
+        N.erf_lattice_energy(A, cc, math.inf, rmax=60.0) - e_dd
+    e_x_lr = N.erf_lattice_energy(A, charges, 0.4, rmax=60.0) - e_cc - N.erf_lattice_energy(A, dc, 0.4, rmax=60.0)
+    assert abs(E["c"] - e_cc) < 1e-12
+    assert abs(E["d"] - e_dd) < 1e-12
+    e_x = E["all"] - E["c"] - E["d"]
+    assert abs(e_x - e_x_full) < 1e-12
+    assert abs(e_x_full - e_x_lr) > 1e-4  # the two kernels are told apart
