@@ -103,7 +103,7 @@ typedef struct {
     double pair_gcut_eps; /* > 0: per-pair G cutoffs (Sec. 2.5, Eq. "AFT screening obj"): each pair
                              record is evaluated only for |G| below the radius where its
                              screening estimate 8 pi eta G (4 pi/G^2) e^{-G^2/4w^2} |rho_ab(G)|
-                             falls under this value (split form only; EUNSUPPORTED with FP64).
+                             falls under this value (split and FP64 forms).
                              0: every pair over the whole sphere. */
     int shard_count;    /* > 1: a record-sharded plan for one of shard_count GPUs: it keeps only
                            share shard_index (0-based) of the screened pair records, a contiguous
@@ -125,6 +125,22 @@ typedef struct {
                            2^tc_wait_log2 clock cycles (0: 2^32, about 2 s), raises the plan's device
                            error word (ftcj_plan_status) and lets the kernel drain and return; 1..40,
                            small values are for tests of that path */
+    int classify;       /* 1: compact/diffuse classification of the pair densities (Sec. 2.6).  A pair
+                           record whose two primitives both have exponents below alpha_cut is DD; the
+                           DD records leave the planewave walks and take the GPW route (App. E): their
+                           density is collocated on a uniform real-space grid of the cell, transformed
+                           onto the G sphere, and their J' back-contracted on the same grid.  Integrals
+                           between two compact pair densities keep the long-range kernel v(G), every
+                           other one takes the full-range 4 pi / (Omega G^2), G = 0 removed.
+                           ftcj_jbuild and ftcj_jbuild_host return that build; the step calls
+                           (ftcj_rho, ftcj_potential, ftcj_jback), ftcj_grad, shard plans and batches
+                           refuse a classified plan (EUNSUPPORTED).
+                           0: every pair record in the long-range walks. */
+    double alpha_cut;   /* classify = 1: the exponent boundary; <= 0: w^2/2 (Eq. "cd cutoff") */
+    int gpw_grid[3];    /* classify = 1: grid points along a_1, a_2, a_3; each <= 0: the smallest count
+                           N_i with N_i |b_i| >= Gcut + sqrt(184 p_max) (every alias of a DD transform,
+                           exponent p <= p_max, below e^{-46} on the sphere) and N_i > 2 max|n_i|;
+                           an explicit count below 2 max|n_i| + 1 is refused (EINVAL) */
 } ftcj_params;
 
 #define FTCJ_CONTRACT_WALK 0
@@ -174,6 +190,13 @@ typedef struct {
     int tc_row_tiles;
     int tc_blocks_per_window; /* (i, j) blocks side by side in one structure-factor window */
     int tc_dens_per_launch;   /* densities per structure-factor launch */
+    int64_t dd_pairs;         /* classified plan: DD pair records (GPW route); npairs, pairs_by_class and
+                                 the pair*G counts above cover the compact records only */
+    int64_t dd_pairs_ordered; /* the DD records' ordered primitive-shell pairs */
+    double alpha_cut;         /* classified plan: the exponent boundary in use, else 0 */
+    int gpw_grid[3];          /* the GPW grid (0 without DD records) */
+    int gpw_separable;        /* 1: orthorhombic cell, per-axis factor tables; 0: per-point lattice images */
+    int gpw_launches;         /* kernel launches of the GPW route in one build over max_dens densities */
 } ftcj_info;
 
 typedef struct ftcj_plan ftcj_plan;

@@ -42,6 +42,13 @@ int whole_plan(const ftcj_plan* P) {
     return FTCJ_OK;
 }
 
+// the step calls expose one potential; a classified plan has two (Sec. 2.6)
+int single_potential(const ftcj_plan* P) {
+    if (P->rec_filter)
+        return fail(FTCJ_EUNSUPPORTED, "a classified plan (compact/diffuse) runs ftcj_jbuild or ftcj_jbuild_host only");
+    return FTCJ_OK;
+}
+
 int check(const ftcj_plan* P, int ndens, bool batch_limit) {
     if (!P) return fail(FTCJ_EINVAL, "null plan");
     if (ndens < 1) return fail(FTCJ_EINVAL, "ndens must be >= 1");
@@ -66,14 +73,23 @@ int build_batch(ftcj_plan* P, int nd, const double* Dk, double* Jk, double* EJ, 
     if ((rc = launch_fold_build(P, nd, Dk, P->d_D0n, s))) return rc;
     if ((rc = mark(1))) return rc;
     if ((rc = launch_hermite_map(P, nd, P->d_D0n, s))) return rc;
+    if (P->gpw && (rc = launch_hermite_map(P->dd, nd, P->d_D0n, s))) return rc;
     if ((rc = mark(2))) return rc;
     if ((rc = rho_walk(P, nd, s))) return rc;
+    if ((rc = launch_gpw_rho(P, nd, s))) return rc;  // the DD records on the grid (classified plans)
     if ((rc = mark(3))) return rc;
-    if ((rc = launch_rho_reduce(P, nd, P->d_rho, P->d_W, EJ, nullptr, s))) return rc;
+    if (P->gpw) {
+        if ((rc = launch_rho_reduce(P, nd, P->d_rho, nullptr, nullptr, nullptr, s))) return rc;
+        if ((rc = launch_gpw_potential(P, nd, EJ, s))) return rc;
+    } else {
+        if ((rc = launch_rho_reduce(P, nd, P->d_rho, P->d_W, EJ, nullptr, s))) return rc;
+    }
     if ((rc = mark(4))) return rc;
     if ((rc = j_walk(P, nd, P->d_W, s))) return rc;
+    if ((rc = launch_gpw_j(P, nd, s))) return rc;
     if ((rc = mark(5))) return rc;
     if ((rc = launch_jtransform_map(P, nd, P->d_J0n, s))) return rc;
+    if (P->gpw && (rc = launch_jtransform_map(P->dd, nd, P->d_J0n, s, false))) return rc;
     if ((rc = mark(6))) return rc;
     if ((rc = launch_unfold(P, nd, P->d_J0n, Jk, s))) return rc;
     if ((rc = mark(7))) return rc;
@@ -95,6 +111,7 @@ int ftcj_rho(ftcj_plan* P, int ndens, const double* D0n, double* rho, void* stre
     int rc = check(P, ndens, true);
     if (rc) return rc;
     if (!D0n || !rho) return fail(FTCJ_EINVAL, "null buffer");
+    if ((rc = single_potential(P))) return rc;
     cudaStream_t s = as_stream(stream);
     if ((rc = launch_hermite_map(P, ndens, D0n, s))) return rc;
     if ((rc = rho_walk(P, ndens, s))) return rc;
@@ -105,6 +122,7 @@ int ftcj_potential(ftcj_plan* P, int ndens, const double* rho, double* W, double
     int rc = check(P, ndens, false);
     if (rc) return rc;
     if (!rho || !W || !EJ) return fail(FTCJ_EINVAL, "null buffer");
+    if ((rc = single_potential(P))) return rc;
     cudaStream_t s = as_stream(stream);
     // batches keep the energy partials inside the plan's scratch
     for (int b0 = 0; b0 < ndens; b0 += P->max_dens) {
@@ -119,6 +137,7 @@ int ftcj_jback(ftcj_plan* P, int ndens, const double* W, double* J0n, void* stre
     int rc = check(P, ndens, true);
     if (rc) return rc;
     if (!W || !J0n) return fail(FTCJ_EINVAL, "null buffer");
+    if ((rc = single_potential(P))) return rc;
     cudaStream_t s = as_stream(stream);
     if ((rc = j_walk(P, ndens, W, s))) return rc;
     return launch_jtransform_map(P, ndens, J0n, s);
@@ -180,6 +199,7 @@ int ftcj_grad(ftcj_plan* P, int ndens, const double* Dk, double* EJ, double* gra
     if (rc) return rc;
     if ((rc = whole_plan(P))) return rc;
     if (!Dk || !EJ || !grad) return fail(FTCJ_EINVAL, "null buffer");
+    if ((rc = single_potential(P))) return rc;
     cudaStream_t s = as_stream(stream);
     size_t per = (size_t)P->nk * P->nao * P->nao * 2;
     for (int b0 = 0; b0 < ndens; b0 += P->max_dens) {

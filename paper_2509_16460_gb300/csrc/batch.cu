@@ -245,6 +245,10 @@ int ftcj_batch_create(int ncell, const ftcj_cell* cells, const ftcj_basis* bases
             rc = fail(FTCJ_EINVAL, "a batch takes whole plans (shard_count <= 1)");
             break;
         }
+        if (p.classify) {
+            rc = fail(FTCJ_EUNSUPPORTED, "a batch takes long-range plans (classify = 0)");
+            break;
+        }
         if (flags & FTCJ_BATCH_AUTOTUNE) rc = ftcj_autotune(&cells[c], &bases[c], kmeshes + 3 * c, &params[c], &p,
                                                             nullptr);
         ftcj_plan* P = nullptr;

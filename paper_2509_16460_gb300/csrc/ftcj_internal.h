@@ -141,6 +141,8 @@ struct CellConst {
     int pad;
 };
 
+struct Gpw;
+
 }  // namespace ftcj
 
 struct ftcj_plan {
@@ -253,6 +255,12 @@ struct ftcj_plan {
     void* d_tc_vs = nullptr;      // bf16 sliced V_ij stage tiles
     int* d_tc_ev = nullptr;       // their column scales
     int rho_rows = 0;            // partial rows the rho reduction sums (walk blocks or tensor-core groups)
+    // density classification (Sec. 2.6): the records a plan keeps (0 all, 1 compact, 2 DD)
+    int rec_filter = 0;
+    double alpha_cut = 0.0;
+    ftcj_plan* dd = nullptr;   // the DD records (GPW route): a plan of their own over the same basis
+    ftcj::Gpw* gpw = nullptr;  // GPW grid, transforms and buffers (gpw.cu)
+    int jp_fixed = 0;          // > 0: partial J' arrays the J -> AO map sums, whatever the walk
     int precision = FTCJ_PREC_FP64;
     bool ortho = false;  // reciprocal metric diagonal (orthorhombic cell)
     ftcj::CellConst cc;
@@ -300,7 +308,7 @@ void host_hermite_tables(const ftcj_plan* P, std::vector<double>& U, std::vector
 // --- per-record maps of the Hermite-density contraction (hmap.cu) ---
 int build_maps(ftcj_plan* P);
 int launch_hermite_map(ftcj_plan* P, int ndens, const double* D0n, cudaStream_t s);
-int launch_jtransform_map(ftcj_plan* P, int ndens, double* J0n, cudaStream_t s);
+int launch_jtransform_map(ftcj_plan* P, int ndens, double* J0n, cudaStream_t s, bool zero = true);
 
 // --- G walks (walk.cu) ---
 int upload_walk_tables(ftcj_plan* P);
@@ -340,7 +348,19 @@ int batch_walks_launches(const BatchWalks* bw);
 void batch_walks_destroy(BatchWalks* bw);
 int tc_j_launches(const ftcj_plan* P, int nd);
 // partial back-contraction sums the J -> AO map adds: one per walk chunk, or per row part of the tensor-core form
-inline int jp_chunks(const ftcj_plan* P) { return P->tc_j ? P->tc_jparts : (int)P->chunks.size(); }
+inline int jp_chunks(const ftcj_plan* P) {
+    return P->jp_fixed > 0 ? P->jp_fixed : (P->tc_j ? P->tc_jparts : (int)P->chunks.size());
+}
+
+// --- GPW route of the DD pair densities (gpw.cu) ---
+int setup_gpw(ftcj_plan* P);  // after the compact plan is built: P->dd, the grid and its buffers
+void free_gpw(ftcj_plan* P);
+int launch_gpw_rho(ftcj_plan* P, int ndens, cudaStream_t s);  // rho_D(G) from P->dd's Hermite terms
+int launch_gpw_potential(ftcj_plan* P, int ndens, double* EJ, cudaStream_t s);  // W_C into P->d_W, W_D, E_J
+int launch_gpw_j(ftcj_plan* P, int ndens, cudaStream_t s);  // J' of the DD records into P->dd->d_Jp
+int gpw_launches(const ftcj_plan* P, int ndens);
+int gpw_grid_dim(const ftcj_plan* P, int axis);
+int gpw_separable(const ftcj_plan* P);
 
 // --- measurement (profile.cu) ---
 void release_profiling(ftcj_plan* P);

@@ -616,9 +616,9 @@ int launch_hermite_map(ftcj_plan* P, int ndens, const double* D0n, cudaStream_t 
     return FTCJ_OK;
 }
 
-int launch_jtransform_map(ftcj_plan* P, int ndens, double* J0n, cudaStream_t s) {
+int launch_jtransform_map(ftcj_plan* P, int ndens, double* J0n, cudaStream_t s, bool zero) {
     const size_t bytes = sizeof(double) * (size_t)ndens * P->nk * P->nao * P->nao;
-    FTCJ_CUDA(cudaMemsetAsync(J0n, 0, bytes, s));
+    if (zero) FTCJ_CUDA(cudaMemsetAsync(J0n, 0, bytes, s));
     if (P->npairs == 0) return FTCJ_OK;
     if (P->maps_df) {
         dim3 g((unsigned)P->rb_outs.bstart[kNclass], ndens);

@@ -307,6 +307,12 @@ void free_device(ftcj_plan* P) {
                     P->d_tc_ebw, P->d_tc_clw};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    free_gpw(P);
+    if (P->dd) {
+        free_device(P->dd);
+        delete P->dd;
+        P->dd = nullptr;
+    }
     if (P->ev_fork) cudaEventDestroy(P->ev_fork);
     if (P->ev_join) cudaEventDestroy(P->ev_join);
     if (P->aux) cudaStreamDestroy(P->aux);
@@ -375,6 +381,14 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     if (P->tc && prm->pair_gcut_eps > 0.0)
         return fail(FTCJ_EUNSUPPORTED, "the tensor-core contraction covers the whole sphere (pair_gcut_eps = 0)");
     if (!(prm->pair_thresh > 0.0 && prm->pair_thresh < 1.0)) return fail(FTCJ_EINVAL, "pair_thresh in (0,1)");
+    if (prm->classify != 0 && prm->classify != 1) return fail(FTCJ_EINVAL, "classify must be 0 or 1");
+    if (prm->classify) {
+        if (P->shard_count > 1)
+            return fail(FTCJ_EUNSUPPORTED, "a classified plan (compact/diffuse) is not record-sharded");
+        if (!finite(prm->alpha_cut)) return fail(FTCJ_EINVAL, "alpha_cut must be finite");
+        P->alpha_cut = prm->alpha_cut > 0.0 ? prm->alpha_cut : 0.5 * prm->omega * prm->omega;
+        P->rec_filter = 1;
+    }
     P->omega = prm->omega;
     P->cc.vpar[0] = 4.0 * M_PI / P->vol;
     P->cc.vpar[1] = 1.0 / (4.0 * prm->omega * prm->omega);
@@ -555,6 +569,7 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
     if ((rc = launch_vg(P))) return rc;
     if ((rc = launch_twiddles(P))) return rc;
     if ((rc = setup_fold(P))) return rc;
+    if (prm->classify && (rc = setup_gpw(P))) return rc;
     FTCJ_CUDA(cudaDeviceSynchronize());
     return FTCJ_OK;
 }
@@ -650,6 +665,18 @@ int ftcj_plan_info(const ftcj_plan* P, ftcj_info* o) {
         o->tc_row_tiles = P->tc_mtiles;
         o->tc_blocks_per_window = P->tc_G;
         o->tc_dens_per_launch = P->tc_nd;
+    }
+    o->alpha_cut = P->rec_filter ? P->alpha_cut : 0.0;
+    if (P->dd) {
+        o->dd_pairs = P->dd->npairs;
+        o->dd_pairs_ordered = P->dd->npairs_ordered;
+    }
+    if (P->gpw) {
+        o->gpw_grid[0] = gpw_grid_dim(P, 0);
+        o->gpw_grid[1] = gpw_grid_dim(P, 1);
+        o->gpw_grid[2] = gpw_grid_dim(P, 2);
+        o->gpw_separable = gpw_separable(P);
+        o->gpw_launches = gpw_launches(P, P->max_dens);
     }
     return FTCJ_OK;
 }

@@ -31,6 +31,7 @@ int64_t launches_per_batch(const ftcj_plan* P) {
              : 0;  // a6
     n += P->npairs > 0 ? 1 : 0;                        // a7
     n += fold;                                         // a8
+    n += gpw_launches(P, P->max_dens);                 // the DD records' GPW route (classified plans)
     return n;
 }
 

@@ -1,5 +1,6 @@
 // Step a1 on the device: screen candidate primitive pairs (group a in the home
-// cell, group b in cell L) by their overlap bound, keep one record per mirror
+// cell, group b in cell L) by their overlap bound (and, in a classified plan,
+// by density class: compact or DD, Sec. 2.6), keep one record per mirror
 // couple (a0,bL) <-> (b0,a-L), and sort the survivors stably by the pair
 // class L = l_a + l_b (counting sort by tiles).  The epilogue computes each
 // record's Gaussian-product data (Eqs. GPT) and the constants of the G walk.
@@ -127,7 +128,7 @@ __device__ __forceinline__ Cand decode(const long long* __restrict__ off, const 
 
 __global__ void k_screen_eval(const GroupDev* __restrict__ G, int ng, double thr, const long long* __restrict__ off,
                               const int* __restrict__ lim, long long C, unsigned char* __restrict__ flag,
-                              unsigned char* __restrict__ key, CellConst cc) {
+                              unsigned char* __restrict__ key, CellConst cc, double acut, int filter) {
     long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
     Cand q = decode(off, lim, ng, c);
@@ -146,6 +147,10 @@ __global__ void k_screen_eval(const GroupDev* __restrict__ G, int ng, double thr
     if (q.ga == q.gb) {  // keep one of (a0,aL) and (a0,a-L)
         bool nonneg = q.L0 > 0 || (q.L0 == 0 && (q.L1 > 0 || (q.L1 == 0 && q.L2 >= 0)));
         ok = ok && nonneg;
+    }
+    if (filter) {  // density classes (Sec. 2.6): DD when both exponents lie below alpha_cut
+        const bool dd = a < acut && b < acut;
+        ok = ok && (filter == 2 ? dd : !dd);
     }
     flag[c] = ok ? 1 : 0;
     key[c] = (unsigned char)(A.lmax + B.lmax);
@@ -344,7 +349,8 @@ int screen_and_sort(ftcj_plan* P) {
     FTCJ_CUDA(s.get(&tc, (size_t)(ntiles * kNclass)));
     FTCJ_CUDA(s.get(&toff, (size_t)(ntiles * kNclass)));
     if (C > 0) {
-        k_screen_eval<<<(unsigned)((C + 255) / 256), 256>>>(P->d_groups, ng, thr, off, lim, C, flag, key, cc);
+        k_screen_eval<<<(unsigned)((C + 255) / 256), 256>>>(P->d_groups, ng, thr, off, lim, C, flag, key, cc,
+                                                             P->alpha_cut, P->rec_filter);
         FTCJ_CUDA(cudaGetLastError());
     }
     k_tile_count<<<(unsigned)ntiles, kSortTile>>>(flag, key, C, ntiles, tc);

@@ -42,7 +42,8 @@ class Params(ctypes.Structure):
     _fields_ = [("omega", _c_double), ("gcut", _c_double), ("eps_g", _c_double), ("pair_thresh", _c_double),
                 ("precision", _c_int), ("max_dens", _c_int), ("chunk_points", _c_int), ("rho_blocks", _c_int),
                 ("pair_gcut_eps", _c_double), ("shard_count", _c_int), ("shard_index", _c_int),
-                ("contraction", _c_int), ("tc_wait_log2", _c_int)]
+                ("contraction", _c_int), ("tc_wait_log2", _c_int), ("classify", _c_int),
+                ("alpha_cut", _c_double), ("gpw_grid", _c_int * 3)]
 
 
 class Info(ctypes.Structure):
@@ -56,11 +57,14 @@ class Info(ctypes.Structure):
                 ("rho_walk_launches", _c_int), ("j_walk_launches", _c_int), ("contraction", _c_int),
                 ("tc_mma_flops", ctypes.c_int64), ("j_contraction", _c_int), ("tc_j_mma_flops", ctypes.c_int64),
                 ("tc_column_axis", _c_int), ("tc_rows", _c_int), ("tc_row_tiles", _c_int),
-                ("tc_blocks_per_window", _c_int), ("tc_dens_per_launch", _c_int)]
+                ("tc_blocks_per_window", _c_int), ("tc_dens_per_launch", _c_int),
+                ("dd_pairs", ctypes.c_int64), ("dd_pairs_ordered", ctypes.c_int64), ("alpha_cut", _c_double),
+                ("gpw_grid", _c_int * 3), ("gpw_separable", _c_int), ("gpw_launches", _c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["pairs_by_class"] = list(self.pairs_by_class)
+        d["gpw_grid"] = list(self.gpw_grid)
         return d
 
 
@@ -203,7 +207,7 @@ def _params_of(w, precision=FTCJ_PREC_FP64, max_dens=None, chunk_points=0, rho_b
                contraction=0):
     return Params(float(w.omega), float(w.gcut), float(w.eps_g), float(w.pair_thresh), int(precision),
                   int(max_dens or w.ndens), int(chunk_points), int(rho_blocks), float(pair_gcut_eps), 0, 0,
-                  int(contraction), 0)
+                  int(contraction), 0, 0, 0.0, (_c_int * 3)(0, 0, 0))
 
 
 def shard_bounds(class_counts, precision, shard_count):
@@ -325,14 +329,16 @@ class Plan:
 
     def __init__(self, A, xyz, shells, kmesh, omega, eps_g=1e-14, gcut=0.0, pair_thresh=1e-12,
                  precision=FTCJ_PREC_FP64, max_dens=1, chunk_points=0, rho_blocks=0, pair_gcut_eps=0.0,
-                 shard_count=0, shard_index=0, contraction=FTCJ_CONTRACT_WALK, tc_wait_log2=0):
+                 shard_count=0, shard_index=0, contraction=FTCJ_CONTRACT_WALK, tc_wait_log2=0, classify=False,
+                 alpha_cut=0.0, gpw_grid=None):
         L = lib()
         self._keep = []
         cell, basis = _describe(A, xyz, shells, self._keep)
         km = (ctypes.c_int * 3)(*[int(k) for k in kmesh])
         prm = Params(float(omega), float(gcut), float(eps_g), float(pair_thresh), int(precision), int(max_dens),
                      int(chunk_points), int(rho_blocks), float(pair_gcut_eps), int(shard_count), int(shard_index),
-                     int(contraction), int(tc_wait_log2))
+                     int(contraction), int(tc_wait_log2), int(classify), float(alpha_cut),
+                     (_c_int * 3)(*[int(v) for v in (gpw_grid or (0, 0, 0))]))
         self.shard_count = max(1, int(shard_count))
         self.shard_index = int(shard_index)
         h = _c_void_p()
@@ -352,11 +358,12 @@ class Plan:
     @classmethod
     def from_workload(cls, w, max_dens=None, precision=FTCJ_PREC_FP64, chunk_points=0, rho_blocks=0,
                       pair_gcut_eps=0.0, shard_count=0, shard_index=0, contraction=FTCJ_CONTRACT_WALK,
-                      tc_wait_log2=0):
+                      tc_wait_log2=0, classify=False, alpha_cut=0.0, gpw_grid=None):
         return cls(w.A, w.xyz, w.shells, w.kmesh, w.omega, eps_g=w.eps_g, gcut=w.gcut, pair_thresh=w.pair_thresh,
                    precision=precision, max_dens=max_dens or w.ndens, chunk_points=chunk_points,
                    pair_gcut_eps=pair_gcut_eps, rho_blocks=rho_blocks, shard_count=shard_count,
-                   shard_index=shard_index, contraction=contraction, tc_wait_log2=tc_wait_log2)
+                   shard_index=shard_index, contraction=contraction, tc_wait_log2=tc_wait_log2,
+                   classify=classify, alpha_cut=alpha_cut, gpw_grid=gpw_grid)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -83,6 +83,10 @@ CASES = [
     ("contraction 2", None, {"contraction": 2, "precision": 1}, "invalid argument", "contraction"),
     ("wait budget 41", None, {"tc_wait_log2": 41, "precision": 1, "contraction": 1}, "invalid argument",
      "tc_wait_log2"),
+    ("classify 2", None, {"classify": 2}, "invalid argument", "classify"),
+    ("classified shard", None, {"classify": True, "shard_count": 2, "shard_index": 0}, "unsupported input",
+     "record-sharded"),
+    ("alpha_cut nan", None, {"classify": True, "alpha_cut": float("nan")}, "invalid argument", "alpha_cut"),
 ]
 
 
