@@ -337,7 +337,7 @@ class Plan:
         km = (ctypes.c_int * 3)(*[int(k) for k in kmesh])
         prm = Params(float(omega), float(gcut), float(eps_g), float(pair_thresh), int(precision), int(max_dens),
                      int(chunk_points), int(rho_blocks), float(pair_gcut_eps), int(shard_count), int(shard_index),
-                     int(contraction), int(tc_wait_log2), int(classify), float(alpha_cut),
+                     int(contraction), int(tc_wait_log2), int(classify), float(alpha_cut or 0.0),
                      (_c_int * 3)(*[int(v) for v in (gpw_grid or (0, 0, 0))]))
         self.shard_count = max(1, int(shard_count))
         self.shard_index = int(shard_index)

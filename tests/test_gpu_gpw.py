@@ -110,7 +110,10 @@ def test_classified_without_diffuse_pairs_is_the_plain_build(F):
     cls, J1, E1 = build(F, w, classify=True, alpha_cut=0.01)
     try:
         assert cls.info["dd_pairs"] == 0 and cls.info["gpw_launches"] == 0
-        assert np.array_equal(J0, J1) and np.array_equal(E0, E1)
+        # E_J comes from fixed-order sums; the J -> AO map adds with atomics, so J^k
+        # agrees to the rounding of its summation order
+        assert np.array_equal(E0, E1)
+        assert np.abs(J1 - J0).max() <= 1e-14 * float(np.abs(J0).max())
     finally:
         plain.close()
         cls.close()
