@@ -63,7 +63,7 @@ def parse():
                     help="skip the secondary diamond line and the batch and slab legs")
     ap.add_argument("--forms", default="split_tc,split,fp64,split_pair_gcut,fp64_pair_gcut",
                     help="comma list of the headline forms to time (split is always timed)")
-    ap.add_argument("--leg", choices=["batch", "molecular_crystal", "slab", "diamond"], default=None,
+    ap.add_argument("--leg", choices=["batch", "molecular_crystal", "slab", "diamond", "gpw"], default=None,
                     help="run only this extra workload (one GPU, rank 0) and print its JSON; for profiling")
     return ap.parse_args()
 
@@ -589,6 +589,70 @@ def slab_leg(ftcj, W, torch, flush, steps):
     return out
 
 
+def gpw_leg(ctx, forms=("split_tc", "fp64")):
+    """The molecular crystal with the compact/diffuse classification (Sec. 2.6):
+    the default alpha_cut = w^2/2 = 0.125 makes the 0.1 s exponent of every
+    centre diffuse, and the s-s pairs of those primitives (with their lattice
+    images) take the GPW route (App. E): collocation on the real-space grid,
+    the separable transform onto the sphere, the full-range potential and the
+    adjoint integration, all FP64.  The classified build is a different
+    Coulomb operator from the long-range headline (every integral touching a
+    DD density takes the full-range kernel), so its time is context for the
+    route, not a comparison."""
+    import numpy as np
+    ftcj, torch, W = ctx["ftcj"], ctx["torch"], ctx["W"]
+    flush, stream = ctx["flush"], ctx["stream"]
+    steps = max(3, min(ctx["args"].steps, 10))
+    w = W.cfg3()
+    Dk = ctx["Dk"]
+    out = {"workload": WORKLOADS[HEADLINE] + ", compact/diffuse classified (alpha_cut = w^2/2)",
+           "ndens": w.ndens}
+    res = {}
+    for form in forms:
+        prec, _, con = FORMS[form]
+        p = ftcj.Plan.from_workload(w, precision=prec, contraction=con, classify=True)
+        info = p.info
+        units = float(info["npairs_ordered"] + info["dd_pairs_ordered"]) * info["ng_full"] * w.ndens
+        J, E = p.jbuild(Dk)
+        for _ in range(2):
+            p.jbuild(Dk, J, E)
+        torch.cuda.synchronize()
+        p.profile_enable(steps)
+        ms = time_events(lambda: p.jbuild(Dk, J, E), steps, flush, stream)
+        phase_ms, batches, launches = p.profile_read()
+        p.profile_enable(0)
+        ph = {k: v / max(batches, 1) for k, v in phase_ms.items()}
+        npts = float(np.prod(info["gpw_grid"]))
+        # collocation and integration: 2 (L + 1) flops per DD record, grid point and density each
+        flops = sum(2.0 * (c + 1) * n for c, n in enumerate(info["dd_pairs_by_class"])) * npts * w.ndens * 2
+        gpw_ms = ph["gpw_rho"] + ph["gpw_j"]
+        peak = ctx["peaks"]["fp64"]
+        r = {"ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT,
+             "dd_records": info["dd_pairs"], "dd_ordered_pairs": info["dd_pairs_ordered"],
+             "dd_records_by_class": info["dd_pairs_by_class"], "compact_records": info["npairs"],
+             "alpha_cut": info["alpha_cut"], "gpw_grid": info["gpw_grid"], "gpw_separable": info["gpw_separable"],
+             "gpw_launches": info["gpw_launches"], "phase_ms_per_step": ph, "gpw_ms_per_step": gpw_ms,
+             "gpw_share": gpw_ms / ms,
+             "gpw_roofline": {"bound": "alu", "pipe": "fp64", "achieved": flops / (gpw_ms * 1e-3) * 1e-12,
+                              "peak": peak * 1e-12, "unit": "TFLOP/s",
+                              "frac": flops / (gpw_ms * 1e-3) / peak,
+                              "flops_per_step": flops,
+                              "note": "algorithmic flops of the collocation and integration contractions over "
+                                      "the time of both GPW phases (their reduction and six transform passes "
+                                      "included); peak: the FP64 FMA probe of this run"}}
+        if con == ftcj.FTCJ_CONTRACT_TC:
+            r["status"] = p.status()
+        out[form] = r
+        res[form] = (J.clone(), E.clone())
+        p.close()
+    if "fp64" in res:
+        for f in res:
+            if f != "fp64":
+                out[f]["max_abs_dJ_vs_fp64"] = float((res[f][0] - res["fp64"][0]).abs().max())
+                out[f]["abs_dEJ_vs_fp64"] = float((res[f][1] - res["fp64"][1]).abs().max())
+    return out
+
+
 def run_reference(args, world, rank):
     """The reference arm is the CPU oracle, timed as it stands on the host
     cores, on a bounded sample of the headline workload per step (every
@@ -666,6 +730,10 @@ def main():
             out = batch_leg(ftcj, W, torch, flush, steps)
         elif args.leg == "slab":
             out = slab_leg(ftcj, W, torch, flush, steps)
+        elif args.leg == "gpw":
+            w3 = W.cfg3()
+            ctx["Dk"] = torch.from_numpy(np.ascontiguousarray(w3.Dk)).cuda()
+            out = gpw_leg(ctx)
         else:
             out = autotune_leg(ftcj, W, torch, flush, steps)
         print(json.dumps({"leg": args.leg, **out}), flush=True)
@@ -725,6 +793,7 @@ def main():
         extra_steps = max(3, min(args.steps, 10))
         line["diamond"] = diamond_leg(ctx)
         line["batch"] = batch_leg(ftcj, W, torch, flush, extra_steps)
+        line["gpw"] = gpw_leg(ctx)
         line["workloads"] = {"slab": slab_leg(ftcj, W, torch, flush, extra_steps),
                              "molecular_crystal_autotuned": autotune_leg(ftcj, W, torch, flush, extra_steps)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

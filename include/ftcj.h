@@ -197,6 +197,8 @@ typedef struct {
     int gpw_grid[3];          /* the GPW grid (0 without DD records) */
     int gpw_separable;        /* 1: orthorhombic cell, per-axis factor tables; 0: per-point lattice images */
     int gpw_launches;         /* kernel launches of the GPW route in one build over max_dens densities */
+    int64_t dd_pairs_by_class[5]; /* DD records of class L = l_a + l_b (the GPW route's cost per grid point
+                                     and density is 2 (L + 1) flops in each of collocation and integration) */
 } ftcj_info;
 
 typedef struct ftcj_plan ftcj_plan;
@@ -416,7 +418,12 @@ int ftcj_autotune(const ftcj_cell* cell, const ftcj_basis* basis, const int kmes
 #define FTCJ_PHASE_JWALK 4     /* a6: back-contraction walk */
 #define FTCJ_PHASE_JAO 5       /* a7: transform to AOs (and the J^{0n} clear) */
 #define FTCJ_PHASE_UNFOLD 6    /* a8: BvK -> k transform stages */
-#define FTCJ_NPHASE 7
+#define FTCJ_PHASE_GPW_RHO 7   /* classified plans, inside FTCJ_PHASE_RHO: the DD records' collocation on the
+                                  grid and its transform onto the sphere (0 otherwise) */
+#define FTCJ_PHASE_GPW_J 8     /* classified plans, inside FTCJ_PHASE_JWALK: the adjoint transform and the DD
+                                  records' integration on the grid (0 otherwise) */
+#define FTCJ_NPHASE 9
+/* Phases 0..6 partition the build; 7 and 8 are parts of phases 2 and 4. */
 
 /* Turn per-phase CUDA-event timing of ftcj_jbuild / ftcj_jbuild_host on
  * (max_batches > 0: events for that many batches are created now) or off

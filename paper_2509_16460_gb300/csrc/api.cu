@@ -61,7 +61,7 @@ int build_batch(ftcj_plan* P, int nd, const double* Dk, double* Jk, double* EJ, 
     int rc;
     cudaEvent_t* ev = nullptr;
     if (P->prof_used < P->prof_max) {
-        ev = P->prof_events.data() + (size_t)P->prof_used * (FTCJ_NPHASE + 1);
+        ev = P->prof_events.data() + (size_t)P->prof_used * kProfEvents;
         ++P->prof_used;
         P->prof_launches += launches_per_batch(P);
     }
@@ -76,7 +76,9 @@ int build_batch(ftcj_plan* P, int nd, const double* Dk, double* Jk, double* EJ, 
     if (P->gpw && (rc = launch_hermite_map(P->dd, nd, P->d_D0n, s))) return rc;
     if ((rc = mark(2))) return rc;
     if ((rc = rho_walk(P, nd, s))) return rc;
+    if ((rc = mark(8))) return rc;
     if ((rc = launch_gpw_rho(P, nd, s))) return rc;  // the DD records on the grid (classified plans)
+    if ((rc = mark(9))) return rc;
     if ((rc = mark(3))) return rc;
     if (P->gpw) {
         if ((rc = launch_rho_reduce(P, nd, P->d_rho, nullptr, nullptr, nullptr, s))) return rc;
@@ -86,7 +88,9 @@ int build_batch(ftcj_plan* P, int nd, const double* Dk, double* Jk, double* EJ, 
     }
     if ((rc = mark(4))) return rc;
     if ((rc = j_walk(P, nd, P->d_W, s))) return rc;
+    if ((rc = mark(10))) return rc;
     if ((rc = launch_gpw_j(P, nd, s))) return rc;
+    if ((rc = mark(11))) return rc;
     if ((rc = mark(5))) return rc;
     if ((rc = launch_jtransform_map(P, nd, P->d_J0n, s))) return rc;
     if (P->gpw && (rc = launch_jtransform_map(P->dd, nd, P->d_J0n, s, false))) return rc;

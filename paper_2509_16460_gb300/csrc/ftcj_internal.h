@@ -21,6 +21,9 @@ constexpr int kBatch = 32;                 // points per rho reduction batch
 constexpr int kChunkMax = 4096;            // G points per walk chunk
 constexpr int kRedPoints = 4;  // G points per block of the rho row reduction
 constexpr int kSortTile = 1024;            // candidates per sort tile
+// events of one profiled batch: the 8 bounds of phases 0..6, then the start
+// and end of each of the two GPW phases
+constexpr int kProfEvents = 12;
 // The split walks form n^i and n2^j n3^k (i, j + k <= degree) as exact FP32
 // integers: |n| <= 63 keeps degree 4 below 2^24, |n| <= 27 degree 5 (the
 // gradient's sums).
@@ -267,7 +270,7 @@ struct ftcj_plan {
     int nEblocks = 0;
     size_t device_bytes = 0;
     // per-phase event timing (ftcj_profile_enable)
-    std::vector<cudaEvent_t> prof_events;  // [max_batches][FTCJ_NPHASE + 1]
+    std::vector<cudaEvent_t> prof_events;  // [max_batches][kProfEvents]
     int prof_max = 0, prof_used = 0;
     int64_t prof_launches = 0;
 };

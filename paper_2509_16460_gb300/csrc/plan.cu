@@ -670,6 +670,8 @@ int ftcj_plan_info(const ftcj_plan* P, ftcj_info* o) {
     if (P->dd) {
         o->dd_pairs = P->dd->npairs;
         o->dd_pairs_ordered = P->dd->npairs_ordered;
+        for (int c = 0; c < kNclass && c < 5; ++c)
+            o->dd_pairs_by_class[c] = P->dd->class_start[c + 1] - P->dd->class_start[c];
     }
     if (P->gpw) {
         o->gpw_grid[0] = gpw_grid_dim(P, 0);

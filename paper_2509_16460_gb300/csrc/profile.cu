@@ -71,7 +71,7 @@ int ftcj_profile_enable(ftcj_plan* P, int max_batches) {
     if (!P || max_batches < 0) return fail(FTCJ_EINVAL, "bad argument");
     release_profiling(P);
     if (max_batches == 0) return FTCJ_OK;
-    P->prof_events.assign((size_t)max_batches * (FTCJ_NPHASE + 1), nullptr);
+    P->prof_events.assign((size_t)max_batches * kProfEvents, nullptr);
     for (auto& e : P->prof_events) FTCJ_CUDA(cudaEventCreate(&e));
     P->prof_max = max_batches;
     return FTCJ_OK;
@@ -81,11 +81,13 @@ int ftcj_profile_read(ftcj_plan* P, double ms[FTCJ_NPHASE], int* batches, int64_
     if (!P || !ms) return fail(FTCJ_EINVAL, "bad argument");
     for (int i = 0; i < FTCJ_NPHASE; ++i) ms[i] = 0.0;
     for (int b = 0; b < P->prof_used; ++b) {
-        cudaEvent_t* ev = P->prof_events.data() + (size_t)b * (FTCJ_NPHASE + 1);
-        FTCJ_CUDA(cudaEventSynchronize(ev[FTCJ_NPHASE]));
+        cudaEvent_t* ev = P->prof_events.data() + (size_t)b * kProfEvents;
+        FTCJ_CUDA(cudaEventSynchronize(ev[7]));
         for (int i = 0; i < FTCJ_NPHASE; ++i) {
+            // phases 0..6 between consecutive bounds; 7 and 8 from their own pairs
+            const int e0 = i < 7 ? i : 8 + 2 * (i - 7), e1 = i < 7 ? i + 1 : e0 + 1;
             float t = 0.f;
-            FTCJ_CUDA(cudaEventElapsedTime(&t, ev[i], ev[i + 1]));
+            FTCJ_CUDA(cudaEventElapsedTime(&t, ev[e0], ev[e1]));
             ms[i] += t;
         }
     }

@@ -59,12 +59,14 @@ class Info(ctypes.Structure):
                 ("tc_column_axis", _c_int), ("tc_rows", _c_int), ("tc_row_tiles", _c_int),
                 ("tc_blocks_per_window", _c_int), ("tc_dens_per_launch", _c_int),
                 ("dd_pairs", ctypes.c_int64), ("dd_pairs_ordered", ctypes.c_int64), ("alpha_cut", _c_double),
-                ("gpw_grid", _c_int * 3), ("gpw_separable", _c_int), ("gpw_launches", _c_int)]
+                ("gpw_grid", _c_int * 3), ("gpw_separable", _c_int), ("gpw_launches", _c_int),
+                ("dd_pairs_by_class", ctypes.c_int64 * 5)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["pairs_by_class"] = list(self.pairs_by_class)
         d["gpw_grid"] = list(self.gpw_grid)
+        d["dd_pairs_by_class"] = list(self.dd_pairs_by_class)
         return d
 
 
@@ -86,7 +88,7 @@ FTCJ_BATCH_PERSISTENT = 2
 
 FTCJ_NOALLOC_MAX_PARTIALS = 16384
 
-PHASES = ["fold", "hermite", "rho_walk", "potential", "j_walk", "j_to_ao", "unfold"]
+PHASES = ["fold", "hermite", "rho_walk", "potential", "j_walk", "j_to_ao", "unfold", "gpw_rho", "gpw_j"]
 
 _lock = threading.Lock()
 _lib: Optional[ctypes.CDLL] = None
