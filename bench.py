@@ -609,7 +609,8 @@ def gpw_leg(ctx, forms=("split_tc", "fp64")):
            "ndens": w.ndens}
     res = {}
     for form in forms:
-        prec, _, con = FORMS[form]
+        pipe, _, con = FORMS[form]
+        prec = ftcj.FTCJ_PREC_SPLIT if pipe == "split" else ftcj.FTCJ_PREC_FP64
         p = ftcj.Plan.from_workload(w, precision=prec, contraction=con, classify=True)
         info = p.info
         units = float(info["npairs_ordered"] + info["dd_pairs_ordered"]) * info["ng_full"] * w.ndens
