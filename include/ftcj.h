@@ -195,7 +195,8 @@ typedef struct {
     int64_t dd_pairs_ordered; /* the DD records' ordered primitive-shell pairs */
     double alpha_cut;         /* classified plan: the exponent boundary in use, else 0 */
     int gpw_grid[3];          /* the GPW grid (0 without DD records) */
-    int gpw_separable;        /* 1: orthorhombic cell, per-axis factor tables; 0: per-point lattice images */
+    int gpw_separable;        /* 1: orthorhombic cell, per-axis factor tables (FP64); 2: the same with the grid
+                                 contractions in double-float (split form); 0: per-point lattice images (FP64) */
     int gpw_launches;         /* kernel launches of the GPW route in one build over max_dens densities */
     int64_t dd_pairs_by_class[5]; /* DD records of class L = l_a + l_b (the GPW route's cost per grid point
                                      and density is 2 (L + 1) flops in each of collocation and integration) */

@@ -42,12 +42,17 @@
 //   W_D = 2 v_FR conj(rho_C + rho_D)                (the DD records, on the grid)
 //   E_J = sum_half v_LR |rho_C|^2 + v_FR (2 Re rho_C conj(rho_D) + |rho_D|^2).
 //
-// Everything here is FP64; the partial grids of the collocation and the energy
-// partials are summed in a fixed order (no atomics).
+// The FP64 form runs everything in FP64.  The split form runs the two grid
+// contractions (collocation and integration, the route's flops) in
+// double-float on the FP32 pipe, with tables and V(r_m) stored as (hi, lo)
+// float pairs; the transforms, potentials and sums stay FP64.  The partial
+// grids of the collocation and the energy partials are summed in a fixed
+// order (no atomics).
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
+#include "df.cuh"
 #include "ftcj_internal.h"
 
 namespace ftcj {
@@ -62,7 +67,10 @@ struct Gpw {
     int nsplit = 1;           // record splits of the collocation (partial grids)
     long long tstride = 0;    // table entries of one record: (lmax + 1)(N1 + N2 + N3)
     double gnorm = 0.0;       // Omega / (N1 N2 N3)
+    bool df = false;          // split form: the grid contractions in double-float on the FP32 pipe
     double* d_tab = nullptr;    // [tstride][nrec], the record index fastest
+    float2* d_tabf = nullptr;   // the same tables as double-float (hi, lo), split form
+    float2* d_vf = nullptr;     // [max_dens][npts]: V(r_m) as double-float, split form
     double* d_part = nullptr;   // [nsplit][max_dens][npts]
     double* d_grid = nullptr;   // [max_dens][npts]: rho_D(r_m), then V(r_m)
     double2* d_t1 = nullptr;    // [max_dens][ncnt0][N2][N3]
@@ -122,7 +130,7 @@ __device__ __forceinline__ void centre_frac(const PairDev& pr, const CellConst& 
 
 // One thread per (record, axis, grid index): T_a[i][m] for i <= class.
 __global__ void k_gpw_tables(const PairDev* __restrict__ pairs, long long nrec, int lmax, int N0, int N1, int N2,
-                             Lattice lat, CellConst cc, double* __restrict__ tab) {
+                             Lattice lat, CellConst cc, double* __restrict__ tab, float2* __restrict__ tabf) {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int Nt = N0 + N1 + N2;
     if (tid >= nrec * Nt) return;
@@ -165,7 +173,13 @@ __global__ void k_gpw_tables(const PairDev* __restrict__ pairs, long long nrec, 
     }
     double scale = ax == 0 ? pow(p / M_PI, 1.5) : 1.0;
     for (int i = 0; i <= lmax; ++i) {
-        tab[((long long)off + (long long)i * n + m) * nrec + r] = i <= L ? acc[i] * scale : 0.0;
+        const double v = i <= L ? acc[i] * scale : 0.0;
+        const long long e = ((long long)off + (long long)i * n + m) * nrec + r;
+        tab[e] = v;
+        if (tabf) {
+            const float hi = (float)v;
+            tabf[e] = make_float2(hi, (float)(v - (double)hi));
+        }
         scale *= 1.0 / (2.0 * M_PI);
     }
 }
@@ -232,6 +246,81 @@ __global__ void __launch_bounds__(kGpwThreads) k_gpw_collocate_sep(const double*
             if (q < mcnt) {
                 double* o = out + (long long)(mb + q) * lines;
                 *o = add ? *o + acc[q] : acc[q];
+            }
+    }
+}
+
+__device__ __forceinline__ df ld_df(const float2* p) {
+    const float2 v = __ldg(p);
+    return df{v.x, v.y};
+}
+
+// The separable collocation in double-float (split form): the same sums as
+// k_gpw_collocate_sep, every product and sum an error-free double-float step
+// on the FP32 pipe (D'_ijk split from FP64 with integer operations); the
+// accumulators are renormalised every four records and joined to FP64 once.
+template <int L>
+__global__ void __launch_bounds__(kGpwThreads) k_gpw_collocate_sep_df(const float2* __restrict__ tabf, long long nrec,
+                                                                     int lmax, int N0, int N1, int N2,
+                                                                     const double* __restrict__ Dp, DdLayout lay,
+                                                                     int nsplit, int nd, long long npts, bool add,
+                                                                     double* __restrict__ part) {
+    const int d = blockIdx.z, split = blockIdx.y;
+    const int lines = N1 * N2;
+    const int line = blockIdx.x * kGpwThreads + threadIdx.x;
+    if (line >= lines) return;
+    const int m2 = line / N2, m3 = line % N2;
+    const long long cnt = lay.start[L + 1] - lay.start[L];
+    const long long r0 = lay.start[L] + cnt * split / nsplit, r1 = lay.start[L] + cnt * (split + 1) / nsplit;
+    const long long off1 = (long long)(lmax + 1) * N0, off2 = (long long)(lmax + 1) * (N0 + N1);
+    const double* Dd = Dp + (long long)d * lay.total + lay.base[L] - lay.start[L];
+    double* out = part + ((long long)split * nd + d) * npts + line;
+    constexpr int M = L == 0 ? kM1 : (L <= 2 ? kM1 / 2 : kM1 / 4);
+    for (int mb = 0; mb < N0; mb += M) {
+        const int mcnt = min(M, N0 - mb);
+        df acc[M];
+#pragma unroll
+        for (int q = 0; q < M; ++q) acc[q] = df{0.f, 0.f};
+        for (long long r = r0; r < r1; ++r) {
+            df t2[L + 1], t3[L + 1], w[L + 1];
+#pragma unroll
+            for (int i = 0; i <= L; ++i) {
+                t2[i] = ld_df(tabf + (off1 + (long long)i * N1 + m2) * nrec + r);
+                t3[i] = ld_df(tabf + (off2 + (long long)i * N2 + m3) * nrec + r);
+                w[i] = df{0.f, 0.f};
+            }
+            int t = 0;
+#pragma unroll
+            for (int lam = 0; lam <= L; ++lam)
+#pragma unroll
+                for (int a = lam; a >= 0; --a)
+#pragma unroll
+                    for (int b = lam - a; b >= 0; --b, ++t)
+                        w[a] = df_add_u(w[a], df_mul_u(split_double(__ldg(Dd + (long long)t * cnt + r)),
+                                                       df_mul_u(t2[b], t3[lam - a - b])));
+#pragma unroll
+            for (int a = 0; a <= L; ++a) w[a] = df_norm(w[a]);
+            const float2* T1 = tabf + (long long)mb * nrec + r;
+#pragma unroll
+            for (int q = 0; q < M; ++q) {
+                if (q < mcnt) {
+                    df v = acc[q];
+#pragma unroll
+                    for (int a = 0; a <= L; ++a) v = df_add_u(v, df_mul_u(ld_df(T1 + ((long long)a * N0 + q) * nrec), w[a]));
+                    acc[q] = v;
+                }
+            }
+            if (((r - r0) & 3) == 3) {
+#pragma unroll
+                for (int q = 0; q < M; ++q) acc[q] = df_norm(acc[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < M; ++q)
+            if (q < mcnt) {
+                double* o = out + (long long)(mb + q) * lines;
+                const double v = join_df(df_norm(acc[q]));
+                *o = add ? *o + v : v;
             }
     }
 }
@@ -489,7 +578,7 @@ __global__ void k_gpw_adj2(const double2* __restrict__ u2, int N1, int N2, int n
 
 // pass 1^T: V[m1][m2][m3] = (Omega/N) Re sum_n1 u1[n1][m2][m3] e^{-2 pi i n1 m1 / N0}
 __global__ void k_gpw_adj1(const double2* __restrict__ u1, int N0, int N1, int N2, int nlo0, int ncnt0,
-                           long long npts, double gnorm, double* __restrict__ V) {
+                           long long npts, double gnorm, double* __restrict__ V, float2* __restrict__ Vf) {
     const int d = blockIdx.y;
     const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= npts) return;
@@ -504,7 +593,12 @@ __global__ void k_gpw_adj1(const double2* __restrict__ u1, int N0, int N1, int N
         const double2 v = src[(long long)n1i * lines];
         re += v.x * c - v.y * s;
     }
-    V[(long long)d * npts + m] = gnorm * re;
+    const double v = gnorm * re;
+    V[(long long)d * npts + m] = v;
+    if (Vf) {
+        const float hi = (float)v;
+        Vf[(long long)d * npts + m] = make_float2(hi, (float)(v - (double)hi));
+    }
 }
 
 // ---- integration: J'_ijk = sum_m c_ijk(r_m) V(r_m) ---------------------------------
@@ -557,6 +651,80 @@ __global__ void __launch_bounds__(kGpwThreads) k_gpw_integrate_sep(const double*
     }
 #pragma unroll
     for (int t = 0; t < NT; ++t) Jp[(long long)d * lay.total + lay.base[L] + (long long)t * cnt + loc] = J[t];
+}
+
+// The separable integration in double-float (split form): per grid line
+// a_i = sum_m1 T_1[i][m1] V(m1, m2, m3) and J'_ijk += a_i T_2[j][m2] T_3[k][m3]
+// as error-free double-float steps; a class-0 record keeps its T_1 row in
+// registers when N0 <= 32.
+template <int L>
+__global__ void __launch_bounds__(kGpwThreads) k_gpw_integrate_sep_df(const float2* __restrict__ tabf, long long nrec,
+                                                                     int lmax, int N0, int N1, int N2, DdLayout lay,
+                                                                     const float2* __restrict__ Vf, long long npts,
+                                                                     double* __restrict__ Jp) {
+    constexpr int NT = nterms(L);
+    constexpr int R = 32;  // T_1 entries a class-0 thread keeps in registers
+    const int d = blockIdx.y;
+    const long long loc = (long long)blockIdx.x * kGpwThreads + threadIdx.x;
+    const long long cnt = lay.start[L + 1] - lay.start[L];
+    if (loc >= cnt) return;
+    const long long r = lay.start[L] + loc;
+    const long long off1 = (long long)(lmax + 1) * N0, off2 = (long long)(lmax + 1) * (N0 + N1);
+    const long long lines = (long long)N1 * N2;
+    const float2* Vd = Vf + (long long)d * npts;
+    const bool regs = L == 0 && N0 <= R;
+    df t1r[L == 0 ? R : 1];
+    if (regs) {
+#pragma unroll
+        for (int q = 0; q < (L == 0 ? R : 1); ++q) t1r[q] = q < N0 ? ld_df(tabf + (long long)q * nrec + r) : df{0.f, 0.f};
+    }
+    df J[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) J[t] = df{0.f, 0.f};
+    for (int m2 = 0; m2 < N1; ++m2) {
+        df t2[L + 1];
+#pragma unroll
+        for (int j = 0; j <= L; ++j) t2[j] = ld_df(tabf + (off1 + (long long)j * N1 + m2) * nrec + r);
+        for (int m3 = 0; m3 < N2; ++m3) {
+            const long long line = (long long)m2 * N2 + m3;
+            df a[L + 1];
+#pragma unroll
+            for (int i = 0; i <= L; ++i) a[i] = df{0.f, 0.f};
+            if (regs) {
+#pragma unroll
+                for (int q = 0; q < (L == 0 ? R : 1); ++q) {
+                    if (q < N0) {
+                        const df v = ld_df(Vd + (long long)q * lines + line);
+                        a[0] = df_add_u(a[0], df_mul_u(t1r[q], v));
+                        if ((q & 7) == 7) a[0] = df_norm(a[0]);
+                    }
+                }
+            } else {
+                for (int m1 = 0; m1 < N0; ++m1) {
+                    const df v = ld_df(Vd + (long long)m1 * lines + line);
+#pragma unroll
+                    for (int i = 0; i <= L; ++i) a[i] = df_add_u(a[i], df_mul_u(ld_df(tabf + ((long long)i * N0 + m1) * nrec + r), v));
+                    if ((m1 & 7) == 7) {
+#pragma unroll
+                        for (int i = 0; i <= L; ++i) a[i] = df_norm(a[i]);
+                    }
+                }
+            }
+            df t3[L + 1];
+#pragma unroll
+            for (int k = 0; k <= L; ++k) t3[k] = ld_df(tabf + (off2 + (long long)k * N2 + m3) * nrec + r);
+            int t = 0;
+#pragma unroll
+            for (int lam = 0; lam <= L; ++lam)
+#pragma unroll
+                for (int i = lam; i >= 0; --i)
+#pragma unroll
+                    for (int j = lam - i; j >= 0; --j, ++t)
+                        J[t] = df_norm(df_add_u(J[t], df_mul_u(df_norm(a[i]), df_mul_u(t2[j], t3[lam - i - j]))));
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NT; ++t) Jp[(long long)d * lay.total + lay.base[L] + (long long)t * cnt + loc] = join_df(J[t]);
 }
 
 // General cell: one thread per record, every grid point and lattice image in reach.
@@ -752,6 +920,7 @@ int setup_gpw(ftcj_plan* P) {
     g->npts = (long long)g->N[0] * g->N[1] * g->N[2];
     g->gnorm = P->vol / (double)g->npts;
     g->sep = P->ortho;
+    g->df = g->sep && P->precision == FTCJ_PREC_SPLIT;
     g->lmax = 0;
     for (int c = 0; c < kNclass; ++c)
         if (D->class_start[c + 1] > D->class_start[c]) g->lmax = c;
@@ -768,13 +937,15 @@ int setup_gpw(ftcj_plan* P) {
     if (g->sep) {
         g->tstride = (long long)(g->lmax + 1) * (g->N[0] + g->N[1] + g->N[2]);
         if ((rc = galloc(P, g, &g->d_tab, (size_t)(g->tstride * nrec)))) return rc;
+        if (g->df && (rc = galloc(P, g, &g->d_tabf, (size_t)(g->tstride * nrec)))) return rc;
         const long long nt = nrec * (g->N[0] + g->N[1] + g->N[2]);
         k_gpw_tables<<<(unsigned)((nt + 255) / 256), 256>>>(D->d_pairs, nrec, g->lmax, g->N[0], g->N[1], g->N[2],
-                                                            lattice_of(P), P->cc, g->d_tab);
+                                                            lattice_of(P), P->cc, g->d_tab, g->d_tabf);
         FTCJ_CUDA(cudaGetLastError());
     }
     if ((rc = galloc(P, g, &g->d_part, (size_t)g->nsplit * md * g->npts))) return rc;
     if ((rc = galloc(P, g, &g->d_grid, (size_t)md * g->npts))) return rc;
+    if (g->df && (rc = galloc(P, g, &g->d_vf, (size_t)md * g->npts))) return rc;
     if ((rc = galloc(P, g, &g->d_t1, (size_t)md * g->ncnt[0] * lines))) return rc;
     if ((rc = galloc(P, g, &g->d_t2, (size_t)md * g->ncnt[0] * g->ncnt[1] * g->N[2]))) return rc;
     if ((rc = galloc(P, g, &g->d_rhoD, (size_t)md * P->ng_half))) return rc;
@@ -808,7 +979,7 @@ int setup_gpw(ftcj_plan* P) {
 void free_gpw(ftcj_plan* P) {
     Gpw* g = P->gpw;
     if (!g) return;
-    void* ptrs[] = {g->d_tab, g->d_part, g->d_grid, g->d_t1, g->d_t2, g->d_rhoD, g->d_WD, g->d_vfr, g->d_Epart,
+    void* ptrs[] = {g->d_tab, g->d_tabf, g->d_vf, g->d_part, g->d_grid, g->d_t1, g->d_t2, g->d_rhoD, g->d_WD, g->d_vfr, g->d_Epart,
                     g->d_cstart, g->d_clist};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -827,13 +998,23 @@ int launch_gpw_rho(ftcj_plan* P, int nd, cudaStream_t s) {
         bool add = false;
         for (int c = 0; c < kNclass; ++c) {
             if (D->class_start[c + 1] == D->class_start[c]) continue;
-            auto kern = c == 0 ? k_gpw_collocate_sep<0>
-                      : c == 1 ? k_gpw_collocate_sep<1>
-                      : c == 2 ? k_gpw_collocate_sep<2>
-                      : c == 3 ? k_gpw_collocate_sep<3>
-                               : k_gpw_collocate_sep<4>;
-            kern<<<grid, kGpwThreads, 0, s>>>(g->d_tab, D->npairs, g->lmax, g->N[0], g->N[1], g->N[2], D->d_Dp, lay,
-                                              g->nsplit, nd, g->npts, add, g->d_part);
+            if (g->df) {
+                auto kern = c == 0 ? k_gpw_collocate_sep_df<0>
+                          : c == 1 ? k_gpw_collocate_sep_df<1>
+                          : c == 2 ? k_gpw_collocate_sep_df<2>
+                          : c == 3 ? k_gpw_collocate_sep_df<3>
+                                   : k_gpw_collocate_sep_df<4>;
+                kern<<<grid, kGpwThreads, 0, s>>>(g->d_tabf, D->npairs, g->lmax, g->N[0], g->N[1], g->N[2], D->d_Dp,
+                                                  lay, g->nsplit, nd, g->npts, add, g->d_part);
+            } else {
+                auto kern = c == 0 ? k_gpw_collocate_sep<0>
+                          : c == 1 ? k_gpw_collocate_sep<1>
+                          : c == 2 ? k_gpw_collocate_sep<2>
+                          : c == 3 ? k_gpw_collocate_sep<3>
+                                   : k_gpw_collocate_sep<4>;
+                kern<<<grid, kGpwThreads, 0, s>>>(g->d_tab, D->npairs, g->lmax, g->N[0], g->N[1], g->N[2], D->d_Dp,
+                                                  lay, g->nsplit, nd, g->npts, add, g->d_part);
+            }
             FTCJ_CUDA(cudaGetLastError());
             add = true;
         }
@@ -895,7 +1076,7 @@ int launch_gpw_j(ftcj_plan* P, int nd, cudaStream_t s) {
     FTCJ_CUDA(cudaGetLastError());
     k_gpw_adj1<<<dim3((unsigned)((g->npts + 255) / 256), nd), 256, 0, s>>>(g->d_t1, g->N[0], g->N[1], g->N[2],
                                                                          g->nlo[0], g->ncnt[0], g->npts, g->gnorm,
-                                                                         g->d_grid);
+                                                                         g->d_grid, g->d_vf);
     FTCJ_CUDA(cudaGetLastError());
     const DdLayout lay = dd_layout(D);
     if (g->sep) {
@@ -903,13 +1084,23 @@ int launch_gpw_j(ftcj_plan* P, int nd, cudaStream_t s) {
             const long long cnt = D->class_start[c + 1] - D->class_start[c];
             if (cnt == 0) continue;
             dim3 grid((unsigned)((cnt + kGpwThreads - 1) / kGpwThreads), nd);
-            auto kern = c == 0 ? k_gpw_integrate_sep<0>
-                      : c == 1 ? k_gpw_integrate_sep<1>
-                      : c == 2 ? k_gpw_integrate_sep<2>
-                      : c == 3 ? k_gpw_integrate_sep<3>
-                               : k_gpw_integrate_sep<4>;
-            kern<<<grid, kGpwThreads, 0, s>>>(g->d_tab, D->npairs, g->lmax, g->N[0], g->N[1], g->N[2], lay, g->d_grid,
-                                              g->npts, D->d_Jp);
+            if (g->df) {
+                auto kern = c == 0 ? k_gpw_integrate_sep_df<0>
+                          : c == 1 ? k_gpw_integrate_sep_df<1>
+                          : c == 2 ? k_gpw_integrate_sep_df<2>
+                          : c == 3 ? k_gpw_integrate_sep_df<3>
+                                   : k_gpw_integrate_sep_df<4>;
+                kern<<<grid, kGpwThreads, 0, s>>>(g->d_tabf, D->npairs, g->lmax, g->N[0], g->N[1], g->N[2], lay,
+                                                  g->d_vf, g->npts, D->d_Jp);
+            } else {
+                auto kern = c == 0 ? k_gpw_integrate_sep<0>
+                          : c == 1 ? k_gpw_integrate_sep<1>
+                          : c == 2 ? k_gpw_integrate_sep<2>
+                          : c == 3 ? k_gpw_integrate_sep<3>
+                                   : k_gpw_integrate_sep<4>;
+                kern<<<grid, kGpwThreads, 0, s>>>(g->d_tab, D->npairs, g->lmax, g->N[0], g->N[1], g->N[2], lay,
+                                                  g->d_grid, g->npts, D->d_Jp);
+            }
             FTCJ_CUDA(cudaGetLastError());
         }
     } else {
@@ -922,7 +1113,7 @@ int launch_gpw_j(ftcj_plan* P, int nd, cudaStream_t s) {
 }
 
 int gpw_grid_dim(const ftcj_plan* P, int axis) { return P->gpw ? P->gpw->N[axis] : 0; }
-int gpw_separable(const ftcj_plan* P) { return P->gpw && P->gpw->sep ? 1 : 0; }
+int gpw_separable(const ftcj_plan* P) { return P->gpw && P->gpw->sep ? (P->gpw->df ? 2 : 1) : 0; }
 
 int gpw_launches(const ftcj_plan* P, int nd) {
     (void)nd;

@@ -65,7 +65,7 @@ def test_classified_orthorhombic_all_classes(orc, F, precision, tol):
     classes 0..4, the separable (per-axis table) collocation and integration."""
     w = W.tiny(seed=7, kmesh=(2, 1, 2), ndens=2)
     info, _, _ = compare(orc, F, w, 0.9, tol, precision=precision)
-    assert info["gpw_separable"] == 1
+    assert info["gpw_separable"] == (2 if precision == 1 else 1)
 
 
 @pytest.mark.parametrize("precision,tol", [(0, J_FP64), (1, J_SPLIT)], ids=["fp64", "split"])
@@ -101,7 +101,7 @@ def test_classified_reduced_crystal_default_cut(orc, F, crystal, precision, cont
     w, ref = crystal
     info, _, _ = compare(orc, F, w, None, tol, ref=ref, precision=precision, contraction=contraction)
     assert abs(info["alpha_cut"] - 0.125) < 1e-15
-    assert info["gpw_separable"] == 1
+    assert info["gpw_separable"] == (2 if precision == 1 else 1)
 
 
 def test_classified_without_diffuse_pairs_is_the_plain_build(F):
