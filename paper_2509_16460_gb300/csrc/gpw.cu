@@ -70,6 +70,7 @@ struct Gpw {
     bool df = false;          // split form: the grid contractions in double-float on the FP32 pipe
     double* d_tab = nullptr;    // [tstride][nrec], the record index fastest
     float2* d_tabf = nullptr;   // the same tables as double-float (hi, lo), split form
+    float2* d_tabfr = nullptr;  // [nrec][tstride]: the double-float tables record by record (collocation)
     float2* d_vf = nullptr;     // [max_dens][npts]: V(r_m) as double-float, split form
     double* d_part = nullptr;   // [nsplit][max_dens][npts]
     double* d_grid = nullptr;   // [max_dens][npts]: rho_D(r_m), then V(r_m)
@@ -130,7 +131,8 @@ __device__ __forceinline__ void centre_frac(const PairDev& pr, const CellConst& 
 
 // One thread per (record, axis, grid index): T_a[i][m] for i <= class.
 __global__ void k_gpw_tables(const PairDev* __restrict__ pairs, long long nrec, int lmax, int N0, int N1, int N2,
-                             Lattice lat, CellConst cc, double* __restrict__ tab, float2* __restrict__ tabf) {
+                             Lattice lat, CellConst cc, double* __restrict__ tab, float2* __restrict__ tabf,
+                             float2* __restrict__ tabfr) {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int Nt = N0 + N1 + N2;
     if (tid >= nrec * Nt) return;
@@ -179,6 +181,7 @@ __global__ void k_gpw_tables(const PairDev* __restrict__ pairs, long long nrec, 
         if (tabf) {
             const float hi = (float)v;
             tabf[e] = make_float2(hi, (float)(v - (double)hi));
+            tabfr[r * ((long long)(lmax + 1) * (N0 + N1 + N2)) + off + (long long)i * n + m] = tabf[e];
         }
         scale *= 1.0 / (2.0 * M_PI);
     }
@@ -259,12 +262,16 @@ __device__ __forceinline__ df ld_df(const float2* p) {
 // k_gpw_collocate_sep, every product and sum an error-free double-float step
 // on the FP32 pipe (D'_ijk split from FP64 with integer operations); the
 // accumulators are renormalised every four records and joined to FP64 once.
+// The tables are read record by record (tabfr), so a warp's T_2[j][m2] and
+// T_3[k][m3] are a few contiguous lines, and the next record's values are
+// loaded while the current one is added.
 template <int L>
-__global__ void __launch_bounds__(kGpwThreads) k_gpw_collocate_sep_df(const float2* __restrict__ tabf, long long nrec,
+__global__ void __launch_bounds__(kGpwThreads) k_gpw_collocate_sep_df(const float2* __restrict__ tabfr, long long nrec,
                                                                      int lmax, int N0, int N1, int N2,
                                                                      const double* __restrict__ Dp, DdLayout lay,
                                                                      int nsplit, int nd, long long npts, bool add,
                                                                      double* __restrict__ part) {
+    constexpr int NT = nterms(L);
     const int d = blockIdx.z, split = blockIdx.y;
     const int lines = N1 * N2;
     const int line = blockIdx.x * kGpwThreads + threadIdx.x;
@@ -272,6 +279,7 @@ __global__ void __launch_bounds__(kGpwThreads) k_gpw_collocate_sep_df(const floa
     const int m2 = line / N2, m3 = line % N2;
     const long long cnt = lay.start[L + 1] - lay.start[L];
     const long long r0 = lay.start[L] + cnt * split / nsplit, r1 = lay.start[L] + cnt * (split + 1) / nsplit;
+    const long long tstride = (long long)(lmax + 1) * (N0 + N1 + N2);
     const long long off1 = (long long)(lmax + 1) * N0, off2 = (long long)(lmax + 1) * (N0 + N1);
     const double* Dd = Dp + (long long)d * lay.total + lay.base[L] - lay.start[L];
     double* out = part + ((long long)split * nd + d) * npts + line;
@@ -281,13 +289,39 @@ __global__ void __launch_bounds__(kGpwThreads) k_gpw_collocate_sep_df(const floa
         df acc[M];
 #pragma unroll
         for (int q = 0; q < M; ++q) acc[q] = df{0.f, 0.f};
-        for (long long r = r0; r < r1; ++r) {
-            df t2[L + 1], t3[L + 1], w[L + 1];
+        // the first record's per-thread values
+        float2 n2[L + 1], n3[L + 1];
+        double nD[NT];
+        if (r0 < r1) {
+            const float2* row = tabfr + r0 * tstride;
 #pragma unroll
             for (int i = 0; i <= L; ++i) {
-                t2[i] = ld_df(tabf + (off1 + (long long)i * N1 + m2) * nrec + r);
-                t3[i] = ld_df(tabf + (off2 + (long long)i * N2 + m3) * nrec + r);
+                n2[i] = __ldg(row + off1 + (long long)i * N1 + m2);
+                n3[i] = __ldg(row + off2 + (long long)i * N2 + m3);
+            }
+#pragma unroll
+            for (int t = 0; t < NT; ++t) nD[t] = __ldg(Dd + (long long)t * cnt + r0);
+        }
+        for (long long r = r0; r < r1; ++r) {
+            df t2[L + 1], t3[L + 1], w[L + 1];
+            double Dv[NT];
+#pragma unroll
+            for (int i = 0; i <= L; ++i) {
+                t2[i] = df{n2[i].x, n2[i].y};
+                t3[i] = df{n3[i].x, n3[i].y};
                 w[i] = df{0.f, 0.f};
+            }
+#pragma unroll
+            for (int t = 0; t < NT; ++t) Dv[t] = nD[t];
+            if (r + 1 < r1) {
+                const float2* row = tabfr + (r + 1) * tstride;
+#pragma unroll
+                for (int i = 0; i <= L; ++i) {
+                    n2[i] = __ldg(row + off1 + (long long)i * N1 + m2);
+                    n3[i] = __ldg(row + off2 + (long long)i * N2 + m3);
+                }
+#pragma unroll
+                for (int t = 0; t < NT; ++t) nD[t] = __ldg(Dd + (long long)t * cnt + r + 1);
             }
             int t = 0;
 #pragma unroll
@@ -296,17 +330,19 @@ __global__ void __launch_bounds__(kGpwThreads) k_gpw_collocate_sep_df(const floa
                 for (int a = lam; a >= 0; --a)
 #pragma unroll
                     for (int b = lam - a; b >= 0; --b, ++t)
-                        w[a] = df_add_u(w[a], df_mul_u(split_double(__ldg(Dd + (long long)t * cnt + r)),
-                                                       df_mul_u(t2[b], t3[lam - a - b])));
+                        w[a] = df_add_u(w[a], df_mul_u(split_double(Dv[t]), df_mul_u(t2[b], t3[lam - a - b])));
 #pragma unroll
             for (int a = 0; a <= L; ++a) w[a] = df_norm(w[a]);
-            const float2* T1 = tabf + (long long)mb * nrec + r;
+            const float2* T1 = tabfr + r * tstride + mb;
 #pragma unroll
             for (int q = 0; q < M; ++q) {
                 if (q < mcnt) {
                     df v = acc[q];
 #pragma unroll
-                    for (int a = 0; a <= L; ++a) v = df_add_u(v, df_mul_u(ld_df(T1 + ((long long)a * N0 + q) * nrec), w[a]));
+                    for (int a = 0; a <= L; ++a) {
+                        const float2 x = __ldg(T1 + (long long)a * N0 + q);
+                        v = df_add_u(v, df_mul_u(df{x.x, x.y}, w[a]));
+                    }
                     acc[q] = v;
                 }
             }
@@ -926,11 +962,11 @@ int setup_gpw(ftcj_plan* P) {
         if (D->class_start[c + 1] > D->class_start[c]) g->lmax = c;
     const long long nrec = D->npairs;
     const int md = P->max_dens;
-    // record splits: about two waves of blocks, at least 8 records a split,
+    // record splits: about four blocks per SM, at least 8 records a split,
     // partial grids within 1 GB
     const long long lines = (long long)g->N[1] * g->N[2];
     const long long blocks = g->sep ? (lines + kGpwThreads - 1) / kGpwThreads : (g->npts + kGpwThreads - 1) / kGpwThreads;
-    long long ns = (2LL * P->num_sms + blocks * md - 1) / (blocks * md);
+    long long ns = (4LL * P->num_sms + blocks * md - 1) / (blocks * md);
     ns = std::min<long long>(ns, std::max<long long>(1, nrec / 8));
     ns = std::min<long long>(ns, std::max<long long>(1, (1LL << 27) / ((long long)md * g->npts)));
     g->nsplit = (int)std::max<long long>(1, std::min<long long>(ns, 65535));
@@ -938,9 +974,10 @@ int setup_gpw(ftcj_plan* P) {
         g->tstride = (long long)(g->lmax + 1) * (g->N[0] + g->N[1] + g->N[2]);
         if ((rc = galloc(P, g, &g->d_tab, (size_t)(g->tstride * nrec)))) return rc;
         if (g->df && (rc = galloc(P, g, &g->d_tabf, (size_t)(g->tstride * nrec)))) return rc;
+        if (g->df && (rc = galloc(P, g, &g->d_tabfr, (size_t)(g->tstride * nrec)))) return rc;
         const long long nt = nrec * (g->N[0] + g->N[1] + g->N[2]);
         k_gpw_tables<<<(unsigned)((nt + 255) / 256), 256>>>(D->d_pairs, nrec, g->lmax, g->N[0], g->N[1], g->N[2],
-                                                            lattice_of(P), P->cc, g->d_tab, g->d_tabf);
+                                                            lattice_of(P), P->cc, g->d_tab, g->d_tabf, g->d_tabfr);
         FTCJ_CUDA(cudaGetLastError());
     }
     if ((rc = galloc(P, g, &g->d_part, (size_t)g->nsplit * md * g->npts))) return rc;
@@ -979,7 +1016,7 @@ int setup_gpw(ftcj_plan* P) {
 void free_gpw(ftcj_plan* P) {
     Gpw* g = P->gpw;
     if (!g) return;
-    void* ptrs[] = {g->d_tab, g->d_tabf, g->d_vf, g->d_part, g->d_grid, g->d_t1, g->d_t2, g->d_rhoD, g->d_WD, g->d_vfr, g->d_Epart,
+    void* ptrs[] = {g->d_tab, g->d_tabf, g->d_tabfr, g->d_vf, g->d_part, g->d_grid, g->d_t1, g->d_t2, g->d_rhoD, g->d_WD, g->d_vfr, g->d_Epart,
                     g->d_cstart, g->d_clist};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1004,7 +1041,7 @@ int launch_gpw_rho(ftcj_plan* P, int nd, cudaStream_t s) {
                           : c == 2 ? k_gpw_collocate_sep_df<2>
                           : c == 3 ? k_gpw_collocate_sep_df<3>
                                    : k_gpw_collocate_sep_df<4>;
-                kern<<<grid, kGpwThreads, 0, s>>>(g->d_tabf, D->npairs, g->lmax, g->N[0], g->N[1], g->N[2], D->d_Dp,
+                kern<<<grid, kGpwThreads, 0, s>>>(g->d_tabfr, D->npairs, g->lmax, g->N[0], g->N[1], g->N[2], D->d_Dp,
                                                   lay, g->nsplit, nd, g->npts, add, g->d_part);
             } else {
                 auto kern = c == 0 ? k_gpw_collocate_sep<0>
