@@ -80,6 +80,7 @@ struct Gpw {
     double2* d_WD = nullptr;    // [max_dens][ng_half]
     double* d_vfr = nullptr;    // [ng_half]
     double* d_Epart = nullptr;  // [max_dens][nEb]
+    double2* d_tw = nullptr;    // e^{-2 pi i k / N_a} for k < N_a, the three axes one after the other
     int* d_cstart = nullptr;    // [ncnt0 ncnt1 + 1]: the half sphere's points by (n1, n2)
     int* d_clist = nullptr;     // [ng_half]
     int nEb = 0;
@@ -104,14 +105,23 @@ struct Lattice {
     double bn[3];   // |b_i| / (2 pi)
 };
 
-__device__ __forceinline__ void twiddle(long long k, int n, double& c, double& s) {
-    // exp(-2 pi i k / n), k reduced into [0, n) exactly
+// exp(-2 pi i k / n) from the axis's table, k reduced into [0, n) exactly
+__device__ __forceinline__ void twiddle(const double2* __restrict__ tw, long long k, int n, double& c, double& s) {
     long long r = k % n;
     if (r < 0) r += n;
+    const double2 v = __ldg(tw + r);
+    c = v.x;
+    s = v.y;
+}
+
+__global__ void k_gpw_twiddles(int N0, int N1, int N2, double2* __restrict__ tw) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N0 + N1 + N2) return;
+    const int n = k < N0 ? N0 : (k < N0 + N1 ? N1 : N2);
+    const int j = k < N0 ? k : (k < N0 + N1 ? k - N0 : k - N0 - N1);
     double sn, cs;
-    sincospi(2.0 * (double)r / (double)n, &sn, &cs);
-    c = cs;
-    s = -sn;
+    sincospi(2.0 * (double)j / (double)n, &sn, &cs);
+    tw[k] = make_double2(cs, -sn);
 }
 
 __device__ __forceinline__ int rec_class(const DdLayout& lay, long long r) {
@@ -458,8 +468,8 @@ __global__ void k_gpw_reduce(const double* __restrict__ part, int nsplit, int nd
 // ---- grid <-> sphere transforms ---------------------------------------------
 
 // pass 1: t1[n1][m2][m3] = sum_m1 rho(m1, m2, m3) e^{-2 pi i n1 m1 / N0}
-__global__ void k_gpw_dft1(const double* __restrict__ grid, int N0, int N1, int N2, int nlo0, int ncnt0,
-                           long long npts, double2* __restrict__ t1) {
+__global__ void k_gpw_dft1(const double* __restrict__ grid, const double2* __restrict__ tw, int N0, int N1, int N2,
+                           int nlo0, int ncnt0, long long npts, double2* __restrict__ t1) {
     const int d = blockIdx.y;
     const long long lines = (long long)N1 * N2;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -470,7 +480,7 @@ __global__ void k_gpw_dft1(const double* __restrict__ grid, int N0, int N1, int 
     double re = 0.0, im = 0.0;
     for (int m1 = 0; m1 < N0; ++m1) {
         double c, s;
-        twiddle((long long)n1 * m1, N0, c, s);
+        twiddle(tw, (long long)n1 * m1, N0, c, s);
         const double v = src[(long long)m1 * lines];
         re = fma(v, c, re);
         im = fma(v, s, im);
@@ -479,8 +489,8 @@ __global__ void k_gpw_dft1(const double* __restrict__ grid, int N0, int N1, int 
 }
 
 // pass 2: t2[n1][n2][m3] = sum_m2 t1[n1][m2][m3] e^{-2 pi i n2 m2 / N1}
-__global__ void k_gpw_dft2(const double2* __restrict__ t1, int N1, int N2, int ncnt0, int nlo1, int ncnt1,
-                           double2* __restrict__ t2) {
+__global__ void k_gpw_dft2(const double2* __restrict__ t1, const double2* __restrict__ tw, int N1, int N2, int ncnt0,
+                           int nlo1, int ncnt1, double2* __restrict__ t2) {
     const int d = blockIdx.y;
     const long long total = (long long)ncnt0 * ncnt1 * N2;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -492,7 +502,7 @@ __global__ void k_gpw_dft2(const double2* __restrict__ t1, int N1, int N2, int n
     double re = 0.0, im = 0.0;
     for (int m2 = 0; m2 < N1; ++m2) {
         double c, s;
-        twiddle((long long)n2 * m2, N1, c, s);
+        twiddle(tw, (long long)n2 * m2, N1, c, s);
         const double2 v = src[(long long)m2 * N2];
         re += v.x * c - v.y * s;
         im += v.x * s + v.y * c;
@@ -501,8 +511,9 @@ __global__ void k_gpw_dft2(const double2* __restrict__ t1, int N1, int N2, int n
 }
 
 // pass 3: rho_D(G_p) = (Omega/N) sum_m3 t2[n1][n2][m3] e^{-2 pi i n3 m3 / N2}
-__global__ void k_gpw_dft3(const double2* __restrict__ t2, const int* __restrict__ gvec, long long ng, int N2,
-                           int nlo0, int ncnt0, int nlo1, int ncnt1, double gnorm, double2* __restrict__ rho) {
+__global__ void k_gpw_dft3(const double2* __restrict__ t2, const double2* __restrict__ tw, const int* __restrict__ gvec,
+                           long long ng, int N2, int nlo0, int ncnt0, int nlo1, int ncnt1, double gnorm,
+                           double2* __restrict__ rho) {
     const int d = blockIdx.y;
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= ng) return;
@@ -511,7 +522,7 @@ __global__ void k_gpw_dft3(const double2* __restrict__ t2, const int* __restrict
     double re = 0.0, im = 0.0;
     for (int m3 = 0; m3 < N2; ++m3) {
         double c, s;
-        twiddle((long long)n3 * m3, N2, c, s);
+        twiddle(tw, (long long)n3 * m3, N2, c, s);
         const double2 v = src[m3];
         re += v.x * c - v.y * s;
         im += v.x * s + v.y * c;
@@ -571,9 +582,9 @@ __global__ void k_gpw_vfr(const int* __restrict__ gvec, long long n, CellConst c
 // ---- adjoint passes: V(r_m) = (Omega/N) Re sum_half W_D(G) e^{-iG.r_m} -----------
 
 // pass 3^T: u2[n1][n2][m3] = sum over the points of (n1, n2) of W_D e^{-2 pi i n3 m3 / N2}
-__global__ void k_gpw_adj3(const double2* __restrict__ WD, const int* __restrict__ gvec, long long ng,
-                           const int* __restrict__ cstart, const int* __restrict__ clist, int N2, int ncnt0, int ncnt1,
-                           double2* __restrict__ u2) {
+__global__ void k_gpw_adj3(const double2* __restrict__ WD, const double2* __restrict__ tw, const int* __restrict__ gvec,
+                           long long ng, const int* __restrict__ cstart, const int* __restrict__ clist, int N2,
+                           int ncnt0, int ncnt1, double2* __restrict__ u2) {
     const int d = blockIdx.y;
     const long long total = (long long)ncnt0 * ncnt1 * N2;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -584,7 +595,7 @@ __global__ void k_gpw_adj3(const double2* __restrict__ WD, const int* __restrict
     for (int k = cstart[cell]; k < cstart[cell + 1]; ++k) {
         const int p = clist[k];
         double c, s;
-        twiddle((long long)gvec[3 * p + 2] * m3, N2, c, s);
+        twiddle(tw, (long long)gvec[3 * p + 2] * m3, N2, c, s);
         const double2 w = WD[(long long)d * ng + p];
         re += w.x * c - w.y * s;
         im += w.x * s + w.y * c;
@@ -593,8 +604,8 @@ __global__ void k_gpw_adj3(const double2* __restrict__ WD, const int* __restrict
 }
 
 // pass 2^T: u1[n1][m2][m3] = sum_n2 u2[n1][n2][m3] e^{-2 pi i n2 m2 / N1}
-__global__ void k_gpw_adj2(const double2* __restrict__ u2, int N1, int N2, int ncnt0, int nlo1, int ncnt1,
-                           double2* __restrict__ u1) {
+__global__ void k_gpw_adj2(const double2* __restrict__ u2, const double2* __restrict__ tw, int N1, int N2, int ncnt0,
+                           int nlo1, int ncnt1, double2* __restrict__ u1) {
     const int d = blockIdx.y;
     const long long total = (long long)ncnt0 * N1 * N2;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -604,7 +615,7 @@ __global__ void k_gpw_adj2(const double2* __restrict__ u2, int N1, int N2, int n
     double re = 0.0, im = 0.0;
     for (int n2i = 0; n2i < ncnt1; ++n2i) {
         double c, s;
-        twiddle((long long)(nlo1 + n2i) * m2, N1, c, s);
+        twiddle(tw, (long long)(nlo1 + n2i) * m2, N1, c, s);
         const double2 v = src[(long long)n2i * N2];
         re += v.x * c - v.y * s;
         im += v.x * s + v.y * c;
@@ -613,8 +624,9 @@ __global__ void k_gpw_adj2(const double2* __restrict__ u2, int N1, int N2, int n
 }
 
 // pass 1^T: V[m1][m2][m3] = (Omega/N) Re sum_n1 u1[n1][m2][m3] e^{-2 pi i n1 m1 / N0}
-__global__ void k_gpw_adj1(const double2* __restrict__ u1, int N0, int N1, int N2, int nlo0, int ncnt0,
-                           long long npts, double gnorm, double* __restrict__ V, float2* __restrict__ Vf) {
+__global__ void k_gpw_adj1(const double2* __restrict__ u1, const double2* __restrict__ tw, int N0, int N1, int N2,
+                           int nlo0, int ncnt0, long long npts, double gnorm, double* __restrict__ V,
+                           float2* __restrict__ Vf) {
     const int d = blockIdx.y;
     const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= npts) return;
@@ -625,7 +637,7 @@ __global__ void k_gpw_adj1(const double2* __restrict__ u1, int N0, int N1, int N
     double re = 0.0;
     for (int n1i = 0; n1i < ncnt0; ++n1i) {
         double c, s;
-        twiddle((long long)(nlo0 + n1i) * m1, N0, c, s);
+        twiddle(tw, (long long)(nlo0 + n1i) * m1, N0, c, s);
         const double2 v = src[(long long)n1i * lines];
         re += v.x * c - v.y * s;
     }
@@ -980,6 +992,9 @@ int setup_gpw(ftcj_plan* P) {
                                                             lattice_of(P), P->cc, g->d_tab, g->d_tabf, g->d_tabfr);
         FTCJ_CUDA(cudaGetLastError());
     }
+    if ((rc = galloc(P, g, &g->d_tw, (size_t)(g->N[0] + g->N[1] + g->N[2])))) return rc;
+    k_gpw_twiddles<<<(unsigned)((g->N[0] + g->N[1] + g->N[2] + 255) / 256), 256>>>(g->N[0], g->N[1], g->N[2], g->d_tw);
+    FTCJ_CUDA(cudaGetLastError());
     if ((rc = galloc(P, g, &g->d_part, (size_t)g->nsplit * md * g->npts))) return rc;
     if ((rc = galloc(P, g, &g->d_grid, (size_t)md * g->npts))) return rc;
     if (g->df && (rc = galloc(P, g, &g->d_vf, (size_t)md * g->npts))) return rc;
@@ -1016,7 +1031,7 @@ int setup_gpw(ftcj_plan* P) {
 void free_gpw(ftcj_plan* P) {
     Gpw* g = P->gpw;
     if (!g) return;
-    void* ptrs[] = {g->d_tab, g->d_tabf, g->d_tabfr, g->d_vf, g->d_part, g->d_grid, g->d_t1, g->d_t2, g->d_rhoD, g->d_WD, g->d_vfr, g->d_Epart,
+    void* ptrs[] = {g->d_tab, g->d_tabf, g->d_tabfr, g->d_vf, g->d_tw, g->d_part, g->d_grid, g->d_t1, g->d_t2, g->d_rhoD, g->d_WD, g->d_vfr, g->d_Epart,
                     g->d_cstart, g->d_clist};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1065,15 +1080,16 @@ int launch_gpw_rho(ftcj_plan* P, int nd, cudaStream_t s) {
                                                                            g->d_grid);
     FTCJ_CUDA(cudaGetLastError());
     const long long n1 = (long long)g->ncnt[0] * lines;
-    k_gpw_dft1<<<dim3((unsigned)((n1 + 255) / 256), nd), 256, 0, s>>>(g->d_grid, g->N[0], g->N[1], g->N[2], g->nlo[0],
-                                                                    g->ncnt[0], g->npts, g->d_t1);
+    k_gpw_dft1<<<dim3((unsigned)((n1 + 255) / 256), nd), 256, 0, s>>>(g->d_grid, g->d_tw, g->N[0], g->N[1], g->N[2],
+                                                                    g->nlo[0], g->ncnt[0], g->npts, g->d_t1);
     FTCJ_CUDA(cudaGetLastError());
     const long long n2 = (long long)g->ncnt[0] * g->ncnt[1] * g->N[2];
-    k_gpw_dft2<<<dim3((unsigned)((n2 + 255) / 256), nd), 256, 0, s>>>(g->d_t1, g->N[1], g->N[2], g->ncnt[0], g->nlo[1],
-                                                                    g->ncnt[1], g->d_t2);
+    k_gpw_dft2<<<dim3((unsigned)((n2 + 255) / 256), nd), 256, 0, s>>>(g->d_t1, g->d_tw + g->N[0], g->N[1], g->N[2],
+                                                                    g->ncnt[0], g->nlo[1], g->ncnt[1], g->d_t2);
     FTCJ_CUDA(cudaGetLastError());
     k_gpw_dft3<<<dim3((unsigned)((P->ng_half + 255) / 256), nd), 256, 0, s>>>(
-        g->d_t2, P->d_gvec, P->ng_half, g->N[2], g->nlo[0], g->ncnt[0], g->nlo[1], g->ncnt[1], g->gnorm, g->d_rhoD);
+        g->d_t2, g->d_tw + g->N[0] + g->N[1], P->d_gvec, P->ng_half, g->N[2], g->nlo[0], g->ncnt[0], g->nlo[1],
+        g->ncnt[1], g->gnorm, g->d_rhoD);
     FTCJ_CUDA(cudaGetLastError());
     return FTCJ_OK;
 }
@@ -1103,15 +1119,15 @@ int launch_gpw_j(ftcj_plan* P, int nd, cudaStream_t s) {
     }
     const long long lines = (long long)g->N[1] * g->N[2];
     const long long n2 = (long long)g->ncnt[0] * g->ncnt[1] * g->N[2];
-    k_gpw_adj3<<<dim3((unsigned)((n2 + 255) / 256), nd), 256, 0, s>>>(g->d_WD, P->d_gvec, P->ng_half, g->d_cstart,
-                                                                    g->d_clist, g->N[2], g->ncnt[0], g->ncnt[1],
-                                                                    g->d_t2);
+    k_gpw_adj3<<<dim3((unsigned)((n2 + 255) / 256), nd), 256, 0, s>>>(g->d_WD, g->d_tw + g->N[0] + g->N[1], P->d_gvec,
+                                                                    P->ng_half, g->d_cstart, g->d_clist, g->N[2],
+                                                                    g->ncnt[0], g->ncnt[1], g->d_t2);
     FTCJ_CUDA(cudaGetLastError());
     const long long n1 = (long long)g->ncnt[0] * lines;
-    k_gpw_adj2<<<dim3((unsigned)((n1 + 255) / 256), nd), 256, 0, s>>>(g->d_t2, g->N[1], g->N[2], g->ncnt[0], g->nlo[1],
-                                                                    g->ncnt[1], g->d_t1);
+    k_gpw_adj2<<<dim3((unsigned)((n1 + 255) / 256), nd), 256, 0, s>>>(g->d_t2, g->d_tw + g->N[0], g->N[1], g->N[2],
+                                                                    g->ncnt[0], g->nlo[1], g->ncnt[1], g->d_t1);
     FTCJ_CUDA(cudaGetLastError());
-    k_gpw_adj1<<<dim3((unsigned)((g->npts + 255) / 256), nd), 256, 0, s>>>(g->d_t1, g->N[0], g->N[1], g->N[2],
+    k_gpw_adj1<<<dim3((unsigned)((g->npts + 255) / 256), nd), 256, 0, s>>>(g->d_t1, g->d_tw, g->N[0], g->N[1], g->N[2],
                                                                          g->nlo[0], g->ncnt[0], g->npts, g->gnorm,
                                                                          g->d_grid, g->d_vf);
     FTCJ_CUDA(cudaGetLastError());
