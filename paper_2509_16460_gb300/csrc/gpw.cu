@@ -81,6 +81,8 @@ struct Gpw {
     double* d_vfr = nullptr;    // [ng_half]
     double* d_Epart = nullptr;  // [max_dens][nEb]
     double2* d_tw = nullptr;    // e^{-2 pi i k / N_a} for k < N_a, the three axes one after the other
+    int nsj = 1;                // splits of the m2 rows in the integration (partial J' summed in order)
+    double* d_jpart = nullptr;  // [nsj][max_dens][total_terms of the DD records]
     int* d_cstart = nullptr;    // [ncnt0 ncnt1 + 1]: the half sphere's points by (n1, n2)
     int* d_clist = nullptr;     // [ng_half]
     int nEb = 0;
@@ -272,9 +274,13 @@ __device__ __forceinline__ df ld_df(const float2* p) {
 // k_gpw_collocate_sep, every product and sum an error-free double-float step
 // on the FP32 pipe (D'_ijk split from FP64 with integer operations); the
 // accumulators are renormalised every four records and joined to FP64 once.
-// The tables are read record by record (tabfr), so a warp's T_2[j][m2] and
-// T_3[k][m3] are a few contiguous lines, and the next record's values are
-// loaded while the current one is added.
+// The block stages the T_1 rows and D' terms of 32 records at a time in
+// shared memory (one coalesced load per chunk instead of a dependent load per
+// record); each thread reads its T_2[j][m2] and T_3[k][m3] from the
+// record-major tables (tabfr), a few contiguous lines per warp, loading the
+// next record's while the current one is added.
+constexpr int kColChunk = 32;
+
 template <int L>
 __global__ void __launch_bounds__(kGpwThreads) k_gpw_collocate_sep_df(const float2* __restrict__ tabfr, long long nrec,
                                                                      int lmax, int N0, int N1, int N2,
@@ -282,26 +288,26 @@ __global__ void __launch_bounds__(kGpwThreads) k_gpw_collocate_sep_df(const floa
                                                                      int nsplit, int nd, long long npts, bool add,
                                                                      double* __restrict__ part) {
     constexpr int NT = nterms(L);
+    constexpr int M = L == 0 ? kM1 : (L <= 2 ? kM1 / 2 : kM1 / 4);
+    __shared__ float2 sT1[kColChunk][L + 1][M];
+    __shared__ double sD[kColChunk][NT];
     const int d = blockIdx.z, split = blockIdx.y;
     const int lines = N1 * N2;
     const int line = blockIdx.x * kGpwThreads + threadIdx.x;
-    if (line >= lines) return;
-    const int m2 = line / N2, m3 = line % N2;
+    const bool live = line < lines;
+    const int m2 = live ? line / N2 : 0, m3 = live ? line % N2 : 0;
     const long long cnt = lay.start[L + 1] - lay.start[L];
     const long long r0 = lay.start[L] + cnt * split / nsplit, r1 = lay.start[L] + cnt * (split + 1) / nsplit;
     const long long tstride = (long long)(lmax + 1) * (N0 + N1 + N2);
     const long long off1 = (long long)(lmax + 1) * N0, off2 = (long long)(lmax + 1) * (N0 + N1);
     const double* Dd = Dp + (long long)d * lay.total + lay.base[L] - lay.start[L];
     double* out = part + ((long long)split * nd + d) * npts + line;
-    constexpr int M = L == 0 ? kM1 : (L <= 2 ? kM1 / 2 : kM1 / 4);
     for (int mb = 0; mb < N0; mb += M) {
         const int mcnt = min(M, N0 - mb);
         df acc[M];
 #pragma unroll
         for (int q = 0; q < M; ++q) acc[q] = df{0.f, 0.f};
-        // the first record's per-thread values
         float2 n2[L + 1], n3[L + 1];
-        double nD[NT];
         if (r0 < r1) {
             const float2* row = tabfr + r0 * tstride;
 #pragma unroll
@@ -309,65 +315,72 @@ __global__ void __launch_bounds__(kGpwThreads) k_gpw_collocate_sep_df(const floa
                 n2[i] = __ldg(row + off1 + (long long)i * N1 + m2);
                 n3[i] = __ldg(row + off2 + (long long)i * N2 + m3);
             }
-#pragma unroll
-            for (int t = 0; t < NT; ++t) nD[t] = __ldg(Dd + (long long)t * cnt + r0);
         }
-        for (long long r = r0; r < r1; ++r) {
-            df t2[L + 1], t3[L + 1], w[L + 1];
-            double Dv[NT];
-#pragma unroll
-            for (int i = 0; i <= L; ++i) {
-                t2[i] = df{n2[i].x, n2[i].y};
-                t3[i] = df{n3[i].x, n3[i].y};
-                w[i] = df{0.f, 0.f};
+        for (long long c0 = r0; c0 < r1; c0 += kColChunk) {
+            const int kc = (int)min((long long)kColChunk, r1 - c0);
+            __syncthreads();  // the previous chunk is consumed
+            for (int e = threadIdx.x; e < kc * (L + 1) * M; e += kGpwThreads) {
+                const int rec = e / ((L + 1) * M), a = (e / M) % (L + 1), q = e % M;
+                sT1[rec][a][q] = q < mcnt ? __ldg(tabfr + (c0 + rec) * tstride + (long long)a * N0 + mb + q)
+                                          : make_float2(0.f, 0.f);
             }
-#pragma unroll
-            for (int t = 0; t < NT; ++t) Dv[t] = nD[t];
-            if (r + 1 < r1) {
-                const float2* row = tabfr + (r + 1) * tstride;
+            for (int e = threadIdx.x; e < kc * NT; e += kGpwThreads) {
+                const int rec = e / NT, t = e % NT;
+                sD[rec][t] = __ldg(Dd + (long long)t * cnt + c0 + rec);
+            }
+            __syncthreads();
+            for (int rec = 0; rec < kc; ++rec) {
+                const long long r = c0 + rec;
+                df t2[L + 1], t3[L + 1], w[L + 1];
 #pragma unroll
                 for (int i = 0; i <= L; ++i) {
-                    n2[i] = __ldg(row + off1 + (long long)i * N1 + m2);
-                    n3[i] = __ldg(row + off2 + (long long)i * N2 + m3);
+                    t2[i] = df{n2[i].x, n2[i].y};
+                    t3[i] = df{n3[i].x, n3[i].y};
+                    w[i] = df{0.f, 0.f};
                 }
+                if (r + 1 < r1) {
+                    const float2* row = tabfr + (r + 1) * tstride;
 #pragma unroll
-                for (int t = 0; t < NT; ++t) nD[t] = __ldg(Dd + (long long)t * cnt + r + 1);
-            }
-            int t = 0;
+                    for (int i = 0; i <= L; ++i) {
+                        n2[i] = __ldg(row + off1 + (long long)i * N1 + m2);
+                        n3[i] = __ldg(row + off2 + (long long)i * N2 + m3);
+                    }
+                }
+                int t = 0;
 #pragma unroll
-            for (int lam = 0; lam <= L; ++lam)
+                for (int lam = 0; lam <= L; ++lam)
 #pragma unroll
-                for (int a = lam; a >= 0; --a)
+                    for (int a = lam; a >= 0; --a)
 #pragma unroll
-                    for (int b = lam - a; b >= 0; --b, ++t)
-                        w[a] = df_add_u(w[a], df_mul_u(split_double(Dv[t]), df_mul_u(t2[b], t3[lam - a - b])));
+                        for (int b = lam - a; b >= 0; --b, ++t)
+                            w[a] = df_add_u(w[a], df_mul_u(split_double(sD[rec][t]), df_mul_u(t2[b], t3[lam - a - b])));
 #pragma unroll
-            for (int a = 0; a <= L; ++a) w[a] = df_norm(w[a]);
-            const float2* T1 = tabfr + r * tstride + mb;
+                for (int a = 0; a <= L; ++a) w[a] = df_norm(w[a]);
 #pragma unroll
-            for (int q = 0; q < M; ++q) {
-                if (q < mcnt) {
+                for (int q = 0; q < M; ++q) {
                     df v = acc[q];
 #pragma unroll
                     for (int a = 0; a <= L; ++a) {
-                        const float2 x = __ldg(T1 + (long long)a * N0 + q);
+                        const float2 x = sT1[rec][a][q];
                         v = df_add_u(v, df_mul_u(df{x.x, x.y}, w[a]));
                     }
                     acc[q] = v;
                 }
-            }
-            if (((r - r0) & 3) == 3) {
+                if ((rec & 3) == 3) {
 #pragma unroll
-                for (int q = 0; q < M; ++q) acc[q] = df_norm(acc[q]);
+                    for (int q = 0; q < M; ++q) acc[q] = df_norm(acc[q]);
+                }
             }
         }
+        if (live) {
 #pragma unroll
-        for (int q = 0; q < M; ++q)
-            if (q < mcnt) {
-                double* o = out + (long long)(mb + q) * lines;
-                const double v = join_df(df_norm(acc[q]));
-                *o = add ? *o + v : v;
-            }
+            for (int q = 0; q < M; ++q)
+                if (q < mcnt) {
+                    double* o = out + (long long)(mb + q) * lines;
+                    const double v = join_df(df_norm(acc[q]));
+                    *o = add ? *o + v : v;
+                }
+        }
     }
 }
 
@@ -660,7 +673,8 @@ __global__ void __launch_bounds__(kGpwThreads) k_gpw_integrate_sep(const double*
                                                                   const double* __restrict__ V, long long npts,
                                                                   double* __restrict__ Jp) {
     constexpr int NT = nterms(L);
-    const int d = blockIdx.y;
+    const int d = blockIdx.y, sj = blockIdx.z, nsj = gridDim.z;
+    const int m2lo = N1 * sj / nsj, m2hi = N1 * (sj + 1) / nsj;
     const long long loc = (long long)blockIdx.x * kGpwThreads + threadIdx.x;
     const long long cnt = lay.start[L + 1] - lay.start[L];
     if (loc >= cnt) return;
@@ -671,7 +685,7 @@ __global__ void __launch_bounds__(kGpwThreads) k_gpw_integrate_sep(const double*
     double J[NT];
 #pragma unroll
     for (int t = 0; t < NT; ++t) J[t] = 0.0;
-    for (int m2 = 0; m2 < N1; ++m2) {
+    for (int m2 = m2lo; m2 < m2hi; ++m2) {
         double t2[L + 1];
 #pragma unroll
         for (int j = 0; j <= L; ++j) t2[j] = __ldg(tab + (off1 + (long long)j * N1 + m2) * nrec + r);
@@ -697,8 +711,9 @@ __global__ void __launch_bounds__(kGpwThreads) k_gpw_integrate_sep(const double*
                     for (int j = lam - i; j >= 0; --j, ++t) J[t] = fma(a[i], t2[j] * t3[lam - i - j], J[t]);
         }
     }
+    double* out = Jp + ((long long)sj * gridDim.y + d) * lay.total + lay.base[L] + loc;
 #pragma unroll
-    for (int t = 0; t < NT; ++t) Jp[(long long)d * lay.total + lay.base[L] + (long long)t * cnt + loc] = J[t];
+    for (int t = 0; t < NT; ++t) out[(long long)t * cnt] = J[t];
 }
 
 // The separable integration in double-float (split form): per grid line
@@ -712,7 +727,8 @@ __global__ void __launch_bounds__(kGpwThreads) k_gpw_integrate_sep_df(const floa
                                                                      double* __restrict__ Jp) {
     constexpr int NT = nterms(L);
     constexpr int R = 32;  // T_1 entries a class-0 thread keeps in registers
-    const int d = blockIdx.y;
+    const int d = blockIdx.y, sj = blockIdx.z, nsj = gridDim.z;
+    const int m2lo = N1 * sj / nsj, m2hi = N1 * (sj + 1) / nsj;
     const long long loc = (long long)blockIdx.x * kGpwThreads + threadIdx.x;
     const long long cnt = lay.start[L + 1] - lay.start[L];
     if (loc >= cnt) return;
@@ -729,7 +745,7 @@ __global__ void __launch_bounds__(kGpwThreads) k_gpw_integrate_sep_df(const floa
     df J[NT];
 #pragma unroll
     for (int t = 0; t < NT; ++t) J[t] = df{0.f, 0.f};
-    for (int m2 = 0; m2 < N1; ++m2) {
+    for (int m2 = m2lo; m2 < m2hi; ++m2) {
         df t2[L + 1];
 #pragma unroll
         for (int j = 0; j <= L; ++j) t2[j] = ld_df(tabf + (off1 + (long long)j * N1 + m2) * nrec + r);
@@ -771,8 +787,19 @@ __global__ void __launch_bounds__(kGpwThreads) k_gpw_integrate_sep_df(const floa
                         J[t] = df_norm(df_add_u(J[t], df_mul_u(df_norm(a[i]), df_mul_u(t2[j], t3[lam - i - j]))));
         }
     }
+    double* out = Jp + ((long long)sj * gridDim.y + d) * lay.total + lay.base[L] + loc;
 #pragma unroll
-    for (int t = 0; t < NT; ++t) Jp[(long long)d * lay.total + lay.base[L] + (long long)t * cnt + loc] = join_df(J[t]);
+    for (int t = 0; t < NT; ++t) out[(long long)t * cnt] = join_df(J[t]);
+}
+
+// J'_t = the partial sums of the m2 splits, in split order
+__global__ void k_gpw_jsum(const double* __restrict__ part, int nsj, int nd, long long total, double* __restrict__ Jp) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int d = blockIdx.y;
+    if (e >= total) return;
+    double v = 0.0;
+    for (int q = 0; q < nsj; ++q) v += part[((long long)q * nd + d) * total + e];
+    Jp[(long long)d * total + e] = v;
 }
 
 // General cell: one thread per record, every grid point and lattice image in reach.
@@ -992,6 +1019,12 @@ int setup_gpw(ftcj_plan* P) {
                                                             lattice_of(P), P->cc, g->d_tab, g->d_tabf, g->d_tabfr);
         FTCJ_CUDA(cudaGetLastError());
     }
+    if (g->sep) {
+        // row splits of the integration: about four blocks per SM
+        const long long rb = (nrec + kGpwThreads - 1) / kGpwThreads;
+        g->nsj = (int)std::max<long long>(1, std::min<long long>(g->N[1], (4LL * P->num_sms + rb * md - 1) / (rb * md)));
+        if ((rc = galloc(P, g, &g->d_jpart, (size_t)g->nsj * md * D->total_terms))) return rc;
+    }
     if ((rc = galloc(P, g, &g->d_tw, (size_t)(g->N[0] + g->N[1] + g->N[2])))) return rc;
     k_gpw_twiddles<<<(unsigned)((g->N[0] + g->N[1] + g->N[2] + 255) / 256), 256>>>(g->N[0], g->N[1], g->N[2], g->d_tw);
     FTCJ_CUDA(cudaGetLastError());
@@ -1031,7 +1064,7 @@ int setup_gpw(ftcj_plan* P) {
 void free_gpw(ftcj_plan* P) {
     Gpw* g = P->gpw;
     if (!g) return;
-    void* ptrs[] = {g->d_tab, g->d_tabf, g->d_tabfr, g->d_vf, g->d_tw, g->d_part, g->d_grid, g->d_t1, g->d_t2, g->d_rhoD, g->d_WD, g->d_vfr, g->d_Epart,
+    void* ptrs[] = {g->d_tab, g->d_tabf, g->d_tabfr, g->d_vf, g->d_tw, g->d_jpart, g->d_part, g->d_grid, g->d_t1, g->d_t2, g->d_rhoD, g->d_WD, g->d_vfr, g->d_Epart,
                     g->d_cstart, g->d_clist};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1136,7 +1169,7 @@ int launch_gpw_j(ftcj_plan* P, int nd, cudaStream_t s) {
         for (int c = 0; c < kNclass; ++c) {
             const long long cnt = D->class_start[c + 1] - D->class_start[c];
             if (cnt == 0) continue;
-            dim3 grid((unsigned)((cnt + kGpwThreads - 1) / kGpwThreads), nd);
+            dim3 grid((unsigned)((cnt + kGpwThreads - 1) / kGpwThreads), nd, g->nsj);
             if (g->df) {
                 auto kern = c == 0 ? k_gpw_integrate_sep_df<0>
                           : c == 1 ? k_gpw_integrate_sep_df<1>
@@ -1144,7 +1177,7 @@ int launch_gpw_j(ftcj_plan* P, int nd, cudaStream_t s) {
                           : c == 3 ? k_gpw_integrate_sep_df<3>
                                    : k_gpw_integrate_sep_df<4>;
                 kern<<<grid, kGpwThreads, 0, s>>>(g->d_tabf, D->npairs, g->lmax, g->N[0], g->N[1], g->N[2], lay,
-                                                  g->d_vf, g->npts, D->d_Jp);
+                                                  g->d_vf, g->npts, g->d_jpart);
             } else {
                 auto kern = c == 0 ? k_gpw_integrate_sep<0>
                           : c == 1 ? k_gpw_integrate_sep<1>
@@ -1152,10 +1185,13 @@ int launch_gpw_j(ftcj_plan* P, int nd, cudaStream_t s) {
                           : c == 3 ? k_gpw_integrate_sep<3>
                                    : k_gpw_integrate_sep<4>;
                 kern<<<grid, kGpwThreads, 0, s>>>(g->d_tab, D->npairs, g->lmax, g->N[0], g->N[1], g->N[2], lay,
-                                                  g->d_grid, g->npts, D->d_Jp);
+                                                  g->d_grid, g->npts, g->d_jpart);
             }
             FTCJ_CUDA(cudaGetLastError());
         }
+        k_gpw_jsum<<<dim3((unsigned)((D->total_terms + 255) / 256), nd), 256, 0, s>>>(g->d_jpart, g->nsj, nd,
+                                                                                      D->total_terms, D->d_Jp);
+        FTCJ_CUDA(cudaGetLastError());
     } else {
         dim3 grid((unsigned)((D->npairs + kGpwThreads - 1) / kGpwThreads), nd);
         k_gpw_integrate_gen<<<grid, kGpwThreads, 0, s>>>(D->d_pairs, D->npairs, g->N[0], g->N[1], g->N[2], lay,
@@ -1178,10 +1214,11 @@ int gpw_launches(const ftcj_plan* P, int nd) {
     } else {
         integ = 1;
     }
-    // collocation and integration (per class present in the separable form),
-    // reduction, three passes, potential and energy, three adjoint passes, and
-    // the DD records' a3 and a7 maps
-    return integ + 1 + 3 + 2 + 3 + integ + 2;
+    // collocation and integration (per class present in the separable form,
+    // whose integration adds the sum of its row splits), reduction, three
+    // passes, potential and energy, three adjoint passes, and the DD records'
+    // a3 and a7 maps
+    return integ + 1 + 3 + 2 + 3 + integ + (g->sep ? 1 : 0) + 2;
 }
 
 }  // namespace ftcj
