@@ -627,20 +627,24 @@ def gpw_leg(ctx, forms=("split_tc", "fp64")):
         # collocation and integration: 2 (L + 1) flops per DD record, grid point and density each
         flops = sum(2.0 * (c + 1) * n for c, n in enumerate(info["dd_pairs_by_class"])) * npts * w.ndens * 2
         gpw_ms = ph["gpw_rho"] + ph["gpw_j"]
-        peak = ctx["peaks"]["fp64"]
+        # the split form runs the two grid contractions in double-float on the FP32 pipe
+        dfp = info["gpw_separable"] == 2
+        peak = ctx["peaks"]["split" if dfp else "fp64"]
         r = {"ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT,
              "dd_records": info["dd_pairs"], "dd_ordered_pairs": info["dd_pairs_ordered"],
              "dd_records_by_class": info["dd_pairs_by_class"], "compact_records": info["npairs"],
              "alpha_cut": info["alpha_cut"], "gpw_grid": info["gpw_grid"], "gpw_separable": info["gpw_separable"],
              "gpw_launches": info["gpw_launches"], "phase_ms_per_step": ph, "gpw_ms_per_step": gpw_ms,
              "gpw_share": gpw_ms / ms,
-             "gpw_roofline": {"bound": "alu", "pipe": "fp64", "achieved": flops / (gpw_ms * 1e-3) * 1e-12,
+             "gpw_roofline": {"bound": "alu", "pipe": "fp32 (double-float)" if dfp else "fp64",
+                              "achieved": flops / (gpw_ms * 1e-3) * 1e-12,
                               "peak": peak * 1e-12, "unit": "TFLOP/s",
                               "frac": flops / (gpw_ms * 1e-3) / peak,
                               "flops_per_step": flops,
                               "note": "algorithmic flops of the collocation and integration contractions over "
-                                      "the time of both GPW phases (their reduction and six transform passes "
-                                      "included); peak: the FP64 FMA probe of this run"}}
+                                      "the time of both GPW phases (their reduction, six transform passes and "
+                                      "row sums included); peak: the FMA probe of this run for the pipe the "
+                                      "contractions run on (FP64, or FP32 for double-float), measured"}}
         if con == ftcj.FTCJ_CONTRACT_TC:
             r["status"] = p.status()
         out[form] = r

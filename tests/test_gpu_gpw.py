@@ -1,8 +1,9 @@
 """The classified build (Sec. 2.6) with the DD pair densities on the GPW
 route (App. E), against the classified FP64 oracle: J^k element by element
 and E_J.  Bars: 1e-10 Eh for the FP64 form and 1e-8 Eh for the split and
-tensor-core forms (the GPW route itself is FP64 in every form; the grid keeps
-every alias of a DD transform below e^{-46} of its peak).  Also: a classified
+tensor-core forms (the GPW route runs in FP64 in the FP64 form; the split form
+takes its two grid contractions in double-float, in orthorhombic cells; the
+grid keeps every alias of a DD transform below e^{-46} of its peak).  Also: a classified
 plan without DD records is the plain build, an explicit denser grid agrees
 with the automatic one, the end-to-end call agrees with the device call, and
 the plan refuses what it does not run."""
