@@ -194,6 +194,16 @@ def test_pair_cutoffs_against_the_whole_sphere(orc, F, eps):
         plan.close()
 
 
-def test_pair_cutoffs_need_the_split_form(F):
-    with pytest.raises(F.FtcjError, match="split form"):
-        F.Plan.from_workload(W.cfg1(), precision=F.FTCJ_PREC_FP64, pair_gcut_eps=1e-12)
+def test_pair_cutoffs_in_both_walk_forms(F):
+    """Per-pair cutoffs run in the FP64 walks as in the split walks: both plans
+    walk the same radius-limited units (the same records, radii and tiles)."""
+    w = W.cfg1()
+    p64 = F.Plan.from_workload(w, precision=F.FTCJ_PREC_FP64, pair_gcut_eps=1e-12)
+    psp = F.Plan.from_workload(w, precision=F.FTCJ_PREC_SPLIT, pair_gcut_eps=1e-12)
+    try:
+        a, b = p64.info, psp.info
+        assert a["pair_g_units_walked"] == b["pair_g_units_walked"]
+        assert a["pair_g_units_walked"] <= a["pair_g_units_screened"]
+    finally:
+        p64.close()
+        psp.close()
