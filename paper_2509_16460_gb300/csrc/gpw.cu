@@ -82,6 +82,7 @@ struct Gpw {
     double* d_Epart = nullptr;  // [max_dens][nEb]
     double2* d_tw = nullptr;    // e^{-2 pi i k / N_a} for k < N_a, the three axes one after the other
     int nsj = 1;                // splits of the m2 rows in the integration (partial J' summed in order)
+    size_t vplane_bytes = 0;    // shared memory of the double-float integration: one plane V(., m2, .)
     double* d_jpart = nullptr;  // [nsj][max_dens][total_terms of the DD records]
     int* d_cstart = nullptr;    // [ncnt0 ncnt1 + 1]: the half sphere's points by (n1, n2)
     int* d_clist = nullptr;     // [ng_half]
@@ -718,8 +719,10 @@ __global__ void __launch_bounds__(kGpwThreads) k_gpw_integrate_sep(const double*
 
 // The separable integration in double-float (split form): per grid line
 // a_i = sum_m1 T_1[i][m1] V(m1, m2, m3) and J'_ijk += a_i T_2[j][m2] T_3[k][m3]
-// as error-free double-float steps; a class-0 record keeps its T_1 row in
-// registers when N0 <= 32.
+// as error-free double-float steps.  For each m2 row the block stages the
+// plane V(., m2, .) in shared memory (one coalesced load; every thread then
+// reads the same values); a class-0 record keeps its T_1 row in registers
+// when N0 <= 32.  Threads past the class's records take part in the staging.
 template <int L>
 __global__ void __launch_bounds__(kGpwThreads) k_gpw_integrate_sep_df(const float2* __restrict__ tabf, long long nrec,
                                                                      int lmax, int N0, int N1, int N2, DdLayout lay,
@@ -727,12 +730,13 @@ __global__ void __launch_bounds__(kGpwThreads) k_gpw_integrate_sep_df(const floa
                                                                      double* __restrict__ Jp) {
     constexpr int NT = nterms(L);
     constexpr int R = 32;  // T_1 entries a class-0 thread keeps in registers
+    extern __shared__ float2 sV[];  // [N0][N2]: V(m1, m2, m3) of the current m2
     const int d = blockIdx.y, sj = blockIdx.z, nsj = gridDim.z;
     const int m2lo = N1 * sj / nsj, m2hi = N1 * (sj + 1) / nsj;
     const long long loc = (long long)blockIdx.x * kGpwThreads + threadIdx.x;
     const long long cnt = lay.start[L + 1] - lay.start[L];
-    if (loc >= cnt) return;
-    const long long r = lay.start[L] + loc;
+    const bool live = loc < cnt;
+    const long long r = lay.start[L] + (live ? loc : 0);
     const long long off1 = (long long)(lmax + 1) * N0, off2 = (long long)(lmax + 1) * (N0 + N1);
     const long long lines = (long long)N1 * N2;
     const float2* Vd = Vf + (long long)d * npts;
@@ -740,17 +744,27 @@ __global__ void __launch_bounds__(kGpwThreads) k_gpw_integrate_sep_df(const floa
     df t1r[L == 0 ? R : 1];
     if (regs) {
 #pragma unroll
-        for (int q = 0; q < (L == 0 ? R : 1); ++q) t1r[q] = q < N0 ? ld_df(tabf + (long long)q * nrec + r) : df{0.f, 0.f};
+        for (int q = 0; q < (L == 0 ? R : 1); ++q)
+            t1r[q] = q < N0 && live ? ld_df(tabf + (long long)q * nrec + r) : df{0.f, 0.f};
     }
     df J[NT];
 #pragma unroll
     for (int t = 0; t < NT; ++t) J[t] = df{0.f, 0.f};
     for (int m2 = m2lo; m2 < m2hi; ++m2) {
+        __syncthreads();  // the previous plane is consumed
+        for (int e = threadIdx.x; e < N0 * N2; e += kGpwThreads) {
+            const int m1 = e / N2, m3 = e % N2;
+            sV[e] = __ldg(Vd + (long long)m1 * lines + (long long)m2 * N2 + m3);
+        }
+        __syncthreads();
+        if (!live) continue;
         df t2[L + 1];
 #pragma unroll
         for (int j = 0; j <= L; ++j) t2[j] = ld_df(tabf + (off1 + (long long)j * N1 + m2) * nrec + r);
         for (int m3 = 0; m3 < N2; ++m3) {
-            const long long line = (long long)m2 * N2 + m3;
+            df t3[L + 1];
+#pragma unroll
+            for (int k = 0; k <= L; ++k) t3[k] = ld_df(tabf + (off2 + (long long)k * N2 + m3) * nrec + r);
             df a[L + 1];
 #pragma unroll
             for (int i = 0; i <= L; ++i) a[i] = df{0.f, 0.f};
@@ -758,25 +772,23 @@ __global__ void __launch_bounds__(kGpwThreads) k_gpw_integrate_sep_df(const floa
 #pragma unroll
                 for (int q = 0; q < (L == 0 ? R : 1); ++q) {
                     if (q < N0) {
-                        const df v = ld_df(Vd + (long long)q * lines + line);
-                        a[0] = df_add_u(a[0], df_mul_u(t1r[q], v));
+                        const float2 v = sV[q * N2 + m3];
+                        a[0] = df_add_u(a[0], df_mul_u(t1r[q], df{v.x, v.y}));
                         if ((q & 7) == 7) a[0] = df_norm(a[0]);
                     }
                 }
             } else {
                 for (int m1 = 0; m1 < N0; ++m1) {
-                    const df v = ld_df(Vd + (long long)m1 * lines + line);
+                    const float2 v = sV[m1 * N2 + m3];
 #pragma unroll
-                    for (int i = 0; i <= L; ++i) a[i] = df_add_u(a[i], df_mul_u(ld_df(tabf + ((long long)i * N0 + m1) * nrec + r), v));
+                    for (int i = 0; i <= L; ++i)
+                        a[i] = df_add_u(a[i], df_mul_u(ld_df(tabf + ((long long)i * N0 + m1) * nrec + r), df{v.x, v.y}));
                     if ((m1 & 7) == 7) {
 #pragma unroll
                         for (int i = 0; i <= L; ++i) a[i] = df_norm(a[i]);
                     }
                 }
             }
-            df t3[L + 1];
-#pragma unroll
-            for (int k = 0; k <= L; ++k) t3[k] = ld_df(tabf + (off2 + (long long)k * N2 + m3) * nrec + r);
             int t = 0;
 #pragma unroll
             for (int lam = 0; lam <= L; ++lam)
@@ -787,6 +799,7 @@ __global__ void __launch_bounds__(kGpwThreads) k_gpw_integrate_sep_df(const floa
                         J[t] = df_norm(df_add_u(J[t], df_mul_u(df_norm(a[i]), df_mul_u(t2[j], t3[lam - i - j]))));
         }
     }
+    if (!live) return;
     double* out = Jp + ((long long)sj * gridDim.y + d) * lay.total + lay.base[L] + loc;
 #pragma unroll
     for (int t = 0; t < NT; ++t) out[(long long)t * cnt] = join_df(J[t]);
@@ -996,6 +1009,14 @@ int setup_gpw(ftcj_plan* P) {
     g->gnorm = P->vol / (double)g->npts;
     g->sep = P->ortho;
     g->df = g->sep && P->precision == FTCJ_PREC_SPLIT;
+    if (g->df) {
+        g->vplane_bytes = sizeof(float2) * (size_t)g->N[0] * g->N[2];
+        const void* kerns[] = {(const void*)k_gpw_integrate_sep_df<0>, (const void*)k_gpw_integrate_sep_df<1>,
+                               (const void*)k_gpw_integrate_sep_df<2>, (const void*)k_gpw_integrate_sep_df<3>,
+                               (const void*)k_gpw_integrate_sep_df<4>};
+        for (const void* k : kerns)
+            if ((rc = allow_dynamic_smem(k, g->vplane_bytes))) return rc;
+    }
     g->lmax = 0;
     for (int c = 0; c < kNclass; ++c)
         if (D->class_start[c + 1] > D->class_start[c]) g->lmax = c;
@@ -1176,8 +1197,8 @@ int launch_gpw_j(ftcj_plan* P, int nd, cudaStream_t s) {
                           : c == 2 ? k_gpw_integrate_sep_df<2>
                           : c == 3 ? k_gpw_integrate_sep_df<3>
                                    : k_gpw_integrate_sep_df<4>;
-                kern<<<grid, kGpwThreads, 0, s>>>(g->d_tabf, D->npairs, g->lmax, g->N[0], g->N[1], g->N[2], lay,
-                                                  g->d_vf, g->npts, g->d_jpart);
+                kern<<<grid, kGpwThreads, g->vplane_bytes, s>>>(g->d_tabf, D->npairs, g->lmax, g->N[0], g->N[1],
+                                                                g->N[2], lay, g->d_vf, g->npts, g->d_jpart);
             } else {
                 auto kern = c == 0 ? k_gpw_integrate_sep<0>
                           : c == 1 ? k_gpw_integrate_sep<1>
