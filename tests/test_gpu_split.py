@@ -202,8 +202,11 @@ def test_pair_cutoffs_in_both_walk_forms(F):
     psp = F.Plan.from_workload(w, precision=F.FTCJ_PREC_SPLIT, pair_gcut_eps=1e-12)
     try:
         a, b = p64.info, psp.info
+        # the same records, radii and tiles: the same units inside the records' radii
+        # (screened) and inside their tiles' radii (walked)
         assert a["pair_g_units_walked"] == b["pair_g_units_walked"]
-        assert a["pair_g_units_walked"] <= a["pair_g_units_screened"]
+        assert a["pair_g_units_screened"] == b["pair_g_units_screened"]
+        assert a["pair_g_units_screened"] <= a["pair_g_units_walked"] <= a["pair_g_units"]
     finally:
         p64.close()
         psp.close()
