@@ -127,12 +127,6 @@ __global__ void k_gpw_twiddles(int N0, int N1, int N2, double2* __restrict__ tw)
     tw[k] = make_double2(cs, -sn);
 }
 
-__device__ __forceinline__ int rec_class(const DdLayout& lay, long long r) {
-    int c = 0;
-    while (c < kNclass - 1 && r >= lay.start[c + 1]) ++c;
-    return c;
-}
-
 // fractional coordinates of the record's product centre P
 __device__ __forceinline__ void centre_frac(const PairDev& pr, const CellConst& cc, double F[3]) {
 #pragma unroll
