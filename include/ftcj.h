@@ -134,7 +134,7 @@ typedef struct {
                            other one takes the full-range 4 pi / (Omega G^2), G = 0 removed.
                            ftcj_jbuild and ftcj_jbuild_host return that build; the step calls
                            (ftcj_rho, ftcj_potential, ftcj_jback), ftcj_grad, shard plans and batches
-                           refuse a classified plan (EUNSUPPORTED).
+                           refuse a classified plan, and it takes no per-pair cutoffs (EUNSUPPORTED).
                            0: every pair record in the long-range walks. */
     double alpha_cut;   /* classify = 1: the exponent boundary; <= 0: w^2/2 (Eq. "cd cutoff") */
     int gpw_grid[3];    /* classify = 1: grid points along a_1, a_2, a_3; each <= 0: the smallest count

@@ -386,6 +386,9 @@ int create(const ftcj_cell* cell, const ftcj_basis* basis, const int kmesh[3], c
         if (P->shard_count > 1)
             return fail(FTCJ_EUNSUPPORTED, "a classified plan (compact/diffuse) is not record-sharded");
         if (!finite(prm->alpha_cut)) return fail(FTCJ_EINVAL, "alpha_cut must be finite");
+        if (prm->pair_gcut_eps > 0.0)
+            return fail(FTCJ_EUNSUPPORTED, "per-pair cutoffs are derived for the long-range kernel alone; a "
+                                           "classified plan walks the whole sphere (pair_gcut_eps = 0)");
         P->alpha_cut = prm->alpha_cut > 0.0 ? prm->alpha_cut : 0.5 * prm->omega * prm->omega;
         P->rec_filter = 1;
     }

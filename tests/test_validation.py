@@ -87,6 +87,8 @@ CASES = [
     ("classified shard", None, {"classify": True, "shard_count": 2, "shard_index": 0}, "unsupported input",
      "record-sharded"),
     ("alpha_cut nan", None, {"classify": True, "alpha_cut": float("nan")}, "invalid argument", "alpha_cut"),
+    ("classified with cutoffs", None, {"classify": True, "pair_gcut_eps": 1e-12}, "unsupported input",
+     "classified plan"),
 ]
 
 
