@@ -479,3 +479,21 @@ def test_classified_energy_terms_match_erf_lattice_sums(orc):
     e_x = E["all"] - E["c"] - E["d"]
     assert abs(e_x - e_x_full) < 1e-12
     assert abs(e_x_full - e_x_lr) > 1e-4  # the two kernels are told apart
+
+
+def test_gpw_grid_rule_without_margin_is_alias_free(orc):
+    """At the smallest grid the alias rule allows (N_i |b_i| >= Gcut + sqrt(184 p_max),
+    N_i > 2 max|n_i|, no extra points) the grid transform of the DD density still
+    equals the pair transforms to 1e-12 of max|rho_D|; at a third of those points per
+    axis it does not (the rule is what keeps the aliases out)."""
+    w = W.tiny(seed=7, kmesh=(2, 1, 2), ndens=1)
+    acut = 0.9
+    r = orc.lrj_classified(w, alpha_cut=acut)
+    nmax = np.abs(r["G"]).max(axis=0)
+    grid = [max(int(2 * nmax[i] + 1), g) for i, g in enumerate(dense_gpw_grid(w, pmax=1.6, margin=0))]
+    scale = np.abs(r["rhoD"]).max()
+    rg = orc.grid_transform(w.A, orc.gpw_density(w, grid, alpha_cut=acut), r["G"])
+    assert np.abs(rg - r["rhoD"]).max() < 1e-12 * scale
+    coarse = [max(int(2 * nmax[i] + 1), g // 3) for i, g in enumerate(grid)]
+    rc = orc.grid_transform(w.A, orc.gpw_density(w, coarse, alpha_cut=acut), r["G"])
+    assert np.abs(rc - r["rhoD"]).max() > 1e-6 * scale
